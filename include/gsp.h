@@ -1,0 +1,210 @@
+/*
+ * gsp.h - C ABI of libgsp: brute-force incoherent dedispersion of an 8-bit
+ * filterbank fused with a single-pulse (boxcar matched-filter) search, on one
+ * GB300 (sm_103a).
+ *
+ * Method: arXiv 2110.12749 ("GSP").  Dedispersion is the sum over channels of
+ * time-shifted samples with the shifts taken from a numdm x numchan delay
+ * matrix (Sec. 2.3, Alg. 2 and Alg. 3); the single-pulse search that follows
+ * it is named in Sec. 2.1-2.2 and specified here by the library (block
+ * detrend, robust normalisation, boxcar filter, threshold, per-window
+ * maximum).
+ *
+ * Conventions shared by every entry point
+ *   - Input filterbank X: uint8, channel-major, X[c][t] at byte
+ *     c * x_stride + t, c in [0, nchan), t in [0, n_in).  The merged buffer of
+ *     Alg. 3 generalises to: every DM row uses the same output length
+ *     n_out = n_in - max_delay, so that t + delay < n_in for every output.
+ *   - Channel c (ascending order) has centre f_lo + (c + 1/2)(f_hi - f_lo)/nchan
+ *     MHz; with freq_descending row 0 is the highest channel.  The top channel
+ *     (highest centre) has delay 0 and all delays are >= 0.
+ *   - Delay of (dm, c) in samples: floor(x + 1/2) with
+ *     x = 4.148808e3 * DM * (1/f_c^2 - 1/f_top^2) / t_samp (f in MHz, t_samp in s),
+ *     computed on the host in IEEE FP64 without contraction.
+ *   - Dedispersed series D: int32 [ndm][n_out], exact integer sums.
+ *   - Device pointers are CUDA device (or managed) addresses owned by the
+ *     caller; host pointers are ordinary host memory owned by the caller.
+ *   - "stream" is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Calls that take a stream only enqueue work on it; only the
+ *     functions documented as synchronising wait for the GPU.
+ *   - Every function returns a gsp_status; nothing aborts, traps or prints.
+ *     A CUDA failure returns GSP_ERR_CUDA and its text is available from
+ *     gsp_last_error_string() in the calling thread.
+ *   - A plan may be used by one host thread and one stream at a time.
+ */
+#ifndef GSP_H
+#define GSP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    GSP_OK = 0,
+    GSP_ERR_INVALID_ARG = 1, /* bad pointer, size, stride or descriptor field */
+    GSP_ERR_OOM = 2,         /* device or host allocation failed */
+    GSP_ERR_CUDA = 3,        /* a CUDA runtime call or kernel launch failed */
+    GSP_ERR_TOO_SHORT = 4,   /* n_in <= max delay: no output sample exists */
+    GSP_ERR_CAPACITY = 5,    /* more candidates than storage: list truncated */
+    GSP_ERR_TIMEOUT = 6,     /* a bounded wait gave up */
+    GSP_ERR_TIE = 7,         /* a delay lies within 1e-9 of a rounding tie */
+    GSP_ERR_ALIGN = 8,       /* pointer or stride violates a stated alignment */
+    GSP_ERR_STATE = 9        /* call out of order (e.g. no search yet) */
+} gsp_status;
+
+/* Plan flags (gsp_plan_desc.flags). */
+#define GSP_FLAG_TIMING 1    /* record CUDA events around each kernel phase */
+#define GSP_FLAG_SIMPLE_DD 2 /* use the simple reference dedispersion kernel */
+
+typedef struct gsp_plan_s *gsp_plan_t;
+
+/* Plan descriptor: host values, copied by gsp_plan_create.  Fill it with
+ * gsp_plan_desc_init() first; then set the band, sampling and DM grid. */
+typedef struct {
+    int32_t nchan;           /* channels C >= 1 */
+    double f_lo_mhz;         /* bottom edge of the band */
+    double f_hi_mhz;         /* top edge of the band (> f_lo_mhz > 0) */
+    int32_t freq_descending; /* 0: row 0 = lowest channel; 1: row 0 = highest */
+    double t_samp_s;         /* sampling time (s) */
+    int32_t ndm;             /* number of DM trials >= 1 */
+    const double *dms;       /* [ndm] DM values (pc cm^-3), or NULL for dm_lo + i*dm_step */
+    double dm_lo, dm_step;
+    const int32_t *delays;   /* optional explicit delay table [ndm][nchan] (>= 0);
+                                overrides the band/DM description (Sec. 2.3 matrix) */
+    int64_t nsamp_max;       /* largest n_in any call will pass (sizes scratch) */
+    const int32_t *widths;   /* boxcar widths, ascending, >= 1; NULL = default 13 */
+    int32_t nwidths;
+    int32_t block_len;       /* detrend block B (default 1024, >= max width) */
+    int32_t window_len;      /* candidate window L_win (default 1024) */
+    float threshold;         /* event if S/N >= threshold (default 6) */
+    float bad_lo, bad_hi;    /* block bad if sigma_b outside [bad_lo, bad_hi]*sigma_ref
+                                (default 0.5, 2.5) */
+    int64_t max_cands;       /* device candidate capacity (default 1<<20) */
+    int32_t flags;           /* GSP_FLAG_* */
+} gsp_plan_desc;
+
+/* One single-pulse candidate: the best (t, width) of one DM row inside one
+ * candidate window (fields after the per-candidate record of Sec. 2.2). */
+typedef struct {
+    int32_t dm_idx; /* DM trial index */
+    int32_t width;  /* boxcar width (samples) */
+    int64_t t;      /* start sample of the boxcar, relative to D[.][0] */
+    float snr;      /* matched-filter S/N */
+    int32_t beam;   /* beam label (0 for single-beam calls) */
+} gsp_cand;
+
+/* Fill *desc with defaults (13 widths {1,2,3,4,6,9,14,20,30,45,70,100,150},
+ * B = L_win = 1024, threshold 6, bad bounds 0.5/2.5, max_cands 2^20) and
+ * zeros elsewhere.  Host only. */
+gsp_status gsp_plan_desc_init(gsp_plan_desc *desc);
+
+/* Compute the delay table [ndm][nchan] of a descriptor on the host, exactly
+ * as gsp_plan_create does (Sec. 2.3 delay matrix).  min_margin (optional)
+ * receives min |frac(x) - 1/2| over the table.  No GPU is touched. */
+gsp_status gsp_compute_delays(const gsp_plan_desc *desc, int32_t *host_out,
+                              double *min_margin);
+
+/* Create a plan: validate the descriptor, compute the delay table (returns
+ * GSP_ERR_TIE if any entry is within 1e-9 of a rounding tie), choose tiles,
+ * and allocate device memory for the delay table, search statistics and the
+ * candidate buffer.  The dedispersed-series scratch used by gsp_search when
+ * the caller passes no output buffer is allocated on first use.  Uses the
+ * current CUDA device. */
+gsp_status gsp_plan_create(gsp_plan_t *out, const gsp_plan_desc *desc);
+
+/* Free everything the plan owns (synchronises the device first). */
+gsp_status gsp_plan_destroy(gsp_plan_t plan);
+
+/* Largest entry of the delay table, or -1 for a NULL plan. */
+int64_t gsp_plan_max_delay(gsp_plan_t plan);
+
+/* n_out = n_in - max_delay (may be <= 0), or -1 for a NULL plan. */
+int64_t gsp_plan_nout(gsp_plan_t plan, int64_t n_in);
+
+/* Copy the plan's delay table [ndm][nchan] to host memory. */
+gsp_status gsp_plan_delays(gsp_plan_t plan, int32_t *host_out);
+
+/* Dedispersion only (Sec. 2.3, Alg. 3 semantics):
+ *   d_out[dm * out_stride + t] = sum_c X[c][t + delay[dm][c]],  t < n_out.
+ * d_x: device, n_in <= nsamp_max samples per channel, x_stride >= n_in bytes.
+ * d_out: device int32, out_stride >= n_out elements.
+ * Alignment: d_x and x_stride multiples of 16 bytes, d_out 16-byte aligned
+ * and out_stride a multiple of 4 (else GSP_ERR_ALIGN).
+ * GSP_ERR_TOO_SHORT if n_in <= max delay.  Asynchronous on stream. */
+gsp_status gsp_dedisperse(gsp_plan_t plan, const uint8_t *d_x, int64_t n_in,
+                          int64_t x_stride, int32_t *d_out, int64_t out_stride,
+                          void *stream);
+
+/* Dedispersion fused with the single-pulse search (the whole hot path).
+ * D goes to d_out (same layout rules as gsp_dedisperse) or, if d_out is
+ * NULL, to plan-owned scratch.  t_offset is the absolute sample index of
+ * output sample 0 (candidate windows are aligned to absolute indices).
+ * Candidates stay on the device until gsp_candidates.  Search steps per DM
+ * row: blocks of B samples (samples beyond the last whole block are not
+ * searched); least-squares line per block, residual RMS sigma_b; sigma_ref =
+ * lower median of sigma_b; blocks outside [bad_lo, bad_hi]*sigma_ref are
+ * zeroed; S/N(t, w) = sum_{k<w} r[t+k] / (sigma_ref sqrt(w)); best width per t
+ * (ties: smaller w); event if S/N >= threshold; per window the largest event
+ * (ties: smaller t).  Asynchronous on stream. */
+gsp_status gsp_search(gsp_plan_t plan, const uint8_t *d_x, int64_t n_in,
+                      int64_t x_stride, int64_t t_offset, int32_t *d_out,
+                      int64_t out_stride, void *stream);
+
+/* Search only, on caller-provided dedispersed series d_D [ndm][stride]
+ * (int32, device), n_out samples per row.  Same search as gsp_search. */
+gsp_status gsp_search_series(gsp_plan_t plan, const int32_t *d_D, int64_t n_out,
+                             int64_t stride, int64_t t_offset, void *stream);
+
+/* S/N of every (dm, width, t) for caller-provided series (parity surface):
+ * d_snr[(dm * nwidths + iw) * Ls + t], Ls = B * floor(n_out / B), float,
+ * NaN where t + w > Ls, 0 for rows with sigma_ref == 0.  Also leaves the
+ * candidates of this search in the plan.  Asynchronous on stream. */
+gsp_status gsp_boxcar_snr(gsp_plan_t plan, const int32_t *d_D, int64_t n_out,
+                          int64_t stride, float *d_snr, void *stream);
+
+/* Per-row statistics of the last search, copied to host (synchronises):
+ * sigma_b [ndm][nb] (nb = floor(n_out/B)), bad [ndm][nb] (1 = bad block),
+ * sigma_ref [ndm].  Any pointer may be NULL; nb_out receives nb. */
+gsp_status gsp_search_stats(gsp_plan_t plan, double *sigma_b, uint8_t *bad,
+                            double *sigma_ref, int64_t *nb_out);
+
+/* Candidates of the last search (synchronises with its stream).  Copies up
+ * to cap records, sorted by (dm_idx, t, width), to host_out and the true
+ * count to *n_total.  Returns GSP_ERR_CAPACITY if the device buffer
+ * (max_cands) or cap was too small; the stored prefix is then the first
+ * records in sorted order among those the device kept. */
+gsp_status gsp_candidates(gsp_plan_t plan, gsp_cand *host_out, int64_t cap,
+                          int64_t *n_total);
+
+/* End-to-end call on HOST data: copies h_x (host, pinned or pageable,
+ * x_stride bytes per channel) to plan-owned device memory, runs gsp_search
+ * and returns the candidates as gsp_candidates does.  Synchronises. */
+gsp_status gsp_search_host(gsp_plan_t plan, const uint8_t *h_x, int64_t n_in,
+                           int64_t x_stride, int64_t t_offset, gsp_cand *host_out,
+                           int64_t cap, int64_t *n_total, void *stream);
+
+/* Device durations (ms) of the dedispersion kernel and of the search
+ * kernels of the last gsp_search / gsp_dedisperse call, measured with CUDA
+ * events on its stream; requires GSP_FLAG_TIMING (else GSP_ERR_STATE).
+ * Synchronises. */
+gsp_status gsp_plan_timing(gsp_plan_t plan, float *ms_dedisperse, float *ms_search);
+
+/* Kernel launches the last gsp_search / gsp_dedisperse call made. */
+int32_t gsp_plan_launches(gsp_plan_t plan);
+
+/* Static text for a status code. */
+const char *gsp_status_string(gsp_status s);
+
+/* Text of the last CUDA error seen by this thread ("" if none). */
+const char *gsp_last_error_string(void);
+
+/* Library version, major*10000 + minor*100 + patch. */
+int32_t gsp_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GSP_H */
