@@ -176,9 +176,14 @@ static void detrend_block(const int64_t *Dblk, int64_t B, double *alpha,
         double r = (double)Dblk[j] - a - b * (double)j;
         ss += r * r;
     }
+    double sg = sqrt(ss / (double)B);
+    /* D is integer, so B (B^2 - 1) * sum r_j^2 is a non-negative integer and a
+     * nonzero sigma is at least 1 / (B sqrt(B^2 - 1)).  A value below half of
+     * that is rounding noise of an exactly linear block: it is 0. */
+    if (B > 1 && sg < 0.5 / ((double)B * sqrt((double)B * (double)B - 1.0))) sg = 0.0;
     *alpha = a;
     *beta = b;
-    *sigma = sqrt(ss / (double)B);
+    *sigma = sg;
 }
 
 static int cmp_double(const void *a, const void *b) {
