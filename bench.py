@@ -1,0 +1,310 @@
+"""Benchmark of the GSP hot path: brute-force dedispersion + single-pulse search.
+
+One step = one gsp_search over one CRAFTS-like beam already resident in HBM
+(4096 channels, 1000-1500 MHz, 49.152 us, 2^20 samples, 2000 DM trials 0-999.5)
+with the candidates left on the device; the e2e figure runs gsp_search_host on
+a pinned host copy (H2D of the filterbank, search, D2H of the candidates).
+Metric: seconds of sky data per wall second (higher is better), plus
+DM*channel*sample/s against the integer-add roofline of the dedispersion
+kernel.  Under torchrun every rank searches its own beam (weak scaling, no
+data-path collective); rank 0 prints one JSON line.
+
+--impl reference times the CPU oracle on the host cores on a bounded sample
+of the same workload (a subset of DM rows, full length and all channels),
+scaled linearly in the number of DM rows.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+NOMINAL_SMS = 152
+INT_LANES_PER_SM = 128          # issue slots per SM per clock (4 schedulers x 32 lanes)
+SM_MAX_MHZ = 2070.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gsp", choices=["gsp", "reference"])
+    ap.add_argument("--workload", default="crafts")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--cpu-rows", type=int, default=0, help="DM rows of the oracle sample (0: auto)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def workload_desc(wl):
+    return ("%s: %d ch %.0f-%.0f MHz, t_samp %.3f us, %d samples, %d DMs %.1f-%.1f"
+            % (wl.name, wl.nchan, wl.f_lo, wl.f_hi, wl.t_samp * 1e6, wl.n_in, wl.ndm,
+               wl.dm_lo, wl.dm_lo + wl.dm_step * (wl.ndm - 1)))
+
+
+def cpu_model():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=10)
+            except Exception:
+                self.proc.kill()
+                out = ""
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        mhz, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in getattr(self, "lines", []):
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                mhz.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(mhz) if mhz else None,
+                "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(mhz)}
+
+
+def make_input(wl, delays_fn, n_out, beam):
+    from paper_2110_12749_gb300 import synth
+    t0 = time.time()
+    x, rfi, bursts, pulses = synth.workload_filterbank(wl, delays_fn, n_out, beam=beam)
+    return x, pulses, time.time() - t0
+
+
+def oracle_sample(x, wl, dl, nrows, seed=0):
+    """Time the CPU oracle (dedispersion of nrows DM rows + their search)."""
+    import oracle
+    rng = np.random.default_rng(seed)
+    rows = np.sort(rng.choice(wl.ndm, size=nrows, replace=False))
+    n_out = wl.n_in - oracle.max_delay(dl)
+    t0 = time.perf_counter()
+    D = oracle.dedisperse(x, wl.n_in, dl, rows=rows, n_out=n_out)
+    oracle.search_rows(D, dm_idx=rows.astype(np.int32))
+    dt = time.perf_counter() - t0
+    full = dt * wl.ndm / nrows           # the work is linear in the number of DM rows
+    return {"value": wl.sky_seconds() / full, "unit": "sky-s/s",
+            "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": "%d of %d DM rows (all %d channels, %d samples), dedispersion + search, "
+                      "%.2f s, scaled x%.1f to the full job" % (nrows, wl.ndm, wl.nchan, wl.n_in,
+                                                                dt, wl.ndm / nrows),
+            "seconds": dt, "cpu": cpu_model()}
+
+
+def auto_rows():
+    import oracle
+    return max(2, 2 * oracle.num_threads())
+
+
+def run_reference(args):
+    """The oracle as the reference arm: each step a bounded sample."""
+    import oracle
+    from paper_2110_12749_gb300 import synth
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    wl = synth.WORKLOADS[args.workload]
+    dl, _ = oracle.delays(wl.nchan, wl.f_lo, wl.f_hi, wl.t_samp, wl.dms)
+    n_out = wl.n_in - oracle.max_delay(dl)
+    x, pulses, gen_s = make_input(
+        wl, lambda dm: oracle.delays(wl.nchan, wl.f_lo, wl.f_hi, wl.t_samp, [dm])[0][0],
+        n_out, beam=0)
+    nrows = args.cpu_rows or auto_rows()
+    for i in range(args.warmup):
+        oracle_sample(x, wl, dl, nrows, seed=100 + i)
+    res = [oracle_sample(x, wl, dl, nrows, seed=i) for i in range(args.steps)]
+    per_step_full = [r["seconds"] * wl.ndm / nrows for r in res]
+    t = sum(per_step_full) / len(per_step_full)
+    value = wl.sky_seconds() / t
+    line = {"metric": "sky-s processed per wall-s", "value": value, "unit": "sky-s/s",
+            "impl": "reference", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int64+fp64", "data": "synthetic",
+            "config": {"workload": workload_desc(wl), "l2": "inputs larger than L2"},
+            "cpu_baseline": dict(res[-1], value=value),
+            "e2e": {"value": value, "unit": "sky-s/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0},
+            "gpu_launches": 0}
+    print(json.dumps(line))
+    return 0
+
+
+def run_gsp(args):
+    import torch
+    from paper_2110_12749_gb300 import gsp, synth
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    wl = synth.WORKLOADS[args.workload]
+    desc, keep = gsp.make_desc(wl.nchan, wl.f_lo, wl.f_hi, wl.t_samp, wl.n_in, ndm=wl.ndm,
+                               dm_lo=wl.dm_lo, dm_step=wl.dm_step, flags=gsp.GSP_FLAG_TIMING)
+    plan = gsp.gsp_plan_create(desc, keep)
+    n_out = gsp.gsp_plan_nout(plan, wl.n_in)
+
+    def delays_fn(dm):
+        d1, k1 = gsp.make_desc(wl.nchan, wl.f_lo, wl.f_hi, wl.t_samp, wl.n_in, dms=[dm])
+        return gsp.gsp_compute_delays(d1)[0][0]
+
+    x, pulses, gen_s = make_input(wl, delays_fn, n_out, beam=rank)
+    xd = torch.from_numpy(x).cuda()
+    xh = torch.from_numpy(x).pin_memory()
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+            torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        gsp.gsp_search(plan, xd, wl.n_in)
+        gsp.gsp_plan_timing(plan)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    dd_ms, se_ms, launches = [], [], 0
+    barrier()
+    with ClockSampler(local) as clk:
+        t_wall0 = time.perf_counter()
+        for i in range(args.steps):
+            ev[i][0].record(stream)
+            gsp.gsp_search(plan, xd, wl.n_in)
+            ev[i][1].record(stream)
+            launches += gsp.gsp_plan_launches(plan)
+            a, b = gsp.gsp_plan_timing(plan)     # synchronises: per-step kernel durations
+            dd_ms.append(a)
+            se_ms.append(b)
+        barrier()
+        t_wall = time.perf_counter() - t_wall0
+    step_ms = [s.elapsed_time(e) for s, e in ev]
+    total_ms = sum(step_ms)
+    if world > 1:
+        tt = torch.tensor([total_ms], device="cuda")
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    ms_step = total_ms / args.steps
+    value = world * wl.sky_seconds() / (ms_step / 1e3)
+    cands, ncand, _ = gsp.gsp_candidates(plan)
+
+    # end to end through the host-buffer entry point
+    e2e_ms, h2d = [], x.shape[0] * x.shape[1]
+    gsp.gsp_search_host(plan, xh, wl.n_in)
+    for _ in range(args.e2e_steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        c2, n2, _ = gsp.gsp_search_host(plan, xh, wl.n_in)
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    e2e_step = statistics.median(e2e_ms)
+    if world > 1:
+        tt = torch.tensor([e2e_step], device="cuda")
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        e2e_step = float(tt.item())
+    e2e_value = world * wl.sky_seconds() / (e2e_step / 1e3)
+
+    adds = float(wl.ndm) * wl.nchan * n_out            # algorithmic byte adds per launch
+    dd_avg = sum(dd_ms) / len(dd_ms)
+    achieved = adds / (dd_avg / 1e3) / 1e12            # T adds / s
+    nsm = torch.cuda.get_device_properties(local).multi_processor_count
+    clocks = clk.summary()
+    peak = nsm * INT_LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
+    line = None
+    if rank == 0:
+        cpu = None
+        if not args.no_cpu_baseline:
+            dl = gsp.gsp_plan_delays(plan)
+            cpu = oracle_sample(x, wl, dl, args.cpu_rows or auto_rows())
+        line = {
+            "metric": "sky-s processed per wall-s", "value": value, "unit": "sky-s/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "int32+fp32", "data": "synthetic",
+            "config": {"workload": workload_desc(wl), "n_out": n_out,
+                       "beams": world, "l2": "inputs larger than L2 (4.3 GB filterbank, "
+                                             "8 GB series per step)",
+                       "parallelism": "independent beams" if world > 1 else "single gpu"},
+            "dm_chan_samples_per_s": world * adds / (ms_step / 1e3),
+            "kernel_ms": {"dedisperse": dd_avg, "search": sum(se_ms) / len(se_ms)},
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tadd/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "peak_basis": "%d SMs x %d int lanes x %.0f MHz (max clock)"
+                                       % (nsm, INT_LANES_PER_SM, SM_MAX_MHZ),
+                         "frac_at_run_clock": (achieved / (nsm * INT_LANES_PER_SM * clocks["sm_mhz"] * 1e-6)
+                                               if clocks["sm_mhz"] else None)},
+            "e2e": {"value": e2e_value, "unit": "sky-s/s", "ms_per_step": e2e_step,
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 8 + 24 * int(n2)},
+            "gpu_launches": launches, "clocks": clocks, "candidates": int(ncand),
+            "input_gen_s": gen_s, "wall_s": t_wall,
+        }
+        if cpu is not None:
+            line["cpu_baseline"] = cpu
+        print(json.dumps(line))
+    gsp.gsp_plan_destroy(plan)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gsp(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

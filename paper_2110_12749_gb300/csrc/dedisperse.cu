@@ -1,0 +1,416 @@
+// Brute-force incoherent dedispersion kernels (Sec. 2.3, Alg. 2/3):
+//   D[dm][t] = sum_c X[c][t + delay[dm][c]],  t < n_out = n_in - max delay.
+//
+// The tiled kernel (dd_tiled_kernel) is the performance path.  Each CTA owns
+// a tile of KW*8 consecutive DM trials x T_EFF output samples and streams the
+// channels through a ring of shared-memory stages (32 channels per stage).
+// A producer warp fills a stage with one TMA bulk copy per channel: the
+// bytes X[c][s_c .. s_c + L) where s_c = floor16(t0 + min delay of the DM
+// block), which cover every delay of the block.  Eight consumer warps each
+// own KW DM trials; lane l of a warp owns the 4-sample words w = l + 32k
+// (k < M) of the tile.  For a (channel, DM) pair the word a lane needs starts
+// q = t0 + delay - s_c bytes into the window; the kernel reads the aligned
+// word at q & ~3 and files its bytes under the phase p = q & 3 (output
+// sample of byte i is 4w + i - p).  Channels are visited sorted by phase, so
+// each phase accumulates into its own registers and the byte shift is
+// resolved once per 256 channels, not per add.
+//
+// Accumulation (exact, SWAR): per word three 32-bit views are summed over
+// channels: S = sum w (raw), E = sum (w & 0x00ff00ff) (bytes 0 and 2 in
+// 16-bit lanes), H = sum (w >> 24) (byte 3, on the multiply-add pipe).  Then
+//   b0 = E & 0xffff, b2 = E >> 16, b3 = H, b1 = ((S - E - (H << 24)) mod 2^32) >> 8
+// are the exact per-byte sums as long as a 16-bit lane of E holds at most
+// 256 * 255 < 2^16, i.e. every 256 channels the views are flushed into int32
+// accumulators.
+#include <algorithm>
+#include <vector>
+
+#include "dd_tiled.cuh"
+#include "gsp_internal.cuh"
+
+namespace gsp {
+
+// ---------------------------------------------------------------------------
+// Simple kernel: the direct form of Alg. 3.  One thread per (dm, 4 outputs),
+// channel loop in registers, byte loads through L1.  Kept as a second,
+// independent device implementation (GSP_FLAG_SIMPLE_DD) and as the path
+// for delay tables whose spread within a DM block does not fit the tiles.
+__global__ void __launch_bounds__(256) dd_simple_kernel(const uint8_t *__restrict__ x,
+                                                        int64_t x_stride,
+                                                        const int32_t *__restrict__ delays,
+                                                        int nchan, int64_t n_out,
+                                                        int32_t *__restrict__ out,
+                                                        int64_t out_stride) {
+    const int dm = blockIdx.y;
+    const int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4;
+    if (t >= n_out) return;
+    const int32_t *dl = delays + (int64_t)dm * nchan;
+    int32_t a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+    const bool full = t + 4 <= n_out;
+    for (int c = 0; c < nchan; c++) {
+        const uint8_t *p = x + (int64_t)c * x_stride + t + __ldg(dl + c);
+        a0 += __ldg(p);
+        if (full) {
+            a1 += __ldg(p + 1);
+            a2 += __ldg(p + 2);
+            a3 += __ldg(p + 3);
+        } else {
+            if (t + 1 < n_out) a1 += __ldg(p + 1);
+            if (t + 2 < n_out) a2 += __ldg(p + 2);
+        }
+    }
+    int32_t *o = out + (int64_t)dm * out_stride + t;
+    if (full) {
+        *reinterpret_cast<int4 *>(o) = make_int4(a0, a1, a2, a3);
+    } else {
+        o[0] = a0;
+        if (t + 1 < n_out) o[1] = a1;
+        if (t + 2 < n_out) o[2] = a2;
+    }
+}
+
+cudaError_t launch_dedisperse_simple(const gsp_plan_s *p, const uint8_t *x, int64_t x_stride,
+                                     int64_t n_out, int32_t *out, int64_t out_stride,
+                                     cudaStream_t s, int32_t *nlaunch) {
+    const int64_t quads = (n_out + 3) / 4;
+    dim3 grid((unsigned)((quads + 255) / 256), (unsigned)p->desc.ndm);
+    dd_simple_kernel<<<grid, 256, 0, s>>>(x, x_stride, p->d_delays, p->desc.nchan, n_out, out,
+                                          out_stride);
+    *nlaunch += 1;
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Tiled kernel.
+namespace {
+
+constexpr int kM = 4;            // words per lane: T = 128 * kM output samples per warp pass
+constexpr int kKW = 2;           // DM trials per consumer warp
+constexpr int kCW = 8;           // consumer warps
+constexpr int kCB = 32;          // channels per stage
+constexpr int kT = 128 * kM;     // samples computed per tile
+constexpr int kTEff = kT - 4;    // samples stored per tile (the last word is incomplete)
+constexpr int kKDM = kCW * kKW;  // DM trials per CTA
+constexpr int kThreads = (kCW + 1) * 32;
+constexpr int kFlushStages = 256 / kCB;  // stages between SWAR flushes (256 channels)
+constexpr long long kWaitBudget = 4000000000ll;  // ~2 s of SM clock per wait
+
+struct TiledArgs {
+    const uint8_t *x;
+    int64_t x_stride;
+    int64_t n_in;
+    int64_t n_out;
+    const int32_t *delays;  // [ndm][nchan]
+    const int32_t *blkmin;  // [nblk][nchan]
+    int32_t *out;
+    int64_t out_stride;
+    int nchan;
+    int ndm;
+    int nblk;
+    int win;       // bytes per channel window (multiple of 16)
+    int stages;    // ring depth
+    uint32_t mulhi;  // 256, passed at run time so that the multiply stays a multiply
+    int *err;      // set to 1 if a bounded wait gave up
+};
+
+__device__ __forceinline__ uint32_t lanemask_lt() {
+    uint32_t m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+__device__ __forceinline__ void fail(int *err) { atomicExch(err, 1); }
+
+__global__ void __launch_bounds__(kThreads, 1) dd_tiled_kernel(const TiledArgs a) {
+    extern __shared__ __align__(128) uint8_t smem[];
+    const int slot_bytes = kCB * a.win;
+    int32_t *lists = reinterpret_cast<int32_t *>(smem + (size_t)a.stages * slot_bytes);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(lists + kCW * kKW * 4 * 32);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int blk = (int)(blockIdx.x % (unsigned)a.nblk);
+    const int64_t t0 = (int64_t)(blockIdx.x / (unsigned)a.nblk) * kTEff;
+    const int dm0 = blk * kKDM;
+    const int nst = (a.nchan + kCB - 1) / kCB;
+    const int32_t *bmin = a.blkmin + (int64_t)blk * a.nchan;
+    auto full = [&](int i) { return ptx::smem_addr(bars + i); };
+    auto empty = [&](int i) { return ptx::smem_addr(bars + a.stages + i); };
+
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < a.stages; i++) {
+            ptx::mbar_init(full(i), 32);
+            ptx::mbar_init(empty(i), kCW);
+        }
+        ptx::fence_barrier_init();
+    }
+    __syncthreads();
+
+    if (warp == kCW) {
+        // ------------------------------------------------------- producer warp
+        int issued = 0;
+        bool ok = true;
+        for (int st = 0; st < nst && ok; st++) {
+            const int slot = st % a.stages, round = st / a.stages;
+            if (round > 0) {
+                const bool w = ptx::mbar_wait(empty(slot), (round - 1) & 1, kWaitBudget);
+                if (!__all_sync(0xffffffffu, w)) {
+                    ok = false;
+                    break;
+                }
+            }
+            const int c = st * kCB + lane;
+            int64_t s_c = 0, avail = 0;
+            uint32_t len16 = 0;
+            if (c < a.nchan) {
+                s_c = (t0 + bmin[c]) & ~(int64_t)15;
+                avail = a.n_in - s_c;
+                len16 = (uint32_t)min((int64_t)a.win, avail & ~(int64_t)15);
+            }
+            uint32_t tot = len16;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
+            if (lane == 0)
+                asm volatile("mbarrier.expect_tx.shared::cta.b64 [%0], %1;" ::"r"(full(slot)),
+                             "r"(tot)
+                             : "memory");
+            __syncwarp();
+            uint8_t *dst = smem + (size_t)slot * slot_bytes + (size_t)lane * a.win;
+            if (len16 > 0) {
+                const uint8_t *src = a.x + (int64_t)c * a.x_stride + s_c;
+                ptx::bulk_g2s(ptx::smem_addr(dst), src, len16, full(slot));
+            }
+            if (c < a.nchan) {
+                const int64_t end = min((int64_t)a.win, avail);
+                for (int64_t i = len16; i < end; i++) dst[i] = a.x[(int64_t)c * a.x_stride + s_c + i];
+            }
+            ptx::mbar_arrive(full(slot));
+            issued = st + 1;
+        }
+        if (!ok && lane == 0) fail(a.err);
+        // never leave with copies in flight: wait for the last phase of each slot
+        for (int st = max(0, issued - a.stages); st < issued; st++) {
+            const bool w = ptx::mbar_wait(full(st % a.stages), (st / a.stages) & 1, kWaitBudget);
+            if (!__all_sync(0xffffffffu, w)) {
+                if (lane == 0) fail(a.err);
+                break;
+            }
+        }
+        return;
+    }
+
+    // ------------------------------------------------------- consumer warps
+    const int dmw = dm0 + warp * kKW;
+    int32_t *mylist = lists + warp * (kKW * 4 * 32);
+    uint32_t acc[kKW][kM][4];
+    uint32_t S[kKW][4][kM], E[kKW][4][kM], H[kKW][4][kM];
+#pragma unroll
+    for (int i = 0; i < kKW; i++)
+#pragma unroll
+        for (int k = 0; k < kM; k++) {
+#pragma unroll
+            for (int j = 0; j < 4; j++) acc[i][k][j] = 0;
+#pragma unroll
+            for (int p = 0; p < 4; p++) S[i][p][k] = E[i][p][k] = H[i][p][k] = 0;
+        }
+    const uint32_t mul = a.mulhi;
+    const uint32_t lmask = lanemask_lt();
+
+    for (int st = 0; st < nst; st++) {
+        const int slot = st % a.stages, round = st / a.stages;
+        const int c = st * kCB + lane;
+        const bool valid = c < a.nchan;
+        const int64_t s_c = valid ? ((t0 + bmin[c]) & ~(int64_t)15) : 0;
+        int cnt[kKW][4];
+#pragma unroll
+        for (int i = 0; i < kKW; i++) {
+            const int d = min(dmw + i, a.ndm - 1);
+            const int dl = valid ? a.delays[(int64_t)d * a.nchan + c] : 0;
+            const int q = (int)(t0 + dl - s_c);
+            const int p = q & 3;
+            const int entry = slot * slot_bytes + lane * a.win + (q & ~3);
+#pragma unroll
+            for (int P = 0; P < 4; P++) {
+                const uint32_t m = __ballot_sync(0xffffffffu, valid && p == P);
+                if (valid && p == P) mylist[(i * 4 + P) * 32 + __popc(m & lmask)] = entry;
+                cnt[i][P] = __popc(m);
+            }
+        }
+        __syncwarp();
+        const bool landed = ptx::mbar_wait(full(slot), round & 1, kWaitBudget);
+        if (!__all_sync(0xffffffffu, landed)) {
+            if (lane == 0) fail(a.err);
+            return;
+        }
+        const uint8_t *lanebase = smem + lane * 4;
+#pragma unroll
+        for (int i = 0; i < kKW; i++) {
+#pragma unroll
+            for (int P = 0; P < 4; P++) {
+                const int n = cnt[i][P];
+                const int32_t *lp = mylist + (i * 4 + P) * 32;
+                int j = 0;
+                for (; j + 2 <= n; j += 2) {
+                    const int2 e = *reinterpret_cast<const int2 *>(lp + j);
+                    const uint32_t *p1 = reinterpret_cast<const uint32_t *>(lanebase + e.x);
+                    const uint32_t *p2 = reinterpret_cast<const uint32_t *>(lanebase + e.y);
+#pragma unroll
+                    for (int k = 0; k < kM; k++) {
+                        const uint32_t w1 = p1[32 * k], w2 = p2[32 * k];
+                        S[i][P][k] += w1 + w2;
+                        E[i][P][k] += (w1 & 0x00ff00ffu) + (w2 & 0x00ff00ffu);
+                        H[i][P][k] = ptx::mad_hi(w1, mul, ptx::mad_hi(w2, mul, H[i][P][k]));
+                    }
+                }
+                if (j < n) {
+                    const uint32_t *p1 = reinterpret_cast<const uint32_t *>(lanebase + lp[j]);
+#pragma unroll
+                    for (int k = 0; k < kM; k++) {
+                        const uint32_t w1 = p1[32 * k];
+                        S[i][P][k] += w1;
+                        E[i][P][k] += w1 & 0x00ff00ffu;
+                        H[i][P][k] = ptx::mad_hi(w1, mul, H[i][P][k]);
+                    }
+                }
+            }
+        }
+        __syncwarp();
+        if (lane == 0) ptx::mbar_arrive(empty(slot));
+
+        if ((st + 1) % kFlushStages == 0 || st == nst - 1) {
+#pragma unroll
+            for (int i = 0; i < kKW; i++) {
+                uint32_t sp[kM][3];
+#pragma unroll
+                for (int k = 0; k < kM; k++) {
+                    sp[k][0] = sp[k][1] = sp[k][2] = 0;
+#pragma unroll
+                    for (int P = 0; P < 4; P++) {
+                        const uint32_t e = E[i][P][k], h = H[i][P][k];
+                        uint32_t b[4];
+                        b[0] = e & 0xffffu;
+                        b[2] = e >> 16;
+                        b[3] = h;
+                        b[1] = (S[i][P][k] - e - (h << 24)) >> 8;
+#pragma unroll
+                        for (int q = 0; q < 4; q++) {
+                            const int jj = q - P;  // output slot, negative = previous word
+                            if (jj >= 0) acc[i][k][jj] += b[q];
+                            else sp[k][jj + 3] += b[q];
+                        }
+                        S[i][P][k] = E[i][P][k] = H[i][P][k] = 0;
+                    }
+                }
+                // previous word of (lane, k) is (lane - 1, k), or (31, k - 1) for lane 0
+#pragma unroll
+                for (int k = 0; k < kM; k++) {
+#pragma unroll
+                    for (int jj = 0; jj < 3; jj++) {
+                        const uint32_t r = __shfl_sync(0xffffffffu, sp[k][jj], (lane + 1) & 31);
+                        const uint32_t rn =
+                            (k + 1 < kM) ? __shfl_sync(0xffffffffu, sp[(k + 1) % kM][jj], (lane + 1) & 31) : 0u;
+                        if (lane < 31) acc[i][k][jj + 1] += r;
+                        else if (k + 1 < kM) acc[i][k][jj + 1] += rn;
+                    }
+                }
+            }
+        }
+    }
+
+    // ------------------------------------------------------- store the tile
+#pragma unroll
+    for (int i = 0; i < kKW; i++) {
+        const int d = dmw + i;
+        if (d >= a.ndm) continue;
+        int32_t *orow = a.out + (int64_t)d * a.out_stride;
+#pragma unroll
+        for (int k = 0; k < kM; k++) {
+            const int w = lane + 32 * k;
+            const int64_t tt = t0 + 4 * w;
+            if (4 * w + 3 < kTEff && tt + 3 < a.n_out) {
+                *reinterpret_cast<int4 *>(orow + tt) =
+                    make_int4((int)acc[i][k][0], (int)acc[i][k][1], (int)acc[i][k][2], (int)acc[i][k][3]);
+            } else {
+#pragma unroll
+                for (int j = 0; j < 4; j++)
+                    if (4 * w + j < kTEff && tt + j < a.n_out) orow[tt + j] = (int32_t)acc[i][k][j];
+            }
+        }
+    }
+}
+
+}  // namespace
+
+// Per-DM-block minimum delay per channel, the largest spread of delays within
+// a block, and from it the shared-memory window per channel and ring depth.
+bool plan_dedisperse_tiled(gsp_plan_s *p, std::vector<int32_t> *blkmin) {
+    const int C = p->desc.nchan, ndm = p->desc.ndm;
+    const int nblk = (ndm + kKDM - 1) / kKDM;
+    blkmin->assign((size_t)nblk * C, 0);
+    int64_t spread = 0;
+    for (int b = 0; b < nblk; b++) {
+        for (int c = 0; c < C; c++) {
+            int32_t lo = INT32_MAX, hi = 0;
+            for (int d = b * kKDM; d < std::min(ndm, (b + 1) * kKDM); d++) {
+                const int32_t v = p->delays_h[(size_t)d * C + c];
+                lo = std::min(lo, v);
+                hi = std::max(hi, v);
+            }
+            (*blkmin)[(size_t)b * C + c] = lo;
+            spread = std::max<int64_t>(spread, (int64_t)hi - lo);
+        }
+    }
+    const int64_t win = (kT + 15 + spread + 15) & ~(int64_t)15;
+    const int64_t fixed = (int64_t)kCW * kKW * 4 * 32 * 4 + 2 * 8 * 8;
+    const int64_t budget = 227 * 1024 - fixed;
+    const int64_t stages = std::min<int64_t>(8, budget / ((int64_t)kCB * win));
+    if (stages < 2) {
+        blkmin->clear();
+        return false;
+    }
+    DDGeom &g = p->geom;
+    g.kdm = kKDM;
+    g.t_cta = kT;
+    g.t_eff = kTEff;
+    g.cb = kCB;
+    g.win = (int)win;
+    g.stages = (int)stages;
+    g.smem = (int)(stages * kCB * win + fixed);
+    g.nblk = nblk;
+    return true;
+}
+
+cudaError_t launch_dedisperse_tiled(const gsp_plan_s *p, const uint8_t *x, int64_t n_in,
+                                    int64_t x_stride, int64_t n_out, int32_t *out,
+                                    int64_t out_stride, cudaStream_t s, int32_t *nlaunch) {
+    const DDGeom &g = p->geom;
+    static int configured_smem = 0;
+    if (g.smem > configured_smem) {
+        cudaError_t e = cudaFuncSetAttribute(dd_tiled_kernel,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, g.smem);
+        if (e != cudaSuccess) return e;
+        configured_smem = g.smem;
+    }
+    TiledArgs a;
+    a.x = x;
+    a.x_stride = x_stride;
+    a.n_in = n_in;
+    a.n_out = n_out;
+    a.delays = p->d_delays;
+    a.blkmin = p->d_blkmin;
+    a.out = out;
+    a.out_stride = out_stride;
+    a.nchan = p->desc.nchan;
+    a.ndm = p->desc.ndm;
+    a.nblk = g.nblk;
+    a.win = g.win;
+    a.stages = g.stages;
+    a.mulhi = 256u;
+    a.err = p->d_err;
+    const int64_t ntiles = (n_out + kTEff - 1) / kTEff;
+    const int64_t nctas = ntiles * g.nblk;
+    if (nctas > 0x7fffffffll) return cudaErrorInvalidConfiguration;
+    dd_tiled_kernel<<<(unsigned)nctas, kThreads, g.smem, s>>>(a);
+    *nlaunch += 1;
+    return cudaGetLastError();
+}
+
+}  // namespace gsp

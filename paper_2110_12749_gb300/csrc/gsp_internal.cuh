@@ -1,0 +1,96 @@
+// Internal declarations of libgsp (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <vector>
+
+#include "gsp.h"
+
+namespace gsp {
+
+constexpr int kMaxWidths = 32;
+
+// Per-block parameters consumed by the boxcar kernel, derived in FP64 from
+// exact integer block sums and rounded once to FP32:
+//   m    = nearest integer to the block mean (the integer series is D - m),
+//   c0   = alpha - m  (intercept of the fitted line minus m),
+//   beta = slope of the fitted line,
+//   good = 1 if the block is searched, 0 if it is bad (zeroed).
+struct BlockParam {
+    int32_t m;
+    float c0;
+    float beta;
+    int32_t good;
+};
+
+// Tile geometry of the performance dedispersion kernel, chosen per plan.
+struct DDGeom {
+    int kdm = 0;       // DM trials per CTA
+    int t_cta = 0;     // output samples computed per CTA (t_eff stored)
+    int t_eff = 0;     // output samples stored per CTA (tiles overlap)
+    int cb = 0;        // channels per shared-memory stage
+    int win = 0;       // bytes per channel window in shared memory
+    int stages = 0;    // pipeline depth
+    int smem = 0;      // dynamic shared memory bytes
+    int nblk = 0;      // DM blocks
+    int variant = 0;   // template variant index
+};
+
+}  // namespace gsp
+
+struct gsp_plan_s {
+    gsp_plan_desc desc{};
+    std::vector<double> dms;
+    std::vector<int32_t> delays_h;  // [ndm][nchan]
+    std::vector<int32_t> widths;
+    int64_t max_delay = 0;
+    int device = 0;
+    int num_sms = 0;
+    bool simple_dd = false;
+
+    // device memory owned by the plan
+    int32_t *d_delays = nullptr;     // [ndm][nchan]
+    int32_t *d_blkmin = nullptr;     // [nblk][nchan] min delay of each DM block
+    int *d_err = nullptr;            // set by a kernel whose bounded wait gave up
+    double *d_sigma_b = nullptr;     // [ndm][nb_max]
+    uint8_t *d_bad = nullptr;        // [ndm][nb_max]
+    gsp::BlockParam *d_bparam = nullptr;  // [ndm][nb_max]
+    float *d_scale = nullptr;        // [ndm][nwidths] 1/(sigma_ref sqrt(w)), 0 if sigma_ref == 0
+    double *d_sref = nullptr;        // [ndm]
+    gsp_cand *d_cands = nullptr;     // [max_cands]
+    unsigned long long *d_ncand = nullptr;
+    int32_t *d_D = nullptr;          // lazily allocated dedispersed scratch
+    size_t d_D_elems = 0;
+    uint8_t *d_xstage = nullptr;     // lazily allocated input staging for host calls
+    size_t d_xstage_bytes = 0;
+    int64_t nb_max = 0;
+
+    gsp::DDGeom geom;
+
+    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+    bool timed = false;
+    cudaStream_t last_stream = nullptr;
+    int64_t last_nout = -1;
+    int64_t last_nb = 0;
+    bool have_search = false;
+    int32_t launches = 0;
+};
+
+namespace gsp {
+
+// Kernel launchers (dedisperse.cu, search.cu).  Each returns the CUDA error
+// of its launch(es) and adds the number of kernels it launched to *nlaunch.
+cudaError_t launch_dedisperse_simple(const gsp_plan_s *p, const uint8_t *x, int64_t x_stride,
+                                     int64_t n_out, int32_t *out, int64_t out_stride,
+                                     cudaStream_t s, int32_t *nlaunch);
+cudaError_t launch_dedisperse_tiled(const gsp_plan_s *p, const uint8_t *x, int64_t n_in,
+                                    int64_t x_stride, int64_t n_out, int32_t *out,
+                                    int64_t out_stride, cudaStream_t s, int32_t *nlaunch);
+bool plan_dedisperse_tiled(gsp_plan_s *p, std::vector<int32_t> *blkmin);
+
+cudaError_t launch_search(gsp_plan_s *p, const int32_t *D, int64_t n_out, int64_t stride,
+                          int64_t t_offset, float *snr_out, cudaStream_t s, int32_t *nlaunch);
+
+}  // namespace gsp

@@ -1,0 +1,368 @@
+// Single-pulse search of dedispersed series (the step after dedispersion in
+// the pipeline of Sec. 2.1-2.2; the paper names it, the steps are these):
+//   1. blocks [bB, (b+1)B) of each DM row; least-squares line per block from
+//      exact integer sums, residual RMS sigma_b (block_stats_kernel);
+//   2. sigma_ref = lower median of sigma_b per row, bad-block flags
+//      (row_sigma_kernel);
+//   3. boxcar S/N over the widths, best width per sample, threshold and the
+//      per-window maximum, appended to the candidate buffer (boxcar_kernel).
+#include <cfloat>
+#include <cmath>
+
+#include "gsp_internal.cuh"
+
+namespace gsp {
+
+namespace {
+
+constexpr int kStatThreads = 256;
+constexpr int kBoxThreads = 256;
+constexpr int kChunk = 1024;  // samples per boxcar sub-chunk
+
+struct WidthTable {
+    int w[kMaxWidths];
+    float tri[kMaxWidths];  // w (w - 1) / 2
+    int n;
+    int wmax;
+};
+
+__device__ __forceinline__ long long warp_sum_ll(long long v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Step 1.  One CTA per (block, row).  Exact int64 sums S0 = sum D_j,
+// S1 = sum j D_j, S2 = sum D_j^2 over j = 0..B-1, then in exact 128-bit
+// integers U = B S2 - S0^2, V = 2 S1 - (B-1) S0 and
+// N = U (B^2 - 1) - 3 V^2 = B^2 (B^2 - 1) * sigma_b^2, so that
+// sigma_b = sqrt(N / (B^2 (B^2 - 1))) (population RMS of the residual from
+// the least-squares line) and beta = 6 V / (B (B^2 - 1)).
+__global__ void __launch_bounds__(kStatThreads) block_stats_kernel(
+    const int32_t *__restrict__ D, int64_t stride, int B, int64_t nb_max,
+    double *__restrict__ sigma_b, BlockParam *__restrict__ bparam) {
+    const int b = blockIdx.x;
+    const int row = blockIdx.y;
+    const int32_t *d = D + (int64_t)row * stride + (int64_t)b * B;
+    long long s0 = 0, s1 = 0, s2 = 0;
+    for (int j = threadIdx.x; j < B; j += kStatThreads) {
+        const long long v = d[j];
+        s0 += v;
+        s1 += (long long)j * v;
+        s2 += v * v;
+    }
+    s0 = warp_sum_ll(s0);
+    s1 = warp_sum_ll(s1);
+    s2 = warp_sum_ll(s2);
+    __shared__ long long red[3][kStatThreads / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) {
+        red[0][wid] = s0;
+        red[1][wid] = s1;
+        red[2][wid] = s2;
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    s0 = s1 = s2 = 0;
+    for (int i = 0; i < kStatThreads / 32; i++) {
+        s0 += red[0][i];
+        s1 += red[1][i];
+        s2 += red[2][i];
+    }
+    const __int128 Bi = B;
+    const __int128 bb1 = Bi * Bi - 1;
+    double sig = 0.0, beta = 0.0;
+    if (B > 1) {
+        const __int128 U = Bi * (__int128)s2 - (__int128)s0 * (__int128)s0;
+        const __int128 V = 2 * (__int128)s1 - (Bi - 1) * (__int128)s0;
+        const __int128 N = U * bb1 - 3 * V * V;
+        const double den = (double)B * (double)B * (double)bb1;
+        sig = N > 0 ? sqrt((double)N / den) : 0.0;
+        beta = 6.0 * (double)V / ((double)B * (double)bb1);
+    }
+    const double mean = (double)s0 / (double)B;
+    const long long m = (long long)floor(mean + 0.5);
+    const double jbar = 0.5 * (double)(B - 1);
+    const double c0 = (double)(s0 - m * (long long)B) / (double)B - beta * jbar;
+    const int64_t idx = (int64_t)row * nb_max + b;
+    sigma_b[idx] = sig;
+    BlockParam bp;
+    bp.m = (int32_t)m;
+    bp.c0 = (float)c0;
+    bp.beta = (float)beta;
+    bp.good = 1;
+    bparam[idx] = bp;
+}
+
+// Step 2.  One CTA per row: lower median of the nb block sigmas (bitonic sort
+// in shared memory, or rank counting when nb exceeds the shared buffer), bad
+// flags, and the per-width S/N scale 1 / (sigma_ref sqrt(w)).
+constexpr int kSortMax = 4096;  // 32 KB of doubles, within the default limit
+
+__global__ void __launch_bounds__(512) row_sigma_kernel(
+    const double *__restrict__ sigma_b, int64_t nb, int64_t nb_max, double bad_lo,
+    double bad_hi, WidthTable wt, double *__restrict__ sref_out, float *__restrict__ scale_out,
+    uint8_t *__restrict__ bad_out, BlockParam *__restrict__ bparam) {
+    extern __shared__ double sbuf[];
+    __shared__ double s_ref;
+    const int row = blockIdx.x;
+    const double *sg = sigma_b + (int64_t)row * nb_max;
+    const int64_t k = (nb - 1) / 2;
+    if (nb <= kSortMax) {
+        int n2 = 1;
+        while (n2 < nb) n2 <<= 1;
+        for (int i = threadIdx.x; i < n2; i += blockDim.x) sbuf[i] = i < nb ? sg[i] : DBL_MAX;
+        __syncthreads();
+        for (int size = 2; size <= n2; size <<= 1) {
+            for (int stride = size >> 1; stride > 0; stride >>= 1) {
+                for (int i = threadIdx.x; i < n2; i += blockDim.x) {
+                    const int jx = i ^ stride;
+                    if (jx > i) {
+                        const bool up = (i & size) == 0;
+                        const double a = sbuf[i], c = sbuf[jx];
+                        if ((a > c) == up) {
+                            sbuf[i] = c;
+                            sbuf[jx] = a;
+                        }
+                    }
+                }
+                __syncthreads();
+            }
+        }
+        if (threadIdx.x == 0) s_ref = sbuf[k];
+    } else {
+        // rank of element i: #(smaller) + #(equal with lower index)
+        for (int64_t i = threadIdx.x; i < nb; i += blockDim.x) {
+            const double v = sg[i];
+            int64_t r = 0;
+            for (int64_t q = 0; q < nb; q++) {
+                const double u = sg[q];
+                r += (u < v) || (u == v && q < i);
+            }
+            if (r == k) s_ref = v;
+        }
+    }
+    __syncthreads();
+    const double sref = s_ref;
+    if (threadIdx.x == 0) sref_out[row] = sref;
+    if (threadIdx.x < wt.n)
+        scale_out[(int64_t)row * wt.n + threadIdx.x] =
+            sref > 0.0 ? (float)(1.0 / (sref * sqrt((double)wt.w[threadIdx.x]))) : 0.0f;
+    for (int64_t b = threadIdx.x; b < nb; b += blockDim.x) {
+        const double v = sg[b];
+        const bool bad = !(sref > 0.0) || v < bad_lo * sref || v > bad_hi * sref;
+        bad_out[(int64_t)row * nb_max + b] = bad ? 1 : 0;
+        bparam[(int64_t)row * nb_max + b].good = bad ? 0 : 1;
+    }
+}
+
+struct Best {
+    float snr;
+    int64_t t;
+    int w;
+};
+
+__device__ __forceinline__ bool better(const Best &a, const Best &b) {
+    // larger S/N wins; equal S/N: smaller t
+    return a.snr > b.snr || (a.snr == b.snr && a.t < b.t);
+}
+
+// Step 3.  One CTA per (candidate window, row).  The window's samples are
+// processed in sub-chunks of kChunk: exact uint32 prefix sums of the integer
+// series y = D - m_b (0 in bad blocks) give every boxcar's integer sum
+// Y(t, w); the fitted-line part Cr(t, w) = sum (c0_b + beta_b j) over the
+// same samples is evaluated in closed form per block segment; then
+// S/N = (Y - Cr) / (sigma_ref sqrt(w)).
+template <bool kWriteSnr>
+__global__ void __launch_bounds__(kBoxThreads) boxcar_kernel(
+    const int32_t *__restrict__ D, int64_t stride, int64_t Ls, int B, int64_t nb_max,
+    int64_t t_offset, int64_t win_len, int64_t k0, WidthTable wt,
+    const BlockParam *__restrict__ bparam, const float *__restrict__ scale, float threshold,
+    int ndm_total, float *__restrict__ snr_out, gsp_cand *__restrict__ cands,
+    unsigned long long *__restrict__ ncand, int64_t max_cands) {
+    extern __shared__ uint32_t sP[];  // prefix sums, kChunk + wmax entries
+    __shared__ uint32_t warp_tot[kBoxThreads / 32];
+    __shared__ Best wbest[kBoxThreads / 32];
+    __shared__ float s_scale[kMaxWidths];
+    const int row = blockIdx.y;
+    const int64_t win = k0 + blockIdx.x;
+    int64_t ws = win * win_len - t_offset, we = ws + win_len;
+    if (ws < 0) ws = 0;
+    if (we > Ls) we = Ls;
+    const int32_t *d = D + (int64_t)row * stride;
+    const BlockParam *bp = bparam + (int64_t)row * nb_max;
+    if (threadIdx.x < wt.n) s_scale[threadIdx.x] = scale[(int64_t)row * wt.n + threadIdx.x];
+    __syncthreads();
+    const bool live = s_scale[0] != 0.0f;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    Best run{-FLT_MAX, 0, 0};
+    bool have = false;
+
+    for (int64_t s = ws; s < we; s += kChunk) {
+        const int64_t e = min(s + (int64_t)kChunk, we);
+        const int64_t pe = min(e + (int64_t)wt.wmax - 1, Ls);  // prefix covers [s, pe)
+        const int len = (int)(pe - s);
+        // per-thread consecutive segment of the scan
+        const int per = (len + kBoxThreads - 1) / kBoxThreads;
+        const int i0 = threadIdx.x * per;
+        uint32_t loc = 0;
+        for (int i = i0; i < min(i0 + per, len); i++) {
+            const int64_t t = s + i;
+            const BlockParam q = bp[t / B];
+            loc += q.good ? (uint32_t)(d[t] - q.m) : 0u;
+        }
+        // block exclusive scan of the per-thread totals
+        uint32_t incl = loc;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += v;
+        }
+        if (lane == 31) warp_tot[wid] = incl;
+        __syncthreads();
+        uint32_t wpre = 0;
+        for (int q = 0; q < wid; q++) wpre += warp_tot[q];
+        uint32_t run_p = wpre + incl - loc;
+        for (int i = i0; i < min(i0 + per, len); i++) {
+            sP[i] = run_p;
+            const int64_t t = s + i;
+            const BlockParam q = bp[t / B];
+            run_p += q.good ? (uint32_t)(d[t] - q.m) : 0u;
+        }
+        if (threadIdx.x == kBoxThreads - 1) sP[len] = run_p;  // total (exclusive end)
+        __syncthreads();
+
+        Best mine{-FLT_MAX, 0, 0};
+        bool mine_ok = false;
+        for (int64_t t = s + threadIdx.x; t < e; t += kBoxThreads) {
+            const int i = (int)(t - s);
+            const int64_t b = t / B;
+            const int j1 = (int)(t - b * B);
+            const BlockParam q = bp[b];
+            const int rem = B - j1;  // samples left in block b
+            BlockParam q2 = q;
+            if (b + 1 < Ls / B) q2 = bp[b + 1];
+            const float g = q.good ? q.c0 + q.beta * (float)j1 : 0.0f;
+            const float beta1 = q.good ? q.beta : 0.0f;
+            const float c02 = q2.good ? q2.c0 : 0.0f;
+            const float beta2 = q2.good ? q2.beta : 0.0f;
+            const uint32_t p0 = sP[i];
+            float bsnr = -FLT_MAX;
+            int bw = 0;
+            for (int iw = 0; iw < wt.n; iw++) {
+                const int w = wt.w[iw];
+                float v;
+                if (t + w > Ls) {
+                    v = __int_as_float(0x7fc00000);  // NaN
+                } else {
+                    const int32_t Y = (int32_t)(sP[i + w] - p0);
+                    float cr;
+                    if (w <= rem) {
+                        cr = (float)w * g + beta1 * wt.tri[iw];
+                    } else {
+                        const int n1 = rem, n2 = w - rem;
+                        cr = (float)n1 * g + beta1 * (0.5f * (float)n1 * (float)(n1 - 1)) +
+                             (float)n2 * c02 + beta2 * (0.5f * (float)n2 * (float)(n2 - 1));
+                    }
+                    v = ((float)Y - cr) * s_scale[iw];
+                    if (v > bsnr) {
+                        bsnr = v;
+                        bw = w;
+                    }
+                }
+                if (kWriteSnr) snr_out[((int64_t)row * wt.n + iw) * Ls + t] = v;
+            }
+            if (live && bw > 0 && bsnr >= threshold) {
+                Best c{bsnr, t, bw};
+                if (!mine_ok || better(c, mine)) {
+                    mine = c;
+                    mine_ok = true;
+                }
+            }
+        }
+        // block argmax (S/N desc, t asc)
+        if (!mine_ok) mine = Best{-FLT_MAX, INT64_MAX, 0};
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            Best other;
+            other.snr = __shfl_xor_sync(0xffffffffu, mine.snr, o);
+            other.t = __shfl_xor_sync(0xffffffffu, mine.t, o);
+            other.w = __shfl_xor_sync(0xffffffffu, mine.w, o);
+            if (better(other, mine)) mine = other;
+        }
+        if (lane == 0) wbest[wid] = mine;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            Best bb = wbest[0];
+            for (int q = 1; q < kBoxThreads / 32; q++)
+                if (better(wbest[q], bb)) bb = wbest[q];
+            if (bb.w > 0 && (!have || bb.snr > run.snr)) {
+                run = bb;
+                have = true;
+            }
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0 && have) {
+        const unsigned long long idx = atomicAdd(ncand, 1ull);
+        if ((int64_t)idx < max_cands) {
+            gsp_cand c;
+            c.dm_idx = row;
+            c.width = run.w;
+            c.t = run.t;
+            c.snr = run.snr;
+            c.beam = 0;
+            cands[idx] = c;
+        }
+    }
+    (void)ndm_total;
+}
+
+}  // namespace
+
+cudaError_t launch_search(gsp_plan_s *p, const int32_t *D, int64_t n_out, int64_t stride,
+                          int64_t t_offset, float *snr_out, cudaStream_t s, int32_t *nlaunch) {
+    const int B = p->desc.block_len;
+    const int64_t nb = n_out / B;
+    const int64_t Ls = nb * B;
+    const int ndm = p->desc.ndm;
+    cudaError_t e = cudaMemsetAsync(p->d_ncand, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return e;
+    if (nb == 0) return cudaSuccess;
+    WidthTable wt{};
+    wt.n = (int)p->widths.size();
+    wt.wmax = 0;
+    for (int i = 0; i < wt.n; i++) {
+        wt.w[i] = p->widths[i];
+        wt.tri[i] = 0.5f * (float)p->widths[i] * (float)(p->widths[i] - 1);
+        wt.wmax = max(wt.wmax, p->widths[i]);
+    }
+    block_stats_kernel<<<dim3((unsigned)nb, (unsigned)ndm), kStatThreads, 0, s>>>(
+        D, stride, B, p->nb_max, p->d_sigma_b, p->d_bparam);
+    *nlaunch += 1;
+    int n2 = 1;
+    while (n2 < nb) n2 <<= 1;
+    const size_t sm_sort = nb <= kSortMax ? (size_t)n2 * sizeof(double) : 0;
+    row_sigma_kernel<<<ndm, 512, sm_sort, s>>>(p->d_sigma_b, nb, p->nb_max, (double)p->desc.bad_lo,
+                                               (double)p->desc.bad_hi, wt, p->d_sref, p->d_scale,
+                                               p->d_bad, p->d_bparam);
+    *nlaunch += 1;
+    const int64_t L = p->desc.window_len;
+    auto fdiv = [](int64_t a, int64_t b) { return a >= 0 ? a / b : -((-a + b - 1) / b); };
+    const int64_t k0 = fdiv(t_offset, L);
+    const int64_t k1 = fdiv(t_offset + Ls - 1, L);
+    const size_t sm_box = (size_t)(kChunk + wt.wmax + 1) * sizeof(uint32_t);
+    dim3 grid((unsigned)(k1 - k0 + 1), (unsigned)ndm);
+    if (snr_out)
+        boxcar_kernel<true><<<grid, kBoxThreads, sm_box, s>>>(
+            D, stride, Ls, B, p->nb_max, t_offset, L, k0, wt, p->d_bparam, p->d_scale,
+            p->desc.threshold, ndm, snr_out, p->d_cands, p->d_ncand, p->desc.max_cands);
+    else
+        boxcar_kernel<false><<<grid, kBoxThreads, sm_box, s>>>(
+            D, stride, Ls, B, p->nb_max, t_offset, L, k0, wt, p->d_bparam, p->d_scale,
+            p->desc.threshold, ndm, snr_out, p->d_cands, p->d_ncand, p->desc.max_cands);
+    *nlaunch += 1;
+    return cudaGetLastError();
+}
+
+}  // namespace gsp

@@ -1,0 +1,334 @@
+"""Thin ctypes binding of libgsp (include/gsp.h) with the same entry-point names.
+
+Argument marshalling only: every step of the hot path runs in the library's
+CUDA kernels.  Device buffers are torch CUDA tensors (``data_ptr()``); streams
+default to torch's current stream.  There is no fallback: if libgsp.so has not
+been built, ``lib()`` raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libgsp.so")
+
+GSP_OK = 0
+GSP_ERR_INVALID_ARG = 1
+GSP_ERR_OOM = 2
+GSP_ERR_CUDA = 3
+GSP_ERR_TOO_SHORT = 4
+GSP_ERR_CAPACITY = 5
+GSP_ERR_TIMEOUT = 6
+GSP_ERR_TIE = 7
+GSP_ERR_ALIGN = 8
+GSP_ERR_STATE = 9
+
+GSP_FLAG_TIMING = 1
+GSP_FLAG_SIMPLE_DD = 2
+
+DEFAULT_WIDTHS = (1, 2, 3, 4, 6, 9, 14, 20, 30, 45, 70, 100, 150)
+
+
+class GspError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = status
+        msg = "%s: %s" % (where, gsp_status_string(status))
+        if status == GSP_ERR_CUDA:
+            msg += " [%s]" % gsp_last_error_string()
+        super().__init__(msg)
+
+
+class gsp_plan_desc(ctypes.Structure):
+    _fields_ = [
+        ("nchan", ctypes.c_int32),
+        ("f_lo_mhz", ctypes.c_double),
+        ("f_hi_mhz", ctypes.c_double),
+        ("freq_descending", ctypes.c_int32),
+        ("t_samp_s", ctypes.c_double),
+        ("ndm", ctypes.c_int32),
+        ("dms", ctypes.c_void_p),
+        ("dm_lo", ctypes.c_double),
+        ("dm_step", ctypes.c_double),
+        ("delays", ctypes.c_void_p),
+        ("nsamp_max", ctypes.c_int64),
+        ("widths", ctypes.c_void_p),
+        ("nwidths", ctypes.c_int32),
+        ("block_len", ctypes.c_int32),
+        ("window_len", ctypes.c_int32),
+        ("threshold", ctypes.c_float),
+        ("bad_lo", ctypes.c_float),
+        ("bad_hi", ctypes.c_float),
+        ("max_cands", ctypes.c_int64),
+        ("flags", ctypes.c_int32),
+    ]
+
+
+CAND_DTYPE = np.dtype([("dm_idx", np.int32), ("width", np.int32), ("t", np.int64),
+                       ("snr", np.float32), ("beam", np.int32)], align=True)
+assert CAND_DTYPE.itemsize == 24
+
+_lib = None
+_vp = ctypes.c_void_p
+_i64 = ctypes.c_int64
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libgsp.so is not built (run __graft_entry__.build())")
+        L = ctypes.CDLL(LIB_PATH)
+        sig = {
+            "gsp_plan_desc_init": ([_vp], ctypes.c_int),
+            "gsp_compute_delays": ([_vp, _vp, _vp], ctypes.c_int),
+            "gsp_plan_create": ([_vp, _vp], ctypes.c_int),
+            "gsp_plan_destroy": ([_vp], ctypes.c_int),
+            "gsp_plan_max_delay": ([_vp], _i64),
+            "gsp_plan_nout": ([_vp, _i64], _i64),
+            "gsp_plan_delays": ([_vp, _vp], ctypes.c_int),
+            "gsp_dedisperse": ([_vp, _vp, _i64, _i64, _vp, _i64, _vp], ctypes.c_int),
+            "gsp_search": ([_vp, _vp, _i64, _i64, _i64, _vp, _i64, _vp], ctypes.c_int),
+            "gsp_search_series": ([_vp, _vp, _i64, _i64, _i64, _vp], ctypes.c_int),
+            "gsp_boxcar_snr": ([_vp, _vp, _i64, _i64, _vp, _vp], ctypes.c_int),
+            "gsp_search_stats": ([_vp, _vp, _vp, _vp, _vp], ctypes.c_int),
+            "gsp_candidates": ([_vp, _vp, _i64, _vp], ctypes.c_int),
+            "gsp_search_host": ([_vp, _vp, _i64, _i64, _i64, _vp, _i64, _vp, _vp], ctypes.c_int),
+            "gsp_plan_timing": ([_vp, _vp, _vp], ctypes.c_int),
+            "gsp_plan_launches": ([_vp], ctypes.c_int32),
+            "gsp_status_string": ([ctypes.c_int], ctypes.c_char_p),
+            "gsp_last_error_string": ([], ctypes.c_char_p),
+            "gsp_version": ([], ctypes.c_int32),
+        }
+        for name, (args, res) in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = L
+    return _lib
+
+
+def _np_ptr(a):
+    return a.ctypes.data_as(_vp) if a is not None else None
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return _vp(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return _vp(stream)
+    return _vp(stream.cuda_stream)
+
+
+def _check(st, where):
+    if st != GSP_OK:
+        raise GspError(st, where)
+
+
+def gsp_status_string(st):
+    return lib().gsp_status_string(int(st)).decode()
+
+
+def gsp_last_error_string():
+    return lib().gsp_last_error_string().decode()
+
+
+def gsp_version():
+    return int(lib().gsp_version())
+
+
+class Plan:
+    """Owns a gsp_plan_t and the host arrays its descriptor points to."""
+
+    def __init__(self, handle, desc, keep):
+        self.handle = handle
+        self.desc = desc
+        self._keep = keep
+
+    @property
+    def ndm(self):
+        return int(self.desc.ndm)
+
+    @property
+    def nchan(self):
+        return int(self.desc.nchan)
+
+    @property
+    def widths(self):
+        return self._keep.get("widths_list", DEFAULT_WIDTHS)
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            try:
+                _lib.gsp_plan_destroy(self.handle)
+            except Exception:
+                pass
+            self.handle = None
+
+
+def gsp_plan_desc_init():
+    d = gsp_plan_desc()
+    _check(lib().gsp_plan_desc_init(ctypes.byref(d)), "gsp_plan_desc_init")
+    return d
+
+
+def make_desc(nchan, f_lo, f_hi, t_samp, nsamp_max, dms=None, dm_lo=0.0, dm_step=1.0,
+              ndm=None, delays=None, freq_descending=False, widths=None, block_len=None,
+              window_len=None, threshold=None, bad_lo=None, bad_hi=None, max_cands=None,
+              flags=0):
+    """Descriptor plus the arrays it points to (keep both alive together)."""
+    d = gsp_plan_desc_init()
+    keep = {}
+    d.nchan = nchan
+    d.f_lo_mhz, d.f_hi_mhz, d.t_samp_s = f_lo, f_hi, t_samp
+    d.freq_descending = int(bool(freq_descending))
+    d.nsamp_max = nsamp_max
+    if dms is not None:
+        arr = np.ascontiguousarray(np.asarray(dms, dtype=np.float64).reshape(-1))
+        keep["dms"] = arr
+        d.dms = arr.ctypes.data
+        d.ndm = arr.size
+    elif ndm is not None:
+        d.ndm = ndm
+        d.dm_lo, d.dm_step = dm_lo, dm_step
+    if delays is not None:
+        arr = np.ascontiguousarray(np.asarray(delays, dtype=np.int32))
+        keep["delays"] = arr
+        d.delays = arr.ctypes.data
+        d.ndm = arr.shape[0]
+    if widths is not None:
+        arr = np.ascontiguousarray(np.asarray(widths, dtype=np.int32))
+        keep["widths"] = arr
+        keep["widths_list"] = tuple(int(w) for w in widths)
+        d.widths = arr.ctypes.data
+        d.nwidths = arr.size
+    if block_len is not None:
+        d.block_len = block_len
+    if window_len is not None:
+        d.window_len = window_len
+    if threshold is not None:
+        d.threshold = threshold
+    if bad_lo is not None:
+        d.bad_lo = bad_lo
+    if bad_hi is not None:
+        d.bad_hi = bad_hi
+    if max_cands is not None:
+        d.max_cands = max_cands
+    d.flags = flags
+    return d, keep
+
+
+def gsp_compute_delays(desc):
+    out = np.empty((desc.ndm, desc.nchan), dtype=np.int32)
+    m = ctypes.c_double(0.0)
+    _check(lib().gsp_compute_delays(ctypes.byref(desc), _np_ptr(out), ctypes.byref(m)),
+           "gsp_compute_delays")
+    return out, m.value
+
+
+def gsp_plan_create(desc, keep=None):
+    h = _vp()
+    _check(lib().gsp_plan_create(ctypes.byref(h), ctypes.byref(desc)), "gsp_plan_create")
+    return Plan(h, desc, keep or {})
+
+
+def gsp_plan_destroy(plan):
+    if plan.handle:
+        st = lib().gsp_plan_destroy(plan.handle)
+        plan.handle = None
+        _check(st, "gsp_plan_destroy")
+
+
+def gsp_plan_max_delay(plan):
+    return int(lib().gsp_plan_max_delay(plan.handle))
+
+
+def gsp_plan_nout(plan, n_in):
+    return int(lib().gsp_plan_nout(plan.handle, n_in))
+
+
+def gsp_plan_delays(plan):
+    out = np.empty((plan.ndm, plan.nchan), dtype=np.int32)
+    _check(lib().gsp_plan_delays(plan.handle, _np_ptr(out)), "gsp_plan_delays")
+    return out
+
+
+def gsp_dedisperse(plan, x, n_in, out, stream=None):
+    """x: torch uint8 CUDA [nchan][stride]; out: torch int32 CUDA [ndm][>= n_out]."""
+    st = lib().gsp_dedisperse(plan.handle, _vp(x.data_ptr()), n_in, x.stride(0),
+                              _vp(out.data_ptr()), out.stride(0), _stream(stream))
+    _check(st, "gsp_dedisperse")
+
+
+def gsp_search(plan, x, n_in, t_offset=0, out=None, stream=None):
+    st = lib().gsp_search(plan.handle, _vp(x.data_ptr()), n_in, x.stride(0), t_offset,
+                          _vp(out.data_ptr()) if out is not None else None,
+                          out.stride(0) if out is not None else 0, _stream(stream))
+    _check(st, "gsp_search")
+
+
+def gsp_search_series(plan, D, n_out, t_offset=0, stream=None):
+    st = lib().gsp_search_series(plan.handle, _vp(D.data_ptr()), n_out, D.stride(0), t_offset,
+                                 _stream(stream))
+    _check(st, "gsp_search_series")
+
+
+def gsp_boxcar_snr(plan, D, n_out, snr_out, stream=None):
+    st = lib().gsp_boxcar_snr(plan.handle, _vp(D.data_ptr()), n_out, D.stride(0),
+                              _vp(snr_out.data_ptr()), _stream(stream))
+    _check(st, "gsp_boxcar_snr")
+
+
+def gsp_search_stats(plan, n_out):
+    nb = n_out // plan.desc.block_len
+    sig = np.zeros((plan.ndm, max(nb, 1)), np.float64)
+    bad = np.zeros((plan.ndm, max(nb, 1)), np.uint8)
+    sref = np.zeros(plan.ndm, np.float64)
+    nbo = ctypes.c_int64(0)
+    _check(lib().gsp_search_stats(plan.handle, _np_ptr(sig), _np_ptr(bad), _np_ptr(sref),
+                                  ctypes.byref(nbo)), "gsp_search_stats")
+    nb = nbo.value
+    return {"sigma_b": sig[:, :nb], "bad": bad[:, :nb].astype(bool), "sigma_ref": sref}
+
+
+def gsp_candidates(plan, cap=None):
+    """Returns (candidates sorted by (dm_idx, t, width), true count, status)."""
+    if cap is None:
+        cap = int(plan.desc.max_cands)
+    out = np.zeros(max(cap, 1), dtype=CAND_DTYPE)
+    n = ctypes.c_int64(0)
+    st = lib().gsp_candidates(plan.handle, _np_ptr(out), cap, ctypes.byref(n))
+    if st not in (GSP_OK, GSP_ERR_CAPACITY):
+        _check(st, "gsp_candidates")
+    return out[:min(n.value, cap)].copy(), n.value, st
+
+
+def gsp_search_host(plan, x_host, n_in, t_offset=0, cap=None, stream=None):
+    """x_host: numpy uint8 [nchan][stride] or a (pinned) CPU torch tensor."""
+    if cap is None:
+        cap = int(plan.desc.max_cands)
+    out = np.zeros(max(cap, 1), dtype=CAND_DTYPE)
+    n = ctypes.c_int64(0)
+    if isinstance(x_host, np.ndarray):
+        ptr, stride = _np_ptr(x_host), x_host.strides[0]
+    else:
+        ptr, stride = _vp(x_host.data_ptr()), x_host.stride(0)
+    st = lib().gsp_search_host(plan.handle, ptr, n_in, stride, t_offset, _np_ptr(out), cap,
+                               ctypes.byref(n), _stream(stream))
+    if st not in (GSP_OK, GSP_ERR_CAPACITY):
+        _check(st, "gsp_search_host")
+    return out[:min(n.value, cap)].copy(), n.value, st
+
+
+def gsp_plan_timing(plan):
+    a, b = ctypes.c_float(0), ctypes.c_float(0)
+    _check(lib().gsp_plan_timing(plan.handle, ctypes.byref(a), ctypes.byref(b)),
+           "gsp_plan_timing")
+    return a.value, b.value
+
+
+def gsp_plan_launches(plan):
+    return int(lib().gsp_plan_launches(plan.handle))
