@@ -42,6 +42,10 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-rows", type=int, default=0, help="DM rows of the oracle sample (0: auto)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--n-in", type=int, default=0,
+                    help="samples per channel (0: the workload's); smaller only for profiling")
+    ap.add_argument("--variant", type=int, default=-1,
+                    help="tiled dedispersion kernel variant (GSP_DD_VARIANT); -1: library default")
     return ap.parse_args()
 
 
@@ -192,6 +196,11 @@ def run_gsp(args):
         import torch.distributed as dist
         dist.init_process_group("nccl")
     wl = synth.WORKLOADS[args.workload]
+    if args.n_in:
+        import dataclasses
+        wl = dataclasses.replace(wl, n_in=args.n_in)
+    if args.variant >= 0:
+        os.environ["GSP_DD_VARIANT"] = str(args.variant)
     desc, keep = gsp.make_desc(wl.nchan, wl.f_lo, wl.f_hi, wl.t_samp, wl.n_in, ndm=wl.ndm,
                                dm_lo=wl.dm_lo, dm_step=wl.dm_step, flags=gsp.GSP_FLAG_TIMING)
     plan = gsp.gsp_plan_create(desc, keep)
@@ -288,6 +297,7 @@ def run_gsp(args):
             "e2e": {"value": e2e_value, "unit": "sky-s/s", "ms_per_step": e2e_step,
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 8 + 24 * int(n2)},
             "gpu_launches": launches, "clocks": clocks, "candidates": int(ncand),
+            "dd_variant": os.environ.get("GSP_DD_VARIANT", "default"),
             "input_gen_s": gen_s, "wall_s": t_wall,
         }
         if cpu is not None:

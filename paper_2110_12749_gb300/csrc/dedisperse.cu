@@ -23,6 +23,7 @@
 // 256 * 255 < 2^16, i.e. every 256 channels the views are flushed into int32
 // accumulators.
 #include <algorithm>
+#include <cstdlib>
 #include <vector>
 
 #include "dd_tiled.cuh"
@@ -85,13 +86,10 @@ cudaError_t launch_dedisperse_simple(const gsp_plan_s *p, const uint8_t *x, int6
 namespace {
 
 constexpr int kM = 4;            // words per lane: T = 128 * kM output samples per warp pass
-constexpr int kKW = 2;           // DM trials per consumer warp
-constexpr int kCW = 8;           // consumer warps
 constexpr int kCB = 32;          // channels per stage
 constexpr int kT = 128 * kM;     // samples computed per tile
 constexpr int kTEff = kT - 4;    // samples stored per tile (the last word is incomplete)
-constexpr int kKDM = kCW * kKW;  // DM trials per CTA
-constexpr int kThreads = (kCW + 1) * 32;
+constexpr int kKDM = 16;         // DM trials per CTA (= consumer warps x DM trials per warp)
 constexpr int kFlushStages = 256 / kCB;  // stages between SWAR flushes (256 channels)
 constexpr long long kWaitBudget = 4000000000ll;  // ~2 s of SM clock per wait
 
@@ -121,7 +119,12 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
 
 __device__ __forceinline__ void fail(int *err) { atomicExch(err, 1); }
 
-__global__ void __launch_bounds__(kThreads, 1) dd_tiled_kernel(const TiledArgs a) {
+// KW: DM trials per consumer warp; kCW = kKDM / KW consumer warps + 1 producer.
+// QUAD: visit channels four at a time (more loads in flight per warp).
+template <int KW, bool QUAD>
+__global__ void __launch_bounds__((kKDM / KW + 1) * 32, 1) dd_tiled_kernel(const TiledArgs a) {
+    constexpr int kKW = KW;
+    constexpr int kCW = kKDM / KW;
     extern __shared__ __align__(128) uint8_t smem[];
     const int slot_bytes = kCB * a.win;
     int32_t *lists = reinterpret_cast<int32_t *>(smem + (size_t)a.stages * slot_bytes);
@@ -248,6 +251,26 @@ __global__ void __launch_bounds__(kThreads, 1) dd_tiled_kernel(const TiledArgs a
                 const int n = cnt[i][P];
                 const int32_t *lp = mylist + (i * 4 + P) * 32;
                 int j = 0;
+                if (QUAD) {
+                    for (; j + 4 <= n; j += 4) {
+                        const int4 e = *reinterpret_cast<const int4 *>(lp + j);
+                        const uint32_t *p1 = reinterpret_cast<const uint32_t *>(lanebase + e.x);
+                        const uint32_t *p2 = reinterpret_cast<const uint32_t *>(lanebase + e.y);
+                        const uint32_t *p3 = reinterpret_cast<const uint32_t *>(lanebase + e.z);
+                        const uint32_t *p4 = reinterpret_cast<const uint32_t *>(lanebase + e.w);
+#pragma unroll
+                        for (int k = 0; k < kM; k++) {
+                            const uint32_t w1 = p1[32 * k], w2 = p2[32 * k];
+                            const uint32_t w3 = p3[32 * k], w4 = p4[32 * k];
+                            S[i][P][k] += w1 + w2;
+                            S[i][P][k] += w3 + w4;
+                            E[i][P][k] += (w1 & 0x00ff00ffu) + (w2 & 0x00ff00ffu);
+                            E[i][P][k] += (w3 & 0x00ff00ffu) + (w4 & 0x00ff00ffu);
+                            H[i][P][k] = ptx::mad_hi(w1, mul, ptx::mad_hi(w2, mul, H[i][P][k]));
+                            H[i][P][k] = ptx::mad_hi(w3, mul, ptx::mad_hi(w4, mul, H[i][P][k]));
+                        }
+                    }
+                }
                 for (; j + 2 <= n; j += 2) {
                     const int2 e = *reinterpret_cast<const int2 *>(lp + j);
                     const uint32_t *p1 = reinterpret_cast<const uint32_t *>(lanebase + e.x);
@@ -337,10 +360,27 @@ __global__ void __launch_bounds__(kThreads, 1) dd_tiled_kernel(const TiledArgs a
     }
 }
 
-}  // namespace
-
 // Per-DM-block minimum delay per channel, the largest spread of delays within
 // a block, and from it the shared-memory window per channel and ring depth.
+typedef void (*TiledKernel)(const TiledArgs);
+
+struct TiledVariant {
+    TiledKernel fn;
+    int kw;
+};
+
+// Tuning variants of the tiled kernel (same result, different schedule).
+const TiledVariant kVariants[] = {
+    {dd_tiled_kernel<2, false>, 2},
+    {dd_tiled_kernel<1, false>, 1},
+    {dd_tiled_kernel<2, true>, 2},
+    {dd_tiled_kernel<1, true>, 1},
+};
+constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
+constexpr int kDefaultVariant = 0;
+
+}  // namespace
+
 bool plan_dedisperse_tiled(gsp_plan_s *p, std::vector<int32_t> *blkmin) {
     const int C = p->desc.nchan, ndm = p->desc.ndm;
     const int nblk = (ndm + kKDM - 1) / kKDM;
@@ -359,7 +399,7 @@ bool plan_dedisperse_tiled(gsp_plan_s *p, std::vector<int32_t> *blkmin) {
         }
     }
     const int64_t win = (kT + 15 + spread + 15) & ~(int64_t)15;
-    const int64_t fixed = (int64_t)kCW * kKW * 4 * 32 * 4 + 2 * 8 * 8;
+    const int64_t fixed = (int64_t)kKDM * 4 * 32 * 4 + 2 * 8 * 8;
     const int64_t budget = 227 * 1024 - fixed;
     const int64_t stages = std::min<int64_t>(8, budget / ((int64_t)kCB * win));
     if (stages < 2) {
@@ -375,6 +415,12 @@ bool plan_dedisperse_tiled(gsp_plan_s *p, std::vector<int32_t> *blkmin) {
     g.stages = (int)stages;
     g.smem = (int)(stages * kCB * win + fixed);
     g.nblk = nblk;
+    // GSP_DD_VARIANT selects a tuning variant of the tiled kernel (default 0).
+    g.variant = kDefaultVariant;
+    if (const char *v = std::getenv("GSP_DD_VARIANT")) {
+        const int k = std::atoi(v);
+        if (k >= 0 && k < kNumVariants) g.variant = k;
+    }
     return true;
 }
 
@@ -382,12 +428,13 @@ cudaError_t launch_dedisperse_tiled(const gsp_plan_s *p, const uint8_t *x, int64
                                     int64_t x_stride, int64_t n_out, int32_t *out,
                                     int64_t out_stride, cudaStream_t s, int32_t *nlaunch) {
     const DDGeom &g = p->geom;
-    static int configured_smem = 0;
-    if (g.smem > configured_smem) {
-        cudaError_t e = cudaFuncSetAttribute(dd_tiled_kernel,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, g.smem);
+    const TiledVariant &v = kVariants[g.variant];
+    static int configured_smem[kNumVariants] = {0};
+    if (g.smem > configured_smem[g.variant]) {
+        cudaError_t e = cudaFuncSetAttribute(v.fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             g.smem);
         if (e != cudaSuccess) return e;
-        configured_smem = g.smem;
+        configured_smem[g.variant] = g.smem;
     }
     TiledArgs a;
     a.x = x;
@@ -408,7 +455,7 @@ cudaError_t launch_dedisperse_tiled(const gsp_plan_s *p, const uint8_t *x, int64
     const int64_t ntiles = (n_out + kTEff - 1) / kTEff;
     const int64_t nctas = ntiles * g.nblk;
     if (nctas > 0x7fffffffll) return cudaErrorInvalidConfiguration;
-    dd_tiled_kernel<<<(unsigned)nctas, kThreads, g.smem, s>>>(a);
+    v.fn<<<(unsigned)nctas, (kKDM / v.kw + 1) * 32, g.smem, s>>>(a);
     *nlaunch += 1;
     return cudaGetLastError();
 }

@@ -64,9 +64,10 @@ def test_tiny_dedisperse_bit_exact(gsp, orc, tiny, flags):
     assert (o[:, n_out:] == -7).all()          # nothing written past n_out
 
 
-def test_tiny_search_parity(gsp, orc, tiny):
+@pytest.mark.parametrize("thr", [6.0, 3.5])
+def test_tiny_search_parity(gsp, orc, tiny, thr):
     wl, dl, x, n_out, pulses, Dref = tiny
-    plan = _plan(gsp, dl, wl.n_in)
+    plan = _plan(gsp, dl, wl.n_in, threshold=thr)
     Dd = torch.from_numpy(Dref.astype(np.int32)).cuda()
     W = len(gsp.DEFAULT_WIDTHS)
     Ls = (n_out // 1024) * 1024
@@ -79,18 +80,18 @@ def test_tiny_search_parity(gsp, orc, tiny):
     contenders = {}
     ora = []
     for r in range(wl.ndm):
-        det = orc.search_row(Dref[r], dm_idx=r, detail=True)
+        det = orc.search_row(Dref[r], dm_idx=r, threshold=thr, detail=True)
         assert np.allclose(st["sigma_b"][r], det["sigma_b"], rtol=1e-12, atol=0)
         assert st["sigma_ref"][r] == pytest.approx(det["sigma_ref"], rel=1e-12)
         assert (st["bad"][r] == det["bad"]).all()
         ok, msg = snr_close(snr[r], det["snr"])
         assert ok, "row %d: %s" % (r, msg)
-        contenders[r] = window_contenders(det, 1024, 0, 6.0)
+        contenders[r] = window_contenders(det, 1024, 0, thr)
         ora.append(det["cands"])
     ora = np.concatenate(ora)
-    ncmp, bad = compare_candidates(cands, ora, 6.0, 1024, 0, contenders)
+    ncmp, bad = compare_candidates(cands, ora, thr, 1024, 0, contenders)
     assert not bad, bad[:10]
-    assert ncmp > 10
+    assert ncmp >= (5 if thr == 6.0 else 1000)
     # the injected pulse (DM 50, w 5, S/N 15) is found at its DM and time
     p = pulses[0]
     hit = [c for c in cands if abs(int(c["dm_idx"]) - 50) <= 1 and abs(int(c["t"]) - p.t0) <= 5]
@@ -138,7 +139,7 @@ def test_explicit_unsorted_delay_table(gsp, orc):
     rng = np.random.default_rng(12)
     nchan, ndm, n_in = 77, 33, 5000
     dl = rng.integers(0, 900, (ndm, nchan)).astype(np.int32)
-    x = rng.integers(0, 256, (nchan, n_in), dtype=np.uint8)
+    x = rng.integers(0, 256, (nchan, 5008), dtype=np.uint8)
     n_out = n_in - int(dl.max())
     Dref = orc.dedisperse(x, n_in, dl)
     plan = _plan(gsp, dl, n_in)
