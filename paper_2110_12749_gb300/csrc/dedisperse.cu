@@ -216,20 +216,41 @@ __global__ void __launch_bounds__((kKDM / KW + 1) * 32, 1) dd_tiled_kernel(const
         }
     const uint32_t mul = a.mulhi;
     const uint32_t lmask = lanemask_lt();
+    // delays of the next stage are loaded one stage ahead (hides L2 latency)
+    int nx_min = 0, nx_dl[kKW];
+    {
+        const bool v0 = lane < a.nchan;
+        nx_min = v0 ? bmin[lane] : 0;
+#pragma unroll
+        for (int i = 0; i < kKW; i++)
+            nx_dl[i] = v0 ? a.delays[(int64_t)min(dmw + i, a.ndm - 1) * a.nchan + lane] : 0;
+    }
 
     for (int st = 0; st < nst; st++) {
         const int slot = st % a.stages, round = st / a.stages;
         const int c = st * kCB + lane;
         const bool valid = c < a.nchan;
-        const int64_t s_c = valid ? ((t0 + bmin[c]) & ~(int64_t)15) : 0;
+        const int cur_min = nx_min;
+        int cur_dl[kKW];
+#pragma unroll
+        for (int i = 0; i < kKW; i++) cur_dl[i] = nx_dl[i];
+        {
+            const int cn = c + kCB;
+            const bool vn = cn < a.nchan;
+            nx_min = vn ? bmin[cn] : 0;
+#pragma unroll
+            for (int i = 0; i < kKW; i++)
+                nx_dl[i] = vn ? a.delays[(int64_t)min(dmw + i, a.ndm - 1) * a.nchan + cn] : 0;
+        }
+        const int64_t s_c = valid ? ((t0 + cur_min) & ~(int64_t)15) : 0;
         int cnt[kKW][4];
 #pragma unroll
         for (int i = 0; i < kKW; i++) {
-            const int d = min(dmw + i, a.ndm - 1);
-            const int dl = valid ? a.delays[(int64_t)d * a.nchan + c] : 0;
+            const int dl = valid ? cur_dl[i] : 0;
             const int q = (int)(t0 + dl - s_c);
             const int p = q & 3;
-            const int entry = slot * slot_bytes + lane * a.win + (q & ~3);
+            // word index of the aligned word of this (channel, DM) in shared memory
+            const int entry = (slot * slot_bytes + lane * a.win + (q & ~3)) >> 2;
 #pragma unroll
             for (int P = 0; P < 4; P++) {
                 const uint32_t m = __ballot_sync(0xffffffffu, valid && p == P);
@@ -243,7 +264,7 @@ __global__ void __launch_bounds__((kKDM / KW + 1) * 32, 1) dd_tiled_kernel(const
             if (lane == 0) fail(a.err);
             return;
         }
-        const uint8_t *lanebase = smem + lane * 4;
+        const uint32_t *lanebase = reinterpret_cast<const uint32_t *>(smem) + lane;
 #pragma unroll
         for (int i = 0; i < kKW; i++) {
 #pragma unroll
@@ -254,10 +275,10 @@ __global__ void __launch_bounds__((kKDM / KW + 1) * 32, 1) dd_tiled_kernel(const
                 if (QUAD) {
                     for (; j + 4 <= n; j += 4) {
                         const int4 e = *reinterpret_cast<const int4 *>(lp + j);
-                        const uint32_t *p1 = reinterpret_cast<const uint32_t *>(lanebase + e.x);
-                        const uint32_t *p2 = reinterpret_cast<const uint32_t *>(lanebase + e.y);
-                        const uint32_t *p3 = reinterpret_cast<const uint32_t *>(lanebase + e.z);
-                        const uint32_t *p4 = reinterpret_cast<const uint32_t *>(lanebase + e.w);
+                        const uint32_t *p1 = lanebase + e.x;
+                        const uint32_t *p2 = lanebase + e.y;
+                        const uint32_t *p3 = lanebase + e.z;
+                        const uint32_t *p4 = lanebase + e.w;
 #pragma unroll
                         for (int k = 0; k < kM; k++) {
                             const uint32_t w1 = p1[32 * k], w2 = p2[32 * k];
@@ -273,8 +294,8 @@ __global__ void __launch_bounds__((kKDM / KW + 1) * 32, 1) dd_tiled_kernel(const
                 }
                 for (; j + 2 <= n; j += 2) {
                     const int2 e = *reinterpret_cast<const int2 *>(lp + j);
-                    const uint32_t *p1 = reinterpret_cast<const uint32_t *>(lanebase + e.x);
-                    const uint32_t *p2 = reinterpret_cast<const uint32_t *>(lanebase + e.y);
+                    const uint32_t *p1 = lanebase + e.x;
+                    const uint32_t *p2 = lanebase + e.y;
 #pragma unroll
                     for (int k = 0; k < kM; k++) {
                         const uint32_t w1 = p1[32 * k], w2 = p2[32 * k];
@@ -284,7 +305,7 @@ __global__ void __launch_bounds__((kKDM / KW + 1) * 32, 1) dd_tiled_kernel(const
                     }
                 }
                 if (j < n) {
-                    const uint32_t *p1 = reinterpret_cast<const uint32_t *>(lanebase + lp[j]);
+                    const uint32_t *p1 = lanebase + lp[j];
 #pragma unroll
                     for (int k = 0; k < kM; k++) {
                         const uint32_t w1 = p1[32 * k];
@@ -377,7 +398,7 @@ const TiledVariant kVariants[] = {
     {dd_tiled_kernel<1, true>, 1},
 };
 constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
-constexpr int kDefaultVariant = 0;
+constexpr int kDefaultVariant = 1;
 
 }  // namespace
 
