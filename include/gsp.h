@@ -74,7 +74,7 @@ typedef struct {
     const int32_t *delays;   /* optional explicit delay table [ndm][nchan] (>= 0);
                                 overrides the band/DM description (Sec. 2.3 matrix) */
     int64_t nsamp_max;       /* largest n_in any call will pass (sizes scratch) */
-    const int32_t *widths;   /* boxcar widths, ascending, >= 1; NULL = default 13 */
+    const int32_t *widths;   /* boxcar widths, ascending, 1..min(block_len, 1024); NULL = default 13 */
     int32_t nwidths;
     int32_t block_len;       /* detrend block B (default 1024, >= max width) */
     int32_t window_len;      /* candidate window L_win (default 1024) */

@@ -109,6 +109,10 @@ struct TiledArgs {
     int stages;    // ring depth
     uint32_t mulhi;  // 256, passed at run time so that the multiply stays a multiply
     int *err;      // set to 1 if a bounded wait gave up
+    unsigned long long *bsum;  // optional [ndm][nb_max][3] block sums {S0, S1, S2}
+    int64_t nb_max;
+    int64_t Ls;    // searched length: block_len * floor(n_out / block_len)
+    int B;         // block_len (>= kTEff, so a tile touches at most two blocks)
 };
 
 __device__ __forceinline__ uint32_t lanemask_lt() {
@@ -364,6 +368,53 @@ __global__ void __launch_bounds__((kKDM / KW + 1) * 32, 1) dd_tiled_kernel(const
     for (int i = 0; i < kKW; i++) {
         const int d = dmw + i;
         if (d >= a.ndm) continue;
+        if (a.bsum != nullptr) {
+            // exact sums of the stored samples for the (at most two) search blocks
+            // the tile touches: S0 = sum D, S1 = sum j D (j inside the block), S2 = sum D^2
+            const int64_t ba = t0 / a.B;
+            const int64_t tb = (ba + 1) * a.B;
+            long long sm[2][3] = {{0, 0, 0}, {0, 0, 0}};
+#pragma unroll
+            for (int k = 0; k < kM; k++) {
+                const int w = lane + 32 * k;
+#pragma unroll
+                for (int j = 0; j < 4; j++) {
+                    const int64_t t = t0 + 4 * w + j;
+                    if (4 * w + j < kTEff && t < a.Ls) {
+                        const long long v = (long long)(int32_t)acc[i][k][j];
+                        if (t < tb) {
+                            sm[0][0] += v;
+                            sm[0][1] += (t - ba * a.B) * v;
+                            sm[0][2] += v * v;
+                        } else {
+                            sm[1][0] += v;
+                            sm[1][1] += (t - tb) * v;
+                            sm[1][2] += v * v;
+                        }
+                    }
+                }
+            }
+#pragma unroll
+            for (int h = 0; h < 2; h++)
+#pragma unroll
+                for (int f = 0; f < 3; f++) {
+                    long long v = sm[h][f];
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                    sm[h][f] = v;
+                }
+            if (lane == 0) {
+#pragma unroll
+                for (int h = 0; h < 2; h++) {
+                    const int64_t b = ba + h;
+                    if (b * a.B < a.Ls) {
+                        unsigned long long *q = a.bsum + ((int64_t)d * a.nb_max + b) * 3;
+#pragma unroll
+                        for (int f = 0; f < 3; f++) atomicAdd(q + f, (unsigned long long)sm[h][f]);
+                    }
+                }
+            }
+        }
         int32_t *orow = a.out + (int64_t)d * a.out_stride;
 #pragma unroll
         for (int k = 0; k < kM; k++) {
@@ -447,7 +498,8 @@ bool plan_dedisperse_tiled(gsp_plan_s *p, std::vector<int32_t> *blkmin) {
 
 cudaError_t launch_dedisperse_tiled(const gsp_plan_s *p, const uint8_t *x, int64_t n_in,
                                     int64_t x_stride, int64_t n_out, int32_t *out,
-                                    int64_t out_stride, cudaStream_t s, int32_t *nlaunch) {
+                                    int64_t out_stride, unsigned long long *bsum,
+                                    cudaStream_t s, int32_t *nlaunch) {
     const DDGeom &g = p->geom;
     const TiledVariant &v = kVariants[g.variant];
     static int configured_smem[kNumVariants] = {0};
@@ -473,6 +525,10 @@ cudaError_t launch_dedisperse_tiled(const gsp_plan_s *p, const uint8_t *x, int64
     a.stages = g.stages;
     a.mulhi = 256u;
     a.err = p->d_err;
+    a.bsum = bsum;
+    a.nb_max = p->nb_max;
+    a.B = p->desc.block_len;
+    a.Ls = (n_out / a.B) * a.B;
     const int64_t ntiles = (n_out + kTEff - 1) / kTEff;
     const int64_t nctas = ntiles * g.nblk;
     if (nctas > 0x7fffffffll) return cudaErrorInvalidConfiguration;

@@ -89,6 +89,7 @@ void free_plan(gsp_plan_s *p) {
     cudaFree(p->d_delays);
     cudaFree(p->d_blkmin);
     cudaFree(p->d_err);
+    cudaFree(p->d_bsum);
     cudaFree(p->d_sigma_b);
     cudaFree(p->d_bad);
     cudaFree(p->d_bparam);
@@ -160,14 +161,21 @@ gsp_status ensure_scratch_D(gsp_plan_s *p, int64_t n_out) {
     return GSP_OK;
 }
 
+// Block sums are fused into the tiled kernel when it can produce them (a
+// tile of 508 samples then touches at most two search blocks).
+bool fused_stats(const gsp_plan_s *p) {
+    return !p->simple_dd && p->d_bsum != nullptr && p->desc.block_len >= p->geom.t_eff;
+}
+
 gsp_status run_dedisperse(gsp_plan_s *p, const uint8_t *x, int64_t n_in, int64_t x_stride,
-                          int64_t n_out, int32_t *out, int64_t out_stride, cudaStream_t s) {
+                          int64_t n_out, int32_t *out, int64_t out_stride,
+                          unsigned long long *bsum, cudaStream_t s) {
     if (fault("launch")) return GSP_ERR_CUDA;
     cudaError_t e;
     if (p->simple_dd)
         e = gsp::launch_dedisperse_simple(p, x, x_stride, n_out, out, out_stride, s, &p->launches);
     else
-        e = gsp::launch_dedisperse_tiled(p, x, n_in, x_stride, n_out, out, out_stride, s,
+        e = gsp::launch_dedisperse_tiled(p, x, n_in, x_stride, n_out, out, out_stride, bsum, s,
                                          &p->launches);
     if (e != cudaSuccess) {
         set_err(e, "dedisperse launch");
@@ -177,9 +185,11 @@ gsp_status run_dedisperse(gsp_plan_s *p, const uint8_t *x, int64_t n_in, int64_t
 }
 
 gsp_status run_search(gsp_plan_s *p, const int32_t *D, int64_t n_out, int64_t stride,
-                      int64_t t_offset, float *snr_out, cudaStream_t s) {
+                      int64_t t_offset, float *snr_out, const unsigned long long *bsum,
+                      cudaStream_t s) {
     if (fault("launch")) return GSP_ERR_CUDA;
-    cudaError_t e = gsp::launch_search(p, D, n_out, stride, t_offset, snr_out, s, &p->launches);
+    cudaError_t e =
+        gsp::launch_search(p, D, n_out, stride, t_offset, snr_out, bsum, s, &p->launches);
     if (e != cudaSuccess) {
         set_err(e, "search launch");
         return GSP_ERR_CUDA;
@@ -247,7 +257,7 @@ gsp_status gsp_plan_create(gsp_plan_t *out, const gsp_plan_desc *d) {
             return GSP_ERR_INVALID_ARG;
         }
     }
-    if (p->widths.back() > d->block_len) {
+    if (p->widths.back() > d->block_len || p->widths.back() > 1024) {
         delete p;
         return GSP_ERR_INVALID_ARG;
     }
@@ -301,6 +311,7 @@ gsp_status gsp_plan_create(gsp_plan_t *out, const gsp_plan_desc *d) {
     if (st == GSP_OK) st = dalloc(&p->d_cands, (size_t)d->max_cands);
     if (st == GSP_OK) st = dalloc(&p->d_ncand, 1);
     if (st == GSP_OK) st = dalloc(&p->d_err, 1);
+    if (st == GSP_OK && !p->simple_dd) st = dalloc(&p->d_bsum, rows_blocks * 3);
     if (st != GSP_OK) {
         free_plan(p);
         return st;
@@ -352,7 +363,7 @@ gsp_status gsp_dedisperse(gsp_plan_t p, const uint8_t *d_x, int64_t n_in, int64_
     cudaStream_t s = (cudaStream_t)stream;
     p->launches = 0;
     if (p->timed) GSP_CK(cudaEventRecord(p->ev[0], s));
-    st = run_dedisperse(p, d_x, n_in, x_stride, n_out, d_out, out_stride, s);
+    st = run_dedisperse(p, d_x, n_in, x_stride, n_out, d_out, out_stride, nullptr, s);
     if (st != GSP_OK) return st;
     if (p->timed) {
         GSP_CK(cudaEventRecord(p->ev[1], s));
@@ -377,11 +388,17 @@ gsp_status gsp_search(gsp_plan_t p, const uint8_t *d_x, int64_t n_in, int64_t x_
         stride = (n_out + 3) & ~(int64_t)3;
     }
     p->launches = 0;
+    unsigned long long *bsum = nullptr;
+    const int64_t nb = n_out / p->desc.block_len;
+    if (fused_stats(p) && nb > 0) {
+        bsum = p->d_bsum;
+        GSP_CK(cudaMemsetAsync(bsum, 0, (size_t)p->desc.ndm * p->nb_max * 3 * sizeof(*bsum), s));
+    }
     if (p->timed) GSP_CK(cudaEventRecord(p->ev[0], s));
-    st = run_dedisperse(p, d_x, n_in, x_stride, n_out, D, stride, s);
+    st = run_dedisperse(p, d_x, n_in, x_stride, n_out, D, stride, bsum, s);
     if (st != GSP_OK) return st;
     if (p->timed) GSP_CK(cudaEventRecord(p->ev[1], s));
-    st = run_search(p, D, n_out, stride, t_offset, nullptr, s);
+    st = run_search(p, D, n_out, stride, t_offset, nullptr, bsum, s);
     if (st != GSP_OK) return st;
     if (p->timed) GSP_CK(cudaEventRecord(p->ev[2], s));
     return GSP_OK;
@@ -397,7 +414,7 @@ gsp_status gsp_search_series(gsp_plan_t p, const int32_t *d_D, int64_t n_out, in
         GSP_CK(cudaEventRecord(p->ev[0], s));
         GSP_CK(cudaEventRecord(p->ev[1], s));
     }
-    gsp_status st = run_search(p, d_D, n_out, stride, t_offset, nullptr, s);
+    gsp_status st = run_search(p, d_D, n_out, stride, t_offset, nullptr, nullptr, s);
     if (st != GSP_OK) return st;
     if (p->timed) GSP_CK(cudaEventRecord(p->ev[2], s));
     return GSP_OK;
@@ -408,7 +425,7 @@ gsp_status gsp_boxcar_snr(gsp_plan_t p, const int32_t *d_D, int64_t n_out, int64
     if (!p || !d_D || !d_snr || n_out <= 0 || stride < n_out) return GSP_ERR_INVALID_ARG;
     if (n_out / p->desc.block_len > p->nb_max) return GSP_ERR_INVALID_ARG;
     p->launches = 0;
-    return run_search(p, d_D, n_out, stride, 0, d_snr, (cudaStream_t)stream);
+    return run_search(p, d_D, n_out, stride, 0, d_snr, nullptr, (cudaStream_t)stream);
 }
 
 gsp_status gsp_search_stats(gsp_plan_t p, double *sigma_b, uint8_t *bad, double *sigma_ref,

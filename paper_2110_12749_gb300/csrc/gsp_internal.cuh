@@ -54,6 +54,7 @@ struct gsp_plan_s {
     int32_t *d_delays = nullptr;     // [ndm][nchan]
     int32_t *d_blkmin = nullptr;     // [nblk][nchan] min delay of each DM block
     int *d_err = nullptr;            // set by a kernel whose bounded wait gave up
+    unsigned long long *d_bsum = nullptr;  // [ndm][nb_max][3] block sums (tiled path)
     double *d_sigma_b = nullptr;     // [ndm][nb_max]
     uint8_t *d_bad = nullptr;        // [ndm][nb_max]
     gsp::BlockParam *d_bparam = nullptr;  // [ndm][nb_max]
@@ -85,12 +86,17 @@ namespace gsp {
 cudaError_t launch_dedisperse_simple(const gsp_plan_s *p, const uint8_t *x, int64_t x_stride,
                                      int64_t n_out, int32_t *out, int64_t out_stride,
                                      cudaStream_t s, int32_t *nlaunch);
+// bsum (optional): int64 [ndm][nb_max][3] exact block sums {S0, S1, S2} over
+// blocks of block_len samples, accumulated atomically (must be zeroed first).
 cudaError_t launch_dedisperse_tiled(const gsp_plan_s *p, const uint8_t *x, int64_t n_in,
                                     int64_t x_stride, int64_t n_out, int32_t *out,
-                                    int64_t out_stride, cudaStream_t s, int32_t *nlaunch);
+                                    int64_t out_stride, unsigned long long *bsum,
+                                    cudaStream_t s, int32_t *nlaunch);
 bool plan_dedisperse_tiled(gsp_plan_s *p, std::vector<int32_t> *blkmin);
 
+// bsum (optional): block sums left by the tiled dedispersion kernel.
 cudaError_t launch_search(gsp_plan_s *p, const int32_t *D, int64_t n_out, int64_t stride,
-                          int64_t t_offset, float *snr_out, cudaStream_t s, int32_t *nlaunch);
+                          int64_t t_offset, float *snr_out, const unsigned long long *bsum,
+                          cudaStream_t s, int32_t *nlaunch);
 
 }  // namespace gsp

@@ -32,6 +32,39 @@ __device__ __forceinline__ long long warp_sum_ll(long long v) {
     return v;
 }
 
+// Closed form of the block's least-squares line from exact integer sums
+// S0 = sum D_j, S1 = sum j D_j, S2 = sum D_j^2 (j = 0..B-1), in exact 128-bit
+// integers U = B S2 - S0^2, V = 2 S1 - (B-1) S0 and
+// N = U (B^2 - 1) - 3 V^2 = B^2 (B^2 - 1) * sigma_b^2, so that
+// sigma_b = sqrt(N / (B^2 (B^2 - 1))) (population RMS of the residual from
+// the line) and beta = 6 V / (B (B^2 - 1)).
+__device__ __forceinline__ void finish_block(long long s0, long long s1, long long s2, int B,
+                                             int64_t idx, double *__restrict__ sigma_b,
+                                             BlockParam *__restrict__ bparam) {
+    const __int128 Bi = B;
+    const __int128 bb1 = Bi * Bi - 1;
+    double sig = 0.0, beta = 0.0;
+    if (B > 1) {
+        const __int128 U = Bi * (__int128)s2 - (__int128)s0 * (__int128)s0;
+        const __int128 V = 2 * (__int128)s1 - (Bi - 1) * (__int128)s0;
+        const __int128 N = U * bb1 - 3 * V * V;
+        const double den = (double)B * (double)B * (double)bb1;
+        sig = N > 0 ? sqrt((double)N / den) : 0.0;
+        beta = 6.0 * (double)V / ((double)B * (double)bb1);
+    }
+    const double mean = (double)s0 / (double)B;
+    const long long m = (long long)floor(mean + 0.5);
+    const double jbar = 0.5 * (double)(B - 1);
+    const double c0 = (double)(s0 - m * (long long)B) / (double)B - beta * jbar;
+    sigma_b[idx] = sig;
+    BlockParam bp;
+    bp.m = (int32_t)m;
+    bp.c0 = (float)c0;
+    bp.beta = (float)beta;
+    bp.good = 1;
+    bparam[idx] = bp;
+}
+
 // Step 1.  One CTA per (block, row).  Exact int64 sums S0 = sum D_j,
 // S1 = sum j D_j, S2 = sum D_j^2 over j = 0..B-1, then in exact 128-bit
 // integers U = B S2 - S0^2, V = 2 S1 - (B-1) S0 and
@@ -69,29 +102,21 @@ __global__ void __launch_bounds__(kStatThreads) block_stats_kernel(
         s1 += red[1][i];
         s2 += red[2][i];
     }
-    const __int128 Bi = B;
-    const __int128 bb1 = Bi * Bi - 1;
-    double sig = 0.0, beta = 0.0;
-    if (B > 1) {
-        const __int128 U = Bi * (__int128)s2 - (__int128)s0 * (__int128)s0;
-        const __int128 V = 2 * (__int128)s1 - (Bi - 1) * (__int128)s0;
-        const __int128 N = U * bb1 - 3 * V * V;
-        const double den = (double)B * (double)B * (double)bb1;
-        sig = N > 0 ? sqrt((double)N / den) : 0.0;
-        beta = 6.0 * (double)V / ((double)B * (double)bb1);
-    }
-    const double mean = (double)s0 / (double)B;
-    const long long m = (long long)floor(mean + 0.5);
-    const double jbar = 0.5 * (double)(B - 1);
-    const double c0 = (double)(s0 - m * (long long)B) / (double)B - beta * jbar;
-    const int64_t idx = (int64_t)row * nb_max + b;
-    sigma_b[idx] = sig;
-    BlockParam bp;
-    bp.m = (int32_t)m;
-    bp.c0 = (float)c0;
-    bp.beta = (float)beta;
-    bp.good = 1;
-    bparam[idx] = bp;
+    finish_block(s0, s1, s2, B, (int64_t)row * nb_max + b, sigma_b, bparam);
+}
+
+// Step 1 when the dedispersion kernel has already accumulated the exact block
+// sums (bsum[row][b] = {S0, S1, S2}): one thread per (row, block).
+__global__ void __launch_bounds__(256) block_params_kernel(
+    const unsigned long long *__restrict__ bsum, int64_t nb, int B, int64_t nb_max, int ndm,
+    double *__restrict__ sigma_b, BlockParam *__restrict__ bparam) {
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= nb * ndm) return;
+    const int row = (int)(g / nb);
+    const int64_t b = g - (int64_t)row * nb;
+    const unsigned long long *q = bsum + ((int64_t)row * nb_max + b) * 3;
+    finish_block((long long)q[0], (long long)q[1], (long long)q[2], B, (int64_t)row * nb_max + b,
+                 sigma_b, bparam);
 }
 
 // Step 2.  One CTA per row: lower median of the nb block sigmas (bitonic sort
@@ -178,7 +203,7 @@ __global__ void __launch_bounds__(kBoxThreads) boxcar_kernel(
     const int32_t *__restrict__ D, int64_t stride, int64_t Ls, int B, int64_t nb_max,
     int64_t t_offset, int64_t win_len, int64_t k0, WidthTable wt,
     const BlockParam *__restrict__ bparam, const float *__restrict__ scale, float threshold,
-    int ndm_total, float *__restrict__ snr_out, gsp_cand *__restrict__ cands,
+    float *__restrict__ snr_out, gsp_cand *__restrict__ cands,
     unsigned long long *__restrict__ ncand, int64_t max_cands) {
     extern __shared__ uint32_t sP[];  // prefix sums, kChunk + wmax entries
     __shared__ uint32_t warp_tot[kBoxThreads / 32];
@@ -191,25 +216,45 @@ __global__ void __launch_bounds__(kBoxThreads) boxcar_kernel(
     if (we > Ls) we = Ls;
     const int32_t *d = D + (int64_t)row * stride;
     const BlockParam *bp = bparam + (int64_t)row * nb_max;
+    const int nb = (int)(Ls / B);
     if (threadIdx.x < wt.n) s_scale[threadIdx.x] = scale[(int64_t)row * wt.n + threadIdx.x];
     __syncthreads();
     const bool live = s_scale[0] != 0.0f;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     Best run{-FLT_MAX, 0, 0};
     bool have = false;
+    constexpr int kPer = (kChunk + 1024 + kBoxThreads - 1) / kBoxThreads;  // <= 8 samples/thread
 
     for (int64_t s = ws; s < we; s += kChunk) {
         const int64_t e = min(s + (int64_t)kChunk, we);
         const int64_t pe = min(e + (int64_t)wt.wmax - 1, Ls);  // prefix covers [s, pe)
         const int len = (int)(pe - s);
-        // per-thread consecutive segment of the scan
+        const int64_t b_s = s / B;                 // block of the sub-chunk's first sample
+        const int j_s = (int)(s - b_s * B);        // its index inside that block
+        // integer series y = D - m_b (0 in bad blocks), per-thread consecutive segment
         const int per = (len + kBoxThreads - 1) / kBoxThreads;
         const int i0 = threadIdx.x * per;
+        uint32_t y[kPer];
         uint32_t loc = 0;
-        for (int i = i0; i < min(i0 + per, len); i++) {
-            const int64_t t = s + i;
-            const BlockParam q = bp[t / B];
-            loc += q.good ? (uint32_t)(d[t] - q.m) : 0u;
+        {
+            const int rel = j_s + i0;
+            int b = (int)b_s + rel / B;
+            int j = rel - (b - (int)b_s) * B;
+            BlockParam q = bp[min(b, nb - 1)];
+#pragma unroll
+            for (int r = 0; r < kPer; r++) {
+                y[r] = 0;
+                if (r < per && i0 + r < len) {
+                    if (j == B) {
+                        b++;
+                        j = 0;
+                        q = bp[b];
+                    }
+                    y[r] = q.good ? (uint32_t)(d[s + i0 + r] - q.m) : 0u;
+                    loc += y[r];
+                    j++;
+                }
+            }
         }
         // block exclusive scan of the per-thread totals
         uint32_t incl = loc;
@@ -220,68 +265,83 @@ __global__ void __launch_bounds__(kBoxThreads) boxcar_kernel(
         }
         if (lane == 31) warp_tot[wid] = incl;
         __syncthreads();
-        uint32_t wpre = 0;
-        for (int q = 0; q < wid; q++) wpre += warp_tot[q];
-        uint32_t run_p = wpre + incl - loc;
-        for (int i = i0; i < min(i0 + per, len); i++) {
-            sP[i] = run_p;
-            const int64_t t = s + i;
-            const BlockParam q = bp[t / B];
-            run_p += q.good ? (uint32_t)(d[t] - q.m) : 0u;
+        uint32_t run_p = incl - loc;
+        for (int q = 0; q < wid; q++) run_p += warp_tot[q];
+#pragma unroll
+        for (int r = 0; r < kPer; r++) {
+            if (r < per && i0 + r < len) {
+                sP[i0 + r] = run_p;
+                run_p += y[r];
+            }
         }
-        if (threadIdx.x == kBoxThreads - 1) sP[len] = run_p;  // total (exclusive end)
+        if (threadIdx.x == kBoxThreads - 1) sP[len] = run_p;  // running total at pe
         __syncthreads();
 
-        Best mine{-FLT_MAX, 0, 0};
-        bool mine_ok = false;
-        for (int64_t t = s + threadIdx.x; t < e; t += kBoxThreads) {
-            const int i = (int)(t - s);
-            const int64_t b = t / B;
-            const int j1 = (int)(t - b * B);
+        Best mine{-FLT_MAX, INT64_MAX, 0};
+        for (int i = threadIdx.x; i < (int)(e - s); i += kBoxThreads) {
+            const int64_t t = s + i;
+            const int rel = j_s + i;
+            const int bo = rel / B;                 // block offset from b_s
+            const int j1 = rel - bo * B;
+            const int b = (int)b_s + bo;
             const BlockParam q = bp[b];
-            const int rem = B - j1;  // samples left in block b
-            BlockParam q2 = q;
-            if (b + 1 < Ls / B) q2 = bp[b + 1];
+            const int rem = B - j1;                 // samples left in block b
             const float g = q.good ? q.c0 + q.beta * (float)j1 : 0.0f;
             const float beta1 = q.good ? q.beta : 0.0f;
-            const float c02 = q2.good ? q2.c0 : 0.0f;
-            const float beta2 = q2.good ? q2.beta : 0.0f;
             const uint32_t p0 = sP[i];
             float bsnr = -FLT_MAX;
             int bw = 0;
-            for (int iw = 0; iw < wt.n; iw++) {
-                const int w = wt.w[iw];
-                float v;
-                if (t + w > Ls) {
-                    v = __int_as_float(0x7fc00000);  // NaN
-                } else {
-                    const int32_t Y = (int32_t)(sP[i + w] - p0);
-                    float cr;
-                    if (w <= rem) {
-                        cr = (float)w * g + beta1 * wt.tri[iw];
-                    } else {
-                        const int n1 = rem, n2 = w - rem;
-                        cr = (float)n1 * g + beta1 * (0.5f * (float)n1 * (float)(n1 - 1)) +
-                             (float)n2 * c02 + beta2 * (0.5f * (float)n2 * (float)(n2 - 1));
-                    }
-                    v = ((float)Y - cr) * s_scale[iw];
-                    if (v > bsnr) {
-                        bsnr = v;
-                        bw = w;
+            if (t + wt.wmax <= Ls && wt.wmax <= rem) {
+                // every boxcar inside block b: no bounds or straddle checks
+#pragma unroll
+                for (int iw = 0; iw < kMaxWidths; iw++) {
+                    if (iw < wt.n) {
+                        const int w = wt.w[iw];
+                        const int32_t Y = (int32_t)(sP[i + w] - p0);
+                        const float cr = (float)w * g + beta1 * wt.tri[iw];
+                        const float v = ((float)Y - cr) * s_scale[iw];
+                        if (kWriteSnr) snr_out[((int64_t)row * wt.n + iw) * Ls + t] = v;
+                        if (v > bsnr) {
+                            bsnr = v;
+                            bw = w;
+                        }
                     }
                 }
-                if (kWriteSnr) snr_out[((int64_t)row * wt.n + iw) * Ls + t] = v;
+            } else {
+                BlockParam q2 = q;
+                if (b + 1 < nb) q2 = bp[b + 1];
+                const float c02 = q2.good ? q2.c0 : 0.0f;
+                const float beta2 = q2.good ? q2.beta : 0.0f;
+                for (int iw = 0; iw < wt.n; iw++) {
+                    const int w = wt.w[iw];
+                    float v;
+                    if (t + w > Ls) {
+                        v = __int_as_float(0x7fc00000);  // NaN: boxcar runs past the last block
+                    } else {
+                        const int32_t Y = (int32_t)(sP[i + w] - p0);
+                        float cr;
+                        if (w <= rem) {
+                            cr = (float)w * g + beta1 * wt.tri[iw];
+                        } else {
+                            const int n1 = rem, n2 = w - rem;
+                            cr = (float)n1 * g + beta1 * (0.5f * (float)n1 * (float)(n1 - 1)) +
+                                 (float)n2 * c02 + beta2 * (0.5f * (float)n2 * (float)(n2 - 1));
+                        }
+                        v = ((float)Y - cr) * s_scale[iw];
+                        if (v > bsnr) {
+                            bsnr = v;
+                            bw = w;
+                        }
+                    }
+                    if (kWriteSnr) snr_out[((int64_t)row * wt.n + iw) * Ls + t] = v;
+                }
             }
             if (live && bw > 0 && bsnr >= threshold) {
-                Best c{bsnr, t, bw};
-                if (!mine_ok || better(c, mine)) {
-                    mine = c;
-                    mine_ok = true;
-                }
+                const Best c{bsnr, t, bw};
+                if (better(c, mine)) mine = c;
             }
         }
         // block argmax (S/N desc, t asc)
-        if (!mine_ok) mine = Best{-FLT_MAX, INT64_MAX, 0};
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             Best other;
@@ -315,13 +375,13 @@ __global__ void __launch_bounds__(kBoxThreads) boxcar_kernel(
             cands[idx] = c;
         }
     }
-    (void)ndm_total;
 }
 
 }  // namespace
 
 cudaError_t launch_search(gsp_plan_s *p, const int32_t *D, int64_t n_out, int64_t stride,
-                          int64_t t_offset, float *snr_out, cudaStream_t s, int32_t *nlaunch) {
+                          int64_t t_offset, float *snr_out, const unsigned long long *bsum,
+                          cudaStream_t s, int32_t *nlaunch) {
     const int B = p->desc.block_len;
     const int64_t nb = n_out / B;
     const int64_t Ls = nb * B;
@@ -337,8 +397,14 @@ cudaError_t launch_search(gsp_plan_s *p, const int32_t *D, int64_t n_out, int64_
         wt.tri[i] = 0.5f * (float)p->widths[i] * (float)(p->widths[i] - 1);
         wt.wmax = max(wt.wmax, p->widths[i]);
     }
-    block_stats_kernel<<<dim3((unsigned)nb, (unsigned)ndm), kStatThreads, 0, s>>>(
-        D, stride, B, p->nb_max, p->d_sigma_b, p->d_bparam);
+    if (bsum) {
+        const int64_t n = nb * ndm;
+        block_params_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(
+            bsum, nb, B, p->nb_max, ndm, p->d_sigma_b, p->d_bparam);
+    } else {
+        block_stats_kernel<<<dim3((unsigned)nb, (unsigned)ndm), kStatThreads, 0, s>>>(
+            D, stride, B, p->nb_max, p->d_sigma_b, p->d_bparam);
+    }
     *nlaunch += 1;
     int n2 = 1;
     while (n2 < nb) n2 <<= 1;
@@ -356,11 +422,11 @@ cudaError_t launch_search(gsp_plan_s *p, const int32_t *D, int64_t n_out, int64_
     if (snr_out)
         boxcar_kernel<true><<<grid, kBoxThreads, sm_box, s>>>(
             D, stride, Ls, B, p->nb_max, t_offset, L, k0, wt, p->d_bparam, p->d_scale,
-            p->desc.threshold, ndm, snr_out, p->d_cands, p->d_ncand, p->desc.max_cands);
+            p->desc.threshold, snr_out, p->d_cands, p->d_ncand, p->desc.max_cands);
     else
         boxcar_kernel<false><<<grid, kBoxThreads, sm_box, s>>>(
             D, stride, Ls, B, p->nb_max, t_offset, L, k0, wt, p->d_bparam, p->d_scale,
-            p->desc.threshold, ndm, snr_out, p->d_cands, p->d_ncand, p->desc.max_cands);
+            p->desc.threshold, snr_out, p->d_cands, p->d_ncand, p->desc.max_cands);
     *nlaunch += 1;
     return cudaGetLastError();
 }

@@ -102,12 +102,15 @@ def test_tiny_fused_search_equals_series_search(gsp, orc, tiny):
     wl, dl, x, n_out, pulses, Dref = tiny
     plan = _plan(gsp, dl, wl.n_in)
     xd = torch.from_numpy(x).cuda()
-    gsp.gsp_search(plan, xd, wl.n_in)                  # D into plan scratch
+    gsp.gsp_search(plan, xd, wl.n_in)                  # D into plan scratch, fused block sums
     c1, n1, _ = gsp.gsp_candidates(plan)
+    st1 = gsp.gsp_search_stats(plan, n_out)
     Dd = torch.from_numpy(Dref.astype(np.int32)).cuda()
-    gsp.gsp_search_series(plan, Dd, n_out)
+    gsp.gsp_search_series(plan, Dd, n_out)              # block sums from the series
     c2, n2, _ = gsp.gsp_candidates(plan)
+    st2 = gsp.gsp_search_stats(plan, n_out)
     assert n1 == n2 and (c1 == c2).all()
+    assert (st1["sigma_b"] == st2["sigma_b"]).all() and (st1["sigma_ref"] == st2["sigma_ref"]).all()
     c3, n3, _ = gsp.gsp_search_host(plan, x, wl.n_in)  # host input path
     assert n3 == n1 and (c3 == c1).all()
 
