@@ -74,6 +74,14 @@ __device__ __forceinline__ uint2 lds64(uint32_t addr) {
     return v;
 }
 
+// a * b + c (low 32 bits) on the integer multiply-add pipe; with b = 1 held in
+// a register this is an addition that does not use the integer ALU pipe.
+__device__ __forceinline__ uint32_t imadd(uint32_t a, uint32_t b, uint32_t c) {
+    uint32_t d;
+    asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+    return d;
+}
+
 // (a * b) >> 32 + c on the integer multiply-add pipe.
 __device__ __forceinline__ uint32_t mad_hi(uint32_t a, uint32_t b, uint32_t c) {
     uint32_t d;

@@ -15,13 +15,12 @@
 // each phase accumulates into its own registers and the byte shift is
 // resolved once per 256 channels, not per add.
 //
-// Accumulation (exact, SWAR): per word three 32-bit views are summed over
-// channels: S = sum w (raw), E = sum (w & 0x00ff00ff) (bytes 0 and 2 in
-// 16-bit lanes), H = sum (w >> 24) (byte 3, on the multiply-add pipe).  Then
-//   b0 = E & 0xffff, b2 = E >> 16, b3 = H, b1 = ((S - E - (H << 24)) mod 2^32) >> 8
-// are the exact per-byte sums as long as a 16-bit lane of E holds at most
-// 256 * 255 < 2^16, i.e. every 256 channels the views are flushed into int32
-// accumulators.
+// Accumulation (exact, SWAR): per word two 32-bit views are summed over
+// channels, E = sum (w & 0x00ff00ff) (bytes 0 and 2 in 16-bit lanes) and
+// O = sum of bytes 1 and 3 placed in 16-bit lanes by one byte permute.  A
+// 16-bit lane holds at most 256 * 255 < 2^16, so every 256 channels the views
+// are flushed into int32 accumulators: b0 = E & 0xffff, b2 = E >> 16,
+// b1 = O & 0xffff, b3 = O >> 16.
 #include <algorithm>
 #include <cstdlib>
 #include <vector>
@@ -107,7 +106,7 @@ struct TiledArgs {
     int nblk;
     int win;       // bytes per channel window (multiple of 16)
     int stages;    // ring depth
-    uint32_t mulhi;  // 256, passed at run time so that the multiply stays a multiply
+    uint32_t one;  // 1, passed at run time so that x * one + acc stays on the multiply-add pipe
     int *err;      // set to 1 if a bounded wait gave up
     unsigned long long *bsum;  // optional [ndm][nb_max][3] block sums {S0, S1, S2}
     int64_t nb_max;
@@ -123,9 +122,31 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
 
 __device__ __forceinline__ void fail(int *err) { atomicExch(err, 1); }
 
+// Accumulate two words of one phase into the even-byte view E (bytes 0 and 2
+// in 16-bit lanes) and the odd-byte view O (bytes 1 and 3).  ACC chooses the
+// pipe of the additions: 0 = IADD3 on the integer ALU, 1 = E on the ALU and
+// O as x * 1 + acc on the multiply-add pipe, 2 = both on the multiply-add
+// pipe.  The byte extraction (LOP3, PRMT) always runs on the ALU.
+template <int ACC>
+__device__ __forceinline__ void acc_pair(uint32_t &E, uint32_t &O, uint32_t w1, uint32_t w2,
+                                         uint32_t one) {
+    const uint32_t e1 = w1 & 0x00ff00ffu, e2 = w2 & 0x00ff00ffu;
+    const uint32_t o1 = __byte_perm(w1, 0, 0x4341), o2 = __byte_perm(w2, 0, 0x4341);
+    if (ACC == 0) {
+        E += e1 + e2;
+        O += o1 + o2;
+    } else if (ACC == 1) {
+        E += e1 + e2;
+        O = ptx::imadd(o1, one, ptx::imadd(o2, one, O));
+    } else {
+        E = ptx::imadd(e1, one, ptx::imadd(e2, one, E));
+        O = ptx::imadd(o1, one, ptx::imadd(o2, one, O));
+    }
+}
+
 // KW: DM trials per consumer warp; kCW = kKDM / KW consumer warps + 1 producer.
 // QUAD: visit channels four at a time (more loads in flight per warp).
-template <int KW, bool QUAD>
+template <int KW, bool QUAD, int ACC>
 __global__ void __launch_bounds__((kKDM / KW + 1) * 32, 1) dd_tiled_kernel(const TiledArgs a) {
     constexpr int kKW = KW;
     constexpr int kCW = kKDM / KW;
@@ -208,7 +229,7 @@ __global__ void __launch_bounds__((kKDM / KW + 1) * 32, 1) dd_tiled_kernel(const
     const int dmw = dm0 + warp * kKW;
     int32_t *mylist = lists + warp * (kKW * 4 * 32);
     uint32_t acc[kKW][kM][4];
-    uint32_t S[kKW][4][kM], E[kKW][4][kM], H[kKW][4][kM];
+    uint32_t E[kKW][4][kM], O[kKW][4][kM];
 #pragma unroll
     for (int i = 0; i < kKW; i++)
 #pragma unroll
@@ -216,9 +237,9 @@ __global__ void __launch_bounds__((kKDM / KW + 1) * 32, 1) dd_tiled_kernel(const
 #pragma unroll
             for (int j = 0; j < 4; j++) acc[i][k][j] = 0;
 #pragma unroll
-            for (int p = 0; p < 4; p++) S[i][p][k] = E[i][p][k] = H[i][p][k] = 0;
+            for (int p = 0; p < 4; p++) E[i][p][k] = O[i][p][k] = 0;
         }
-    const uint32_t mul = a.mulhi;
+    const uint32_t one = a.one;
     const uint32_t lmask = lanemask_lt();
     // delays of the next stage are loaded one stage ahead (hides L2 latency)
     int nx_min = 0, nx_dl[kKW];
@@ -287,12 +308,8 @@ __global__ void __launch_bounds__((kKDM / KW + 1) * 32, 1) dd_tiled_kernel(const
                         for (int k = 0; k < kM; k++) {
                             const uint32_t w1 = p1[32 * k], w2 = p2[32 * k];
                             const uint32_t w3 = p3[32 * k], w4 = p4[32 * k];
-                            S[i][P][k] += w1 + w2;
-                            S[i][P][k] += w3 + w4;
-                            E[i][P][k] += (w1 & 0x00ff00ffu) + (w2 & 0x00ff00ffu);
-                            E[i][P][k] += (w3 & 0x00ff00ffu) + (w4 & 0x00ff00ffu);
-                            H[i][P][k] = ptx::mad_hi(w1, mul, ptx::mad_hi(w2, mul, H[i][P][k]));
-                            H[i][P][k] = ptx::mad_hi(w3, mul, ptx::mad_hi(w4, mul, H[i][P][k]));
+                            acc_pair<ACC>(E[i][P][k], O[i][P][k], w1, w2, one);
+                            acc_pair<ACC>(E[i][P][k], O[i][P][k], w3, w4, one);
                         }
                     }
                 }
@@ -303,9 +320,7 @@ __global__ void __launch_bounds__((kKDM / KW + 1) * 32, 1) dd_tiled_kernel(const
 #pragma unroll
                     for (int k = 0; k < kM; k++) {
                         const uint32_t w1 = p1[32 * k], w2 = p2[32 * k];
-                        S[i][P][k] += w1 + w2;
-                        E[i][P][k] += (w1 & 0x00ff00ffu) + (w2 & 0x00ff00ffu);
-                        H[i][P][k] = ptx::mad_hi(w1, mul, ptx::mad_hi(w2, mul, H[i][P][k]));
+                        acc_pair<ACC>(E[i][P][k], O[i][P][k], w1, w2, one);
                     }
                 }
                 if (j < n) {
@@ -313,9 +328,8 @@ __global__ void __launch_bounds__((kKDM / KW + 1) * 32, 1) dd_tiled_kernel(const
 #pragma unroll
                     for (int k = 0; k < kM; k++) {
                         const uint32_t w1 = p1[32 * k];
-                        S[i][P][k] += w1;
                         E[i][P][k] += w1 & 0x00ff00ffu;
-                        H[i][P][k] = ptx::mad_hi(w1, mul, H[i][P][k]);
+                        O[i][P][k] += __byte_perm(w1, 0, 0x4341);
                     }
                 }
             }
@@ -332,19 +346,19 @@ __global__ void __launch_bounds__((kKDM / KW + 1) * 32, 1) dd_tiled_kernel(const
                     sp[k][0] = sp[k][1] = sp[k][2] = 0;
 #pragma unroll
                     for (int P = 0; P < 4; P++) {
-                        const uint32_t e = E[i][P][k], h = H[i][P][k];
+                        const uint32_t e = E[i][P][k], o = O[i][P][k];
                         uint32_t b[4];
                         b[0] = e & 0xffffu;
+                        b[1] = o & 0xffffu;
                         b[2] = e >> 16;
-                        b[3] = h;
-                        b[1] = (S[i][P][k] - e - (h << 24)) >> 8;
+                        b[3] = o >> 16;
 #pragma unroll
                         for (int q = 0; q < 4; q++) {
                             const int jj = q - P;  // output slot, negative = previous word
                             if (jj >= 0) acc[i][k][jj] += b[q];
                             else sp[k][jj + 3] += b[q];
                         }
-                        S[i][P][k] = E[i][P][k] = H[i][P][k] = 0;
+                        E[i][P][k] = O[i][P][k] = 0;
                     }
                 }
                 // previous word of (lane, k) is (lane - 1, k), or (31, k - 1) for lane 0
@@ -443,10 +457,12 @@ struct TiledVariant {
 
 // Tuning variants of the tiled kernel (same result, different schedule).
 const TiledVariant kVariants[] = {
-    {dd_tiled_kernel<2, false>, 2},
-    {dd_tiled_kernel<1, false>, 1},
-    {dd_tiled_kernel<2, true>, 2},
-    {dd_tiled_kernel<1, true>, 1},
+    {dd_tiled_kernel<2, false, 0>, 2},
+    {dd_tiled_kernel<1, false, 0>, 1},
+    {dd_tiled_kernel<1, false, 1>, 1},
+    {dd_tiled_kernel<1, false, 2>, 1},
+    {dd_tiled_kernel<2, false, 1>, 2},
+    {dd_tiled_kernel<1, true, 1>, 1},
 };
 constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
 constexpr int kDefaultVariant = 1;
@@ -523,7 +539,7 @@ cudaError_t launch_dedisperse_tiled(const gsp_plan_s *p, const uint8_t *x, int64
     a.nblk = g.nblk;
     a.win = g.win;
     a.stages = g.stages;
-    a.mulhi = 256u;
+    a.one = 1u;
     a.err = p->d_err;
     a.bsum = bsum;
     a.nb_max = p->nb_max;
