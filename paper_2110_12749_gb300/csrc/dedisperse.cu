@@ -146,7 +146,7 @@ __device__ __forceinline__ void acc_pair(uint32_t &E, uint32_t &O, uint32_t w1, 
 
 // KW: DM trials per consumer warp; kCW = kKDM / KW consumer warps + 1 producer.
 // QUAD: visit channels four at a time (more loads in flight per warp).
-template <int KW, bool QUAD, int ACC>
+template <int KW, bool QUAD, int ACC, bool A32 = false>
 __global__ void __launch_bounds__((kKDM / KW + 1) * 32, 1) dd_tiled_kernel(const TiledArgs a) {
     constexpr int kKW = KW;
     constexpr int kCW = kKDM / KW;
@@ -241,6 +241,8 @@ __global__ void __launch_bounds__((kKDM / KW + 1) * 32, 1) dd_tiled_kernel(const
         }
     const uint32_t one = a.one;
     const uint32_t lmask = lanemask_lt();
+    const uint32_t smem32 = ptx::smem_addr(smem);
+    const uint32_t lane4 = 4u * lane;
     // delays of the next stage are loaded one stage ahead (hides L2 latency)
     int nx_min = 0, nx_dl[kKW];
     {
@@ -274,8 +276,10 @@ __global__ void __launch_bounds__((kKDM / KW + 1) * 32, 1) dd_tiled_kernel(const
             const int dl = valid ? cur_dl[i] : 0;
             const int q = (int)(t0 + dl - s_c);
             const int p = q & 3;
-            // word index of the aligned word of this (channel, DM) in shared memory
-            const int entry = (slot * slot_bytes + lane * a.win + (q & ~3)) >> 2;
+            // the aligned word of this (channel, DM) in shared memory: its word
+            // index, or (A32) its 32-bit shared-window byte address
+            const int boff = slot * slot_bytes + lane * a.win + (q & ~3);
+            const int entry = A32 ? (int)(smem32 + boff) : (boff >> 2);
 #pragma unroll
             for (int P = 0; P < 4; P++) {
                 const uint32_t m = __ballot_sync(0xffffffffu, valid && p == P);
@@ -290,6 +294,38 @@ __global__ void __launch_bounds__((kKDM / KW + 1) * 32, 1) dd_tiled_kernel(const
             return;
         }
         const uint32_t *lanebase = reinterpret_cast<const uint32_t *>(smem) + lane;
+        if (A32) {
+            // explicit 32-bit shared addresses, immediate offsets per word
+#pragma unroll
+            for (int i = 0; i < kKW; i++) {
+#pragma unroll
+                for (int P = 0; P < 4; P++) {
+                    const int n = cnt[i][P];
+                    const int32_t *lp = mylist + (i * 4 + P) * 32;
+                    int j = 0;
+#pragma unroll 2
+                    for (; j + 2 <= n; j += 2) {
+                        const int2 e = *reinterpret_cast<const int2 *>(lp + j);
+                        const uint32_t a1 = (uint32_t)e.x + lane4, a2 = (uint32_t)e.y + lane4;
+                        uint32_t w1[kM], w2[kM];
+                        ptx::lds_words<kM>(a1, w1);
+                        ptx::lds_words<kM>(a2, w2);
+#pragma unroll
+                        for (int k = 0; k < kM; k++) acc_pair<ACC>(E[i][P][k], O[i][P][k], w1[k], w2[k], one);
+                    }
+                    if (j < n) {
+                        uint32_t w1[kM];
+                        ptx::lds_words<kM>((uint32_t)lp[j] + lane4, w1);
+#pragma unroll
+                        for (int k = 0; k < kM; k++) {
+                            E[i][P][k] += w1[k] & 0x00ff00ffu;
+                            O[i][P][k] += __byte_perm(w1[k], 0, 0x4341);
+                        }
+                    }
+                }
+            }
+        } else
+
 #pragma unroll
         for (int i = 0; i < kKW; i++) {
 #pragma unroll
@@ -463,9 +499,10 @@ const TiledVariant kVariants[] = {
     {dd_tiled_kernel<1, false, 2>, 1},
     {dd_tiled_kernel<2, false, 1>, 2},
     {dd_tiled_kernel<1, true, 1>, 1},
+    {dd_tiled_kernel<1, false, 2, true>, 1},
 };
 constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
-constexpr int kDefaultVariant = 1;
+constexpr int kDefaultVariant = 3;
 
 }  // namespace
 
