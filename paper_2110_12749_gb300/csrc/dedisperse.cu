@@ -84,10 +84,7 @@ cudaError_t launch_dedisperse_simple(const gsp_plan_s *p, const uint8_t *x, int6
 // Tiled kernel.
 namespace {
 
-constexpr int kM = 4;            // words per lane: T = 128 * kM output samples per warp pass
 constexpr int kCB = 32;          // channels per stage
-constexpr int kT = 128 * kM;     // samples computed per tile
-constexpr int kTEff = kT - 4;    // samples stored per tile (the last word is incomplete)
 constexpr int kKDM = 16;         // DM trials per CTA (= consumer warps x DM trials per warp)
 constexpr int kFlushStages = 256 / kCB;  // stages between SWAR flushes (256 channels)
 constexpr long long kWaitBudget = 4000000000ll;  // ~2 s of SM clock per wait
@@ -111,7 +108,7 @@ struct TiledArgs {
     unsigned long long *bsum;  // optional [ndm][nb_max][3] block sums {S0, S1, S2}
     int64_t nb_max;
     int64_t Ls;    // searched length: block_len * floor(n_out / block_len)
-    int B;         // block_len (>= kTEff, so a tile touches at most two blocks)
+    int B;         // block_len (>= stored tile length, so a tile touches at most two blocks)
 };
 
 __device__ __forceinline__ uint32_t lanemask_lt() {
@@ -146,8 +143,13 @@ __device__ __forceinline__ void acc_pair(uint32_t &E, uint32_t &O, uint32_t w1, 
 
 // KW: DM trials per consumer warp; kCW = kKDM / KW consumer warps + 1 producer.
 // QUAD: visit channels four at a time (more loads in flight per warp).
-template <int KW, bool QUAD, int ACC, bool A32 = false>
+// M: 4-sample words per lane, T = 128 M output samples computed per tile and
+// T - 4 stored (the tile's last word is incomplete by construction).
+template <int KW, bool QUAD, int ACC, bool A32 = false, int M = 4>
 __global__ void __launch_bounds__((kKDM / KW + 1) * 32, 1) dd_tiled_kernel(const TiledArgs a) {
+    constexpr int kM = M;
+    constexpr int kT = 128 * kM;
+    constexpr int kTEff = kT - 4;
     constexpr int kKW = KW;
     constexpr int kCW = kKDM / KW;
     extern __shared__ __align__(128) uint8_t smem[];
@@ -489,17 +491,19 @@ typedef void (*TiledKernel)(const TiledArgs);
 struct TiledVariant {
     TiledKernel fn;
     int kw;
+    int m;
 };
 
 // Tuning variants of the tiled kernel (same result, different schedule).
 const TiledVariant kVariants[] = {
-    {dd_tiled_kernel<2, false, 0>, 2},
-    {dd_tiled_kernel<1, false, 0>, 1},
-    {dd_tiled_kernel<1, false, 1>, 1},
-    {dd_tiled_kernel<1, false, 2>, 1},
-    {dd_tiled_kernel<2, false, 1>, 2},
-    {dd_tiled_kernel<1, true, 1>, 1},
-    {dd_tiled_kernel<1, false, 2, true>, 1},
+    {dd_tiled_kernel<2, false, 0>, 2, 4},
+    {dd_tiled_kernel<1, false, 0>, 1, 4},
+    {dd_tiled_kernel<1, false, 1>, 1, 4},
+    {dd_tiled_kernel<1, false, 2>, 1, 4},
+    {dd_tiled_kernel<2, false, 1>, 2, 4},
+    {dd_tiled_kernel<1, true, 1>, 1, 4},
+    {dd_tiled_kernel<1, false, 2, true>, 1, 4},
+    {dd_tiled_kernel<1, false, 2, true, 8>, 1, 8},
 };
 constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
 constexpr int kDefaultVariant = 3;
@@ -523,6 +527,14 @@ bool plan_dedisperse_tiled(gsp_plan_s *p, std::vector<int32_t> *blkmin) {
             spread = std::max<int64_t>(spread, (int64_t)hi - lo);
         }
     }
+    // GSP_DD_VARIANT selects a tuning variant of the tiled kernel.
+    int variant = kDefaultVariant;
+    if (const char *v = std::getenv("GSP_DD_VARIANT")) {
+        const int k = std::atoi(v);
+        if (k >= 0 && k < kNumVariants) variant = k;
+    }
+    const int kT = 128 * kVariants[variant].m;
+    const int kTEff = kT - 4;
     const int64_t win = (kT + 15 + spread + 15) & ~(int64_t)15;
     const int64_t fixed = (int64_t)kKDM * 4 * 32 * 4 + 2 * 8 * 8;
     const int64_t budget = 227 * 1024 - fixed;
@@ -540,12 +552,7 @@ bool plan_dedisperse_tiled(gsp_plan_s *p, std::vector<int32_t> *blkmin) {
     g.stages = (int)stages;
     g.smem = (int)(stages * kCB * win + fixed);
     g.nblk = nblk;
-    // GSP_DD_VARIANT selects a tuning variant of the tiled kernel (default 0).
-    g.variant = kDefaultVariant;
-    if (const char *v = std::getenv("GSP_DD_VARIANT")) {
-        const int k = std::atoi(v);
-        if (k >= 0 && k < kNumVariants) g.variant = k;
-    }
+    g.variant = variant;
     return true;
 }
 
@@ -582,7 +589,7 @@ cudaError_t launch_dedisperse_tiled(const gsp_plan_s *p, const uint8_t *x, int64
     a.nb_max = p->nb_max;
     a.B = p->desc.block_len;
     a.Ls = (n_out / a.B) * a.B;
-    const int64_t ntiles = (n_out + kTEff - 1) / kTEff;
+    const int64_t ntiles = (n_out + g.t_eff - 1) / g.t_eff;
     const int64_t nctas = ntiles * g.nblk;
     if (nctas > 0x7fffffffll) return cudaErrorInvalidConfiguration;
     v.fn<<<(unsigned)nctas, (kKDM / v.kw + 1) * 32, g.smem, s>>>(a);

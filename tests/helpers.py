@@ -32,14 +32,20 @@ def window_contenders(detail, L, t_offset, thr):
     if detail["sigma_ref"] == 0 or Ls == 0:
         return out
     s = np.where(np.isnan(snr), -np.inf, snr)
-    win = (np.arange(Ls) + t_offset) // L
-    for k in np.unique(win):
-        v = s[:, win == k].ravel()
+    k_first = (0 + t_offset) // L
+    k_last = (Ls - 1 + t_offset) // L
+    for k in range(k_first, k_last + 1):
+        a = max(k * L - t_offset, 0)
+        b = min((k + 1) * L - t_offset, Ls)
+        v = s[:, a:b].ravel()
         v = v[v >= thr - THR_BAND]
         if v.size == 0:
             continue
-        v = np.sort(v)[::-1]
-        out[int(k)] = (float(v[0]), float(v[1]) if v.size > 1 else -math.inf)
+        if v.size > 1:
+            top = np.partition(v, v.size - 2)[-2:]
+            out[int(k)] = (float(top[1]), float(top[0]))
+        else:
+            out[int(k)] = (float(v[0]), -math.inf)
     return out
 
 
