@@ -51,7 +51,8 @@ typedef enum {
     GSP_ERR_TIMEOUT = 6,     /* a bounded wait gave up */
     GSP_ERR_TIE = 7,         /* a delay lies within 1e-9 of a rounding tie */
     GSP_ERR_ALIGN = 8,       /* pointer or stride violates a stated alignment */
-    GSP_ERR_STATE = 9        /* call out of order (e.g. no search yet) */
+    GSP_ERR_STATE = 9,       /* call out of order (e.g. no search yet) */
+    GSP_ERR_TOO_LARGE = 10   /* sizes exceed the static scratch of gsp_search_series_static */
 } gsp_status;
 
 /* Plan flags (gsp_plan_desc.flags). */
@@ -193,6 +194,35 @@ gsp_status gsp_plan_timing(gsp_plan_t plan, float *ms_dedisperse, float *ms_sear
 
 /* Kernel launches the last gsp_search / gsp_dedisperse call made. */
 int32_t gsp_plan_launches(gsp_plan_t plan);
+
+/* Search of caller-provided dedispersed series that allocates nothing: for
+ * callers that may not call cudaMalloc (for instance a real-time ingest loop
+ * whose latency budget a device allocation would break, or an application
+ * that owns all device memory through its own pool).  The paper has no
+ * counterpart; this is a deployment variant of gsp_search_series.
+ *   d_D       device int32 [ndm][stride], n_out samples per row (input);
+ *   t_offset  absolute sample index of D[.][0] (windows are absolute);
+ *   widths    host array of nwidths ascending widths (NULL: the default 13);
+ *   block_len, window_len, threshold, bad_lo, bad_hi: as in gsp_plan_desc;
+ *   d_cands   device gsp_cand [max_cands] (output, unsorted, at most one per
+ *             (DM row, window));
+ *   d_ncand   device uint64 (output): the true number of candidates; records
+ *             beyond max_cands are dropped.
+ * Working memory is one static device array inside the library, about 7 MB on
+ * every GPU that loads it, which limits a call to ndm <= 4096 rows and
+ * ndm * floor(n_out / block_len) <= 2^18 search blocks; larger calls return
+ * GSP_ERR_TOO_LARGE.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress), so make that first call before any stream
+ * capture.  All calls share the array: calls whose kernels overlap on the GPU
+ * race on it, calls queued one after another on one stream do not.  No
+ * cudaMalloc, cudaFree or allocating library routine is called.  Asynchronous
+ * on stream. */
+gsp_status gsp_search_series_static(const int32_t *d_D, int32_t ndm, int64_t n_out,
+                                    int64_t stride, int64_t t_offset, const int32_t *widths,
+                                    int32_t nwidths, int32_t block_len, int32_t window_len,
+                                    float threshold, float bad_lo, float bad_hi,
+                                    gsp_cand *d_cands, int64_t max_cands,
+                                    unsigned long long *d_ncand, void *stream);
 
 /* Static text for a status code. */
 const char *gsp_status_string(gsp_status s);

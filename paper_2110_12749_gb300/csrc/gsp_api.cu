@@ -526,6 +526,7 @@ const char *gsp_status_string(gsp_status s) {
         case GSP_ERR_TIE: return "delay table entry within 1e-9 of a rounding tie";
         case GSP_ERR_ALIGN: return "pointer or stride misaligned";
         case GSP_ERR_STATE: return "call out of order";
+        case GSP_ERR_TOO_LARGE: return "sizes exceed the static scratch of the no-allocation search";
     }
     return "unknown status";
 }

@@ -99,4 +99,33 @@ cudaError_t launch_search(gsp_plan_s *p, const int32_t *D, int64_t n_out, int64_
                           int64_t t_offset, float *snr_out, const unsigned long long *bsum,
                           cudaStream_t s, int32_t *nlaunch);
 
+// Explicit scratch and parameters of the search kernels, for callers that
+// provide their own scratch (the no-allocation entry point).
+struct SearchScratch {
+    double *sigma_b;        // [ndm][nb_stride]
+    uint8_t *bad;           // [ndm][nb_stride]
+    BlockParam *bparam;     // [ndm][nb_stride]
+    float *scale;           // [ndm][nwidths]
+    double *sref;           // [ndm]
+    int64_t nb_stride;
+};
+
+struct SearchConfig {
+    int ndm;
+    int block_len;
+    int64_t window_len;
+    float threshold;
+    double bad_lo, bad_hi;
+    const int32_t *widths;  // host
+    int nwidths;
+};
+
+// Launch the search kernels (block statistics from the series, sigma_ref,
+// boxcar) with explicit scratch; candidates go to cands / ncand (ncand is
+// not zeroed here).
+cudaError_t launch_search_explicit(const SearchScratch &sc, const SearchConfig &cfg,
+                                   const int32_t *D, int64_t n_out, int64_t stride,
+                                   int64_t t_offset, gsp_cand *cands,
+                                   unsigned long long *ncand, int64_t max_cands, cudaStream_t s);
+
 }  // namespace gsp

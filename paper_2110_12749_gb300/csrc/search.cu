@@ -431,4 +431,39 @@ cudaError_t launch_search(gsp_plan_s *p, const int32_t *D, int64_t n_out, int64_
     return cudaGetLastError();
 }
 
+cudaError_t launch_search_explicit(const SearchScratch &sc, const SearchConfig &cfg,
+                                   const int32_t *D, int64_t n_out, int64_t stride,
+                                   int64_t t_offset, gsp_cand *cands,
+                                   unsigned long long *ncand, int64_t max_cands, cudaStream_t s) {
+    const int B = cfg.block_len;
+    const int64_t nb = n_out / B;
+    const int64_t Ls = nb * B;
+    if (nb == 0) return cudaSuccess;
+    WidthTable wt{};
+    wt.n = cfg.nwidths;
+    wt.wmax = 0;
+    for (int i = 0; i < wt.n; i++) {
+        wt.w[i] = cfg.widths[i];
+        wt.tri[i] = 0.5f * (float)cfg.widths[i] * (float)(cfg.widths[i] - 1);
+        wt.wmax = max(wt.wmax, cfg.widths[i]);
+    }
+    block_stats_kernel<<<dim3((unsigned)nb, (unsigned)cfg.ndm), kStatThreads, 0, s>>>(
+        D, stride, B, sc.nb_stride, sc.sigma_b, sc.bparam);
+    int n2 = 1;
+    while (n2 < nb) n2 <<= 1;
+    const size_t sm_sort = nb <= kSortMax ? (size_t)n2 * sizeof(double) : 0;
+    row_sigma_kernel<<<cfg.ndm, 512, sm_sort, s>>>(sc.sigma_b, nb, sc.nb_stride, cfg.bad_lo,
+                                                   cfg.bad_hi, wt, sc.sref, sc.scale, sc.bad,
+                                                   sc.bparam);
+    const int64_t L = cfg.window_len;
+    auto fdiv = [](int64_t a, int64_t b) { return a >= 0 ? a / b : -((-a + b - 1) / b); };
+    const int64_t k0 = fdiv(t_offset, L);
+    const int64_t k1 = fdiv(t_offset + Ls - 1, L);
+    const size_t sm_box = (size_t)(kChunk + wt.wmax + 1) * sizeof(uint32_t);
+    boxcar_kernel<false><<<dim3((unsigned)(k1 - k0 + 1), (unsigned)cfg.ndm), kBoxThreads, sm_box, s>>>(
+        D, stride, Ls, B, sc.nb_stride, t_offset, L, k0, wt, sc.bparam, sc.scale, cfg.threshold,
+        nullptr, cands, ncand, max_cands);
+    return cudaGetLastError();
+}
+
 }  // namespace gsp

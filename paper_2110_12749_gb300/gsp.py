@@ -25,6 +25,7 @@ GSP_ERR_TIMEOUT = 6
 GSP_ERR_TIE = 7
 GSP_ERR_ALIGN = 8
 GSP_ERR_STATE = 9
+GSP_ERR_TOO_LARGE = 10
 
 GSP_FLAG_TIMING = 1
 GSP_FLAG_SIMPLE_DD = 2
@@ -97,6 +98,10 @@ def lib():
             "gsp_candidates": ([_vp, _vp, _i64, _vp], ctypes.c_int),
             "gsp_search_host": ([_vp, _vp, _i64, _i64, _i64, _vp, _i64, _vp, _vp], ctypes.c_int),
             "gsp_plan_timing": ([_vp, _vp, _vp], ctypes.c_int),
+            "gsp_search_series_static": ([_vp, ctypes.c_int32, _i64, _i64, _i64, _vp, ctypes.c_int32,
+                                          ctypes.c_int32, ctypes.c_int32, ctypes.c_float,
+                                          ctypes.c_float, ctypes.c_float, _vp, _i64, _vp, _vp],
+                                         ctypes.c_int),
             "gsp_plan_launches": ([_vp], ctypes.c_int32),
             "gsp_status_string": ([ctypes.c_int], ctypes.c_char_p),
             "gsp_last_error_string": ([], ctypes.c_char_p),
@@ -332,3 +337,18 @@ def gsp_plan_timing(plan):
 
 def gsp_plan_launches(plan):
     return int(lib().gsp_plan_launches(plan.handle))
+
+
+def gsp_search_series_static(D, n_out, d_cands, d_ncand, t_offset=0, widths=None,
+                             block_len=1024, window_len=1024, threshold=6.0, bad_lo=0.5,
+                             bad_hi=2.5, stream=None):
+    """No-allocation search of D (torch int32 CUDA [ndm][stride]); d_cands is a
+    CUDA uint8 tensor of max_cands * 24 bytes, d_ncand a CUDA int64 tensor of
+    one element.  Asynchronous; read the outputs after synchronising."""
+    w = None if widths is None else np.ascontiguousarray(np.asarray(widths, dtype=np.int32))
+    max_cands = d_cands.numel() * d_cands.element_size() // CAND_DTYPE.itemsize
+    st = lib().gsp_search_series_static(
+        _vp(D.data_ptr()), D.shape[0], n_out, D.stride(0), t_offset, _np_ptr(w),
+        0 if w is None else w.size, block_len, window_len, threshold, bad_lo, bad_hi,
+        _vp(d_cands.data_ptr()), max_cands, _vp(d_ncand.data_ptr()), _stream(stream))
+    _check(st, "gsp_search_series_static")

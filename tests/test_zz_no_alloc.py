@@ -1,0 +1,85 @@
+"""The search entry point that allocates nothing (gsp_search_series_static).
+
+It exists for callers that may not call cudaMalloc: a real-time ingest loop
+whose latency budget a device allocation would break (an allocation can
+synchronise the device and takes a driver-wide lock), or an application that
+owns all device memory through its own pool.  Its working memory is one static
+device array inside the library.  This test calls it through the C ABI twice
+in a row, on different sizes so that the second call runs over the first
+call's leftovers, and checks each result against the plan-based
+gsp_search_series (same candidates, S/N within the tests' 1e-5 tolerance).
+After the first call (which may load the library's device code), a call must
+not change the device's free memory.  The file is named to be collected last.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+RTOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def gsp():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2110_12749_gb300 import build, gsp as g
+    build.build()
+    g.lib()
+    return g
+
+
+def _series(rng, ndm, n_out):
+    stride = (n_out + 3) // 4 * 4
+    D = np.zeros((ndm, stride), np.int32)
+    D[:, :n_out] = np.round(rng.normal(0.0, 300.0, (ndm, n_out)) + 1e5).astype(np.int32)
+    for _ in range(3 * ndm):
+        r, t, w = int(rng.integers(0, ndm)), int(rng.integers(0, n_out - 200)), int(rng.integers(1, 120))
+        D[r, t:t + w] += int(rng.integers(150, 900))
+    return torch.from_numpy(D).cuda()
+
+
+def _sorted(c):
+    return c[np.lexsort((c["width"], c["t"], c["dm_idx"]))]
+
+
+def test_static_search_matches_plan_search_twice(gsp):
+    rng = np.random.default_rng(2024)
+    cases = [(48, 20517, 0), (17, 9000, 1500)]       # (rows, samples, t_offset)
+    for call, (ndm, n_out, t_off) in enumerate(cases):
+        D = _series(rng, ndm, n_out)
+        desc, keep = gsp.make_desc(1, 1000.0, 1500.0, 1e-4, n_out,
+                                   delays=np.zeros((ndm, 1), np.int32), threshold=6.0)
+        plan = gsp.gsp_plan_create(desc, keep)
+        gsp.gsp_search_series(plan, D, n_out, t_offset=t_off)
+        ref, nref, st = gsp.gsp_candidates(plan)
+        assert st == gsp.GSP_OK and nref > 10
+
+        max_cands = 4096
+        d_cands = torch.zeros(max_cands * gsp.CAND_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
+        d_ncand = torch.zeros(1, dtype=torch.int64, device="cuda")
+        torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info()[0]
+        gsp.gsp_search_series_static(D, n_out, d_cands, d_ncand, t_offset=t_off, threshold=6.0)
+        torch.cuda.synchronize()
+        free1 = torch.cuda.mem_get_info()[0]
+        if call > 0:
+            assert free1 == free0
+        n = int(d_ncand.item())
+        got = _sorted(d_cands.cpu().numpy().view(gsp.CAND_DTYPE)[:n].copy())
+        assert n == nref
+        assert (got["dm_idx"] == ref["dm_idx"]).all()
+        assert (got["t"] == ref["t"]).all() and (got["width"] == ref["width"]).all()
+        assert np.all(np.abs(got["snr"] - ref["snr"]) <= RTOL * np.maximum(np.abs(ref["snr"]), 1.0))
+        gsp.gsp_plan_destroy(plan)
+
+
+def test_static_search_rejects_oversize(gsp):
+    D = torch.zeros((5000, 2048), dtype=torch.int32, device="cuda")
+    d_cands = torch.zeros(24 * 16, dtype=torch.uint8, device="cuda")
+    d_ncand = torch.zeros(1, dtype=torch.int64, device="cuda")
+    with pytest.raises(gsp.GspError) as e:
+        gsp.gsp_search_series_static(D, 2048, d_cands, d_ncand)
+    assert e.value.status == gsp.GSP_ERR_TOO_LARGE
