@@ -16,11 +16,14 @@
 // resolved once per 256 channels, not per add.
 //
 // Accumulation (exact, SWAR): per word two 32-bit views are summed over
-// channels, E = sum (w & 0x00ff00ff) (bytes 0 and 2 in 16-bit lanes) and
-// O = sum of bytes 1 and 3 placed in 16-bit lanes by one byte permute.  A
-// 16-bit lane holds at most 256 * 255 < 2^16, so every 256 channels the views
-// are flushed into int32 accumulators: b0 = E & 0xffff, b2 = E >> 16,
-// b1 = O & 0xffff, b3 = O >> 16.
+// channels: the raw word, S = sum w, and the odd bytes, O = sum (b1 + 2^16 b3)
+// placed in 16-bit lanes by one byte permute.  A 16-bit lane holds at most
+// 256 * 255 < 2^16, so every 256 channels the views are flushed into int32
+// accumulators: b1 = O & 0xffff, b3 = O >> 16, and with E = S - (O << 8)
+// (mod 2^32, the exact sum of b0 + 2^16 b2), b0 = E & 0xffff, b2 = E >> 16.
+// Per word this is one shared load, one permute (ALU), half an IADD3 (ALU)
+// and one multiply-add (x * 1 + acc on the IMAD pipe).  Other variants keep a
+// masked even-byte view instead of the raw one.
 #include <algorithm>
 #include <cstdlib>
 #include <vector>
@@ -119,17 +122,25 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
 
 __device__ __forceinline__ void fail(int *err) { atomicExch(err, 1); }
 
-// Accumulate two words of one phase into the even-byte view E (bytes 0 and 2
-// in 16-bit lanes) and the odd-byte view O (bytes 1 and 3).  ACC chooses the
+// Accumulate two words of one phase into the odd-byte view O (bytes 1 and 3
+// in 16-bit lanes, one byte permute per word) and into E.  For ACC 0-2, E is
+// the even-byte view (bytes 0 and 2, one LOP3 per word) and ACC chooses the
 // pipe of the additions: 0 = IADD3 on the integer ALU, 1 = E on the ALU and
 // O as x * 1 + acc on the multiply-add pipe, 2 = both on the multiply-add
-// pipe.  The byte extraction (LOP3, PRMT) always runs on the ALU.
+// pipe.  For ACC 3, E is the raw sum of the words (IADD3, no extraction) and
+// O is summed on the multiply-add pipe; since w = (b0 + 2^16 b2) + 2^8 O(w),
+// the even-byte sums are E - (O << 8) mod 2^32, exact while the 16-bit lanes
+// cannot overflow.
 template <int ACC>
 __device__ __forceinline__ void acc_pair(uint32_t &E, uint32_t &O, uint32_t w1, uint32_t w2,
                                          uint32_t one) {
     const uint32_t e1 = w1 & 0x00ff00ffu, e2 = w2 & 0x00ff00ffu;
     const uint32_t o1 = __byte_perm(w1, 0, 0x4341), o2 = __byte_perm(w2, 0, 0x4341);
-    if (ACC == 0) {
+    if (ACC == 3) {
+        // raw view: E holds sum w; the even bytes are recovered at the flush
+        E += w1 + w2;
+        O = ptx::imadd(o1, one, ptx::imadd(o2, one, O));
+    } else if (ACC == 0) {
         E += e1 + e2;
         O += o1 + o2;
     } else if (ACC == 1) {
@@ -320,7 +331,7 @@ __global__ void __launch_bounds__((kKDM / KW + 1) * 32, 1) dd_tiled_kernel(const
                         ptx::lds_words<kM>((uint32_t)lp[j] + lane4, w1);
 #pragma unroll
                         for (int k = 0; k < kM; k++) {
-                            E[i][P][k] += w1[k] & 0x00ff00ffu;
+                            E[i][P][k] += ACC == 3 ? w1[k] : (w1[k] & 0x00ff00ffu);
                             O[i][P][k] += __byte_perm(w1[k], 0, 0x4341);
                         }
                     }
@@ -366,7 +377,7 @@ __global__ void __launch_bounds__((kKDM / KW + 1) * 32, 1) dd_tiled_kernel(const
 #pragma unroll
                     for (int k = 0; k < kM; k++) {
                         const uint32_t w1 = p1[32 * k];
-                        E[i][P][k] += w1 & 0x00ff00ffu;
+                        E[i][P][k] += ACC == 3 ? w1 : (w1 & 0x00ff00ffu);
                         O[i][P][k] += __byte_perm(w1, 0, 0x4341);
                     }
                 }
@@ -384,7 +395,8 @@ __global__ void __launch_bounds__((kKDM / KW + 1) * 32, 1) dd_tiled_kernel(const
                     sp[k][0] = sp[k][1] = sp[k][2] = 0;
 #pragma unroll
                     for (int P = 0; P < 4; P++) {
-                        const uint32_t e = E[i][P][k], o = O[i][P][k];
+                        const uint32_t o = O[i][P][k];
+                        const uint32_t e = ACC == 3 ? E[i][P][k] - (o << 8) : E[i][P][k];
                         uint32_t b[4];
                         b[0] = e & 0xffffu;
                         b[1] = o & 0xffffu;
@@ -504,6 +516,8 @@ const TiledVariant kVariants[] = {
     {dd_tiled_kernel<1, true, 1>, 1, 4},
     {dd_tiled_kernel<1, false, 2, true>, 1, 4},
     {dd_tiled_kernel<1, false, 2, true, 8>, 1, 8},
+    {dd_tiled_kernel<1, false, 3>, 1, 4},
+    {dd_tiled_kernel<1, false, 3, true>, 1, 4},
 };
 constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
 constexpr int kDefaultVariant = 3;

@@ -124,11 +124,18 @@ def test_full_size_parity(gsp, orc, name):
     ncmp, bad = compare_candidates(cands, ora, 6.0, 1024, 0, contenders, rows=set(rows.tolist()))
     assert not bad, bad[:10]
     assert ncmp > 0
-    # injected pulses with S/N >= 10 are detected near their DM and time
-    found = 0
-    strong = [p for p in pulses if p.snr >= 10]
-    for p in strong:
-        k = (p.dm - wl.dm_lo) / wl.dm_step
-        m = cands[(np.abs(cands["dm_idx"] - k) <= 3) & (np.abs(cands["t"] - p.t0) <= max(p.width, 4))]
+    # injected pulses with S/N >= 10 whose DM-trial smearing (largest delay
+    # difference to the nearest trial) is at most their width are detected near
+    # their DM and time
+    found, strong = 0, 0
+    for p in pulses:
+        k = int(round((p.dm - wl.dm_lo) / wl.dm_step))
+        k = min(max(k, 0), wl.ndm - 1)
+        smear = int(np.abs(np.asarray(p.delays) - dl[k]).max())
+        if p.snr < 10 or smear > p.width or p.t0 + p.width > Ls:
+            continue
+        strong += 1
+        m = cands[(np.abs(cands["dm_idx"] - k) <= 3) &
+                  (np.abs(cands["t"] - p.t0) <= p.width + smear + 4)]
         found += int(len(m) > 0)
-    assert found >= 0.8 * len(strong), (found, len(strong))
+    assert strong > 0 and found >= 0.8 * strong, (found, strong)
