@@ -87,9 +87,7 @@ cudaError_t launch_dedisperse_simple(const gsp_plan_s *p, const uint8_t *x, int6
 // Tiled kernel.
 namespace {
 
-constexpr int kCB = 32;          // channels per stage
 constexpr int kKDM = 16;         // DM trials per CTA (= consumer warps x DM trials per warp)
-constexpr int kFlushStages = 256 / kCB;  // stages between SWAR flushes (256 channels)
 constexpr long long kWaitBudget = 4000000000ll;  // ~2 s of SM clock per wait
 
 struct TiledArgs {
@@ -156,8 +154,12 @@ __device__ __forceinline__ void acc_pair(uint32_t &E, uint32_t &O, uint32_t w1, 
 // QUAD: visit channels four at a time (more loads in flight per warp).
 // M: 4-sample words per lane, T = 128 M output samples computed per tile and
 // T - 4 stored (the tile's last word is incomplete by construction).
-template <int KW, bool QUAD, int ACC, bool A32 = false, int M = 4>
+// CB: channels per shared-memory stage (a multiple of 32).
+template <int KW, bool QUAD, int ACC, bool A32 = false, int M = 4, int CB = 32>
 __global__ void __launch_bounds__((kKDM / KW + 1) * 32, 1) dd_tiled_kernel(const TiledArgs a) {
+    constexpr int kCB = CB;
+    constexpr int kH = CB / 32;                  // channels per lane per stage
+    constexpr int kFlushStages = 256 / kCB;      // stages between SWAR flushes (256 channels)
     constexpr int kM = M;
     constexpr int kT = 128 * kM;
     constexpr int kTEff = kT - 4;
@@ -166,7 +168,7 @@ __global__ void __launch_bounds__((kKDM / KW + 1) * 32, 1) dd_tiled_kernel(const
     extern __shared__ __align__(128) uint8_t smem[];
     const int slot_bytes = kCB * a.win;
     int32_t *lists = reinterpret_cast<int32_t *>(smem + (size_t)a.stages * slot_bytes);
-    uint64_t *bars = reinterpret_cast<uint64_t *>(lists + kCW * kKW * 4 * 32);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(lists + kCW * kKW * 4 * kCB);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int blk = (int)(blockIdx.x % (unsigned)a.nblk);
     const int64_t t0 = (int64_t)(blockIdx.x / (unsigned)a.nblk) * kTEff;
@@ -198,15 +200,22 @@ __global__ void __launch_bounds__((kKDM / KW + 1) * 32, 1) dd_tiled_kernel(const
                     break;
                 }
             }
-            const int c = st * kCB + lane;
-            int64_t s_c = 0, avail = 0;
-            uint32_t len16 = 0;
-            if (c < a.nchan) {
-                s_c = (t0 + bmin[c]) & ~(int64_t)15;
-                avail = a.n_in - s_c;
-                len16 = (uint32_t)min((int64_t)a.win, avail & ~(int64_t)15);
+            int64_t s_c[kH], avail[kH];
+            uint32_t len16[kH];
+            uint32_t tot = 0;
+#pragma unroll
+            for (int h = 0; h < kH; h++) {
+                const int c = st * kCB + h * 32 + lane;
+                s_c[h] = 0;
+                avail[h] = 0;
+                len16[h] = 0;
+                if (c < a.nchan) {
+                    s_c[h] = (t0 + bmin[c]) & ~(int64_t)15;
+                    avail[h] = a.n_in - s_c[h];
+                    len16[h] = (uint32_t)min((int64_t)a.win, avail[h] & ~(int64_t)15);
+                }
+                tot += len16[h];
             }
-            uint32_t tot = len16;
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
             if (lane == 0)
@@ -214,14 +223,19 @@ __global__ void __launch_bounds__((kKDM / KW + 1) * 32, 1) dd_tiled_kernel(const
                              "r"(tot)
                              : "memory");
             __syncwarp();
-            uint8_t *dst = smem + (size_t)slot * slot_bytes + (size_t)lane * a.win;
-            if (len16 > 0) {
-                const uint8_t *src = a.x + (int64_t)c * a.x_stride + s_c;
-                ptx::bulk_g2s(ptx::smem_addr(dst), src, len16, full(slot));
-            }
-            if (c < a.nchan) {
-                const int64_t end = min((int64_t)a.win, avail);
-                for (int64_t i = len16; i < end; i++) dst[i] = a.x[(int64_t)c * a.x_stride + s_c + i];
+#pragma unroll
+            for (int h = 0; h < kH; h++) {
+                const int c = st * kCB + h * 32 + lane;
+                uint8_t *dst = smem + (size_t)slot * slot_bytes + (size_t)(h * 32 + lane) * a.win;
+                if (len16[h] > 0) {
+                    const uint8_t *src = a.x + (int64_t)c * a.x_stride + s_c[h];
+                    ptx::bulk_g2s(ptx::smem_addr(dst), src, len16[h], full(slot));
+                }
+                if (c < a.nchan) {
+                    const int64_t end = min((int64_t)a.win, avail[h]);
+                    for (int64_t i = len16[h]; i < end; i++)
+                        dst[i] = a.x[(int64_t)c * a.x_stride + s_c[h] + i];
+                }
             }
             ptx::mbar_arrive(full(slot));
             issued = st + 1;
@@ -240,7 +254,7 @@ __global__ void __launch_bounds__((kKDM / KW + 1) * 32, 1) dd_tiled_kernel(const
 
     // ------------------------------------------------------- consumer warps
     const int dmw = dm0 + warp * kKW;
-    int32_t *mylist = lists + warp * (kKW * 4 * 32);
+    int32_t *mylist = lists + warp * (kKW * 4 * kCB);
     uint32_t acc[kKW][kM][4];
     uint32_t E[kKW][4][kM], O[kKW][4][kM];
 #pragma unroll
@@ -257,47 +271,58 @@ __global__ void __launch_bounds__((kKDM / KW + 1) * 32, 1) dd_tiled_kernel(const
     const uint32_t smem32 = ptx::smem_addr(smem);
     const uint32_t lane4 = 4u * lane;
     // delays of the next stage are loaded one stage ahead (hides L2 latency)
-    int nx_min = 0, nx_dl[kKW];
-    {
-        const bool v0 = lane < a.nchan;
-        nx_min = v0 ? bmin[lane] : 0;
+    int nx_min[kH], nx_dl[kKW][kH];
+#pragma unroll
+    for (int h = 0; h < kH; h++) {
+        const int c0 = h * 32 + lane;
+        const bool v0 = c0 < a.nchan;
+        nx_min[h] = v0 ? bmin[c0] : 0;
 #pragma unroll
         for (int i = 0; i < kKW; i++)
-            nx_dl[i] = v0 ? a.delays[(int64_t)min(dmw + i, a.ndm - 1) * a.nchan + lane] : 0;
+            nx_dl[i][h] = v0 ? a.delays[(int64_t)min(dmw + i, a.ndm - 1) * a.nchan + c0] : 0;
     }
 
     for (int st = 0; st < nst; st++) {
         const int slot = st % a.stages, round = st / a.stages;
-        const int c = st * kCB + lane;
-        const bool valid = c < a.nchan;
-        const int cur_min = nx_min;
-        int cur_dl[kKW];
+        int cur_min[kH], cur_dl[kKW][kH];
 #pragma unroll
-        for (int i = 0; i < kKW; i++) cur_dl[i] = nx_dl[i];
-        {
-            const int cn = c + kCB;
+        for (int h = 0; h < kH; h++) {
+            cur_min[h] = nx_min[h];
+#pragma unroll
+            for (int i = 0; i < kKW; i++) cur_dl[i][h] = nx_dl[i][h];
+            const int cn = (st + 1) * kCB + h * 32 + lane;
             const bool vn = cn < a.nchan;
-            nx_min = vn ? bmin[cn] : 0;
+            nx_min[h] = vn ? bmin[cn] : 0;
 #pragma unroll
             for (int i = 0; i < kKW; i++)
-                nx_dl[i] = vn ? a.delays[(int64_t)min(dmw + i, a.ndm - 1) * a.nchan + cn] : 0;
+                nx_dl[i][h] = vn ? a.delays[(int64_t)min(dmw + i, a.ndm - 1) * a.nchan + cn] : 0;
         }
-        const int64_t s_c = valid ? ((t0 + cur_min) & ~(int64_t)15) : 0;
         int cnt[kKW][4];
 #pragma unroll
-        for (int i = 0; i < kKW; i++) {
-            const int dl = valid ? cur_dl[i] : 0;
-            const int q = (int)(t0 + dl - s_c);
-            const int p = q & 3;
-            // the aligned word of this (channel, DM) in shared memory: its word
-            // index, or (A32) its 32-bit shared-window byte address
-            const int boff = slot * slot_bytes + lane * a.win + (q & ~3);
-            const int entry = A32 ? (int)(smem32 + boff) : (boff >> 2);
+        for (int i = 0; i < kKW; i++)
 #pragma unroll
-            for (int P = 0; P < 4; P++) {
-                const uint32_t m = __ballot_sync(0xffffffffu, valid && p == P);
-                if (valid && p == P) mylist[(i * 4 + P) * 32 + __popc(m & lmask)] = entry;
-                cnt[i][P] = __popc(m);
+            for (int P = 0; P < 4; P++) cnt[i][P] = 0;
+#pragma unroll
+        for (int h = 0; h < kH; h++) {
+            const int c = st * kCB + h * 32 + lane;
+            const bool valid = c < a.nchan;
+            const int64_t s_c = valid ? ((t0 + cur_min[h]) & ~(int64_t)15) : 0;
+#pragma unroll
+            for (int i = 0; i < kKW; i++) {
+                const int dl = valid ? cur_dl[i][h] : 0;
+                const int q = (int)(t0 + dl - s_c);
+                const int p = q & 3;
+                // the aligned word of this (channel, DM) in shared memory: its word
+                // index, or (A32) its 32-bit shared-window byte address
+                const int boff = slot * slot_bytes + (h * 32 + lane) * a.win + (q & ~3);
+                const int entry = A32 ? (int)(smem32 + boff) : (boff >> 2);
+#pragma unroll
+                for (int P = 0; P < 4; P++) {
+                    const uint32_t m = __ballot_sync(0xffffffffu, valid && p == P);
+                    if (valid && p == P)
+                        mylist[(i * 4 + P) * kCB + cnt[i][P] + __popc(m & lmask)] = entry;
+                    cnt[i][P] += __popc(m);
+                }
             }
         }
         __syncwarp();
@@ -314,7 +339,7 @@ __global__ void __launch_bounds__((kKDM / KW + 1) * 32, 1) dd_tiled_kernel(const
 #pragma unroll
                 for (int P = 0; P < 4; P++) {
                     const int n = cnt[i][P];
-                    const int32_t *lp = mylist + (i * 4 + P) * 32;
+                    const int32_t *lp = mylist + (i * 4 + P) * kCB;
                     int j = 0;
 #pragma unroll 2
                     for (; j + 2 <= n; j += 2) {
@@ -344,7 +369,7 @@ __global__ void __launch_bounds__((kKDM / KW + 1) * 32, 1) dd_tiled_kernel(const
 #pragma unroll
             for (int P = 0; P < 4; P++) {
                 const int n = cnt[i][P];
-                const int32_t *lp = mylist + (i * 4 + P) * 32;
+                const int32_t *lp = mylist + (i * 4 + P) * kCB;
                 int j = 0;
                 if (QUAD) {
                     for (; j + 4 <= n; j += 4) {
@@ -504,23 +529,26 @@ struct TiledVariant {
     TiledKernel fn;
     int kw;
     int m;
+    int cb;
 };
 
 // Tuning variants of the tiled kernel (same result, different schedule).
 const TiledVariant kVariants[] = {
-    {dd_tiled_kernel<2, false, 0>, 2, 4},
-    {dd_tiled_kernel<1, false, 0>, 1, 4},
-    {dd_tiled_kernel<1, false, 1>, 1, 4},
-    {dd_tiled_kernel<1, false, 2>, 1, 4},
-    {dd_tiled_kernel<2, false, 1>, 2, 4},
-    {dd_tiled_kernel<1, true, 1>, 1, 4},
-    {dd_tiled_kernel<1, false, 2, true>, 1, 4},
-    {dd_tiled_kernel<1, false, 2, true, 8>, 1, 8},
-    {dd_tiled_kernel<1, false, 3>, 1, 4},
-    {dd_tiled_kernel<1, false, 3, true>, 1, 4},
+    {dd_tiled_kernel<2, false, 0>, 2, 4, 32},
+    {dd_tiled_kernel<1, false, 0>, 1, 4, 32},
+    {dd_tiled_kernel<1, false, 1>, 1, 4, 32},
+    {dd_tiled_kernel<1, false, 2>, 1, 4, 32},
+    {dd_tiled_kernel<2, false, 1>, 2, 4, 32},
+    {dd_tiled_kernel<1, true, 1>, 1, 4, 32},
+    {dd_tiled_kernel<1, false, 2, true>, 1, 4, 32},
+    {dd_tiled_kernel<1, false, 2, true, 8>, 1, 8, 32},
+    {dd_tiled_kernel<1, false, 3>, 1, 4, 32},
+    {dd_tiled_kernel<1, false, 3, true>, 1, 4, 32},
+    {dd_tiled_kernel<1, false, 3, false, 4, 64>, 1, 4, 64},
+    {dd_tiled_kernel<1, true, 3, false, 4, 64>, 1, 4, 64},
 };
 constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
-constexpr int kDefaultVariant = 3;
+constexpr int kDefaultVariant = 8;
 
 }  // namespace
 
@@ -550,7 +578,8 @@ bool plan_dedisperse_tiled(gsp_plan_s *p, std::vector<int32_t> *blkmin) {
     const int kT = 128 * kVariants[variant].m;
     const int kTEff = kT - 4;
     const int64_t win = (kT + 15 + spread + 15) & ~(int64_t)15;
-    const int64_t fixed = (int64_t)kKDM * 4 * 32 * 4 + 2 * 8 * 8;
+    const int kCB = kVariants[variant].cb;
+    const int64_t fixed = (int64_t)kKDM * 4 * kCB * 4 + 2 * 8 * 8;
     const int64_t budget = 227 * 1024 - fixed;
     const int64_t stages = std::min<int64_t>(8, budget / ((int64_t)kCB * win));
     if (stages < 2) {

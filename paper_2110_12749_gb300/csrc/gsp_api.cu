@@ -97,6 +97,8 @@ void free_plan(gsp_plan_s *p) {
     cudaFree(p->d_sref);
     cudaFree(p->d_cands);
     cudaFree(p->d_ncand);
+    cudaFree(p->d_slots);
+    cudaFree(p->d_chunk);
     cudaFree(p->d_D);
     cudaFree(p->d_xstage);
     for (auto &e : p->ev)
@@ -310,6 +312,11 @@ gsp_status gsp_plan_create(gsp_plan_t *out, const gsp_plan_desc *d) {
     if (st == GSP_OK) st = dalloc(&p->d_sref, (size_t)ndm);
     if (st == GSP_OK) st = dalloc(&p->d_cands, (size_t)d->max_cands);
     if (st == GSP_OK) st = dalloc(&p->d_ncand, 1);
+    p->nwin_max = d->nsamp_max / d->window_len + 2;
+    const size_t nslots = (size_t)ndm * (size_t)p->nwin_max;
+    if (st == GSP_OK && nslots >= ((size_t)1 << 31)) st = GSP_ERR_INVALID_ARG;
+    if (st == GSP_OK) st = dalloc(&p->d_slots, nslots);
+    if (st == GSP_OK) st = dalloc(&p->d_chunk, (nslots + 1023) / 1024);
     if (st == GSP_OK) st = dalloc(&p->d_err, 1);
     if (st == GSP_OK && !p->simple_dd) st = dalloc(&p->d_bsum, rows_blocks * 3);
     if (st != GSP_OK) {
@@ -459,11 +466,13 @@ gsp_status gsp_candidates(gsp_plan_t p, gsp_cand *host_out, int64_t cap, int64_t
     if (kept > 0)
         GSP_CK(cudaMemcpy(v.data(), p->d_cands, (size_t)kept * sizeof(gsp_cand),
                           cudaMemcpyDeviceToHost));
-    std::sort(v.begin(), v.end(), [](const gsp_cand &a, const gsp_cand &b) {
+    auto less = [](const gsp_cand &a, const gsp_cand &b) {
         if (a.dm_idx != b.dm_idx) return a.dm_idx < b.dm_idx;
         if (a.t != b.t) return a.t < b.t;
         return a.width < b.width;
-    });
+    };
+    // the device list is already in (dm, t) order; sort only if it is not
+    if (!std::is_sorted(v.begin(), v.end(), less)) std::sort(v.begin(), v.end(), less);
     const int64_t m = std::min<int64_t>(kept, cap);
     if (m > 0) std::memcpy(host_out, v.data(), (size_t)m * sizeof(gsp_cand));
     return ((int64_t)n > m) ? GSP_ERR_CAPACITY : GSP_OK;

@@ -62,6 +62,9 @@ struct gsp_plan_s {
     double *d_sref = nullptr;        // [ndm]
     gsp_cand *d_cands = nullptr;     // [max_cands]
     unsigned long long *d_ncand = nullptr;
+    gsp_cand *d_slots = nullptr;     // [ndm][nwin_max] one result per (row, window)
+    unsigned int *d_chunk = nullptr;  // compaction chunk counts / offsets
+    int64_t nwin_max = 0;
     int32_t *d_D = nullptr;          // lazily allocated dedispersed scratch
     size_t d_D_elems = 0;
     uint8_t *d_xstage = nullptr;     // lazily allocated input staging for host calls

@@ -198,13 +198,23 @@ __device__ __forceinline__ bool better(const Best &a, const Best &b) {
 // Y(t, w); the fitted-line part Cr(t, w) = sum (c0_b + beta_b j) over the
 // same samples is evaluated in closed form per block segment; then
 // S/N = (Y - Cr) / (sigma_ref sqrt(w)).
-template <bool kWriteSnr>
+// The default width set {1,2,3,4,6,9,14,20,30,45,70,100,150} as compile-time
+// constants (immediate shared-memory offsets in the specialised kernel).
+__host__ __device__ constexpr int default_width(int i) {
+    return i == 0 ? 1 : i == 1 ? 2 : i == 2 ? 3 : i == 3 ? 4 : i == 4 ? 6 : i == 5 ? 9
+         : i == 6 ? 14 : i == 7 ? 20 : i == 8 ? 30 : i == 9 ? 45 : i == 10 ? 70
+         : i == 11 ? 100 : 150;
+}
+constexpr int kNumDefaultWidths = 13;
+
+template <bool kWriteSnr, bool kDefaultW = false>
 __global__ void __launch_bounds__(kBoxThreads) boxcar_kernel(
     const int32_t *__restrict__ D, int64_t stride, int64_t Ls, int B, int64_t nb_max,
     int64_t t_offset, int64_t win_len, int64_t k0, WidthTable wt,
     const BlockParam *__restrict__ bparam, const float *__restrict__ scale, float threshold,
     float *__restrict__ snr_out, gsp_cand *__restrict__ cands,
-    unsigned long long *__restrict__ ncand, int64_t max_cands) {
+    unsigned long long *__restrict__ ncand, int64_t max_cands,
+    gsp_cand *__restrict__ slots = nullptr) {
     extern __shared__ uint32_t sP[];  // prefix sums, kChunk + wmax entries
     __shared__ uint32_t warp_tot[kBoxThreads / 32];
     __shared__ Best wbest[kBoxThreads / 32];
@@ -220,6 +230,9 @@ __global__ void __launch_bounds__(kBoxThreads) boxcar_kernel(
     if (threadIdx.x < wt.n) s_scale[threadIdx.x] = scale[(int64_t)row * wt.n + threadIdx.x];
     __syncthreads();
     const bool live = s_scale[0] != 0.0f;
+    float sc[kNumDefaultWidths];
+#pragma unroll
+    for (int iw = 0; iw < kNumDefaultWidths; iw++) sc[iw] = kDefaultW ? s_scale[iw] : 0.0f;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     Best run{-FLT_MAX, 0, 0};
     bool have = false;
@@ -291,7 +304,21 @@ __global__ void __launch_bounds__(kBoxThreads) boxcar_kernel(
             const uint32_t p0 = sP[i];
             float bsnr = -FLT_MAX;
             int bw = 0;
-            if (t + wt.wmax <= Ls && wt.wmax <= rem) {
+            if (kDefaultW && t + 150 <= Ls && 150 <= rem) {
+                // default widths, every boxcar inside block b
+#pragma unroll
+                for (int iw = 0; iw < kNumDefaultWidths; iw++) {
+                    const int w = default_width(iw);
+                    const int32_t Y = (int32_t)(sP[i + w] - p0);
+                    const float cr = (float)w * g + beta1 * (0.5f * (float)w * (float)(w - 1));
+                    const float v = ((float)Y - cr) * sc[iw];
+                    if (kWriteSnr) snr_out[((int64_t)row * kNumDefaultWidths + iw) * Ls + t] = v;
+                    if (v > bsnr) {
+                        bsnr = v;
+                        bw = w;
+                    }
+                }
+            } else if (!kDefaultW && t + wt.wmax <= Ls && wt.wmax <= rem) {
                 // every boxcar inside block b: no bounds or straddle checks
 #pragma unroll
                 for (int iw = 0; iw < kMaxWidths; iw++) {
@@ -363,7 +390,18 @@ __global__ void __launch_bounds__(kBoxThreads) boxcar_kernel(
         }
         __syncthreads();
     }
-    if (threadIdx.x == 0 && have) {
+    if (slots != nullptr) {
+        // one slot per (row, window), in (row, window) order; width 0 = empty
+        if (threadIdx.x == 0) {
+            gsp_cand c;
+            c.dm_idx = row;
+            c.width = have ? run.w : 0;
+            c.t = run.t;
+            c.snr = run.snr;
+            c.beam = 0;
+            slots[(int64_t)row * gridDim.x + blockIdx.x] = c;
+        }
+    } else if (threadIdx.x == 0 && have) {
         const unsigned long long idx = atomicAdd(ncand, 1ull);
         if ((int64_t)idx < max_cands) {
             gsp_cand c;
@@ -375,6 +413,71 @@ __global__ void __launch_bounds__(kBoxThreads) boxcar_kernel(
             cands[idx] = c;
         }
     }
+}
+
+// Stream compaction of the (row, window) slots into a dense candidate list in
+// (row, t) order: per chunk of kCompact slots count the non-empty ones, scan
+// the chunk counts, then scatter.  Records beyond max_cands are dropped; the
+// total is written to *ncand.
+constexpr int kCompact = 1024;
+
+__global__ void __launch_bounds__(kCompact) slot_count_kernel(const gsp_cand *__restrict__ slots,
+                                                              int64_t nslots,
+                                                              unsigned int *__restrict__ counts) {
+    const int64_t i = (int64_t)blockIdx.x * kCompact + threadIdx.x;
+    const int f = (i < nslots && slots[i].width > 0) ? 1 : 0;
+    const int c = __syncthreads_count(f);
+    if (threadIdx.x == 0) counts[blockIdx.x] = (unsigned int)c;
+}
+
+__global__ void __launch_bounds__(kCompact) slot_scan_kernel(unsigned int *__restrict__ counts,
+                                                             int64_t nchunks,
+                                                             unsigned long long *__restrict__ ncand) {
+    // exclusive scan of counts in place (one CTA, tiles of kCompact)
+    __shared__ unsigned long long warp_tot[kCompact / 32];
+    __shared__ unsigned long long carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int64_t base = 0; base < nchunks; base += kCompact) {
+        const int64_t i = base + threadIdx.x;
+        const unsigned long long v = i < nchunks ? counts[i] : 0ull;
+        unsigned long long incl = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long u = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += u;
+        }
+        if (lane == 31) warp_tot[wid] = incl;
+        __syncthreads();
+        unsigned long long pre = carry;
+        for (int q = 0; q < wid; q++) pre += warp_tot[q];
+        const unsigned long long excl = pre + incl - v;
+        __syncthreads();
+        if (i < nchunks) counts[i] = (unsigned int)excl;  // fits: total <= nslots < 2^32
+        if (threadIdx.x == kCompact - 1) carry = excl + v;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *ncand = carry;
+}
+
+__global__ void __launch_bounds__(kCompact) slot_scatter_kernel(
+    const gsp_cand *__restrict__ slots, int64_t nslots, const unsigned int *__restrict__ offsets,
+    gsp_cand *__restrict__ cands, int64_t max_cands) {
+    __shared__ unsigned int warp_tot[kCompact / 32];
+    const int64_t i = (int64_t)blockIdx.x * kCompact + threadIdx.x;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    gsp_cand c;
+    c.width = 0;
+    if (i < nslots) c = slots[i];
+    const unsigned int f = c.width > 0 ? 1u : 0u;
+    const unsigned int bal = __ballot_sync(0xffffffffu, f);
+    if (lane == 0) warp_tot[wid] = __popc(bal);
+    __syncthreads();
+    unsigned int pre = offsets[blockIdx.x];
+    for (int q = 0; q < wid; q++) pre += warp_tot[q];
+    pre += __popc(bal & ((1u << lane) - 1u));
+    if (f && (int64_t)pre < max_cands) cands[pre] = c;
 }
 
 }  // namespace
@@ -419,15 +522,33 @@ cudaError_t launch_search(gsp_plan_s *p, const int32_t *D, int64_t n_out, int64_
     const int64_t k1 = fdiv(t_offset + Ls - 1, L);
     const size_t sm_box = (size_t)(kChunk + wt.wmax + 1) * sizeof(uint32_t);
     dim3 grid((unsigned)(k1 - k0 + 1), (unsigned)ndm);
-    if (snr_out)
+    bool dflt = wt.n == kNumDefaultWidths;
+    for (int i = 0; dflt && i < wt.n; i++) dflt = wt.w[i] == default_width(i);
+    if (snr_out && dflt)
+        boxcar_kernel<true, true><<<grid, kBoxThreads, sm_box, s>>>(
+            D, stride, Ls, B, p->nb_max, t_offset, L, k0, wt, p->d_bparam, p->d_scale,
+            p->desc.threshold, snr_out, p->d_cands, p->d_ncand, p->desc.max_cands, p->d_slots);
+    else if (snr_out)
         boxcar_kernel<true><<<grid, kBoxThreads, sm_box, s>>>(
             D, stride, Ls, B, p->nb_max, t_offset, L, k0, wt, p->d_bparam, p->d_scale,
-            p->desc.threshold, snr_out, p->d_cands, p->d_ncand, p->desc.max_cands);
+            p->desc.threshold, snr_out, p->d_cands, p->d_ncand, p->desc.max_cands, p->d_slots);
+    else if (dflt)
+        boxcar_kernel<false, true><<<grid, kBoxThreads, sm_box, s>>>(
+            D, stride, Ls, B, p->nb_max, t_offset, L, k0, wt, p->d_bparam, p->d_scale,
+            p->desc.threshold, snr_out, p->d_cands, p->d_ncand, p->desc.max_cands, p->d_slots);
     else
         boxcar_kernel<false><<<grid, kBoxThreads, sm_box, s>>>(
             D, stride, Ls, B, p->nb_max, t_offset, L, k0, wt, p->d_bparam, p->d_scale,
-            p->desc.threshold, snr_out, p->d_cands, p->d_ncand, p->desc.max_cands);
+            p->desc.threshold, snr_out, p->d_cands, p->d_ncand, p->desc.max_cands, p->d_slots);
     *nlaunch += 1;
+    // dense candidate list in (row, t) order
+    const int64_t nslots = (int64_t)grid.x * ndm;
+    const int64_t nchunks = (nslots + kCompact - 1) / kCompact;
+    slot_count_kernel<<<(unsigned)nchunks, kCompact, 0, s>>>(p->d_slots, nslots, p->d_chunk);
+    slot_scan_kernel<<<1, kCompact, 0, s>>>(p->d_chunk, nchunks, p->d_ncand);
+    slot_scatter_kernel<<<(unsigned)nchunks, kCompact, 0, s>>>(p->d_slots, nslots, p->d_chunk,
+                                                              p->d_cands, p->desc.max_cands);
+    *nlaunch += 3;
     return cudaGetLastError();
 }
 

@@ -166,3 +166,37 @@ def test_extreme_values_no_overflow(gsp, orc):
     assert n == 0
     s = gsp.gsp_search_stats(plan, n_out)
     assert (s["sigma_ref"] == 0).all() and s["bad"].all()
+
+
+def test_custom_widths_blocks_windows_offset(gsp, orc, tiny):
+    """Generic (non-default) width set, block and window lengths, and an absolute
+    sample offset of the series: S/N and candidates against the oracle."""
+    wl, dl, x, n_out, pulses, Dref = tiny
+    widths, B, L, off, thr = (1, 3, 7, 16, 40, 90), 512, 700, 333, 4.5
+    rows = np.arange(0, wl.ndm, 7)
+    desc, keep = gsp.make_desc(dl.shape[1], 1200.0, 1500.0, 1e-4, wl.n_in, delays=dl[rows],
+                               widths=widths, block_len=B, window_len=L, threshold=thr)
+    plan = gsp.gsp_plan_create(desc, keep)
+    stride = (n_out + 3) // 4 * 4
+    Dd = torch.zeros((len(rows), stride), dtype=torch.int32, device="cuda")
+    Dd[:, :n_out] = torch.from_numpy(Dref[rows].astype(np.int32)).cuda()
+    Ls = (n_out // B) * B
+    snr = torch.empty((len(rows), len(widths), Ls), dtype=torch.float32, device="cuda")
+    gsp.gsp_boxcar_snr(plan, Dd, n_out, snr)
+    snr = snr.cpu().numpy()
+    gsp.gsp_search_series(plan, Dd, n_out, t_offset=off)
+    cands, n, st = gsp.gsp_candidates(plan)
+    contenders, ora = {}, []
+    for i, r in enumerate(rows):
+        det = orc.search_row(Dref[r], dm_idx=i, block_len=B, window_len=L, widths=widths,
+                             threshold=thr, detail=True)
+        ok, msg = snr_close(snr[i], det["snr"])
+        assert ok, "row %d: %s" % (r, msg)
+        det_off = orc.search_row(Dref[r], dm_idx=i, block_len=B, window_len=L, widths=widths,
+                                 threshold=thr, t_offset=off, detail=True)
+        contenders[i] = window_contenders(det_off, L, off, thr)
+        ora.append(det_off["cands"])
+    ora = np.concatenate(ora)
+    ncmp, bad = compare_candidates(cands, ora, thr, L, off, contenders)
+    assert not bad, bad[:10]
+    assert ncmp > 20
