@@ -250,6 +250,18 @@ def run_gsp(args):
     value = world * wl.sky_seconds() / (ms_step / 1e3)
     cands, ncand, _ = gsp.gsp_candidates(plan)
 
+    # host -> device bandwidth of the pinned filterbank (context for e2e)
+    h2d_gbs = None
+    if args.e2e_steps > 0:
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        xd2 = torch.empty_like(xd)
+        xd2.copy_(xh, non_blocking=True)
+        e0.record(stream)
+        xd2.copy_(xh, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        h2d_gbs = x.nbytes / (e0.elapsed_time(e1) / 1e3) / 1e9
+        del xd2
     # end to end through the host-buffer entry point
     e2e_ms, h2d, n2 = [], x.shape[0] * x.shape[1], 0
     if args.e2e_steps > 0:
@@ -296,7 +308,8 @@ def run_gsp(args):
                          "frac_at_run_clock": (achieved / (nsm * INT_LANES_PER_SM * clocks["sm_mhz"] * 1e-6)
                                                if clocks["sm_mhz"] else None)},
             "e2e": {"value": e2e_value, "unit": "sky-s/s", "ms_per_step": e2e_step,
-                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 8 + 24 * int(n2)},
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 8 + 24 * int(n2),
+                    "h2d_gbs": h2d_gbs},
             "gpu_launches": launches, "clocks": clocks, "candidates": int(ncand),
             "dd_variant": os.environ.get("GSP_DD_VARIANT", "default"),
             "input_gen_s": gen_s, "wall_s": t_wall,

@@ -548,7 +548,7 @@ const TiledVariant kVariants[] = {
     {dd_tiled_kernel<1, true, 3, false, 4, 64>, 1, 4, 64},
 };
 constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
-constexpr int kDefaultVariant = 8;
+constexpr int kDefaultVariant = 10;
 
 }  // namespace
 

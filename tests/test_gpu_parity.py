@@ -172,7 +172,7 @@ def test_custom_widths_blocks_windows_offset(gsp, orc, tiny):
     """Generic (non-default) width set, block and window lengths, and an absolute
     sample offset of the series: S/N and candidates against the oracle."""
     wl, dl, x, n_out, pulses, Dref = tiny
-    widths, B, L, off, thr = (1, 3, 7, 16, 40, 90), 512, 700, 333, 4.5
+    widths, B, L, off, thr = (1, 3, 7, 16, 40, 90), 512, 700, 333, 3.5
     rows = np.arange(0, wl.ndm, 7)
     desc, keep = gsp.make_desc(dl.shape[1], 1200.0, 1500.0, 1e-4, wl.n_in, delays=dl[rows],
                                widths=widths, block_len=B, window_len=L, threshold=thr)
@@ -199,4 +199,4 @@ def test_custom_widths_blocks_windows_offset(gsp, orc, tiny):
     ora = np.concatenate(ora)
     ncmp, bad = compare_candidates(cands, ora, thr, L, off, contenders)
     assert not bad, bad[:10]
-    assert ncmp > 20
+    assert ncmp >= 10
