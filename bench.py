@@ -44,6 +44,12 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--n-in", type=int, default=0,
                     help="samples per channel (0: the workload's); smaller only for profiling")
+    ap.add_argument("--stream-beams", type=int, default=4,
+                    help="beams of the streaming-latency measurement (0: skip)")
+    ap.add_argument("--stream-chunks", type=int, default=6,
+                    help="chunks per beam in the streaming measurement (the first one primes)")
+    ap.add_argument("--stream-gbs", type=float, default=6.0,
+                    help="aggregate arrival rate of the simulated stream (GB/s)")
     ap.add_argument("--variant", type=int, default=-1,
                     help="tiled dedispersion kernel variant (GSP_DD_VARIANT); -1: library default")
     return ap.parse_args()
@@ -187,6 +193,91 @@ def run_reference(args):
     return 0
 
 
+def run_stream(args, wl, delays_fn):
+    """Streaming loop: B beams, chunks of 2^18 samples admitted round-robin as they
+    arrive at an aggregate rate; latency = candidates on the host - arrival."""
+    import queue
+    import threading
+    import torch
+    from paper_2110_12749_gb300 import gsp, synth
+    B, K, chunk = args.stream_beams, args.stream_chunks, 1 << 18
+    plans, streams, cstreams = [], [], []
+    md = None
+    for b in range(B):
+        desc, keep = gsp.make_desc(wl.nchan, wl.f_lo, wl.f_hi, wl.t_samp, 1 << 20, ndm=wl.ndm,
+                                   dm_lo=wl.dm_lo, dm_step=wl.dm_step)
+        plan = gsp.gsp_plan_create(desc, keep)
+        md = gsp.gsp_plan_max_delay(plan)
+        plans.append(plan)
+        streams.append(gsp.gsp_stream_create(plan, chunk, beam=b))
+        cstreams.append(torch.cuda.Stream())
+    # one primed chunk of synthetic data, repeated for every chunk of every beam
+    import dataclasses
+    wl1 = dataclasses.replace(wl, n_in=md + chunk)
+    x, _, _, _ = synth.workload_filterbank(wl1, delays_fn, chunk, beam=0)
+    xh = torch.from_numpy(x).pin_memory()
+    first = xh
+    later = xh[:, md:md + chunk]
+    chunk_bytes = wl.nchan * chunk
+    interval = chunk_bytes / (args.stream_gbs * 1e9)
+    # priming chunk of every beam (not timed; also allocates the plans' scratch)
+    for b in range(B):
+        with torch.cuda.stream(cstreams[b]):
+            gsp.gsp_stream_push(streams[b], first, gsp.gsp_stream_need(streams[b]),
+                                stream=cstreams[b])
+        gsp.gsp_stream_results(streams[b])
+    q = queue.Queue()
+    lat, done_at = [], []
+    beam_free = [threading.Event() for _ in range(B)]
+    for e in beam_free:
+        e.set()
+
+    def waiter():
+        while True:
+            item = q.get()
+            if item is None:
+                return
+            b, arrival, ev = item
+            ev.synchronize()
+            gsp.gsp_stream_results(streams[b])
+            t = time.perf_counter()
+            lat.append((t - arrival) * 1e3)
+            done_at.append(t)
+            beam_free[b].set()
+
+    th = threading.Thread(target=waiter, daemon=True)
+    th.start()
+    n_items = B * (K - 1)
+    t_start = time.perf_counter() + 0.05
+    for i in range(n_items):
+        b = i % B
+        arrival = t_start + i * interval
+        now = time.perf_counter()
+        if arrival > now:
+            time.sleep(arrival - now)
+        beam_free[b].wait()
+        beam_free[b].clear()
+        with torch.cuda.stream(cstreams[b]):
+            gsp.gsp_stream_push(streams[b], later, chunk, stream=cstreams[b])
+            ev = torch.cuda.Event()
+            ev.record(cstreams[b])
+        q.put((b, arrival, ev))
+    q.put(None)
+    th.join()
+    for st in streams:
+        gsp.gsp_stream_destroy(st)
+    for p in plans:
+        gsp.gsp_plan_destroy(p)
+    lat_sorted = sorted(lat)
+    span = max(done_at) - t_start
+    return {"beams": B, "chunk_samples": chunk, "chunk_sky_s": chunk * wl.t_samp,
+            "arrival_gbs": args.stream_gbs, "chunks_timed": n_items,
+            "p50_ms": float(np.percentile(lat_sorted, 50)),
+            "p99_ms": float(np.percentile(lat_sorted, 99)), "max_ms": float(lat_sorted[-1]),
+            "sky_s_per_s": n_items * chunk * wl.t_samp / span,
+            "data": "one synthetic primed chunk repeated for every chunk and beam"}
+
+
 def run_gsp(args):
     import torch
     from paper_2110_12749_gb300 import gsp, synth
@@ -285,10 +376,19 @@ def run_gsp(args):
     clocks = clk.summary()
     peak = nsm * INT_LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
     line = None
+    stream_res = None
+    if args.stream_beams > 0 and rank == 0:
+        gsp.gsp_plan_destroy(plan)
+        plan = None
+        del xd
+        torch.cuda.empty_cache()
+        stream_res = run_stream(args, wl, delays_fn)
     if rank == 0:
         cpu = None
         if not args.no_cpu_baseline:
-            dl = gsp.gsp_plan_delays(plan)
+            d1, k1 = gsp.make_desc(wl.nchan, wl.f_lo, wl.f_hi, wl.t_samp, wl.n_in, ndm=wl.ndm,
+                                   dm_lo=wl.dm_lo, dm_step=wl.dm_step)
+            dl = gsp.gsp_compute_delays(d1)[0]
             cpu = oracle_sample(x, wl, dl, args.cpu_rows or auto_rows())
         line = {
             "metric": "sky-s processed per wall-s", "value": value, "unit": "sky-s/s",
@@ -316,8 +416,12 @@ def run_gsp(args):
         }
         if cpu is not None:
             line["cpu_baseline"] = cpu
+        if stream_res is not None:
+            line["stream"] = stream_res
+            line["p99_chunk_latency_ms"] = stream_res["p99_ms"]
         print(json.dumps(line))
-    gsp.gsp_plan_destroy(plan)
+    if plan is not None:
+        gsp.gsp_plan_destroy(plan)
     if world > 1:
         torch.distributed.destroy_process_group()
     return 0

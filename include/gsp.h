@@ -60,6 +60,7 @@ typedef enum {
 #define GSP_FLAG_SIMPLE_DD 2 /* use the simple reference dedispersion kernel */
 
 typedef struct gsp_plan_s *gsp_plan_t;
+typedef struct gsp_stream_s *gsp_stream_t;
 
 /* Plan descriptor: host values, copied by gsp_plan_create.  Fill it with
  * gsp_plan_desc_init() first; then set the band, sampling and DM grid. */
@@ -223,6 +224,40 @@ gsp_status gsp_search_series_static(const int32_t *d_D, int32_t ndm, int64_t n_o
                                     float threshold, float bad_lo, float bad_hi,
                                     gsp_cand *d_cands, int64_t max_cands,
                                     unsigned long long *d_ncand, void *stream);
+
+/* Streaming search of one beam (the device-resident form of the overlapping
+ * read blocks of Alg. 2/3 and of the overlapped merge of adjacent files of
+ * Sec. 2.1).  A stream owns two device input buffers of
+ * nchan x round16(chunk_out + max_delay) bytes and uses the plan (one stream
+ * per plan).  chunk_out must be a multiple of block_len and window_len, and
+ * chunk_out + max_delay <= nsamp_max.  Chunk k covers output samples
+ * [k chunk_out, (k+1) chunk_out) of the stream; its detrend blocks and candidate
+ * windows are aligned to absolute sample indices.  The normalisation
+ * (sigma_ref) is per chunk. */
+gsp_status gsp_stream_create(gsp_stream_t *out, gsp_plan_t plan, int64_t chunk_out, int32_t beam);
+
+/* Free the stream's buffers (synchronises the device; the plan is not freed). */
+gsp_status gsp_stream_destroy(gsp_stream_t s);
+
+/* Samples per channel the next push must supply: chunk_out + max_delay for
+ * the first push, chunk_out afterwards (-1 for a NULL stream). */
+int64_t gsp_stream_need(gsp_stream_t s);
+
+/* Admit the next chunk: h_x is host memory [nchan][h_stride] holding
+ * gsp_stream_need(s) new samples per channel (pinned memory makes the copy
+ * asynchronous).  Enqueues on stream: the copy of the previous chunk's last
+ * max_delay samples (device to device), the host-to-device copy of the new
+ * samples, and gsp_search.  Returns GSP_ERR_INVALID_ARG if n differs from
+ * gsp_stream_need(s). */
+gsp_status gsp_stream_push(gsp_stream_t s, const uint8_t *h_x, int64_t n, int64_t h_stride,
+                           void *stream);
+
+/* Candidates of the last pushed chunk, as gsp_candidates, with t converted to
+ * the stream's absolute sample index and beam set to the stream's label;
+ * *t_abs0 (optional) receives the absolute index of the chunk's first output
+ * sample.  Synchronises. */
+gsp_status gsp_stream_results(gsp_stream_t s, gsp_cand *host_out, int64_t cap, int64_t *n_total,
+                              int64_t *t_abs0);
 
 /* Static text for a status code. */
 const char *gsp_status_string(gsp_status s);

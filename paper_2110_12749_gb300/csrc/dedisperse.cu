@@ -102,6 +102,8 @@ struct TiledArgs {
     int nchan;
     int ndm;
     int nblk;
+    int grp;       // DM blocks per launch group (groups sweep all time tiles in turn)
+    int64_t ntiles;
     int win;       // bytes per channel window (multiple of 16)
     int stages;    // ring depth
     uint32_t one;  // 1, passed at run time so that x * one + acc stays on the multiply-add pipe
@@ -170,8 +172,27 @@ __global__ void __launch_bounds__((kKDM / KW + 1) * 32, 1) dd_tiled_kernel(const
     int32_t *lists = reinterpret_cast<int32_t *>(smem + (size_t)a.stages * slot_bytes);
     uint64_t *bars = reinterpret_cast<uint64_t *>(lists + kCW * kKW * 4 * kCB);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int blk = (int)(blockIdx.x % (unsigned)a.nblk);
-    const int64_t t0 = (int64_t)(blockIdx.x / (unsigned)a.nblk) * kTEff;
+    // CTA order: groups of `grp` DM blocks; inside a group, time tiles with the
+    // group's DM blocks fastest.  CTAs that run together then read input spans
+    // whose union (over the group's delays) stays resident in L2.
+    int blk;
+    int64_t tile;
+    {
+        const int64_t idx = blockIdx.x;
+        const int64_t nfull = a.nblk / a.grp;
+        const int64_t per_group = a.ntiles * a.grp;
+        if (idx < nfull * per_group) {
+            const int64_t g = idx / per_group, r = idx - g * per_group;
+            tile = r / a.grp;
+            blk = (int)(g * a.grp + (r - tile * a.grp));
+        } else {
+            const int64_t rem = a.nblk - nfull * a.grp;
+            const int64_t r = idx - nfull * per_group;
+            tile = r / rem;
+            blk = (int)(nfull * a.grp + (r - tile * rem));
+        }
+    }
+    const int64_t t0 = tile * kTEff;
     const int dm0 = blk * kKDM;
     const int nst = (a.nchan + kCB - 1) / kCB;
     const int32_t *bmin = a.blkmin + (int64_t)blk * a.nchan;
@@ -510,8 +531,10 @@ __global__ void __launch_bounds__((kKDM / KW + 1) * 32, 1) dd_tiled_kernel(const
             const int w = lane + 32 * k;
             const int64_t tt = t0 + 4 * w;
             if (4 * w + 3 < kTEff && tt + 3 < a.n_out) {
-                *reinterpret_cast<int4 *>(orow + tt) =
-                    make_int4((int)acc[i][k][0], (int)acc[i][k][1], (int)acc[i][k][2], (int)acc[i][k][3]);
+                // streaming store: the series is not re-read by this kernel
+                __stcs(reinterpret_cast<int4 *>(orow + tt),
+                       make_int4((int)acc[i][k][0], (int)acc[i][k][1], (int)acc[i][k][2],
+                                 (int)acc[i][k][3]));
             } else {
 #pragma unroll
                 for (int j = 0; j < 4; j++)
@@ -595,6 +618,27 @@ bool plan_dedisperse_tiled(gsp_plan_s *p, std::vector<int32_t> *blkmin) {
     g.stages = (int)stages;
     g.smem = (int)(stages * kCB * win + fixed);
     g.nblk = nblk;
+    // largest group of DM blocks whose per-tile input union (sum over channels of
+    // the delay range across the group plus a window) stays within ~24 MB of L2
+    g.grp = 1;
+    for (int G = nblk; G >= 1; G--) {
+        int64_t worst = 0;
+        for (int b0 = 0; b0 < nblk; b0 += G) {
+            int64_t u = 0;
+            const int d_lo = b0 * kKDM, d_hi = std::min(ndm, (b0 + G) * kKDM) - 1;
+            for (int c = 0; c < C; c++) {
+                const int64_t lo = (*blkmin)[(size_t)b0 * C + c];
+                const int64_t hi = p->delays_h[(size_t)d_hi * C + c];
+                u += std::max<int64_t>(hi - lo, 0) + win;
+            }
+            (void)d_lo;
+            worst = std::max(worst, u);
+        }
+        if (worst <= ((int64_t)24 << 20) || G == 1) {
+            g.grp = G;
+            break;
+        }
+    }
     g.variant = variant;
     return true;
 }
@@ -624,6 +668,7 @@ cudaError_t launch_dedisperse_tiled(const gsp_plan_s *p, const uint8_t *x, int64
     a.nchan = p->desc.nchan;
     a.ndm = p->desc.ndm;
     a.nblk = g.nblk;
+    a.grp = g.grp;
     a.win = g.win;
     a.stages = g.stages;
     a.one = 1u;
@@ -633,6 +678,7 @@ cudaError_t launch_dedisperse_tiled(const gsp_plan_s *p, const uint8_t *x, int64
     a.B = p->desc.block_len;
     a.Ls = (n_out / a.B) * a.B;
     const int64_t ntiles = (n_out + g.t_eff - 1) / g.t_eff;
+    a.ntiles = ntiles;
     const int64_t nctas = ntiles * g.nblk;
     if (nctas > 0x7fffffffll) return cudaErrorInvalidConfiguration;
     v.fn<<<(unsigned)nctas, (kKDM / v.kw + 1) * 32, g.smem, s>>>(a);

@@ -35,6 +35,7 @@ struct DDGeom {
     int stages = 0;    // pipeline depth
     int smem = 0;      // dynamic shared memory bytes
     int nblk = 0;      // DM blocks
+    int grp = 1;       // DM blocks per launch group
     int variant = 0;   // template variant index
 };
 

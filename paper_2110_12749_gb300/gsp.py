@@ -103,6 +103,11 @@ def lib():
                                           ctypes.c_float, ctypes.c_float, _vp, _i64, _vp, _vp],
                                          ctypes.c_int),
             "gsp_plan_launches": ([_vp], ctypes.c_int32),
+            "gsp_stream_create": ([_vp, _vp, _i64, ctypes.c_int32], ctypes.c_int),
+            "gsp_stream_destroy": ([_vp], ctypes.c_int),
+            "gsp_stream_need": ([_vp], _i64),
+            "gsp_stream_push": ([_vp, _vp, _i64, _i64, _vp], ctypes.c_int),
+            "gsp_stream_results": ([_vp, _vp, _i64, _vp, _vp], ctypes.c_int),
             "gsp_status_string": ([ctypes.c_int], ctypes.c_char_p),
             "gsp_last_error_string": ([], ctypes.c_char_p),
             "gsp_version": ([], ctypes.c_int32),
@@ -352,3 +357,58 @@ def gsp_search_series_static(D, n_out, d_cands, d_ncand, t_offset=0, widths=None
         0 if w is None else w.size, block_len, window_len, threshold, bad_lo, bad_hi,
         _vp(d_cands.data_ptr()), max_cands, _vp(d_ncand.data_ptr()), _stream(stream))
     _check(st, "gsp_search_series_static")
+
+
+class Stream:
+    """Owns a gsp_stream_t (and keeps its plan alive)."""
+
+    def __init__(self, handle, plan):
+        self.handle = handle
+        self.plan = plan
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            try:
+                _lib.gsp_stream_destroy(self.handle)
+            except Exception:
+                pass
+            self.handle = None
+
+
+def gsp_stream_create(plan, chunk_out, beam=0):
+    h = _vp()
+    _check(lib().gsp_stream_create(ctypes.byref(h), plan.handle, chunk_out, beam),
+           "gsp_stream_create")
+    return Stream(h, plan)
+
+
+def gsp_stream_destroy(s):
+    if s.handle:
+        st = lib().gsp_stream_destroy(s.handle)
+        s.handle = None
+        _check(st, "gsp_stream_destroy")
+
+
+def gsp_stream_need(s):
+    return int(lib().gsp_stream_need(s.handle))
+
+
+def gsp_stream_push(s, x_host, n, stream=None):
+    """x_host: numpy uint8 [nchan][stride] or a (pinned) CPU torch tensor."""
+    if isinstance(x_host, np.ndarray):
+        ptr, stride = _np_ptr(x_host), x_host.strides[0]
+    else:
+        ptr, stride = _vp(x_host.data_ptr()), x_host.stride(0)
+    _check(lib().gsp_stream_push(s.handle, ptr, n, stride, _stream(stream)), "gsp_stream_push")
+
+
+def gsp_stream_results(s, cap=None):
+    """(candidates with absolute t and the beam label, true count, status, t_abs0)."""
+    if cap is None:
+        cap = int(s.plan.desc.max_cands)
+    out = np.zeros(max(cap, 1), dtype=CAND_DTYPE)
+    n, t0 = ctypes.c_int64(0), ctypes.c_int64(0)
+    st = lib().gsp_stream_results(s.handle, _np_ptr(out), cap, ctypes.byref(n), ctypes.byref(t0))
+    if st not in (GSP_OK, GSP_ERR_CAPACITY):
+        _check(st, "gsp_stream_results")
+    return out[:min(n.value, cap)].copy(), n.value, st, t0.value
