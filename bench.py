@@ -27,6 +27,14 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
+# DRAM bytes (read + write) per algorithmic add of the default dedispersion kernel
+# (variant 10): ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch on the
+# CRAFTS-like beam cut to 131072 samples (1.60 GB + 0.667 GB for 6.899e11 adds), the
+# capture size rule keeping full-size multi-pass captures off the GPU; traffic grows
+# with the number of time tiles, i.e. in proportion to the adds.
+DD_TRAFFIC_BYTES_PER_ADD = (1.60e9 + 0.667e9) / 6.899e11
+DD_TRAFFIC_VARIANT = "default"
+
 NOMINAL_SMS = 152
 INT_LANES_PER_SM = 128          # issue slots per SM per clock (4 schedulers x 32 lanes)
 SM_MAX_MHZ = 2070.0
@@ -402,7 +410,10 @@ def run_gsp(args):
             "dm_chan_samples_per_s": world * adds / (ms_step / 1e3),
             "kernel_ms": {"dedisperse": dd_avg, "search": sum(se_ms) / len(se_ms)},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tadd/s",
-                         "frac": achieved / peak, "traffic": None,
+                         "frac": achieved / peak,
+                         "traffic": (DD_TRAFFIC_BYTES_PER_ADD * adds
+                                     if os.environ.get("GSP_DD_VARIANT", "default") == DD_TRAFFIC_VARIANT
+                                     else None),
                          "peak_basis": "%d SMs x %d int lanes x %.0f MHz (max clock)"
                                        % (nsm, INT_LANES_PER_SM, SM_MAX_MHZ),
                          "frac_at_run_clock": (achieved / (nsm * INT_LANES_PER_SM * clocks["sm_mhz"] * 1e-6)
