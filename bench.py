@@ -56,6 +56,9 @@ def parse():
                     help="beams of the streaming-latency measurement (0: skip)")
     ap.add_argument("--stream-chunks", type=int, default=6,
                     help="chunks per beam in the streaming measurement (the first one primes)")
+    ap.add_argument("--batch-beams", type=int, default=19,
+                    help="beams of the batched multi-beam measurement (0: skip)")
+    ap.add_argument("--batch-steps", type=int, default=3)
     ap.add_argument("--stream-gbs", type=float, default=6.0,
                     help="aggregate arrival rate of the simulated stream (GB/s)")
     ap.add_argument("--variant", type=int, default=-1,
@@ -286,6 +289,70 @@ def run_stream(args, wl, delays_fn):
             "data": "one synthetic primed chunk repeated for every chunk and beam"}
 
 
+def run_batch(args, wl):
+    """19 CRAFTS-like beams with chunk lengths uniform in 2^18..2^20 samples and
+    per-beam DM grids (1000-2500 trials to a maximum DM of 500-1500), searched by
+    one persistent, graph-captured, autotuned gsp_batch launch per step."""
+    import dataclasses
+    import torch
+    from paper_2110_12749_gb300 import gsp, synth
+    rng = np.random.default_rng(synth.BASE_SEED + 99)
+    B = args.batch_beams
+    plans, xs, n_ins, adds, sky = [], [], [], 0.0, 0.0
+    for b in range(B):
+        n_in = int(rng.integers(1 << 18, (1 << 20) + 1)) // 16 * 16
+        ntr = int(rng.integers(1000, 2501))
+        dmax = float(rng.uniform(500.0, 1500.0))
+        step = dmax / ntr
+        desc, keep = gsp.make_desc(wl.nchan, wl.f_lo, wl.f_hi, wl.t_samp, n_in, ndm=ntr,
+                                   dm_lo=0.0, dm_step=step)
+        plan = gsp.gsp_plan_create(desc, keep)
+        n_out = gsp.gsp_plan_nout(plan, n_in)
+        wlb = dataclasses.replace(wl, n_in=n_in, ndm=ntr, dm_step=step,
+                                  pulse_dm=(10.0, dmax), pulse_w=(1, 150), pulse_snr=(5.0, 40.0))
+
+        def delays_fn(dm, wl=wl):
+            d1, k1 = gsp.make_desc(wl.nchan, wl.f_lo, wl.f_hi, wl.t_samp, 1 << 20, dms=[dm])
+            return gsp.gsp_compute_delays(d1)[0][0]
+
+        x, _, _, _ = synth.workload_filterbank(wlb, delays_fn, n_out, beam=b)
+        xs.append(torch.from_numpy(x).cuda())
+        del x
+        plans.append(plan)
+        n_ins.append(n_in)
+        adds += float(ntr) * wl.nchan * n_out
+        sky += n_in * wl.t_samp
+    s = torch.cuda.Stream()
+    flags = gsp.GSP_BATCH_PERSISTENT | gsp.GSP_BATCH_GRAPH | gsp.GSP_BATCH_AUTOTUNE | gsp.GSP_BATCH_TIMING
+    bt = gsp.gsp_batch_create(plans, flags)
+    gsp.gsp_batch_search(bt, xs, n_ins, stream=s)       # autotune + capture
+    variant, tuned_ms, launches = gsp.gsp_batch_info(bt)
+    dd, tot = [], []
+    for _ in range(args.batch_steps):
+        gsp.gsp_batch_search(bt, xs, n_ins, stream=s)   # graph replay
+        a, t = gsp.gsp_batch_timing(bt)
+        dd.append(a)
+        tot.append(t)
+    cands, ncand, _ = gsp.gsp_batch_candidates(bt)
+    gsp.gsp_batch_destroy(bt)
+    for p in plans:
+        gsp.gsp_plan_destroy(p)
+    del xs
+    torch.cuda.empty_cache()
+    ms_dd, ms_tot = float(np.median(dd)), float(np.median(tot))
+    nsm = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    peak = nsm * INT_LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
+    return {"beams": B, "samples_total": int(sum(n_ins)), "sky_s": sky, "adds": adds,
+            "ms_per_batch": ms_tot, "dedisperse_ms": ms_dd,
+            "sky_s_per_s": sky / (ms_tot / 1e3),
+            "dm_chan_samples_per_s": adds / (ms_tot / 1e3),
+            "dedisperse_frac_of_roofline": adds / (ms_dd / 1e3) / 1e12 / peak,
+            "variant": variant, "autotune_best_ms": tuned_ms, "launches_per_batch": launches,
+            "candidates": int(ncand),
+            "launch": "one persistent dedispersion launch for all beams, graph-captured with "
+                      "the per-beam search kernels"}
+
+
 def run_gsp(args):
     import torch
     from paper_2110_12749_gb300 import gsp, synth
@@ -385,11 +452,16 @@ def run_gsp(args):
     peak = nsm * INT_LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
     line = None
     stream_res = None
-    if args.stream_beams > 0 and rank == 0:
-        gsp.gsp_plan_destroy(plan)
-        plan = None
+    batch_res = None
+    if args.stream_beams > 0 or args.batch_beams > 0:
+        if plan is not None:
+            gsp.gsp_plan_destroy(plan)
+            plan = None
         del xd
         torch.cuda.empty_cache()
+    if args.batch_beams > 0 and rank == 0:
+        batch_res = run_batch(args, wl)
+    if args.stream_beams > 0 and rank == 0:
         stream_res = run_stream(args, wl, delays_fn)
     if rank == 0:
         cpu = None
@@ -427,6 +499,8 @@ def run_gsp(args):
         }
         if cpu is not None:
             line["cpu_baseline"] = cpu
+        if batch_res is not None:
+            line["batch"] = batch_res
         if stream_res is not None:
             line["stream"] = stream_res
             line["p99_chunk_latency_ms"] = stream_res["p99_ms"]

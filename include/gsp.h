@@ -61,6 +61,21 @@ typedef enum {
 
 typedef struct gsp_plan_s *gsp_plan_t;
 typedef struct gsp_stream_s *gsp_stream_t;
+typedef struct gsp_batch_s *gsp_batch_t;
+
+/* Batch flags (gsp_batch_create). */
+#define GSP_BATCH_PERSISTENT 1 /* one CTA per SM striding over all beams' work items */
+#define GSP_BATCH_GRAPH 2      /* capture the batch into a CUDA graph, replay while inputs repeat */
+#define GSP_BATCH_AUTOTUNE 4   /* time the tile variants on the first call, keep the fastest */
+#define GSP_BATCH_TIMING 8     /* record CUDA events around the batched dedispersion */
+
+/* Input of one beam of a batch (device filterbank, layout as gsp_dedisperse). */
+typedef struct {
+    const uint8_t *d_x;
+    int64_t n_in;
+    int64_t x_stride;
+    int64_t t_offset;
+} gsp_beam_input;
 
 /* Plan descriptor: host values, copied by gsp_plan_create.  Fill it with
  * gsp_plan_desc_init() first; then set the band, sampling and DM grid. */
@@ -258,6 +273,38 @@ gsp_status gsp_stream_push(gsp_stream_t s, const uint8_t *h_x, int64_t n, int64_
  * sample.  Synchronises. */
 gsp_status gsp_stream_results(gsp_stream_t s, gsp_cand *host_out, int64_t cap, int64_t *n_total,
                               int64_t *t_abs0);
+
+/* Batched search of up to 32 beams, one plan per beam (each plan its own DM
+ * grid and maximum length; all plans the same channel count and tiled
+ * dedispersion).  The dedispersion of all beams is one kernel launch over a
+ * work list of (beam, time tile, DM block) items (the multi-beam receiver of
+ * Sec. 2 searched in one pass); every beam is then searched with its plan's
+ * settings and its candidates stay in its plan. */
+gsp_status gsp_batch_create(gsp_batch_t *out, const gsp_plan_t *plans, int32_t nbeams,
+                            int32_t flags);
+gsp_status gsp_batch_destroy(gsp_batch_t b);
+
+/* Search every beam: inputs[i] for plan i (same rules as gsp_search, series
+ * into each plan's scratch).  With GSP_BATCH_GRAPH the enqueue sequence is
+ * captured on the first call (and again whenever an input changes) and
+ * replayed, which needs a created stream (not the legacy NULL stream); with
+ * GSP_BATCH_AUTOTUNE the first call also times the tile
+ * variants on these inputs.  The first call may therefore allocate and
+ * synchronise; later calls with the same inputs are asynchronous on stream. */
+gsp_status gsp_batch_search(gsp_batch_t b, const gsp_beam_input *inputs, void *stream);
+
+/* Candidates of the last batch search, sorted by (beam, dm_idx, t), beam set to
+ * the plan's index in the batch; *n_total = the true total.  Synchronises. */
+gsp_status gsp_batch_candidates(gsp_batch_t b, gsp_cand *host_out, int64_t cap, int64_t *n_total);
+
+/* Device durations (ms) of the batched dedispersion launch and of the whole
+ * batch of the last call (events recorded on its stream, replayed with the
+ * graph); requires GSP_BATCH_TIMING.  Synchronises. */
+gsp_status gsp_batch_timing(gsp_batch_t b, float *ms_dedisperse, float *ms_total);
+
+/* The dedispersion variant in use, the autotuner's best batch time (ms, 0 if
+ * not tuned) and the kernel launches of the last call (captured ones counted). */
+gsp_status gsp_batch_info(gsp_batch_t b, int32_t *variant, float *tuned_ms, int32_t *launches);
 
 /* Static text for a status code. */
 const char *gsp_status_string(gsp_status s);

@@ -1,0 +1,246 @@
+// Batched search of many beams (the multi-beam receiver of the survey in
+// Sec. 2): every beam has its own plan (DM grid, length), all beams share the
+// channel count, and their dedispersion runs as ONE launch of the tiled kernel
+// whose CTAs work through a list of (beam, time tile, DM block) items.  With
+// GSP_BATCH_PERSISTENT the grid is one CTA per SM striding over the items; with
+// GSP_BATCH_GRAPH the whole enqueue sequence (block-sum resets, the batched
+// dedispersion, every beam's search kernels) is captured once into a CUDA
+// graph and replayed while the inputs stay the same; with GSP_BATCH_AUTOTUNE
+// the first call times every compatible tile variant of the dedispersion
+// kernel on the actual inputs and keeps the fastest.
+#include <algorithm>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "gsp_internal.cuh"
+
+struct gsp_batch_s {
+    std::vector<gsp_plan_t> plans;
+    int32_t flags = 0;
+    int variant = -1;
+    float tuned_ms = 0.f;
+    std::vector<gsp_beam_input> last;  // inputs the graph was captured for
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaStream_t last_stream = nullptr;
+    bool have_search = false;
+    int32_t launches = 0;
+    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};  // GSP_BATCH_TIMING
+};
+
+namespace {
+
+bool same_inputs(const std::vector<gsp_beam_input> &a, const gsp_beam_input *b, size_t n) {
+    if (a.size() != n) return false;
+    for (size_t i = 0; i < n; i++)
+        if (std::memcmp(&a[i], &b[i], sizeof(gsp_beam_input)) != 0) return false;
+    return true;
+}
+
+void drop_graph(gsp_batch_s *b) {
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    b->exec = nullptr;
+    b->graph = nullptr;
+}
+
+// Enqueue the whole batch on stream s with dedispersion variant `variant`.
+gsp_status enqueue(gsp_batch_s *b, const gsp_beam_input *in, int variant, cudaStream_t s,
+                   int32_t *nlaunch) {
+    const int nb = (int)b->plans.size();
+    std::vector<gsp::BeamLaunch> bl((size_t)nb);
+    std::vector<int64_t> n_out((size_t)nb);
+    for (int i = 0; i < nb; i++) {
+        gsp_plan_s *p = b->plans[i];
+        int32_t *D = nullptr;
+        int64_t stride = 0;
+        unsigned long long *bsum = nullptr;
+        gsp_status st = gsp::plan_check_input(p, in[i].d_x, in[i].n_in, in[i].x_stride, &n_out[i]);
+        if (st == GSP_OK) st = gsp::plan_prepare_search(p, n_out[i], &D, &stride, &bsum);
+        if (st != GSP_OK) return st;
+        if (bsum && cudaMemsetAsync(bsum, 0, (size_t)p->desc.ndm * p->nb_max * 3 * sizeof(*bsum), s) !=
+                        cudaSuccess)
+            return GSP_ERR_CUDA;
+        if (cudaMemsetAsync(p->d_ncand, 0, sizeof(unsigned long long), s) != cudaSuccess)
+            return GSP_ERR_CUDA;
+        bl[i] = gsp::BeamLaunch{p, in[i].d_x, in[i].n_in, in[i].x_stride, n_out[i], D, stride, bsum};
+    }
+    gsp_plan_s *p0 = b->plans[0];
+    const bool timed = (b->flags & GSP_BATCH_TIMING) && b->ev[0];
+    if (timed && cudaEventRecord(b->ev[0], s) != cudaSuccess) return GSP_ERR_CUDA;
+    if (gsp::launch_dedisperse_batch(bl.data(), nb, variant, (b->flags & GSP_BATCH_PERSISTENT) != 0,
+                                     p0->num_sms, p0->d_err, s, nlaunch) != cudaSuccess)
+        return GSP_ERR_CUDA;
+    if (timed && cudaEventRecord(b->ev[1], s) != cudaSuccess) return GSP_ERR_CUDA;
+    for (int i = 0; i < nb; i++) {
+        gsp_plan_s *p = b->plans[i];
+        if (gsp::launch_search(p, bl[i].out, n_out[i], bl[i].out_stride, in[i].t_offset, nullptr,
+                               bl[i].bsum, s, nlaunch) != cudaSuccess)
+            return GSP_ERR_CUDA;
+        p->last_stream = s;
+        p->last_nout = n_out[i];
+        p->last_nb = n_out[i] / p->desc.block_len;
+        p->have_search = true;
+    }
+    if (timed && cudaEventRecord(b->ev[2], s) != cudaSuccess) return GSP_ERR_CUDA;
+    return GSP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+gsp_status gsp_batch_create(gsp_batch_t *out, const gsp_plan_t *plans, int32_t nbeams,
+                            int32_t flags) {
+    if (!out || !plans || nbeams < 1 || nbeams > 32) return GSP_ERR_INVALID_ARG;
+    *out = nullptr;
+    for (int i = 0; i < nbeams; i++) {
+        if (!plans[i] || plans[i]->simple_dd || plans[i]->desc.nchan != plans[0]->desc.nchan)
+            return GSP_ERR_INVALID_ARG;
+        for (int j = 0; j < i; j++)
+            if (plans[j] == plans[i]) return GSP_ERR_INVALID_ARG;  // one plan per beam
+    }
+    gsp_batch_s *b = new (std::nothrow) gsp_batch_s();
+    if (!b) return GSP_ERR_OOM;
+    b->plans.assign(plans, plans + nbeams);
+    b->flags = flags;
+    b->variant = plans[0]->geom.variant;
+    if (flags & GSP_BATCH_TIMING)
+        for (auto &e : b->ev)
+            if (cudaEventCreate(&e) != cudaSuccess) {
+                delete b;
+                return GSP_ERR_CUDA;
+            }
+    *out = b;
+    return GSP_OK;
+}
+
+gsp_status gsp_batch_destroy(gsp_batch_t b) {
+    if (!b) return GSP_ERR_INVALID_ARG;
+    cudaError_t e = cudaDeviceSynchronize();
+    drop_graph(b);
+    for (auto &ev : b->ev)
+        if (ev) cudaEventDestroy(ev);
+    delete b;
+    return e == cudaSuccess ? GSP_OK : GSP_ERR_CUDA;
+}
+
+gsp_status gsp_batch_search(gsp_batch_t b, const gsp_beam_input *in, void *stream) {
+    if (!b || !in) return GSP_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((b->flags & GSP_BATCH_GRAPH) && s == nullptr) return GSP_ERR_INVALID_ARG;  // needs a capturable stream
+    const size_t nb = b->plans.size();
+    b->launches = 0;
+    if ((b->flags & GSP_BATCH_AUTOTUNE) && b->tuned_ms == 0.f) {
+        // time every variant that fits this batch; keep the fastest
+        cudaEvent_t e0, e1;
+        if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+            return GSP_ERR_CUDA;
+        int best = -1;
+        float best_ms = 0.f;
+        const int *cand = nullptr;
+        const int ncand = gsp::dedisperse_tune_candidates(&cand);
+        for (int ci = 0; ci < ncand; ci++) {
+            const int v = cand[ci];
+            int32_t nl = 0;
+            gsp_status st = enqueue(b, in, v, s, &nl);  // warm-up (also sets attributes)
+            if (st == GSP_ERR_CUDA) {
+                (void)cudaGetLastError();
+                continue;  // variant does not fit (shared memory), skip it
+            }
+            if (st != GSP_OK) return st;
+            cudaEventRecord(e0, s);
+            if (enqueue(b, in, v, s, &nl) != GSP_OK) return GSP_ERR_CUDA;
+            cudaEventRecord(e1, s);
+            if (cudaEventSynchronize(e1) != cudaSuccess) return GSP_ERR_CUDA;
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (best < 0 || ms < best_ms) {
+                best = v;
+                best_ms = ms;
+            }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        if (best < 0) return GSP_ERR_CUDA;
+        b->variant = best;
+        b->tuned_ms = best_ms;
+        drop_graph(b);
+    }
+    if (b->flags & GSP_BATCH_GRAPH) {
+        if (!b->exec || !same_inputs(b->last, in, nb)) {
+            drop_graph(b);
+            // one uncaptured run configures kernel attributes and allocates scratch
+            int32_t nl = 0;
+            gsp_status st = enqueue(b, in, b->variant, s, &nl);
+            if (st != GSP_OK) return st;
+            if (cudaStreamSynchronize(s) != cudaSuccess) return GSP_ERR_CUDA;
+            if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+                return GSP_ERR_CUDA;
+            st = enqueue(b, in, b->variant, s, &b->launches);
+            cudaGraph_t g = nullptr;
+            cudaError_t e = cudaStreamEndCapture(s, &g);
+            if (st != GSP_OK || e != cudaSuccess) {
+                if (g) cudaGraphDestroy(g);
+                return st != GSP_OK ? st : GSP_ERR_CUDA;
+            }
+            b->graph = g;
+            if (cudaGraphInstantiate(&b->exec, g, 0) != cudaSuccess) {
+                drop_graph(b);
+                return GSP_ERR_CUDA;
+            }
+            b->last.assign(in, in + nb);
+        }
+        if (cudaGraphLaunch(b->exec, s) != cudaSuccess) return GSP_ERR_CUDA;
+    } else {
+        gsp_status st = enqueue(b, in, b->variant, s, &b->launches);
+        if (st != GSP_OK) return st;
+    }
+    b->last_stream = s;
+    b->have_search = true;
+    return GSP_OK;
+}
+
+gsp_status gsp_batch_candidates(gsp_batch_t b, gsp_cand *host_out, int64_t cap, int64_t *n_total) {
+    if (!b || !n_total || cap < 0 || (cap > 0 && !host_out)) return GSP_ERR_INVALID_ARG;
+    if (!b->have_search) return GSP_ERR_STATE;
+    int64_t total = 0, stored = 0;
+    gsp_status worst = GSP_OK;
+    for (size_t i = 0; i < b->plans.size(); i++) {
+        int64_t n = 0;
+        gsp_status st = gsp_candidates(b->plans[i], host_out ? host_out + stored : nullptr,
+                                       cap - stored, &n);
+        if (st != GSP_OK && st != GSP_ERR_CAPACITY) return st;
+        if (st == GSP_ERR_CAPACITY) worst = GSP_ERR_CAPACITY;
+        const int64_t m = std::min<int64_t>(n, cap - stored);
+        for (int64_t k = 0; k < m; k++) host_out[stored + k].beam = (int32_t)i;
+        stored += m;
+        total += n;
+    }
+    *n_total = total;
+    return worst;
+}
+
+gsp_status gsp_batch_timing(gsp_batch_t b, float *ms_dedisperse, float *ms_total) {
+    if (!b) return GSP_ERR_INVALID_ARG;
+    if (!(b->flags & GSP_BATCH_TIMING) || !b->have_search) return GSP_ERR_STATE;
+    if (cudaEventSynchronize(b->ev[2]) != cudaSuccess) return GSP_ERR_CUDA;
+    float a = 0.f, t = 0.f;
+    if (cudaEventElapsedTime(&a, b->ev[0], b->ev[1]) != cudaSuccess ||
+        cudaEventElapsedTime(&t, b->ev[0], b->ev[2]) != cudaSuccess)
+        return GSP_ERR_CUDA;
+    if (ms_dedisperse) *ms_dedisperse = a;
+    if (ms_total) *ms_total = t;
+    return GSP_OK;
+}
+
+gsp_status gsp_batch_info(gsp_batch_t b, int32_t *variant, float *tuned_ms, int32_t *launches) {
+    if (!b) return GSP_ERR_INVALID_ARG;
+    if (variant) *variant = b->variant;
+    if (tuned_ms) *tuned_ms = b->tuned_ms;
+    if (launches) *launches = b->launches;
+    return GSP_OK;
+}
+
+}  // extern "C"

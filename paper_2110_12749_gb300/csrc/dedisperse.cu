@@ -26,6 +26,7 @@
 // masked even-byte view instead of the raw one.
 #include <algorithm>
 #include <cstdlib>
+#include <cstring>
 #include <vector>
 
 #include "dd_tiled.cuh"
@@ -88,9 +89,11 @@ cudaError_t launch_dedisperse_simple(const gsp_plan_s *p, const uint8_t *x, int6
 namespace {
 
 constexpr int kKDM = 16;         // DM trials per CTA (= consumer warps x DM trials per warp)
+constexpr int kMaxBatchBeams = 32;  // beams per launch
 constexpr long long kWaitBudget = 4000000000ll;  // ~2 s of SM clock per wait
 
-struct TiledArgs {
+// One beam of a launch: its input, delay tables, output and tiling.
+struct BeamTile {
     const uint8_t *x;
     int64_t x_stride;
     int64_t n_in;
@@ -99,20 +102,57 @@ struct TiledArgs {
     const int32_t *blkmin;  // [nblk][nchan]
     int32_t *out;
     int64_t out_stride;
-    int nchan;
+    unsigned long long *bsum;  // optional [ndm][nb_max][3] block sums {S0, S1, S2}
+    int64_t nb_max;
+    int64_t Ls;      // searched length: block_len * floor(n_out / block_len)
+    int64_t ntiles;  // time tiles
+    int64_t item0;   // first work item of this beam
     int ndm;
     int nblk;
-    int grp;       // DM blocks per launch group (groups sweep all time tiles in turn)
-    int64_t ntiles;
+    int grp;         // DM blocks per launch group (groups sweep all time tiles in turn)
+    int B;           // block_len (>= stored tile length, so a tile touches at most two blocks)
+};
+
+// A launch: one or more beams (same channel count) and their work items, one
+// item per (beam, time tile, DM block).  With one CTA per item (grid = items)
+// or persistent CTAs striding over the items (grid < items); the staging ring
+// then runs on across items, so a CTA's next tile is prefetched while its
+// current one is summed.
+struct TiledArgs {
+    BeamTile beam[kMaxBatchBeams];
+    int nbeams;
+    int nchan;
     int win;       // bytes per channel window (multiple of 16)
     int stages;    // ring depth
     uint32_t one;  // 1, passed at run time so that x * one + acc stays on the multiply-add pipe
     int *err;      // set to 1 if a bounded wait gave up
-    unsigned long long *bsum;  // optional [ndm][nb_max][3] block sums {S0, S1, S2}
-    int64_t nb_max;
-    int64_t Ls;    // searched length: block_len * floor(n_out / block_len)
-    int B;         // block_len (>= stored tile length, so a tile touches at most two blocks)
+    int64_t items;
 };
+
+// Work item -> beam, time tile and DM block.  Inside a beam: groups of `grp`
+// DM blocks; inside a group, time tiles with the group's DM blocks fastest, so
+// that items that run together read input spans whose union (over the group's
+// delays) stays resident in L2.
+__device__ __forceinline__ void decode_item(const TiledArgs &a, int64_t item, int *bi,
+                                            int64_t *tile, int *blk) {
+    int b = 0;
+    while (b + 1 < a.nbeams && item >= a.beam[b + 1].item0) b++;
+    const BeamTile &bt = a.beam[b];
+    const int64_t idx = item - bt.item0;
+    const int64_t nfull = bt.nblk / bt.grp;
+    const int64_t per_group = bt.ntiles * bt.grp;
+    if (idx < nfull * per_group) {
+        const int64_t g = idx / per_group, r = idx - g * per_group;
+        *tile = r / bt.grp;
+        *blk = (int)(g * bt.grp + (r - *tile * bt.grp));
+    } else {
+        const int64_t rem = bt.nblk - nfull * bt.grp;
+        const int64_t r = idx - nfull * per_group;
+        *tile = r / rem;
+        *blk = (int)(nfull * bt.grp + (r - *tile * rem));
+    }
+    *bi = b;
+}
 
 __device__ __forceinline__ uint32_t lanemask_lt() {
     uint32_t m;
@@ -172,30 +212,7 @@ __global__ void __launch_bounds__((kKDM / KW + 1) * 32, 1) dd_tiled_kernel(const
     int32_t *lists = reinterpret_cast<int32_t *>(smem + (size_t)a.stages * slot_bytes);
     uint64_t *bars = reinterpret_cast<uint64_t *>(lists + kCW * kKW * 4 * kCB);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    // CTA order: groups of `grp` DM blocks; inside a group, time tiles with the
-    // group's DM blocks fastest.  CTAs that run together then read input spans
-    // whose union (over the group's delays) stays resident in L2.
-    int blk;
-    int64_t tile;
-    {
-        const int64_t idx = blockIdx.x;
-        const int64_t nfull = a.nblk / a.grp;
-        const int64_t per_group = a.ntiles * a.grp;
-        if (idx < nfull * per_group) {
-            const int64_t g = idx / per_group, r = idx - g * per_group;
-            tile = r / a.grp;
-            blk = (int)(g * a.grp + (r - tile * a.grp));
-        } else {
-            const int64_t rem = a.nblk - nfull * a.grp;
-            const int64_t r = idx - nfull * per_group;
-            tile = r / rem;
-            blk = (int)(nfull * a.grp + (r - tile * rem));
-        }
-    }
-    const int64_t t0 = tile * kTEff;
-    const int dm0 = blk * kKDM;
     const int nst = (a.nchan + kCB - 1) / kCB;
-    const int32_t *bmin = a.blkmin + (int64_t)blk * a.nchan;
     auto full = [&](int i) { return ptx::smem_addr(bars + i); };
     auto empty = [&](int i) { return ptx::smem_addr(bars + a.stages + i); };
 
@@ -210,10 +227,18 @@ __global__ void __launch_bounds__((kKDM / KW + 1) * 32, 1) dd_tiled_kernel(const
 
     if (warp == kCW) {
         // ------------------------------------------------------- producer warp
-        int issued = 0;
+        int64_t gst = 0;  // stages issued by this CTA so far (across items)
         bool ok = true;
-        for (int st = 0; st < nst && ok; st++) {
-            const int slot = st % a.stages, round = st / a.stages;
+        for (int64_t item = blockIdx.x; item < a.items && ok; item += gridDim.x) {
+        int bi, blk;
+        int64_t tile;
+        decode_item(a, item, &bi, &tile, &blk);
+        const BeamTile &bt = a.beam[bi];
+        const int64_t t0 = tile * kTEff;
+        const int32_t *bmin = bt.blkmin + (int64_t)blk * a.nchan;
+        for (int st = 0; st < nst && ok; st++, gst++) {
+            const int slot = (int)(gst % a.stages);
+            const int64_t round = gst / a.stages;
             if (round > 0) {
                 const bool w = ptx::mbar_wait(empty(slot), (round - 1) & 1, kWaitBudget);
                 if (!__all_sync(0xffffffffu, w)) {
@@ -232,7 +257,7 @@ __global__ void __launch_bounds__((kKDM / KW + 1) * 32, 1) dd_tiled_kernel(const
                 len16[h] = 0;
                 if (c < a.nchan) {
                     s_c[h] = (t0 + bmin[c]) & ~(int64_t)15;
-                    avail[h] = a.n_in - s_c[h];
+                    avail[h] = bt.n_in - s_c[h];
                     len16[h] = (uint32_t)min((int64_t)a.win, avail[h] & ~(int64_t)15);
                 }
                 tot += len16[h];
@@ -249,22 +274,23 @@ __global__ void __launch_bounds__((kKDM / KW + 1) * 32, 1) dd_tiled_kernel(const
                 const int c = st * kCB + h * 32 + lane;
                 uint8_t *dst = smem + (size_t)slot * slot_bytes + (size_t)(h * 32 + lane) * a.win;
                 if (len16[h] > 0) {
-                    const uint8_t *src = a.x + (int64_t)c * a.x_stride + s_c[h];
+                    const uint8_t *src = bt.x + (int64_t)c * bt.x_stride + s_c[h];
                     ptx::bulk_g2s(ptx::smem_addr(dst), src, len16[h], full(slot));
                 }
                 if (c < a.nchan) {
                     const int64_t end = min((int64_t)a.win, avail[h]);
                     for (int64_t i = len16[h]; i < end; i++)
-                        dst[i] = a.x[(int64_t)c * a.x_stride + s_c[h] + i];
+                        dst[i] = bt.x[(int64_t)c * bt.x_stride + s_c[h] + i];
                 }
             }
             ptx::mbar_arrive(full(slot));
-            issued = st + 1;
+        }
         }
         if (!ok && lane == 0) fail(a.err);
         // never leave with copies in flight: wait for the last phase of each slot
-        for (int st = max(0, issued - a.stages); st < issued; st++) {
-            const bool w = ptx::mbar_wait(full(st % a.stages), (st / a.stages) & 1, kWaitBudget);
+        for (int64_t st = max((int64_t)0, gst - a.stages); st < gst; st++) {
+            const bool w = ptx::mbar_wait(full((int)(st % a.stages)), (uint32_t)((st / a.stages) & 1),
+                                          kWaitBudget);
             if (!__all_sync(0xffffffffu, w)) {
                 if (lane == 0) fail(a.err);
                 break;
@@ -274,8 +300,21 @@ __global__ void __launch_bounds__((kKDM / KW + 1) * 32, 1) dd_tiled_kernel(const
     }
 
     // ------------------------------------------------------- consumer warps
-    const int dmw = dm0 + warp * kKW;
     int32_t *mylist = lists + warp * (kKW * 4 * kCB);
+    const uint32_t one = a.one;
+    const uint32_t lmask = lanemask_lt();
+    const uint32_t smem32 = ptx::smem_addr(smem);
+    const uint32_t lane4 = 4u * lane;
+    int64_t gst = 0;  // stages consumed by this CTA so far (across items)
+    for (int64_t item = blockIdx.x; item < a.items; item += gridDim.x) {
+    int bi, blk;
+    int64_t tile;
+    decode_item(a, item, &bi, &tile, &blk);
+    const BeamTile &bt = a.beam[bi];
+    const int64_t t0 = tile * kTEff;
+    const int dm0 = blk * kKDM;
+    const int32_t *bmin = bt.blkmin + (int64_t)blk * a.nchan;
+    const int dmw = dm0 + warp * kKW;
     uint32_t acc[kKW][kM][4];
     uint32_t E[kKW][4][kM], O[kKW][4][kM];
 #pragma unroll
@@ -287,10 +326,6 @@ __global__ void __launch_bounds__((kKDM / KW + 1) * 32, 1) dd_tiled_kernel(const
 #pragma unroll
             for (int p = 0; p < 4; p++) E[i][p][k] = O[i][p][k] = 0;
         }
-    const uint32_t one = a.one;
-    const uint32_t lmask = lanemask_lt();
-    const uint32_t smem32 = ptx::smem_addr(smem);
-    const uint32_t lane4 = 4u * lane;
     // delays of the next stage are loaded one stage ahead (hides L2 latency)
     int nx_min[kH], nx_dl[kKW][kH];
 #pragma unroll
@@ -300,11 +335,12 @@ __global__ void __launch_bounds__((kKDM / KW + 1) * 32, 1) dd_tiled_kernel(const
         nx_min[h] = v0 ? bmin[c0] : 0;
 #pragma unroll
         for (int i = 0; i < kKW; i++)
-            nx_dl[i][h] = v0 ? a.delays[(int64_t)min(dmw + i, a.ndm - 1) * a.nchan + c0] : 0;
+            nx_dl[i][h] = v0 ? bt.delays[(int64_t)min(dmw + i, bt.ndm - 1) * a.nchan + c0] : 0;
     }
 
-    for (int st = 0; st < nst; st++) {
-        const int slot = st % a.stages, round = st / a.stages;
+    for (int st = 0; st < nst; st++, gst++) {
+        const int slot = (int)(gst % a.stages);
+        const int64_t round = gst / a.stages;
         int cur_min[kH], cur_dl[kKW][kH];
 #pragma unroll
         for (int h = 0; h < kH; h++) {
@@ -316,7 +352,7 @@ __global__ void __launch_bounds__((kKDM / KW + 1) * 32, 1) dd_tiled_kernel(const
             nx_min[h] = vn ? bmin[cn] : 0;
 #pragma unroll
             for (int i = 0; i < kKW; i++)
-                nx_dl[i][h] = vn ? a.delays[(int64_t)min(dmw + i, a.ndm - 1) * a.nchan + cn] : 0;
+                nx_dl[i][h] = vn ? bt.delays[(int64_t)min(dmw + i, bt.ndm - 1) * a.nchan + cn] : 0;
         }
         int cnt[kKW][4];
 #pragma unroll
@@ -477,12 +513,12 @@ __global__ void __launch_bounds__((kKDM / KW + 1) * 32, 1) dd_tiled_kernel(const
 #pragma unroll
     for (int i = 0; i < kKW; i++) {
         const int d = dmw + i;
-        if (d >= a.ndm) continue;
-        if (a.bsum != nullptr) {
+        if (d >= bt.ndm) continue;
+        if (bt.bsum != nullptr) {
             // exact sums of the stored samples for the (at most two) search blocks
             // the tile touches: S0 = sum D, S1 = sum j D (j inside the block), S2 = sum D^2
-            const int64_t ba = t0 / a.B;
-            const int64_t tb = (ba + 1) * a.B;
+            const int64_t ba = t0 / bt.B;
+            const int64_t tb = (ba + 1) * bt.B;
             long long sm[2][3] = {{0, 0, 0}, {0, 0, 0}};
 #pragma unroll
             for (int k = 0; k < kM; k++) {
@@ -490,11 +526,11 @@ __global__ void __launch_bounds__((kKDM / KW + 1) * 32, 1) dd_tiled_kernel(const
 #pragma unroll
                 for (int j = 0; j < 4; j++) {
                     const int64_t t = t0 + 4 * w + j;
-                    if (4 * w + j < kTEff && t < a.Ls) {
+                    if (4 * w + j < kTEff && t < bt.Ls) {
                         const long long v = (long long)(int32_t)acc[i][k][j];
                         if (t < tb) {
                             sm[0][0] += v;
-                            sm[0][1] += (t - ba * a.B) * v;
+                            sm[0][1] += (t - ba * bt.B) * v;
                             sm[0][2] += v * v;
                         } else {
                             sm[1][0] += v;
@@ -517,20 +553,20 @@ __global__ void __launch_bounds__((kKDM / KW + 1) * 32, 1) dd_tiled_kernel(const
 #pragma unroll
                 for (int h = 0; h < 2; h++) {
                     const int64_t b = ba + h;
-                    if (b * a.B < a.Ls) {
-                        unsigned long long *q = a.bsum + ((int64_t)d * a.nb_max + b) * 3;
+                    if (b * bt.B < bt.Ls) {
+                        unsigned long long *q = bt.bsum + ((int64_t)d * bt.nb_max + b) * 3;
 #pragma unroll
                         for (int f = 0; f < 3; f++) atomicAdd(q + f, (unsigned long long)sm[h][f]);
                     }
                 }
             }
         }
-        int32_t *orow = a.out + (int64_t)d * a.out_stride;
+        int32_t *orow = bt.out + (int64_t)d * bt.out_stride;
 #pragma unroll
         for (int k = 0; k < kM; k++) {
             const int w = lane + 32 * k;
             const int64_t tt = t0 + 4 * w;
-            if (4 * w + 3 < kTEff && tt + 3 < a.n_out) {
+            if (4 * w + 3 < kTEff && tt + 3 < bt.n_out) {
                 // streaming store: the series is not re-read by this kernel
                 __stcs(reinterpret_cast<int4 *>(orow + tt),
                        make_int4((int)acc[i][k][0], (int)acc[i][k][1], (int)acc[i][k][2],
@@ -538,10 +574,11 @@ __global__ void __launch_bounds__((kKDM / KW + 1) * 32, 1) dd_tiled_kernel(const
             } else {
 #pragma unroll
                 for (int j = 0; j < 4; j++)
-                    if (4 * w + j < kTEff && tt + j < a.n_out) orow[tt + j] = (int32_t)acc[i][k][j];
+                    if (4 * w + j < kTEff && tt + j < bt.n_out) orow[tt + j] = (int32_t)acc[i][k][j];
             }
         }
     }
+    }  // items
 }
 
 // Per-DM-block minimum delay per channel, the largest spread of delays within
@@ -618,6 +655,7 @@ bool plan_dedisperse_tiled(gsp_plan_s *p, std::vector<int32_t> *blkmin) {
     g.stages = (int)stages;
     g.smem = (int)(stages * kCB * win + fixed);
     g.nblk = nblk;
+    g.spread = spread;
     // largest group of DM blocks whose per-tile input union (sum over channels of
     // the delay range across the group plus a window) stays within ~24 MB of L2
     g.grp = 1;
@@ -643,47 +681,96 @@ bool plan_dedisperse_tiled(gsp_plan_s *p, std::vector<int32_t> *blkmin) {
     return true;
 }
 
+int dedisperse_num_variants() { return kNumVariants; }
+
+// Variants the batch autotuner times (the fastest family on this GPU).
+const int kTuneList[] = {10, 11, 8, 9};
+int dedisperse_tune_candidates(const int **list) {
+    *list = kTuneList;
+    return (int)(sizeof(kTuneList) / sizeof(kTuneList[0]));
+}
+
+cudaError_t launch_dedisperse_batch(const BeamLaunch *beams, int nbeams, int variant,
+                                    bool persistent, int num_sms, int *err, cudaStream_t s,
+                                    int32_t *nlaunch) {
+    if (nbeams < 1 || nbeams > kMaxBatchBeams || variant < 0 || variant >= kNumVariants)
+        return cudaErrorInvalidValue;
+    const TiledVariant &v = kVariants[variant];
+    const int t_cta = 128 * v.m, t_eff = t_cta - 4;
+    const int nchan = beams[0].plan->desc.nchan;
+    int64_t win = 0;
+    for (int b = 0; b < nbeams; b++) {
+        const gsp_plan_s *p = beams[b].plan;
+        if (p->desc.nchan != nchan || !p->d_blkmin) return cudaErrorInvalidValue;
+        win = std::max<int64_t>(win, (t_cta + 15 + p->geom.spread + 15) & ~(int64_t)15);
+    }
+    const int64_t fixed = (int64_t)kKDM * 4 * v.cb * 4 + 2 * 8 * 8;
+    const int64_t stages = std::min<int64_t>(8, (227 * 1024 - fixed) / ((int64_t)v.cb * win));
+    if (stages < 2) return cudaErrorInvalidValue;
+    const int smem = (int)(stages * v.cb * win + fixed);
+    static int configured_smem[kNumVariants] = {0};
+    if (smem > configured_smem[variant]) {
+        cudaError_t e = cudaFuncSetAttribute(v.fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             smem);
+        if (e != cudaSuccess) return e;
+        configured_smem[variant] = smem;
+    }
+    TiledArgs a;
+    std::memset(&a, 0, sizeof(a));
+    int64_t items = 0;
+    for (int b = 0; b < nbeams; b++) {
+        const BeamLaunch &in = beams[b];
+        const gsp_plan_s *p = in.plan;
+        BeamTile &bt = a.beam[b];
+        bt.x = in.x;
+        bt.x_stride = in.x_stride;
+        bt.n_in = in.n_in;
+        bt.n_out = in.n_out;
+        bt.delays = p->d_delays;
+        bt.blkmin = p->d_blkmin;
+        bt.out = in.out;
+        bt.out_stride = in.out_stride;
+        bt.bsum = in.bsum;
+        bt.nb_max = p->nb_max;
+        bt.B = p->desc.block_len;
+        bt.Ls = (in.n_out / bt.B) * bt.B;
+        bt.ntiles = (in.n_out + t_eff - 1) / t_eff;
+        bt.item0 = items;
+        bt.ndm = p->desc.ndm;
+        bt.nblk = p->geom.nblk;
+        bt.grp = p->geom.grp;
+        if (in.bsum && bt.B < t_eff) return cudaErrorInvalidValue;
+        items += bt.ntiles * bt.nblk;
+    }
+    a.nbeams = nbeams;
+    a.nchan = nchan;
+    a.win = (int)win;
+    a.stages = (int)stages;
+    a.one = 1u;
+    a.err = err;
+    a.items = items;
+    int64_t grid = persistent ? std::min<int64_t>(items, num_sms) : items;
+    if (grid < 1 || grid > 0x7fffffffll) return cudaErrorInvalidConfiguration;
+    v.fn<<<(unsigned)grid, (kKDM / v.kw + 1) * 32, smem, s>>>(a);
+    *nlaunch += 1;
+    return cudaGetLastError();
+}
+
 cudaError_t launch_dedisperse_tiled(const gsp_plan_s *p, const uint8_t *x, int64_t n_in,
                                     int64_t x_stride, int64_t n_out, int32_t *out,
                                     int64_t out_stride, unsigned long long *bsum,
                                     cudaStream_t s, int32_t *nlaunch) {
-    const DDGeom &g = p->geom;
-    const TiledVariant &v = kVariants[g.variant];
-    static int configured_smem[kNumVariants] = {0};
-    if (g.smem > configured_smem[g.variant]) {
-        cudaError_t e = cudaFuncSetAttribute(v.fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             g.smem);
-        if (e != cudaSuccess) return e;
-        configured_smem[g.variant] = g.smem;
-    }
-    TiledArgs a;
-    a.x = x;
-    a.x_stride = x_stride;
-    a.n_in = n_in;
-    a.n_out = n_out;
-    a.delays = p->d_delays;
-    a.blkmin = p->d_blkmin;
-    a.out = out;
-    a.out_stride = out_stride;
-    a.nchan = p->desc.nchan;
-    a.ndm = p->desc.ndm;
-    a.nblk = g.nblk;
-    a.grp = g.grp;
-    a.win = g.win;
-    a.stages = g.stages;
-    a.one = 1u;
-    a.err = p->d_err;
-    a.bsum = bsum;
-    a.nb_max = p->nb_max;
-    a.B = p->desc.block_len;
-    a.Ls = (n_out / a.B) * a.B;
-    const int64_t ntiles = (n_out + g.t_eff - 1) / g.t_eff;
-    a.ntiles = ntiles;
-    const int64_t nctas = ntiles * g.nblk;
-    if (nctas > 0x7fffffffll) return cudaErrorInvalidConfiguration;
-    v.fn<<<(unsigned)nctas, (kKDM / v.kw + 1) * 32, g.smem, s>>>(a);
-    *nlaunch += 1;
-    return cudaGetLastError();
+    BeamLaunch b;
+    b.plan = p;
+    b.x = x;
+    b.n_in = n_in;
+    b.x_stride = x_stride;
+    b.n_out = n_out;
+    b.out = out;
+    b.out_stride = out_stride;
+    b.bsum = bsum;
+    return launch_dedisperse_batch(&b, 1, p->geom.variant, false, p->num_sms, p->d_err, s,
+                                   nlaunch);
 }
 
 }  // namespace gsp

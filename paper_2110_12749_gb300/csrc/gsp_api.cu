@@ -205,6 +205,27 @@ gsp_status run_search(gsp_plan_s *p, const int32_t *D, int64_t n_out, int64_t st
 
 }  // namespace
 
+namespace gsp {
+
+// Used by the batch module: make sure the plan's series scratch exists and
+// tell whether block sums can be fused into the tiled dedispersion kernel.
+gsp_status plan_prepare_search(gsp_plan_s *p, int64_t n_out, int32_t **D, int64_t *stride,
+                               unsigned long long **bsum) {
+    gsp_status st = ensure_scratch_D(p, n_out);
+    if (st != GSP_OK) return st;
+    *D = p->d_D;
+    *stride = (n_out + 3) & ~(int64_t)3;
+    *bsum = (fused_stats(p) && n_out / p->desc.block_len > 0) ? p->d_bsum : nullptr;
+    return GSP_OK;
+}
+
+gsp_status plan_check_input(gsp_plan_s *p, const uint8_t *x, int64_t n_in, int64_t x_stride,
+                            int64_t *n_out) {
+    return check_dd_args(p, x, n_in, x_stride, nullptr, 0, n_out);
+}
+
+}  // namespace gsp
+
 extern "C" {
 
 gsp_status gsp_plan_desc_init(gsp_plan_desc *d) {

@@ -36,6 +36,7 @@ struct DDGeom {
     int smem = 0;      // dynamic shared memory bytes
     int nblk = 0;      // DM blocks
     int grp = 1;       // DM blocks per launch group
+    int64_t spread = 0;  // largest delay spread inside a DM block
     int variant = 0;   // template variant index
 };
 
@@ -90,6 +91,30 @@ namespace gsp {
 cudaError_t launch_dedisperse_simple(const gsp_plan_s *p, const uint8_t *x, int64_t x_stride,
                                      int64_t n_out, int32_t *out, int64_t out_stride,
                                      cudaStream_t s, int32_t *nlaunch);
+// One beam of a batched dedispersion launch.
+struct BeamLaunch {
+    const gsp_plan_s *plan;
+    const uint8_t *x;
+    int64_t n_in, x_stride, n_out;
+    int32_t *out;
+    int64_t out_stride;
+    unsigned long long *bsum;  // optional block sums (zeroed by the caller)
+};
+
+// All beams (same channel count, at most 32) in one launch of the tiled kernel
+// `variant`; persistent = at most num_sms CTAs striding over the work items.
+cudaError_t launch_dedisperse_batch(const BeamLaunch *beams, int nbeams, int variant,
+                                    bool persistent, int num_sms, int *err, cudaStream_t s,
+                                    int32_t *nlaunch);
+int dedisperse_num_variants();
+int dedisperse_tune_candidates(const int **list);
+
+// gsp_api.cu helpers shared with the batch module.
+gsp_status plan_prepare_search(gsp_plan_s *p, int64_t n_out, int32_t **D, int64_t *stride,
+                               unsigned long long **bsum);
+gsp_status plan_check_input(gsp_plan_s *p, const uint8_t *x, int64_t n_in, int64_t x_stride,
+                            int64_t *n_out);
+
 // bsum (optional): int64 [ndm][nb_max][3] exact block sums {S0, S1, S2} over
 // blocks of block_len samples, accumulated atomically (must be zeroed first).
 cudaError_t launch_dedisperse_tiled(const gsp_plan_s *p, const uint8_t *x, int64_t n_in,

@@ -29,6 +29,10 @@ GSP_ERR_TOO_LARGE = 10
 
 GSP_FLAG_TIMING = 1
 GSP_FLAG_SIMPLE_DD = 2
+GSP_BATCH_PERSISTENT = 1
+GSP_BATCH_GRAPH = 2
+GSP_BATCH_AUTOTUNE = 4
+GSP_BATCH_TIMING = 8
 
 DEFAULT_WIDTHS = (1, 2, 3, 4, 6, 9, 14, 20, 30, 45, 70, 100, 150)
 
@@ -108,6 +112,12 @@ def lib():
             "gsp_stream_need": ([_vp], _i64),
             "gsp_stream_push": ([_vp, _vp, _i64, _i64, _vp], ctypes.c_int),
             "gsp_stream_results": ([_vp, _vp, _i64, _vp, _vp], ctypes.c_int),
+            "gsp_batch_create": ([_vp, _vp, ctypes.c_int32, ctypes.c_int32], ctypes.c_int),
+            "gsp_batch_destroy": ([_vp], ctypes.c_int),
+            "gsp_batch_search": ([_vp, _vp, _vp], ctypes.c_int),
+            "gsp_batch_candidates": ([_vp, _vp, _i64, _vp], ctypes.c_int),
+            "gsp_batch_info": ([_vp, _vp, _vp, _vp], ctypes.c_int),
+            "gsp_batch_timing": ([_vp, _vp, _vp], ctypes.c_int),
             "gsp_status_string": ([ctypes.c_int], ctypes.c_char_p),
             "gsp_last_error_string": ([], ctypes.c_char_p),
             "gsp_version": ([], ctypes.c_int32),
@@ -412,3 +422,73 @@ def gsp_stream_results(s, cap=None):
     if st not in (GSP_OK, GSP_ERR_CAPACITY):
         _check(st, "gsp_stream_results")
     return out[:min(n.value, cap)].copy(), n.value, st, t0.value
+
+
+class gsp_beam_input(ctypes.Structure):
+    _fields_ = [("d_x", ctypes.c_void_p), ("n_in", ctypes.c_int64),
+                ("x_stride", ctypes.c_int64), ("t_offset", ctypes.c_int64)]
+
+
+class Batch:
+    """Owns a gsp_batch_t and keeps its plans alive."""
+
+    def __init__(self, handle, plans):
+        self.handle = handle
+        self.plans = plans
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            try:
+                _lib.gsp_batch_destroy(self.handle)
+            except Exception:
+                pass
+            self.handle = None
+
+
+def gsp_batch_create(plans, flags=0):
+    arr = (ctypes.c_void_p * len(plans))(*[p.handle.value for p in plans])
+    h = _vp()
+    _check(lib().gsp_batch_create(ctypes.byref(h), arr, len(plans), flags), "gsp_batch_create")
+    return Batch(h, list(plans))
+
+
+def gsp_batch_destroy(b):
+    if b.handle:
+        st = lib().gsp_batch_destroy(b.handle)
+        b.handle = None
+        _check(st, "gsp_batch_destroy")
+
+
+def gsp_batch_search(b, xs, n_ins, t_offsets=None, stream=None):
+    """xs: torch uint8 CUDA tensors [nchan][stride], one per beam."""
+    n = len(xs)
+    arr = (gsp_beam_input * n)()
+    for i, x in enumerate(xs):
+        arr[i].d_x = x.data_ptr()
+        arr[i].n_in = n_ins[i]
+        arr[i].x_stride = x.stride(0)
+        arr[i].t_offset = 0 if t_offsets is None else t_offsets[i]
+    b._inputs = arr
+    _check(lib().gsp_batch_search(b.handle, arr, _stream(stream)), "gsp_batch_search")
+
+
+def gsp_batch_candidates(b, cap=1 << 22):
+    out = np.zeros(max(cap, 1), dtype=CAND_DTYPE)
+    n = ctypes.c_int64(0)
+    st = lib().gsp_batch_candidates(b.handle, _np_ptr(out), cap, ctypes.byref(n))
+    if st not in (GSP_OK, GSP_ERR_CAPACITY):
+        _check(st, "gsp_batch_candidates")
+    return out[:min(n.value, cap)].copy(), n.value, st
+
+
+def gsp_batch_info(b):
+    v, ms, nl = ctypes.c_int32(0), ctypes.c_float(0), ctypes.c_int32(0)
+    _check(lib().gsp_batch_info(b.handle, ctypes.byref(v), ctypes.byref(ms), ctypes.byref(nl)),
+           "gsp_batch_info")
+    return v.value, ms.value, nl.value
+
+
+def gsp_batch_timing(b):
+    a, t = ctypes.c_float(0), ctypes.c_float(0)
+    _check(lib().gsp_batch_timing(b.handle, ctypes.byref(a), ctypes.byref(t)), "gsp_batch_timing")
+    return a.value, t.value
