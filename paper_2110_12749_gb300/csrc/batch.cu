@@ -68,11 +68,18 @@ gsp_status enqueue(gsp_batch_s *b, const gsp_beam_input *in, int variant, cudaSt
     }
     gsp_plan_s *p0 = b->plans[0];
     const bool timed = (b->flags & GSP_BATCH_TIMING) && b->ev[0];
-    if (timed && cudaEventRecord(b->ev[0], s) != cudaSuccess) return GSP_ERR_CUDA;
+    cudaStreamCaptureStatus cst = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cst) != cudaSuccess) return GSP_ERR_CUDA;
+    const bool capturing = cst == cudaStreamCaptureStatusActive;
+    if (timed && cudaEventRecordWithFlags(b->ev[0], s, capturing ? cudaEventRecordExternal : 0) !=
+                     cudaSuccess)
+        return GSP_ERR_CUDA;
     if (gsp::launch_dedisperse_batch(bl.data(), nb, variant, (b->flags & GSP_BATCH_PERSISTENT) != 0,
                                      p0->num_sms, p0->d_err, s, nlaunch) != cudaSuccess)
         return GSP_ERR_CUDA;
-    if (timed && cudaEventRecord(b->ev[1], s) != cudaSuccess) return GSP_ERR_CUDA;
+    if (timed && cudaEventRecordWithFlags(b->ev[1], s, capturing ? cudaEventRecordExternal : 0) !=
+                     cudaSuccess)
+        return GSP_ERR_CUDA;
     for (int i = 0; i < nb; i++) {
         gsp_plan_s *p = b->plans[i];
         if (gsp::launch_search(p, bl[i].out, n_out[i], bl[i].out_stride, in[i].t_offset, nullptr,
@@ -83,7 +90,9 @@ gsp_status enqueue(gsp_batch_s *b, const gsp_beam_input *in, int variant, cudaSt
         p->last_nb = n_out[i] / p->desc.block_len;
         p->have_search = true;
     }
-    if (timed && cudaEventRecord(b->ev[2], s) != cudaSuccess) return GSP_ERR_CUDA;
+    if (timed && cudaEventRecordWithFlags(b->ev[2], s, capturing ? cudaEventRecordExternal : 0) !=
+                     cudaSuccess)
+        return GSP_ERR_CUDA;
     return GSP_OK;
 }
 
@@ -149,13 +158,20 @@ gsp_status gsp_batch_search(gsp_batch_t b, const gsp_beam_input *in, void *strea
                 (void)cudaGetLastError();
                 continue;  // variant does not fit (shared memory), skip it
             }
+            if (cudaStreamSynchronize(s) != cudaSuccess) return GSP_ERR_CUDA;
             if (st != GSP_OK) return st;
-            cudaEventRecord(e0, s);
-            if (enqueue(b, in, v, s, &nl) != GSP_OK) return GSP_ERR_CUDA;
-            cudaEventRecord(e1, s);
-            if (cudaEventSynchronize(e1) != cudaSuccess) return GSP_ERR_CUDA;
+            cudaError_t ce = cudaEventRecord(e0, s);
+            if (ce == cudaSuccess && enqueue(b, in, v, s, &nl) != GSP_OK) ce = cudaErrorLaunchFailure;
+            if (ce == cudaSuccess) ce = cudaEventRecord(e1, s);
+            if (ce == cudaSuccess) ce = cudaEventSynchronize(e1);
             float ms = 0.f;
-            cudaEventElapsedTime(&ms, e0, e1);
+            if (ce == cudaSuccess) ce = cudaEventElapsedTime(&ms, e0, e1);
+            if (ce != cudaSuccess) {
+                gsp::record_error(ce, "batch autotune timing");
+                cudaEventDestroy(e0);
+                cudaEventDestroy(e1);
+                return GSP_ERR_CUDA;
+            }
             if (best < 0 || ms < best_ms) {
                 best = v;
                 best_ms = ms;

@@ -70,29 +70,23 @@ __device__ __forceinline__ uint32_t lds32(uint32_t addr) {
 
 // N words at addr + 128 * k (k < N): the words one lane owns in a 4-sample
 // word interleave of a warp (immediate offsets, one address register).
+template <int K, int N>
+struct LdsWords {
+    __device__ __forceinline__ static void run(uint32_t addr, uint32_t (&w)[N]) {
+        asm volatile("ld.shared.u32 %0, [%1+%2];" : "=r"(w[K]) : "r"(addr), "n"(K * 128));
+        LdsWords<K + 1, N>::run(addr, w);
+    }
+};
+template <int N>
+struct LdsWords<N, N> {
+    __device__ __forceinline__ static void run(uint32_t, uint32_t (&)[N]) {}
+};
+
+// N words at addr + 128 * k (k < N): the words one lane owns in a 4-sample
+// word interleave of a warp (immediate offsets, one address register).
 template <int N>
 __device__ __forceinline__ void lds_words(uint32_t addr, uint32_t (&w)[N]) {
-    static_assert(N == 4 || N == 8, "4 or 8 words");
-    if (N == 4) {
-        asm volatile(
-            "ld.shared.u32 %0, [%4];\n\t"
-            "ld.shared.u32 %1, [%4+128];\n\t"
-            "ld.shared.u32 %2, [%4+256];\n\t"
-            "ld.shared.u32 %3, [%4+384];"
-            : "=r"(w[0]), "=r"(w[1]), "=r"(w[2]), "=r"(w[3])
-            : "r"(addr));
-    } else {
-#pragma unroll
-        for (int k = 0; k < N; k += 4) {
-            asm volatile(
-                "ld.shared.u32 %0, [%4];\n\t"
-                "ld.shared.u32 %1, [%4+128];\n\t"
-                "ld.shared.u32 %2, [%4+256];\n\t"
-                "ld.shared.u32 %3, [%4+384];"
-                : "=r"(w[k]), "=r"(w[k + 1]), "=r"(w[k + 2]), "=r"(w[k + 3])
-                : "r"(addr + 128u * k));
-        }
-    }
+    LdsWords<0, N>::run(addr, w);
 }
 
 __device__ __forceinline__ uint2 lds64(uint32_t addr) {

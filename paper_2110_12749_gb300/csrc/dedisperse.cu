@@ -171,6 +171,56 @@ __device__ __forceinline__ void fail(int *err) { atomicExch(err, 1); }
 // O is summed on the multiply-add pipe; since w = (b0 + 2^16 b2) + 2^8 O(w),
 // the even-byte sums are E - (O << 8) mod 2^32, exact while the 16-bit lanes
 // cannot overflow.
+// Flush one phase family P into the int32 accumulators: recover the four
+// byte sums of each word, add the ones that belong to this lane's word, and
+// pass the ones that belong to the previous word (phase P > 0 only) one lane
+// down: the previous word of (lane, k) is (lane - 1, k), or (31, k - 1) for
+// lane 0.
+template <int P, int M, int ACC>
+__device__ __forceinline__ void flush_family(uint32_t (&E)[M], uint32_t (&O)[M],
+                                             uint32_t (&acc)[M][4], int lane) {
+    uint32_t sp[M][3];
+#pragma unroll
+    for (int k = 0; k < M; k++) {
+        sp[k][0] = sp[k][1] = sp[k][2] = 0;
+        const uint32_t o = O[k];
+        const uint32_t e = ACC == 3 ? E[k] - (o << 8) : E[k];
+        const uint32_t b[4] = {e & 0xffffu, o & 0xffffu, e >> 16, o >> 16};
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            const int jj = q - P;
+            if (jj >= 0) acc[k][jj] += b[q];
+            else sp[k][jj + 3] += b[q];
+        }
+        E[k] = O[k] = 0;
+    }
+    if (P > 0) {
+#pragma unroll
+        for (int k = 0; k < M; k++) {
+#pragma unroll
+            for (int jj = 3 - P; jj < 3; jj++) {
+                const uint32_t r = __shfl_sync(0xffffffffu, sp[k][jj], (lane + 1) & 31);
+                const uint32_t rn =
+                    (k + 1 < M) ? __shfl_sync(0xffffffffu, sp[(k + 1) % M][jj], (lane + 1) & 31) : 0u;
+                if (lane < 31) acc[k][jj + 1] += r;
+                else if (k + 1 < M) acc[k][jj + 1] += rn;
+            }
+        }
+    }
+}
+
+// The same with the family chosen at run time (a constant after unrolling).
+template <int M, int ACC>
+__device__ __forceinline__ void flush_family_p(int P, uint32_t (&E)[M], uint32_t (&O)[M],
+                                               uint32_t (&acc)[M][4], int lane) {
+    switch (P) {
+        case 0: flush_family<0, M, ACC>(E, O, acc, lane); break;
+        case 1: flush_family<1, M, ACC>(E, O, acc, lane); break;
+        case 2: flush_family<2, M, ACC>(E, O, acc, lane); break;
+        default: flush_family<3, M, ACC>(E, O, acc, lane); break;
+    }
+}
+
 template <int ACC>
 __device__ __forceinline__ void acc_pair(uint32_t &E, uint32_t &O, uint32_t w1, uint32_t w2,
                                          uint32_t one) {
@@ -197,7 +247,9 @@ __device__ __forceinline__ void acc_pair(uint32_t &E, uint32_t &O, uint32_t w1, 
 // M: 4-sample words per lane, T = 128 M output samples computed per tile and
 // T - 4 stored (the tile's last word is incomplete by construction).
 // CB: channels per shared-memory stage (a multiple of 32).
-template <int KW, bool QUAD, int ACC, bool A32 = false, int M = 4, int CB = 32>
+// FF: flush each phase family only when its own channel count would pass 256
+// (instead of all families every 256 channels).
+template <int KW, bool QUAD, int ACC, bool A32 = false, int M = 4, int CB = 32, bool FF = false>
 __global__ void __launch_bounds__((kKDM / KW + 1) * 32, 1) dd_tiled_kernel(const TiledArgs a) {
     constexpr int kCB = CB;
     constexpr int kH = CB / 32;                  // channels per lane per stage
@@ -326,6 +378,11 @@ __global__ void __launch_bounds__((kKDM / KW + 1) * 32, 1) dd_tiled_kernel(const
 #pragma unroll
             for (int p = 0; p < 4; p++) E[i][p][k] = O[i][p][k] = 0;
         }
+    int famcnt[kKW][4];  // channels accumulated per family since its last flush (FF)
+#pragma unroll
+    for (int i = 0; i < kKW; i++)
+#pragma unroll
+        for (int P = 0; P < 4; P++) famcnt[i][P] = 0;
     // delays of the next stage are loaded one stage ahead (hides L2 latency)
     int nx_min[kH], nx_dl[kKW][kH];
 #pragma unroll
@@ -389,13 +446,20 @@ __global__ void __launch_bounds__((kKDM / KW + 1) * 32, 1) dd_tiled_kernel(const
             return;
         }
         const uint32_t *lanebase = reinterpret_cast<const uint32_t *>(smem) + lane;
-        if (A32) {
+        if constexpr (A32) {
             // explicit 32-bit shared addresses, immediate offsets per word
 #pragma unroll
             for (int i = 0; i < kKW; i++) {
 #pragma unroll
                 for (int P = 0; P < 4; P++) {
                     const int n = cnt[i][P];
+                    if constexpr (FF) {
+                        if (famcnt[i][P] + n > 256) {
+                            flush_family_p<kM, ACC>(P, E[i][P], O[i][P], acc[i], lane);
+                            famcnt[i][P] = 0;
+                        }
+                        famcnt[i][P] += n;
+                    }
                     const int32_t *lp = mylist + (i * 4 + P) * kCB;
                     int j = 0;
 #pragma unroll 2
@@ -426,6 +490,13 @@ __global__ void __launch_bounds__((kKDM / KW + 1) * 32, 1) dd_tiled_kernel(const
 #pragma unroll
             for (int P = 0; P < 4; P++) {
                 const int n = cnt[i][P];
+                if constexpr (FF) {
+                    if (famcnt[i][P] + n > 256) {
+                        flush_family_p<kM, ACC>(P, E[i][P], O[i][P], acc[i], lane);
+                        famcnt[i][P] = 0;
+                    }
+                    famcnt[i][P] += n;
+                }
                 const int32_t *lp = mylist + (i * 4 + P) * kCB;
                 int j = 0;
                 if (QUAD) {
@@ -468,7 +539,15 @@ __global__ void __launch_bounds__((kKDM / KW + 1) * 32, 1) dd_tiled_kernel(const
         __syncwarp();
         if (lane == 0) ptx::mbar_arrive(empty(slot));
 
-        if ((st + 1) % kFlushStages == 0 || st == nst - 1) {
+        if (FF && st == nst - 1) {
+#pragma unroll
+            for (int i = 0; i < kKW; i++) {
+                flush_family<0, kM, ACC>(E[i][0], O[i][0], acc[i], lane);
+                flush_family<1, kM, ACC>(E[i][1], O[i][1], acc[i], lane);
+                flush_family<2, kM, ACC>(E[i][2], O[i][2], acc[i], lane);
+                flush_family<3, kM, ACC>(E[i][3], O[i][3], acc[i], lane);
+            }
+        } else if (!FF && ((st + 1) % kFlushStages == 0 || st == nst - 1)) {
 #pragma unroll
             for (int i = 0; i < kKW; i++) {
                 uint32_t sp[kM][3];
@@ -606,6 +685,8 @@ const TiledVariant kVariants[] = {
     {dd_tiled_kernel<1, false, 3, true>, 1, 4, 32},
     {dd_tiled_kernel<1, false, 3, false, 4, 64>, 1, 4, 64},
     {dd_tiled_kernel<1, true, 3, false, 4, 64>, 1, 4, 64},
+    {dd_tiled_kernel<1, false, 3, false, 4, 64, true>, 1, 4, 64},
+    {dd_tiled_kernel<1, false, 3, false, 4, 32, true>, 1, 4, 32},
 };
 constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
 constexpr int kDefaultVariant = 10;
@@ -684,7 +765,7 @@ bool plan_dedisperse_tiled(gsp_plan_s *p, std::vector<int32_t> *blkmin) {
 int dedisperse_num_variants() { return kNumVariants; }
 
 // Variants the batch autotuner times (the fastest family on this GPU).
-const int kTuneList[] = {10, 11, 8, 9};
+const int kTuneList[] = {12, 10, 13, 8};
 int dedisperse_tune_candidates(const int **list) {
     *list = kTuneList;
     return (int)(sizeof(kTuneList) / sizeof(kTuneList[0]));

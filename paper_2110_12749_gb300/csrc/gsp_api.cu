@@ -207,6 +207,8 @@ gsp_status run_search(gsp_plan_s *p, const int32_t *D, int64_t n_out, int64_t st
 
 namespace gsp {
 
+void record_error(cudaError_t e, const char *what) { set_err(e, what); }
+
 // Used by the batch module: make sure the plan's series scratch exists and
 // tell whether block sums can be fused into the tiled dedispersion kernel.
 gsp_status plan_prepare_search(gsp_plan_s *p, int64_t n_out, int32_t **D, int64_t *stride,

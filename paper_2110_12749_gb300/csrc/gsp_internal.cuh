@@ -110,6 +110,7 @@ int dedisperse_num_variants();
 int dedisperse_tune_candidates(const int **list);
 
 // gsp_api.cu helpers shared with the batch module.
+void record_error(cudaError_t e, const char *what);
 gsp_status plan_prepare_search(gsp_plan_s *p, int64_t n_out, int32_t **D, int64_t *stride,
                                unsigned long long **bsum);
 gsp_status plan_check_input(gsp_plan_s *p, const uint8_t *x, int64_t n_in, int64_t x_stride,
