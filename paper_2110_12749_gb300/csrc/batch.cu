@@ -26,6 +26,7 @@ struct gsp_batch_s {
     cudaStream_t last_stream = nullptr;
     bool have_search = false;
     int32_t launches = 0;
+    int32_t graph_launches = 0;  // kernels in the captured graph
     cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};  // GSP_BATCH_TIMING
 };
 
@@ -207,8 +208,10 @@ gsp_status gsp_batch_search(gsp_batch_t b, const gsp_beam_input *in, void *strea
                 return GSP_ERR_CUDA;
             }
             b->last.assign(in, in + nb);
+            b->graph_launches = b->launches;
         }
         if (cudaGraphLaunch(b->exec, s) != cudaSuccess) return GSP_ERR_CUDA;
+        b->launches = b->graph_launches;
     } else {
         gsp_status st = enqueue(b, in, b->variant, s, &b->launches);
         if (st != GSP_OK) return st;

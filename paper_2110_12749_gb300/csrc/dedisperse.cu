@@ -280,6 +280,9 @@ __global__ void __launch_bounds__((kKDM / KW + 1) * 32, 1) dd_tiled_kernel(const
     if (warp == kCW) {
         // ------------------------------------------------------- producer warp
         int64_t gst = 0;  // stages issued by this CTA so far (across items)
+        int slot = 0;           // ring slot of the next stage
+        uint32_t rpar = 0;      // parity of the slot's current round
+        bool wrapped = false;   // the ring has been filled once
         bool ok = true;
         for (int64_t item = blockIdx.x; item < a.items && ok; item += gridDim.x) {
         int bi, blk;
@@ -289,10 +292,8 @@ __global__ void __launch_bounds__((kKDM / KW + 1) * 32, 1) dd_tiled_kernel(const
         const int64_t t0 = tile * kTEff;
         const int32_t *bmin = bt.blkmin + (int64_t)blk * a.nchan;
         for (int st = 0; st < nst && ok; st++, gst++) {
-            const int slot = (int)(gst % a.stages);
-            const int64_t round = gst / a.stages;
-            if (round > 0) {
-                const bool w = ptx::mbar_wait(empty(slot), (round - 1) & 1, kWaitBudget);
+            if (wrapped) {
+                const bool w = ptx::mbar_wait(empty(slot), rpar ^ 1u, kWaitBudget);
                 if (!__all_sync(0xffffffffu, w)) {
                     ok = false;
                     break;
@@ -336,6 +337,11 @@ __global__ void __launch_bounds__((kKDM / KW + 1) * 32, 1) dd_tiled_kernel(const
                 }
             }
             ptx::mbar_arrive(full(slot));
+            if (++slot == a.stages) {
+                slot = 0;
+                rpar ^= 1u;
+                wrapped = true;
+            }
         }
         }
         if (!ok && lane == 0) fail(a.err);
@@ -357,7 +363,8 @@ __global__ void __launch_bounds__((kKDM / KW + 1) * 32, 1) dd_tiled_kernel(const
     const uint32_t lmask = lanemask_lt();
     const uint32_t smem32 = ptx::smem_addr(smem);
     const uint32_t lane4 = 4u * lane;
-    int64_t gst = 0;  // stages consumed by this CTA so far (across items)
+    int slot = 0;       // ring slot of the next stage (no 64-bit division per stage)
+    uint32_t rpar = 0;  // parity of the slot's current round
     for (int64_t item = blockIdx.x; item < a.items; item += gridDim.x) {
     int bi, blk;
     int64_t tile;
@@ -395,9 +402,7 @@ __global__ void __launch_bounds__((kKDM / KW + 1) * 32, 1) dd_tiled_kernel(const
             nx_dl[i][h] = v0 ? bt.delays[(int64_t)min(dmw + i, bt.ndm - 1) * a.nchan + c0] : 0;
     }
 
-    for (int st = 0; st < nst; st++, gst++) {
-        const int slot = (int)(gst % a.stages);
-        const int64_t round = gst / a.stages;
+    for (int st = 0; st < nst; st++) {
         int cur_min[kH], cur_dl[kKW][kH];
 #pragma unroll
         for (int h = 0; h < kH; h++) {
@@ -440,7 +445,7 @@ __global__ void __launch_bounds__((kKDM / KW + 1) * 32, 1) dd_tiled_kernel(const
             }
         }
         __syncwarp();
-        const bool landed = ptx::mbar_wait(full(slot), round & 1, kWaitBudget);
+        const bool landed = ptx::mbar_wait(full(slot), rpar, kWaitBudget);
         if (!__all_sync(0xffffffffu, landed)) {
             if (lane == 0) fail(a.err);
             return;
@@ -538,6 +543,10 @@ __global__ void __launch_bounds__((kKDM / KW + 1) * 32, 1) dd_tiled_kernel(const
         }
         __syncwarp();
         if (lane == 0) ptx::mbar_arrive(empty(slot));
+        if (++slot == a.stages) {
+            slot = 0;
+            rpar ^= 1u;
+        }
 
         if (FF && st == nst - 1) {
 #pragma unroll
