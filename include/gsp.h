@@ -211,6 +211,16 @@ gsp_status gsp_plan_timing(gsp_plan_t plan, float *ms_dedisperse, float *ms_sear
 /* Kernel launches the last gsp_search / gsp_dedisperse call made. */
 int32_t gsp_plan_launches(gsp_plan_t plan);
 
+/* Tile variants of the dedispersion kernel (a tuning knob with no paper
+ * counterpart; every variant computes the same bit-exact series).  Returns
+ * the number of variants; if plan is not NULL and in_use is not NULL, writes
+ * the variant the plan uses, or -1 if it uses the simple kernel.  A plan's
+ * variant is chosen at gsp_plan_create: the default, or the index in the
+ * environment variable GSP_DD_VARIANT if that is in range (variants that need
+ * the packed delay lists fall back to the default when the largest delay is
+ * 2^23 samples or more). */
+int32_t gsp_dedisperse_variants(gsp_plan_t plan, int32_t *in_use);
+
 /* Search of caller-provided dedispersed series that allocates nothing: for
  * callers that may not call cudaMalloc (for instance a real-time ingest loop
  * whose latency budget a device allocation would break, or an application

@@ -100,6 +100,8 @@ struct BeamTile {
     int64_t n_out;
     const int32_t *delays;  // [ndm][nchan]
     const int32_t *blkmin;  // [nblk][nchan]
+    const int32_t *dpos;    // [ndm][nchan] (delay << 8) | list position (64-channel stages)
+    const uint32_t *fcnt;   // [ndm][nst64] channels per phase family, 4 x 8 bits
     int32_t *out;
     int64_t out_stride;
     unsigned long long *bsum;  // optional [ndm][nb_max][3] block sums {S0, S1, S2}
@@ -242,6 +244,64 @@ __device__ __forceinline__ void acc_pair(uint32_t &E, uint32_t &O, uint32_t w1, 
     }
 }
 
+// Merged flush (raw + odd views): combine the four phase families in 16-bit
+// lanes before unpacking.  Every channel belongs to exactly one family, so
+// the contributions of all families to one output slot still come from at
+// most 256 channels and fit a 16-bit lane.  With e_P = E_P - (O_P << 8)
+// (bytes 0 and 2 of family P) and o_P = O_P (bytes 1 and 3), byte q of family
+// P lands in slot q - P, so for this word
+//   A = [slot 0 | slot 2] = e0 + o1 + (e2 >> 16) + (o3 >> 16)
+//   B = [slot 1 | slot 3] = o0 + (e1 >> 16) + (o2 >> 16)
+// and the bytes that land in the previous word (negative slots) are
+//   SA = [0 | slot 2] = (e2 + o3) << 16,  SB = [slot 1 | slot 3] = e3 + ((e1 + o2) << 16).
+// The int32 accumulators then take lo + 2^16 hi (acc[k][0], acc[k][1]) and
+// hi (acc[k][2], acc[k][3]); merged_decode() recovers lo at the end.
+template <int M>
+__device__ __forceinline__ void flush_merged(uint32_t (&E)[4][M], uint32_t (&O)[4][M],
+                                             uint32_t (&acc)[M][4], int lane) {
+    uint32_t A[M], B[M], SA[M], SB[M];
+#pragma unroll
+    for (int k = 0; k < M; k++) {
+        const uint32_t o0 = O[0][k], o1 = O[1][k], o2 = O[2][k], o3 = O[3][k];
+        const uint32_t e0 = E[0][k] - (o0 << 8), e1 = E[1][k] - (o1 << 8);
+        const uint32_t e2 = E[2][k] - (o2 << 8), e3 = E[3][k] - (o3 << 8);
+        A[k] = e0 + o1 + (e2 >> 16) + (o3 >> 16);
+        B[k] = o0 + (e1 >> 16) + (o2 >> 16);
+        SA[k] = (e2 + o3) << 16;
+        SB[k] = e3 + ((e1 + o2) << 16);
+#pragma unroll
+        for (int P = 0; P < 4; P++) E[P][k] = O[P][k] = 0;
+    }
+    // previous word of (lane, k) is (lane - 1, k), or (31, k - 1) for lane 0
+    uint32_t rA[M], rB[M];
+#pragma unroll
+    for (int k = 0; k < M; k++) {
+        rA[k] = __shfl_sync(0xffffffffu, SA[k], (lane + 1) & 31);
+        rB[k] = __shfl_sync(0xffffffffu, SB[k], (lane + 1) & 31);
+    }
+#pragma unroll
+    for (int k = 0; k < M; k++) {
+        const uint32_t xa = lane < 31 ? rA[k] : (k + 1 < M ? rA[(k + 1) % M] : 0u);
+        const uint32_t xb = lane < 31 ? rB[k] : (k + 1 < M ? rB[(k + 1) % M] : 0u);
+        const uint32_t a = A[k] + xa, b = B[k] + xb;
+        acc[k][0] += a;
+        acc[k][2] += a >> 16;
+        acc[k][1] += b;
+        acc[k][3] += b >> 16;
+    }
+}
+
+// acc[k][0] = sum lo + 2^16 sum hi (mod 2^32) and acc[k][2] = sum hi: slot 0
+// is acc[k][0] - (acc[k][2] << 16), exact since the true sum is below 2^32.
+template <int M>
+__device__ __forceinline__ void merged_decode(uint32_t (&acc)[M][4]) {
+#pragma unroll
+    for (int k = 0; k < M; k++) {
+        acc[k][0] -= acc[k][2] << 16;
+        acc[k][1] -= acc[k][3] << 16;
+    }
+}
+
 // KW: DM trials per consumer warp; kCW = kKDM / KW consumer warps + 1 producer.
 // QUAD: visit channels four at a time (more loads in flight per warp).
 // M: 4-sample words per lane, T = 128 M output samples computed per tile and
@@ -249,8 +309,15 @@ __device__ __forceinline__ void acc_pair(uint32_t &E, uint32_t &O, uint32_t w1, 
 // CB: channels per shared-memory stage (a multiple of 32).
 // FF: flush each phase family only when its own channel count would pass 256
 // (instead of all families every 256 channels).
-template <int KW, bool QUAD, int ACC, bool A32 = false, int M = 4, int CB = 32, bool FF = false>
+// PRE: the phase-sorted channel lists come from the plan's precomputed list
+// positions (the phase of a (channel, DM) pair is delay & 3 in every tile,
+// since tiles start at multiples of 4 samples), not from a per-stage ballot sort.
+// MF: merged flush of the four phase families (flush_merged).
+template <int KW, bool QUAD, int ACC, bool A32 = false, int M = 4, int CB = 32, bool FF = false,
+          bool PRE = false, bool MF = false>
 __global__ void __launch_bounds__((kKDM / KW + 1) * 32, 1) dd_tiled_kernel(const TiledArgs a) {
+    static_assert(!PRE || (KW == 1 && CB == 64), "precomputed lists: one DM per warp, 64-channel stages");
+    static_assert(!MF || (ACC == 3 && !FF), "merged flush: raw + odd views, all families together");
     constexpr int kCB = CB;
     constexpr int kH = CB / 32;                  // channels per lane per stage
     constexpr int kFlushStages = 256 / kCB;      // stages between SWAR flushes (256 channels)
@@ -391,7 +458,11 @@ __global__ void __launch_bounds__((kKDM / KW + 1) * 32, 1) dd_tiled_kernel(const
 #pragma unroll
         for (int P = 0; P < 4; P++) famcnt[i][P] = 0;
     // delays of the next stage are loaded one stage ahead (hides L2 latency)
+    // PRE: nx_dl holds the packed (delay << 8) | list position instead of the delay
+    const int32_t *dtab = PRE ? bt.dpos : bt.delays;
+    const uint32_t *fcrow = PRE ? bt.fcnt + (int64_t)min(dmw, bt.ndm - 1) * nst : nullptr;
     int nx_min[kH], nx_dl[kKW][kH];
+    uint32_t nx_fc = PRE ? fcrow[0] : 0u;
 #pragma unroll
     for (int h = 0; h < kH; h++) {
         const int c0 = h * 32 + lane;
@@ -399,11 +470,13 @@ __global__ void __launch_bounds__((kKDM / KW + 1) * 32, 1) dd_tiled_kernel(const
         nx_min[h] = v0 ? bmin[c0] : 0;
 #pragma unroll
         for (int i = 0; i < kKW; i++)
-            nx_dl[i][h] = v0 ? bt.delays[(int64_t)min(dmw + i, bt.ndm - 1) * a.nchan + c0] : 0;
+            nx_dl[i][h] = v0 ? dtab[(int64_t)min(dmw + i, bt.ndm - 1) * a.nchan + c0] : 0;
     }
 
     for (int st = 0; st < nst; st++) {
         int cur_min[kH], cur_dl[kKW][kH];
+        const uint32_t cur_fc = nx_fc;
+        if (PRE && st + 1 < nst) nx_fc = fcrow[st + 1];
 #pragma unroll
         for (int h = 0; h < kH; h++) {
             cur_min[h] = nx_min[h];
@@ -414,13 +487,26 @@ __global__ void __launch_bounds__((kKDM / KW + 1) * 32, 1) dd_tiled_kernel(const
             nx_min[h] = vn ? bmin[cn] : 0;
 #pragma unroll
             for (int i = 0; i < kKW; i++)
-                nx_dl[i][h] = vn ? bt.delays[(int64_t)min(dmw + i, bt.ndm - 1) * a.nchan + cn] : 0;
+                nx_dl[i][h] = vn ? dtab[(int64_t)min(dmw + i, bt.ndm - 1) * a.nchan + cn] : 0;
         }
         int cnt[kKW][4];
 #pragma unroll
         for (int i = 0; i < kKW; i++)
 #pragma unroll
-            for (int P = 0; P < 4; P++) cnt[i][P] = 0;
+            for (int P = 0; P < 4; P++) cnt[i][P] = PRE ? (int)((cur_fc >> (8 * P)) & 0xffu) : 0;
+        if constexpr (PRE) {
+            // each lane files its channel's aligned word at the precomputed position
+            // (family P occupies entries [P * kCB, P * kCB + count_P) of the list)
+            const uint32_t t0lo = (uint32_t)t0;
+#pragma unroll
+            for (int h = 0; h < kH; h++) {
+                const int c = st * kCB + h * 32 + lane;
+                const uint32_t pk = (uint32_t)cur_dl[0][h];
+                const uint32_t q = (t0lo + (pk >> 8)) - ((t0lo + (uint32_t)cur_min[h]) & ~15u);
+                const int boff = slot * slot_bytes + (h * 32 + lane) * a.win + (int)(q & ~3u);
+                if (c < a.nchan) mylist[pk & 0xffu] = A32 ? (int)(smem32 + boff) : (boff >> 2);
+            }
+        } else
 #pragma unroll
         for (int h = 0; h < kH; h++) {
             const int c = st * kCB + h * 32 + lane;
@@ -467,6 +553,22 @@ __global__ void __launch_bounds__((kKDM / KW + 1) * 32, 1) dd_tiled_kernel(const
                     }
                     const int32_t *lp = mylist + (i * 4 + P) * kCB;
                     int j = 0;
+                    if constexpr (QUAD) {
+                        // four channels per step (one 16-byte entry load)
+                        for (; j + 4 <= n; j += 4) {
+                            const int4 e = *reinterpret_cast<const int4 *>(lp + j);
+                            uint32_t w1[kM], w2[kM], w3[kM], w4[kM];
+                            ptx::lds_words<kM>((uint32_t)e.x + lane4, w1);
+                            ptx::lds_words<kM>((uint32_t)e.y + lane4, w2);
+                            ptx::lds_words<kM>((uint32_t)e.z + lane4, w3);
+                            ptx::lds_words<kM>((uint32_t)e.w + lane4, w4);
+#pragma unroll
+                            for (int k = 0; k < kM; k++) {
+                                acc_pair<ACC>(E[i][P][k], O[i][P][k], w1[k], w2[k], one);
+                                acc_pair<ACC>(E[i][P][k], O[i][P][k], w3[k], w4[k], one);
+                            }
+                        }
+                    }
 #pragma unroll 2
                     for (; j + 2 <= n; j += 2) {
                         const int2 e = *reinterpret_cast<const int2 *>(lp + j);
@@ -548,7 +650,10 @@ __global__ void __launch_bounds__((kKDM / KW + 1) * 32, 1) dd_tiled_kernel(const
             rpar ^= 1u;
         }
 
-        if (FF && st == nst - 1) {
+        if (MF && ((st + 1) % kFlushStages == 0 || st == nst - 1)) {
+#pragma unroll
+            for (int i = 0; i < kKW; i++) flush_merged<kM>(E[i], O[i], acc[i], lane);
+        } else if (FF && st == nst - 1) {
 #pragma unroll
             for (int i = 0; i < kKW; i++) {
                 flush_family<0, kM, ACC>(E[i][0], O[i][0], acc[i], lane);
@@ -556,7 +661,7 @@ __global__ void __launch_bounds__((kKDM / KW + 1) * 32, 1) dd_tiled_kernel(const
                 flush_family<2, kM, ACC>(E[i][2], O[i][2], acc[i], lane);
                 flush_family<3, kM, ACC>(E[i][3], O[i][3], acc[i], lane);
             }
-        } else if (!FF && ((st + 1) % kFlushStages == 0 || st == nst - 1)) {
+        } else if (!MF && !FF && ((st + 1) % kFlushStages == 0 || st == nst - 1)) {
 #pragma unroll
             for (int i = 0; i < kKW; i++) {
                 uint32_t sp[kM][3];
@@ -595,6 +700,11 @@ __global__ void __launch_bounds__((kKDM / KW + 1) * 32, 1) dd_tiled_kernel(const
                 }
             }
         }
+    }
+
+    if constexpr (MF) {
+#pragma unroll
+        for (int i = 0; i < kKW; i++) merged_decode<kM>(acc[i]);
     }
 
     // ------------------------------------------------------- store the tile
@@ -678,6 +788,7 @@ struct TiledVariant {
     int kw;
     int m;
     int cb;
+    bool pre;  // needs the plan's precomputed list positions
 };
 
 // Tuning variants of the tiled kernel (same result, different schedule).
@@ -696,13 +807,50 @@ const TiledVariant kVariants[] = {
     {dd_tiled_kernel<1, true, 3, false, 4, 64>, 1, 4, 64},
     {dd_tiled_kernel<1, false, 3, false, 4, 64, true>, 1, 4, 64},
     {dd_tiled_kernel<1, false, 3, false, 4, 32, true>, 1, 4, 32},
+    {dd_tiled_kernel<1, false, 3, false, 4, 64, false, true, false>, 1, 4, 64, true},
+    {dd_tiled_kernel<1, false, 3, false, 4, 64, false, true, true>, 1, 4, 64, true},
+    {dd_tiled_kernel<1, false, 3, false, 4, 64, false, false, true>, 1, 4, 64},
+    {dd_tiled_kernel<1, false, 3, true, 4, 64, false, true, true>, 1, 4, 64, true},
+    {dd_tiled_kernel<1, false, 3, true, 4, 64, false, false, true>, 1, 4, 64},
+    {dd_tiled_kernel<1, true, 3, true, 4, 64, false, true, true>, 1, 4, 64, true},
+    {dd_tiled_kernel<1, true, 3, true, 4, 64, false, false, true>, 1, 4, 64},
 };
 constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
 constexpr int kDefaultVariant = 10;
+constexpr int kFallbackVariant = 10;  // default when the precomputed lists are unavailable
 
 }  // namespace
 
-bool plan_dedisperse_tiled(gsp_plan_s *p, std::vector<int32_t> *blkmin) {
+void plan_phase_lists(const gsp_plan_s *p, std::vector<int32_t> *dpos,
+                      std::vector<uint32_t> *fcnt) {
+    // Phase-sorted lists of 64-channel stages, per DM: channel c of stage st
+    // (in channel order within its family) is filed at position
+    // P * 64 + rank, P = delay & 3, and the stage's four family sizes are
+    // packed 8 bits each.  The phase of a (channel, DM) pair is the same in
+    // every time tile because tiles start at multiples of 4 samples and the
+    // staged windows at multiples of 16 bytes.
+    const int C = p->desc.nchan, ndm = p->desc.ndm;
+    const int nst = (C + 63) / 64;
+    dpos->clear();
+    fcnt->clear();
+    if (p->max_delay >= ((int64_t)1 << 23)) return;  // packed delay field is 23 bits
+    dpos->resize((size_t)ndm * C);
+    fcnt->resize((size_t)ndm * nst);
+    for (int d = 0; d < ndm; d++) {
+        const int32_t *dl = p->delays_h.data() + (size_t)d * C;
+        for (int st = 0; st < nst; st++) {
+            uint32_t cnt[4] = {0, 0, 0, 0};
+            for (int c = st * 64; c < std::min(C, st * 64 + 64); c++) {
+                const int P = dl[c] & 3;
+                (*dpos)[(size_t)d * C + c] = (int32_t)(((uint32_t)dl[c] << 8) | (uint32_t)(P * 64 + cnt[P]));
+                cnt[P]++;
+            }
+            (*fcnt)[(size_t)d * nst + st] = cnt[0] | (cnt[1] << 8) | (cnt[2] << 16) | (cnt[3] << 24);
+        }
+    }
+}
+
+bool plan_dedisperse_tiled(gsp_plan_s *p, std::vector<int32_t> *blkmin, bool have_lists) {
     const int C = p->desc.nchan, ndm = p->desc.ndm;
     const int nblk = (ndm + kKDM - 1) / kKDM;
     blkmin->assign((size_t)nblk * C, 0);
@@ -725,6 +873,7 @@ bool plan_dedisperse_tiled(gsp_plan_s *p, std::vector<int32_t> *blkmin) {
         const int k = std::atoi(v);
         if (k >= 0 && k < kNumVariants) variant = k;
     }
+    if (kVariants[variant].pre && !have_lists) variant = kFallbackVariant;
     const int kT = 128 * kVariants[variant].m;
     const int kTEff = kT - 4;
     const int64_t win = (kT + 15 + spread + 15) & ~(int64_t)15;
@@ -774,7 +923,7 @@ bool plan_dedisperse_tiled(gsp_plan_s *p, std::vector<int32_t> *blkmin) {
 int dedisperse_num_variants() { return kNumVariants; }
 
 // Variants the batch autotuner times (the fastest family on this GPU).
-const int kTuneList[] = {12, 10, 13, 8};
+const int kTuneList[] = {17, 18, 19, 20};
 int dedisperse_tune_candidates(const int **list) {
     *list = kTuneList;
     return (int)(sizeof(kTuneList) / sizeof(kTuneList[0]));
@@ -792,6 +941,7 @@ cudaError_t launch_dedisperse_batch(const BeamLaunch *beams, int nbeams, int var
     for (int b = 0; b < nbeams; b++) {
         const gsp_plan_s *p = beams[b].plan;
         if (p->desc.nchan != nchan || !p->d_blkmin) return cudaErrorInvalidValue;
+        if (v.pre && (!p->d_dpos || !p->d_fcnt)) return cudaErrorInvalidValue;
         win = std::max<int64_t>(win, (t_cta + 15 + p->geom.spread + 15) & ~(int64_t)15);
     }
     const int64_t fixed = (int64_t)kKDM * 4 * v.cb * 4 + 2 * 8 * 8;
@@ -818,6 +968,8 @@ cudaError_t launch_dedisperse_batch(const BeamLaunch *beams, int nbeams, int var
         bt.n_out = in.n_out;
         bt.delays = p->d_delays;
         bt.blkmin = p->d_blkmin;
+        bt.dpos = p->d_dpos;
+        bt.fcnt = p->d_fcnt;
         bt.out = in.out;
         bt.out_stride = in.out_stride;
         bt.bsum = in.bsum;

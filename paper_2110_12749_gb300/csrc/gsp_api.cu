@@ -88,6 +88,8 @@ void free_plan(gsp_plan_s *p) {
     if (!p) return;
     cudaFree(p->d_delays);
     cudaFree(p->d_blkmin);
+    cudaFree(p->d_dpos);
+    cudaFree(p->d_fcnt);
     cudaFree(p->d_err);
     cudaFree(p->d_bsum);
     cudaFree(p->d_sigma_b);
@@ -320,14 +322,22 @@ gsp_status gsp_plan_create(gsp_plan_t *out, const gsp_plan_desc *d) {
         delete p;
         return GSP_ERR_CUDA;
     }
-    std::vector<int32_t> blkmin;
-    if (!p->simple_dd && !gsp::plan_dedisperse_tiled(p, &blkmin)) p->simple_dd = true;
+    std::vector<int32_t> blkmin, dpos;
+    std::vector<uint32_t> fcnt;
+    if (!p->simple_dd) gsp::plan_phase_lists(p, &dpos, &fcnt);
+    if (!p->simple_dd && !gsp::plan_dedisperse_tiled(p, &blkmin, !dpos.empty())) p->simple_dd = true;
+    if (p->simple_dd) {
+        dpos.clear();
+        fcnt.clear();
+    }
 
     p->nb_max = std::max<int64_t>(d->nsamp_max / d->block_len, 1);
     const size_t rows_blocks = (size_t)ndm * (size_t)p->nb_max;
     gsp_status st = GSP_OK;
     if (st == GSP_OK) st = dalloc(&p->d_delays, (size_t)(C * ndm));
     if (st == GSP_OK && !blkmin.empty()) st = dalloc(&p->d_blkmin, blkmin.size());
+    if (st == GSP_OK && !dpos.empty()) st = dalloc(&p->d_dpos, dpos.size());
+    if (st == GSP_OK && !fcnt.empty()) st = dalloc(&p->d_fcnt, fcnt.size());
     if (st == GSP_OK) st = dalloc(&p->d_sigma_b, rows_blocks);
     if (st == GSP_OK) st = dalloc(&p->d_bad, rows_blocks);
     if (st == GSP_OK) st = dalloc(&p->d_bparam, rows_blocks);
@@ -351,6 +361,10 @@ gsp_status gsp_plan_create(gsp_plan_t *out, const gsp_plan_desc *d) {
     if (e == cudaSuccess && !blkmin.empty())
         e = cudaMemcpy(p->d_blkmin, blkmin.data(), blkmin.size() * sizeof(int32_t),
                        cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !dpos.empty())
+        e = cudaMemcpy(p->d_dpos, dpos.data(), dpos.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !fcnt.empty())
+        e = cudaMemcpy(p->d_fcnt, fcnt.data(), fcnt.size() * sizeof(uint32_t), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(p->d_ncand, 0, sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMemset(p->d_err, 0, sizeof(int));
     for (int i = 0; i < 3 && e == cudaSuccess; i++) e = cudaEventCreate(&p->ev[i]);
@@ -545,6 +559,11 @@ gsp_status gsp_plan_timing(gsp_plan_t p, float *ms_dd, float *ms_search) {
 }
 
 int32_t gsp_plan_launches(gsp_plan_t p) { return p ? p->launches : -1; }
+
+int32_t gsp_dedisperse_variants(gsp_plan_t p, int32_t *in_use) {
+    if (p && in_use) *in_use = p->simple_dd ? -1 : p->geom.variant;
+    return gsp::dedisperse_num_variants();
+}
 
 const char *gsp_status_string(gsp_status s) {
     switch (s) {

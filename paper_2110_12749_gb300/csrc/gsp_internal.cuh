@@ -55,6 +55,8 @@ struct gsp_plan_s {
     // device memory owned by the plan
     int32_t *d_delays = nullptr;     // [ndm][nchan]
     int32_t *d_blkmin = nullptr;     // [nblk][nchan] min delay of each DM block
+    int32_t *d_dpos = nullptr;       // [ndm][nchan] (delay << 8) | phase-list position
+    uint32_t *d_fcnt = nullptr;      // [ndm][ceil(nchan / 64)] phase family sizes
     int *d_err = nullptr;            // set by a kernel whose bounded wait gave up
     unsigned long long *d_bsum = nullptr;  // [ndm][nb_max][3] block sums (tiled path)
     double *d_sigma_b = nullptr;     // [ndm][nb_max]
@@ -122,7 +124,11 @@ cudaError_t launch_dedisperse_tiled(const gsp_plan_s *p, const uint8_t *x, int64
                                     int64_t x_stride, int64_t n_out, int32_t *out,
                                     int64_t out_stride, unsigned long long *bsum,
                                     cudaStream_t s, int32_t *nlaunch);
-bool plan_dedisperse_tiled(gsp_plan_s *p, std::vector<int32_t> *blkmin);
+// Phase-sorted list positions of 64-channel stages (empty if the delays do
+// not fit the packed form), then the tile geometry and variant.
+void plan_phase_lists(const gsp_plan_s *p, std::vector<int32_t> *dpos,
+                      std::vector<uint32_t> *fcnt);
+bool plan_dedisperse_tiled(gsp_plan_s *p, std::vector<int32_t> *blkmin, bool have_lists);
 
 // bsum (optional): block sums left by the tiled dedispersion kernel.
 cudaError_t launch_search(gsp_plan_s *p, const int32_t *D, int64_t n_out, int64_t stride,

@@ -107,6 +107,7 @@ def lib():
                                           ctypes.c_float, ctypes.c_float, _vp, _i64, _vp, _vp],
                                          ctypes.c_int),
             "gsp_plan_launches": ([_vp], ctypes.c_int32),
+            "gsp_dedisperse_variants": ([_vp, _vp], ctypes.c_int32),
             "gsp_stream_create": ([_vp, _vp, _i64, ctypes.c_int32], ctypes.c_int),
             "gsp_stream_destroy": ([_vp], ctypes.c_int),
             "gsp_stream_need": ([_vp], _i64),
@@ -352,6 +353,15 @@ def gsp_plan_timing(plan):
 
 def gsp_plan_launches(plan):
     return int(lib().gsp_plan_launches(plan.handle))
+
+
+def gsp_dedisperse_variants(plan=None):
+    """(number of tile variants, variant the plan uses or -1 for the simple
+    kernel; None without a plan)."""
+    used = ctypes.c_int32(-2)
+    n = int(lib().gsp_dedisperse_variants(plan.handle if plan is not None else None,
+                                          ctypes.byref(used)))
+    return n, (int(used.value) if plan is not None else None)
 
 
 def gsp_search_series_static(D, n_out, d_cands, d_ncand, t_offset=0, widths=None,

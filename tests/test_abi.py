@@ -39,6 +39,11 @@ def test_binding_covers_header(gsp):
         assert hasattr(gsp, n), n
 
 
+def test_variant_count_without_plan(gsp):
+    n, used = gsp.gsp_dedisperse_variants()
+    assert n >= 1 and used is None
+
+
 def test_struct_layout(gsp):
     assert ctypes.sizeof(gsp.gsp_plan_desc) == 136
     assert gsp.CAND_DTYPE.itemsize == 24
