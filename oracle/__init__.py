@@ -37,6 +37,13 @@ def lib():
         L.oracle_search_row.restype = ctypes.c_int
         L.oracle_search_rows.argtypes = [vp, i64, i64, i64, vp, vp, vp, i64, vp, vp]
         L.oracle_search_rows.restype = ctypes.c_int
+        L.oracle_downsample.argtypes = [vp, i64, i64, i64, i64, vp, i64]
+        L.oracle_downsample.restype = ctypes.c_int
+        L.oracle_subband_delays.argtypes = [i64, dbl, dbl, ctypes.c_int, dbl, i64, vp, i64, i64,
+                                            vp, vp, vp]
+        L.oracle_subband_delays.restype = ctypes.c_int
+        L.oracle_subband_dedisperse.argtypes = [vp, i64, i64, i64, i64, i64, vp, vp, i64, i64, vp]
+        L.oracle_subband_dedisperse.restype = ctypes.c_int
         L.oracle_num_threads.argtypes = []
         L.oracle_num_threads.restype = ctypes.c_int
         _lib = L
@@ -174,3 +181,60 @@ def search_rows(D, dm_idx=None, block_len=1024, window_len=1024, t_offset=0,
     out = np.concatenate([cands[r, :min(ncand[r], cap)] for r in range(nrows)]) \
         if nrows else np.zeros(0, CAND_DTYPE)
     return out, sref
+
+
+def downsample(x, n_in, ds):
+    """uint8 [nchan][n_in // ds]: rounded-half-up mean of ds consecutive
+    samples (the DownSamp column of the DDplan ranges, Sec. 3.1 Tables 2-3)."""
+    x = np.ascontiguousarray(x, dtype=np.uint8)
+    nchan, stride = x.shape
+    n_ds = n_in // ds
+    out = np.zeros((nchan, max(n_ds, 1)), dtype=np.uint8)
+    rc = lib().oracle_downsample(_ptr(x), nchan, n_in, stride, int(ds), _ptr(out), out.shape[1])
+    if rc != 0:
+        raise ValueError("oracle_downsample failed (%d)" % rc)
+    return out[:, :n_ds]
+
+
+def ddplan_dms(lo, ddm, n):
+    """Trial DMs of one DDplan range: lo + i * ddm, i < n, in FP64 (Sec. 3.1,
+    Tables 2-3: Low DM, dDM, Number of DMs)."""
+    return float(lo) + np.arange(int(n), dtype=np.float64) * float(ddm)
+
+
+def subband_delays(nchan, f_lo, f_hi, t_samp, dms, nsub, group, descending=False):
+    """Two-stage delay tables (d1 int32 [nsdm][nchan], d2 int32 [ndm][nsub],
+    sub-band DM trial indices int32 [nsdm]) of the sub-band algorithm."""
+    dms = np.ascontiguousarray(np.asarray(dms, dtype=np.float64).reshape(-1))
+    ndm = dms.size
+    nsdm = (ndm + group - 1) // group
+    d1 = np.empty((nsdm, nchan), np.int32)
+    d2 = np.empty((ndm, nsub), np.int32)
+    si = np.empty(nsdm, np.int32)
+    rc = lib().oracle_subband_delays(nchan, float(f_lo), float(f_hi), int(bool(descending)),
+                                     float(t_samp), ndm, _ptr(dms), int(nsub), int(group),
+                                     _ptr(d1), _ptr(d2), _ptr(si))
+    if rc != 0:
+        raise ValueError("oracle_subband_delays failed (%d)" % rc)
+    return d1, d2, si
+
+
+def subband_nout(n_in, d1, d2):
+    return n_in - max_delay(d1) - max_delay(d2)
+
+
+def subband_dedisperse(x, n_in, d1, d2, group, n_out=None):
+    """int64 D [ndm][n_out] of the two-stage sub-band dedispersion."""
+    x = np.ascontiguousarray(x, dtype=np.uint8)
+    d1 = np.ascontiguousarray(d1, dtype=np.int32)
+    d2 = np.ascontiguousarray(d2, dtype=np.int32)
+    nchan, stride = x.shape
+    ndm, nsub = d2.shape
+    if n_out is None:
+        n_out = subband_nout(n_in, d1, d2)
+    out = np.empty((ndm, max(n_out, 0)), dtype=np.int64)
+    rc = lib().oracle_subband_dedisperse(_ptr(x), nchan, n_in, stride, nsub, int(group),
+                                         _ptr(d1), _ptr(d2), ndm, n_out, _ptr(out))
+    if rc != 0:
+        raise ValueError("oracle_subband_dedisperse failed (%d)" % rc)
+    return out

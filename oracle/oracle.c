@@ -330,6 +330,133 @@ int oracle_search_rows(const int64_t *D, int64_t nrows, int64_t d_stride,
     return err ? ORACLE_EINVAL : ORACLE_OK;
 }
 
+/* ------------------------------------- DDplan ranges and sub-band dedispersion */
+
+/* Time downsampling by an integer factor ds, as used by the DDplan ranges of
+ * Sec. 3.1 (Tables 2 and 3, column DownSamp): output sample t of channel c
+ * is the mean of input samples t*ds .. t*ds + ds - 1, rounded half up to an
+ * integer, n_ds = floor(n_in / ds) samples (a trailing partial group is
+ * dropped).  The paper names the factor only; the rounded mean that keeps
+ * 8-bit samples is this project's reading.  Computed as
+ * floor((2 * sum + ds) / (2 * ds)) in integers. */
+int oracle_downsample(const uint8_t *x, int64_t nchan, int64_t n_in, int64_t x_stride,
+                      int64_t ds, uint8_t *out, int64_t out_stride) {
+    if (!x || !out || nchan <= 0 || n_in < 0 || ds < 1 || x_stride < n_in ||
+        out_stride < n_in / ds)
+        return ORACLE_EINVAL;
+    int64_t n_ds = n_in / ds;
+    for (int64_t c = 0; c < nchan; c++)
+        for (int64_t t = 0; t < n_ds; t++) {
+            int64_t sum = 0;
+            for (int64_t k = 0; k < ds; k++) sum += x[c * x_stride + t * ds + k];
+            out[c * out_stride + t] = (uint8_t)((2 * sum + ds) / (2 * ds));
+        }
+    return ORACLE_OK;
+}
+
+/* Delay in samples of frequency f at dispersion measure dm (the same law and
+ * rounding as oracle_delays). */
+static int64_t delay_of(double dm, double f, double f_top, double t_samp) {
+    double x = 4.148808e3 * dm * (1.0 / (f * f) - 1.0 / (f_top * f_top)) / t_samp;
+    return (int64_t)floor(x + 0.5);
+}
+
+/* Sub-band (two-stage) delay tables, Sec. 2.3 (the sub-band algorithm of
+ * PRESTO's prepsubband that GSP accelerates).  The nchan channels (storage
+ * order) form nsub sub-bands of nchan/nsub consecutive channels; the
+ * reference channel of a sub-band is its highest-frequency channel.  The DM
+ * trials are taken in groups of `group` consecutive trials; the sub-band DM
+ * of group g is the trial at index min(g*group + group/2, ndm - 1).
+ *   d1[g][c] = delay_c(sdm_g) - delay_ref(s(c))(sdm_g)   (stage 1, >= 0)
+ *   d2[d][s] = delay_ref(s)(DM_d)                          (stage 2)
+ * so a trial that is its group's sub-band DM gets exactly the brute-force
+ * delay delay_c(DM) for every channel.  sdm_idx[g] receives the trial index
+ * of each sub-band DM.  The grouping, the reference channel and the choice
+ * of the middle trial are this project's readings; the paper names the
+ * algorithm only. */
+int oracle_subband_delays(int64_t nchan, double f_lo, double f_hi, int descending,
+                          double t_samp, int64_t ndm, const double *dms, int64_t nsub,
+                          int64_t group, int32_t *d1, int32_t *d2, int32_t *sdm_idx) {
+    if (nchan <= 0 || ndm <= 0 || nsub <= 0 || nchan % nsub != 0 || group <= 0 ||
+        !(f_hi > f_lo) || !(f_lo > 0.0) || !(t_samp > 0.0) || !dms || !d1 || !d2 || !sdm_idx)
+        return ORACLE_EINVAL;
+    int64_t cs = nchan / nsub;
+    int64_t nsdm = (ndm + group - 1) / group;
+    double f_top = f_lo + ((double)(nchan - 1) + 0.5) * ((f_hi - f_lo) / (double)nchan);
+    for (int64_t g = 0; g < nsdm; g++) {
+        int64_t i = g * group + group / 2;
+        if (i > ndm - 1) i = ndm - 1;
+        sdm_idx[g] = (int32_t)i;
+    }
+    for (int64_t s = 0; s < nsub; s++) {
+        int64_t ref = descending ? s * cs : s * cs + cs - 1;
+        double f_ref = channel_freq(ref, nchan, f_lo, f_hi, descending);
+        for (int64_t g = 0; g < nsdm; g++) {
+            double sdm = dms[sdm_idx[g]];
+            if (!(sdm >= 0.0)) return ORACLE_EINVAL;
+            int64_t dref = delay_of(sdm, f_ref, f_top, t_samp);
+            for (int64_t c = s * cs; c < s * cs + cs; c++) {
+                double f = channel_freq(c, nchan, f_lo, f_hi, descending);
+                int64_t v = delay_of(sdm, f, f_top, t_samp) - dref;
+                if (v < 0 || v > 2147483647) return ORACLE_EINVAL;
+                d1[g * nchan + c] = (int32_t)v;
+            }
+        }
+        for (int64_t d = 0; d < ndm; d++) {
+            if (!(dms[d] >= 0.0)) return ORACLE_EINVAL;
+            int64_t v = delay_of(dms[d], f_ref, f_top, t_samp);
+            if (v > 2147483647) return ORACLE_EINVAL;
+            d2[d * nsub + s] = (int32_t)v;
+        }
+    }
+    return ORACLE_OK;
+}
+
+/* Two-stage sub-band dedispersion, int64 throughout:
+ *   stage 1: S[g][s][t] = sum_{c in sub-band s} X[c][t + d1[g][c]],  t < n1
+ *   stage 2: D[d][t]    = sum_s S[group(d)][s][t + d2[d][s]],        t < n_out
+ * with n1 = n_in - max d1 and n_out <= n1 - max d2; group(d) = d / group.
+ * out: int64 [ndm][n_out]. */
+int oracle_subband_dedisperse(const uint8_t *x, int64_t nchan, int64_t n_in,
+                              int64_t x_stride, int64_t nsub, int64_t group,
+                              const int32_t *d1, const int32_t *d2, int64_t ndm,
+                              int64_t n_out, int64_t *out) {
+    if (!x || !d1 || !d2 || !out || nchan <= 0 || nsub <= 0 || nchan % nsub != 0 ||
+        group <= 0 || ndm <= 0 || n_out < 0 || x_stride < n_in)
+        return ORACLE_EINVAL;
+    int64_t cs = nchan / nsub;
+    int64_t nsdm = (ndm + group - 1) / group;
+    int64_t max1 = oracle_max_delay(d1, nsdm, nchan);
+    int64_t max2 = oracle_max_delay(d2, ndm, nsub);
+    int64_t n1 = n_in - max1;
+    if (n1 < 0 || n_out + max2 > n1) return ORACLE_EINVAL;
+    int64_t *S = (int64_t *)calloc((size_t)(nsdm * nsub * (n1 > 0 ? n1 : 1)), sizeof(int64_t));
+    if (!S) return ORACLE_ENOMEM;
+    int64_t gs;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (gs = 0; gs < nsdm * nsub; gs++) {
+        int64_t g = gs / nsub, s = gs % nsub;
+        int64_t *o = S + gs * n1;
+        for (int64_t c = s * cs; c < s * cs + cs; c++) {
+            const uint8_t *xc = x + c * x_stride + d1[g * nchan + c];
+            for (int64_t t = 0; t < n1; t++) o[t] += (int64_t)xc[t];
+        }
+    }
+    int64_t d;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (d = 0; d < ndm; d++) {
+        int64_t g = d / group;
+        int64_t *o = out + d * n_out;
+        for (int64_t t = 0; t < n_out; t++) o[t] = 0;
+        for (int64_t s = 0; s < nsub; s++) {
+            const int64_t *Ss = S + (g * nsub + s) * n1 + d2[d * nsub + s];
+            for (int64_t t = 0; t < n_out; t++) o[t] += Ss[t];
+        }
+    }
+    free(S);
+    return ORACLE_OK;
+}
+
 int oracle_num_threads(void) {
 #ifdef _OPENMP
     extern int omp_get_max_threads(void);

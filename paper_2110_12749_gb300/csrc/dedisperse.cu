@@ -88,7 +88,6 @@ cudaError_t launch_dedisperse_simple(const gsp_plan_s *p, const uint8_t *x, int6
 // Tiled kernel.
 namespace {
 
-constexpr int kKDM = 16;         // DM trials per CTA (= consumer warps x DM trials per warp)
 constexpr int kMaxBatchBeams = 32;  // beams per launch
 constexpr long long kWaitBudget = 4000000000ll;  // ~2 s of SM clock per wait
 
@@ -302,7 +301,7 @@ __device__ __forceinline__ void merged_decode(uint32_t (&acc)[M][4]) {
     }
 }
 
-// KW: DM trials per consumer warp; kCW = kKDM / KW consumer warps + 1 producer.
+// KW: DM trials per consumer warp; kCW = KDM / KW consumer warps + 1 producer.
 // QUAD: visit channels four at a time (more loads in flight per warp).
 // M: 4-sample words per lane, T = 128 M output samples computed per tile and
 // T - 4 stored (the tile's last word is incomplete by construction).
@@ -314,8 +313,8 @@ __device__ __forceinline__ void merged_decode(uint32_t (&acc)[M][4]) {
 // since tiles start at multiples of 4 samples), not from a per-stage ballot sort.
 // MF: merged flush of the four phase families (flush_merged).
 template <int KW, bool QUAD, int ACC, bool A32 = false, int M = 4, int CB = 32, bool FF = false,
-          bool PRE = false, bool MF = false>
-__global__ void __launch_bounds__((kKDM / KW + 1) * 32, 1) dd_tiled_kernel(const TiledArgs a) {
+          bool PRE = false, bool MF = false, int KDM = 16>
+__global__ void __launch_bounds__((KDM / KW + 1) * 32, 1) dd_tiled_kernel(const TiledArgs a) {
     static_assert(!PRE || (KW == 1 && CB == 64), "precomputed lists: one DM per warp, 64-channel stages");
     static_assert(!MF || (ACC == 3 && !FF), "merged flush: raw + odd views, all families together");
     constexpr int kCB = CB;
@@ -325,7 +324,8 @@ __global__ void __launch_bounds__((kKDM / KW + 1) * 32, 1) dd_tiled_kernel(const
     constexpr int kT = 128 * kM;
     constexpr int kTEff = kT - 4;
     constexpr int kKW = KW;
-    constexpr int kCW = kKDM / KW;
+    static_assert(KDM % KW == 0, "DM trials per CTA: a multiple of the DM trials per warp");
+    constexpr int kCW = KDM / KW;
     extern __shared__ __align__(128) uint8_t smem[];
     const int slot_bytes = kCB * a.win;
     int32_t *lists = reinterpret_cast<int32_t *>(smem + (size_t)a.stages * slot_bytes);
@@ -438,7 +438,7 @@ __global__ void __launch_bounds__((kKDM / KW + 1) * 32, 1) dd_tiled_kernel(const
     decode_item(a, item, &bi, &tile, &blk);
     const BeamTile &bt = a.beam[bi];
     const int64_t t0 = tile * kTEff;
-    const int dm0 = blk * kKDM;
+    const int dm0 = blk * KDM;
     const int32_t *bmin = bt.blkmin + (int64_t)blk * a.nchan;
     const int dmw = dm0 + warp * kKW;
     uint32_t acc[kKW][kM][4];
@@ -788,7 +788,8 @@ struct TiledVariant {
     int kw;
     int m;
     int cb;
-    bool pre;  // needs the plan's precomputed list positions
+    bool pre = false;  // needs the plan's precomputed list positions
+    int kdm = 16;      // DM trials per CTA (one of kKdmSizes)
 };
 
 // Tuning variants of the tiled kernel (same result, different schedule).
@@ -814,6 +815,10 @@ const TiledVariant kVariants[] = {
     {dd_tiled_kernel<1, false, 3, true, 4, 64, false, false, true>, 1, 4, 64},
     {dd_tiled_kernel<1, true, 3, true, 4, 64, false, true, true>, 1, 4, 64, true},
     {dd_tiled_kernel<1, true, 3, true, 4, 64, false, false, true>, 1, 4, 64},
+    {dd_tiled_kernel<1, false, 3, true, 4, 64, false, false, true, 15>, 1, 4, 64, false, 15},
+    {dd_tiled_kernel<1, false, 3, true, 4, 64, false, true, true, 15>, 1, 4, 64, true, 15},
+    {dd_tiled_kernel<1, false, 3, false, 4, 64, false, false, true, 15>, 1, 4, 64, false, 15},
+    {dd_tiled_kernel<1, true, 3, true, 4, 64, false, false, true, 15>, 1, 4, 64, false, 15},
 };
 constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
 constexpr int kDefaultVariant = 10;
@@ -850,21 +855,53 @@ void plan_phase_lists(const gsp_plan_s *p, std::vector<int32_t> *dpos,
     }
 }
 
-bool plan_dedisperse_tiled(gsp_plan_s *p, std::vector<int32_t> *blkmin, bool have_lists) {
+bool plan_dedisperse_tiled(gsp_plan_s *p, std::vector<int32_t> (&blkmin)[kNumKdm],
+                           bool have_lists) {
     const int C = p->desc.nchan, ndm = p->desc.ndm;
-    const int nblk = (ndm + kKDM - 1) / kKDM;
-    blkmin->assign((size_t)nblk * C, 0);
-    int64_t spread = 0;
-    for (int b = 0; b < nblk; b++) {
-        for (int c = 0; c < C; c++) {
-            int32_t lo = INT32_MAX, hi = 0;
-            for (int d = b * kKDM; d < std::min(ndm, (b + 1) * kKDM); d++) {
-                const int32_t v = p->delays_h[(size_t)d * C + c];
-                lo = std::min(lo, v);
-                hi = std::max(hi, v);
+    DDGeom &g = p->geom;
+    // DM blocks of each supported block size: per-block minimum delay of every
+    // channel, the largest delay spread inside a block, and the L2 grouping
+    for (int o = 0; o < kNumKdm; o++) {
+        const int kdm = kKdmSizes[o];
+        const int nblk = (ndm + kdm - 1) / kdm;
+        std::vector<int32_t> &bm = blkmin[o];
+        bm.assign((size_t)nblk * C, 0);
+        int64_t spread = 0;
+        for (int b = 0; b < nblk; b++) {
+            for (int c = 0; c < C; c++) {
+                int32_t lo = INT32_MAX, hi = 0;
+                for (int d = b * kdm; d < std::min(ndm, (b + 1) * kdm); d++) {
+                    const int32_t v = p->delays_h[(size_t)d * C + c];
+                    lo = std::min(lo, v);
+                    hi = std::max(hi, v);
+                }
+                bm[(size_t)b * C + c] = lo;
+                spread = std::max<int64_t>(spread, (int64_t)hi - lo);
             }
-            (*blkmin)[(size_t)b * C + c] = lo;
-            spread = std::max<int64_t>(spread, (int64_t)hi - lo);
+        }
+        g.nblk[o] = nblk;
+        g.spread[o] = spread;
+        // largest group of DM blocks whose per-tile input union (sum over channels
+        // of the delay range across the group plus a 512-sample window) stays
+        // within ~24 MB of L2
+        const int64_t win = (512 + 15 + spread + 15) & ~(int64_t)15;
+        g.grp[o] = 1;
+        for (int G = nblk; G >= 1; G--) {
+            int64_t worst = 0;
+            for (int b0 = 0; b0 < nblk; b0 += G) {
+                int64_t u = 0;
+                const int d_hi = std::min(ndm, (b0 + G) * kdm) - 1;
+                for (int c = 0; c < C; c++) {
+                    const int64_t lo = bm[(size_t)b0 * C + c];
+                    const int64_t hi = p->delays_h[(size_t)d_hi * C + c];
+                    u += std::max<int64_t>(hi - lo, 0) + win;
+                }
+                worst = std::max(worst, u);
+            }
+            if (worst <= ((int64_t)24 << 20) || G == 1) {
+                g.grp[o] = G;
+                break;
+            }
         }
     }
     // GSP_DD_VARIANT selects a tuning variant of the tiled kernel.
@@ -874,48 +911,23 @@ bool plan_dedisperse_tiled(gsp_plan_s *p, std::vector<int32_t> *blkmin, bool hav
         if (k >= 0 && k < kNumVariants) variant = k;
     }
     if (kVariants[variant].pre && !have_lists) variant = kFallbackVariant;
-    const int kT = 128 * kVariants[variant].m;
-    const int kTEff = kT - 4;
-    const int64_t win = (kT + 15 + spread + 15) & ~(int64_t)15;
-    const int kCB = kVariants[variant].cb;
-    const int64_t fixed = (int64_t)kKDM * 4 * kCB * 4 + 2 * 8 * 8;
-    const int64_t budget = 227 * 1024 - fixed;
-    const int64_t stages = std::min<int64_t>(8, budget / ((int64_t)kCB * win));
+    const TiledVariant &v = kVariants[variant];
+    const int o = kdm_index(v.kdm);
+    const int kT = 128 * v.m;
+    const int64_t win = (kT + 15 + g.spread[o] + 15) & ~(int64_t)15;
+    const int64_t fixed = (int64_t)v.kdm * 4 * v.cb * 4 + 2 * 8 * 8;
+    const int64_t stages = std::min<int64_t>(8, (227 * 1024 - fixed) / ((int64_t)v.cb * win));
     if (stages < 2) {
-        blkmin->clear();
+        for (auto &b : blkmin) b.clear();
         return false;
     }
-    DDGeom &g = p->geom;
-    g.kdm = kKDM;
+    g.kdm = v.kdm;
     g.t_cta = kT;
-    g.t_eff = kTEff;
-    g.cb = kCB;
+    g.t_eff = kT - 4;
+    g.cb = v.cb;
     g.win = (int)win;
     g.stages = (int)stages;
-    g.smem = (int)(stages * kCB * win + fixed);
-    g.nblk = nblk;
-    g.spread = spread;
-    // largest group of DM blocks whose per-tile input union (sum over channels of
-    // the delay range across the group plus a window) stays within ~24 MB of L2
-    g.grp = 1;
-    for (int G = nblk; G >= 1; G--) {
-        int64_t worst = 0;
-        for (int b0 = 0; b0 < nblk; b0 += G) {
-            int64_t u = 0;
-            const int d_lo = b0 * kKDM, d_hi = std::min(ndm, (b0 + G) * kKDM) - 1;
-            for (int c = 0; c < C; c++) {
-                const int64_t lo = (*blkmin)[(size_t)b0 * C + c];
-                const int64_t hi = p->delays_h[(size_t)d_hi * C + c];
-                u += std::max<int64_t>(hi - lo, 0) + win;
-            }
-            (void)d_lo;
-            worst = std::max(worst, u);
-        }
-        if (worst <= ((int64_t)24 << 20) || G == 1) {
-            g.grp = G;
-            break;
-        }
-    }
+    g.smem = (int)(stages * v.cb * win + fixed);
     g.variant = variant;
     return true;
 }
@@ -923,7 +935,7 @@ bool plan_dedisperse_tiled(gsp_plan_s *p, std::vector<int32_t> *blkmin, bool hav
 int dedisperse_num_variants() { return kNumVariants; }
 
 // Variants the batch autotuner times (the fastest family on this GPU).
-const int kTuneList[] = {17, 18, 19, 20};
+const int kTuneList[] = {18, 21, 22, 24};
 int dedisperse_tune_candidates(const int **list) {
     *list = kTuneList;
     return (int)(sizeof(kTuneList) / sizeof(kTuneList[0]));
@@ -935,16 +947,17 @@ cudaError_t launch_dedisperse_batch(const BeamLaunch *beams, int nbeams, int var
     if (nbeams < 1 || nbeams > kMaxBatchBeams || variant < 0 || variant >= kNumVariants)
         return cudaErrorInvalidValue;
     const TiledVariant &v = kVariants[variant];
+    const int o = kdm_index(v.kdm);
     const int t_cta = 128 * v.m, t_eff = t_cta - 4;
     const int nchan = beams[0].plan->desc.nchan;
     int64_t win = 0;
     for (int b = 0; b < nbeams; b++) {
         const gsp_plan_s *p = beams[b].plan;
-        if (p->desc.nchan != nchan || !p->d_blkmin) return cudaErrorInvalidValue;
+        if (p->desc.nchan != nchan || !p->d_blkmin[o]) return cudaErrorInvalidValue;
         if (v.pre && (!p->d_dpos || !p->d_fcnt)) return cudaErrorInvalidValue;
-        win = std::max<int64_t>(win, (t_cta + 15 + p->geom.spread + 15) & ~(int64_t)15);
+        win = std::max<int64_t>(win, (t_cta + 15 + p->geom.spread[o] + 15) & ~(int64_t)15);
     }
-    const int64_t fixed = (int64_t)kKDM * 4 * v.cb * 4 + 2 * 8 * 8;
+    const int64_t fixed = (int64_t)v.kdm * 4 * v.cb * 4 + 2 * 8 * 8;
     const int64_t stages = std::min<int64_t>(8, (227 * 1024 - fixed) / ((int64_t)v.cb * win));
     if (stages < 2) return cudaErrorInvalidValue;
     const int smem = (int)(stages * v.cb * win + fixed);
@@ -967,7 +980,7 @@ cudaError_t launch_dedisperse_batch(const BeamLaunch *beams, int nbeams, int var
         bt.n_in = in.n_in;
         bt.n_out = in.n_out;
         bt.delays = p->d_delays;
-        bt.blkmin = p->d_blkmin;
+        bt.blkmin = p->d_blkmin[o];
         bt.dpos = p->d_dpos;
         bt.fcnt = p->d_fcnt;
         bt.out = in.out;
@@ -979,8 +992,8 @@ cudaError_t launch_dedisperse_batch(const BeamLaunch *beams, int nbeams, int var
         bt.ntiles = (in.n_out + t_eff - 1) / t_eff;
         bt.item0 = items;
         bt.ndm = p->desc.ndm;
-        bt.nblk = p->geom.nblk;
-        bt.grp = p->geom.grp;
+        bt.nblk = p->geom.nblk[o];
+        bt.grp = p->geom.grp[o];
         if (in.bsum && bt.B < t_eff) return cudaErrorInvalidValue;
         items += bt.ntiles * bt.nblk;
     }
@@ -993,7 +1006,7 @@ cudaError_t launch_dedisperse_batch(const BeamLaunch *beams, int nbeams, int var
     a.items = items;
     int64_t grid = persistent ? std::min<int64_t>(items, num_sms) : items;
     if (grid < 1 || grid > 0x7fffffffll) return cudaErrorInvalidConfiguration;
-    v.fn<<<(unsigned)grid, (kKDM / v.kw + 1) * 32, smem, s>>>(a);
+    v.fn<<<(unsigned)grid, (v.kdm / v.kw + 1) * 32, smem, s>>>(a);
     *nlaunch += 1;
     return cudaGetLastError();
 }

@@ -87,7 +87,7 @@ gsp_status check_band(const gsp_plan_desc *d) {
 void free_plan(gsp_plan_s *p) {
     if (!p) return;
     cudaFree(p->d_delays);
-    cudaFree(p->d_blkmin);
+    for (auto *b : p->d_blkmin) cudaFree(b);
     cudaFree(p->d_dpos);
     cudaFree(p->d_fcnt);
     cudaFree(p->d_err);
@@ -322,10 +322,10 @@ gsp_status gsp_plan_create(gsp_plan_t *out, const gsp_plan_desc *d) {
         delete p;
         return GSP_ERR_CUDA;
     }
-    std::vector<int32_t> blkmin, dpos;
+    std::vector<int32_t> blkmin[gsp::kNumKdm], dpos;
     std::vector<uint32_t> fcnt;
     if (!p->simple_dd) gsp::plan_phase_lists(p, &dpos, &fcnt);
-    if (!p->simple_dd && !gsp::plan_dedisperse_tiled(p, &blkmin, !dpos.empty())) p->simple_dd = true;
+    if (!p->simple_dd && !gsp::plan_dedisperse_tiled(p, blkmin, !dpos.empty())) p->simple_dd = true;
     if (p->simple_dd) {
         dpos.clear();
         fcnt.clear();
@@ -335,7 +335,8 @@ gsp_status gsp_plan_create(gsp_plan_t *out, const gsp_plan_desc *d) {
     const size_t rows_blocks = (size_t)ndm * (size_t)p->nb_max;
     gsp_status st = GSP_OK;
     if (st == GSP_OK) st = dalloc(&p->d_delays, (size_t)(C * ndm));
-    if (st == GSP_OK && !blkmin.empty()) st = dalloc(&p->d_blkmin, blkmin.size());
+    for (int o = 0; o < gsp::kNumKdm; o++)
+        if (st == GSP_OK && !blkmin[o].empty()) st = dalloc(&p->d_blkmin[o], blkmin[o].size());
     if (st == GSP_OK && !dpos.empty()) st = dalloc(&p->d_dpos, dpos.size());
     if (st == GSP_OK && !fcnt.empty()) st = dalloc(&p->d_fcnt, fcnt.size());
     if (st == GSP_OK) st = dalloc(&p->d_sigma_b, rows_blocks);
@@ -358,9 +359,10 @@ gsp_status gsp_plan_create(gsp_plan_t *out, const gsp_plan_desc *d) {
     }
     e = cudaMemcpy(p->d_delays, p->delays_h.data(), (size_t)(C * ndm) * sizeof(int32_t),
                    cudaMemcpyHostToDevice);
-    if (e == cudaSuccess && !blkmin.empty())
-        e = cudaMemcpy(p->d_blkmin, blkmin.data(), blkmin.size() * sizeof(int32_t),
-                       cudaMemcpyHostToDevice);
+    for (int o = 0; o < gsp::kNumKdm; o++)
+        if (e == cudaSuccess && !blkmin[o].empty())
+            e = cudaMemcpy(p->d_blkmin[o], blkmin[o].data(), blkmin[o].size() * sizeof(int32_t),
+                           cudaMemcpyHostToDevice);
     if (e == cudaSuccess && !dpos.empty())
         e = cudaMemcpy(p->d_dpos, dpos.data(), dpos.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
     if (e == cudaSuccess && !fcnt.empty())

@@ -12,6 +12,14 @@ namespace gsp {
 
 constexpr int kMaxWidths = 32;
 
+// DM trials per CTA of the tiled dedispersion kernel (one per consumer warp):
+// 16, or 15 so that the CTA (15 consumer warps + 1 producer) is 16 warps and
+// each thread may hold up to 128 registers.  Plans keep the DM-block tables
+// of both sizes so that any tile variant can run on any plan.
+constexpr int kNumKdm = 2;
+constexpr int kKdmSizes[kNumKdm] = {16, 15};
+inline int kdm_index(int kdm) { return kdm == 15 ? 1 : 0; }
+
 // Per-block parameters consumed by the boxcar kernel, derived in FP64 from
 // exact integer block sums and rounded once to FP32:
 //   m    = nearest integer to the block mean (the integer series is D - m),
@@ -27,16 +35,17 @@ struct BlockParam {
 
 // Tile geometry of the performance dedispersion kernel, chosen per plan.
 struct DDGeom {
-    int kdm = 0;       // DM trials per CTA
+    int kdm = 0;       // DM trials per CTA of the plan's variant
     int t_cta = 0;     // output samples computed per CTA (t_eff stored)
     int t_eff = 0;     // output samples stored per CTA (tiles overlap)
     int cb = 0;        // channels per shared-memory stage
     int win = 0;       // bytes per channel window in shared memory
     int stages = 0;    // pipeline depth
     int smem = 0;      // dynamic shared memory bytes
-    int nblk = 0;      // DM blocks
-    int grp = 1;       // DM blocks per launch group
-    int64_t spread = 0;  // largest delay spread inside a DM block
+    // per DM-block size kKdmSizes[o]:
+    int nblk[kNumKdm] = {0, 0};        // DM blocks
+    int grp[kNumKdm] = {1, 1};         // DM blocks per launch group
+    int64_t spread[kNumKdm] = {0, 0};  // largest delay spread inside a DM block
     int variant = 0;   // template variant index
 };
 
@@ -54,7 +63,7 @@ struct gsp_plan_s {
 
     // device memory owned by the plan
     int32_t *d_delays = nullptr;     // [ndm][nchan]
-    int32_t *d_blkmin = nullptr;     // [nblk][nchan] min delay of each DM block
+    int32_t *d_blkmin[gsp::kNumKdm] = {nullptr, nullptr};  // [nblk][nchan] min delay per DM block
     int32_t *d_dpos = nullptr;       // [ndm][nchan] (delay << 8) | phase-list position
     uint32_t *d_fcnt = nullptr;      // [ndm][ceil(nchan / 64)] phase family sizes
     int *d_err = nullptr;            // set by a kernel whose bounded wait gave up
@@ -128,7 +137,8 @@ cudaError_t launch_dedisperse_tiled(const gsp_plan_s *p, const uint8_t *x, int64
 // not fit the packed form), then the tile geometry and variant.
 void plan_phase_lists(const gsp_plan_s *p, std::vector<int32_t> *dpos,
                       std::vector<uint32_t> *fcnt);
-bool plan_dedisperse_tiled(gsp_plan_s *p, std::vector<int32_t> *blkmin, bool have_lists);
+bool plan_dedisperse_tiled(gsp_plan_s *p, std::vector<int32_t> (&blkmin)[kNumKdm],
+                           bool have_lists);
 
 // bsum (optional): block sums left by the tiled dedispersion kernel.
 cudaError_t launch_search(gsp_plan_s *p, const int32_t *D, int64_t n_out, int64_t stride,
