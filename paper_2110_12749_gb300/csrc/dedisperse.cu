@@ -819,10 +819,12 @@ const TiledVariant kVariants[] = {
     {dd_tiled_kernel<1, false, 3, true, 4, 64, false, true, true, 15>, 1, 4, 64, true, 15},
     {dd_tiled_kernel<1, false, 3, false, 4, 64, false, false, true, 15>, 1, 4, 64, false, 15},
     {dd_tiled_kernel<1, true, 3, true, 4, 64, false, false, true, 15>, 1, 4, 64, false, 15},
+    {dd_tiled_kernel<1, false, 3, false, 4, 64, false, true, true, 15>, 1, 4, 64, true, 15},
+    {dd_tiled_kernel<1, false, 3, true, 4, 32, false, false, true, 15>, 1, 4, 32, false, 15},
 };
 constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
-constexpr int kDefaultVariant = 10;
-constexpr int kFallbackVariant = 10;  // default when the precomputed lists are unavailable
+constexpr int kDefaultVariant = 22;
+constexpr int kFallbackVariant = 21;  // default when the precomputed lists are unavailable
 
 }  // namespace
 
@@ -935,7 +937,7 @@ bool plan_dedisperse_tiled(gsp_plan_s *p, std::vector<int32_t> (&blkmin)[kNumKdm
 int dedisperse_num_variants() { return kNumVariants; }
 
 // Variants the batch autotuner times (the fastest family on this GPU).
-const int kTuneList[] = {18, 21, 22, 24};
+const int kTuneList[] = {22, 25, 21, 23};
 int dedisperse_tune_candidates(const int **list) {
     *list = kTuneList;
     return (int)(sizeof(kTuneList) / sizeof(kTuneList[0]));
