@@ -59,6 +59,10 @@ def parse():
     ap.add_argument("--batch-beams", type=int, default=19,
                     help="beams of the batched multi-beam measurement (0: skip)")
     ap.add_argument("--batch-steps", type=int, default=3)
+    ap.add_argument("--subband-steps", type=int, default=3,
+                    help="timed steps of the two-stage sub-band path on the same beam (0: skip)")
+    ap.add_argument("--ddplan-steps", type=int, default=3,
+                    help="timed steps of the Table 2 (Band1) DDplan search (0: skip)")
     ap.add_argument("--stream-gbs", type=float, default=6.0,
                     help="aggregate arrival rate of the simulated stream (GB/s)")
     ap.add_argument("--variant", type=int, default=-1,
@@ -353,6 +357,94 @@ def run_batch(args, wl):
                       "the per-beam search kernels"}
 
 
+def run_subband(args, wl, plan, xd, n_sub=64, group=16):
+    """Two-stage sub-band dedispersion (Sec. 2.3) of the same beam and DM grid,
+    then the same search; CUDA events around each part."""
+    import torch
+    from paper_2110_12749_gb300 import gsp
+    desc, keep = gsp.make_desc(wl.nchan, wl.f_lo, wl.f_hi, wl.t_samp, wl.n_in, ndm=wl.ndm,
+                               dm_lo=wl.dm_lo, dm_step=wl.dm_step)
+    sb = gsp.gsp_subband_create(desc, n_sub, group)
+    d1, d2, _ = gsp.gsp_subband_delays(sb)
+    n_out = gsp.gsp_subband_nout(sb, wl.n_in)
+    n1 = wl.n_in - int(d1.max())
+    D = torch.empty((wl.ndm, (n_out + 3) // 4 * 4), dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream()
+    for _ in range(2):
+        gsp.gsp_subband_dedisperse(sb, xd, wl.n_in, D)
+        gsp.gsp_search_series(plan, D, n_out)
+    gsp.gsp_subband_finish(sb)
+    dd, se = [], []
+    for _ in range(args.subband_steps):
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        e[0].record(stream)
+        gsp.gsp_subband_dedisperse(sb, xd, wl.n_in, D)
+        e[1].record(stream)
+        gsp.gsp_search_series(plan, D, n_out)
+        e[2].record(stream)
+        gsp.gsp_subband_finish(sb)
+        dd.append(e[0].elapsed_time(e[1]))
+        se.append(e[1].elapsed_time(e[2]))
+    _, ncand, _ = gsp.gsp_candidates(plan)
+    launches = gsp.gsp_subband_launches(sb)
+    gsp.gsp_subband_destroy(sb)
+    del D
+    torch.cuda.empty_cache()
+    nsdm = (wl.ndm + group - 1) // group
+    adds = float(nsdm) * wl.nchan * n1 + float(wl.ndm) * n_sub * n_out
+    ms_dd, ms_se = float(np.median(dd)), float(np.median(se))
+    return {"nsub": n_sub, "group": group, "subband_dms": nsdm, "n_out": n_out,
+            "dedisperse_ms": ms_dd, "search_ms": ms_se,
+            "sky_s_per_s": wl.sky_seconds() / ((ms_dd + ms_se) / 1e3),
+            "adds": adds, "brute_force_adds": float(wl.ndm) * wl.nchan * n_out,
+            "launches": launches + gsp.gsp_plan_launches(plan), "candidates": int(ncand),
+            "exact_rows": "the 125 sub-band DM trials equal brute force; the others carry "
+                          "the sub-band approximation"}
+
+
+def run_ddplan(args):
+    """The eight DM ranges of Table 2 (Band1: 271-398 MHz, 512 channels, 3462 trials,
+    downsampling 1-128) on 2^20 samples of 98.304 us (103 s) of synthetic noise."""
+    import torch
+    from paper_2110_12749_gb300 import gsp, synth
+    ranges = [(0.0, 0.01, 1134, 1), (11.34, 0.03, 362, 2), (22.2, 0.05, 337, 4),
+              (39.05, 0.1, 381, 8), (77.15, 0.2, 383, 16), (153.75, 0.5, 380, 32),
+              (343.75, 1.0, 344, 64), (687.75, 2.0, 141, 128)]
+    nchan, f_lo, f_hi, ts, n_in = 512, 271.0, 398.0, 98.304e-6, 1 << 20
+    x = synth.filterbank(nchan, n_in, synth.BASE_SEED + 7, 128.0, 20.0, threads=8)
+    xd = torch.from_numpy(x).cuda()
+    del x
+    base, keep = gsp.make_desc(nchan, f_lo, f_hi, ts, n_in, ndm=1)
+    dd = gsp.gsp_ddplan_create(base, ranges)
+    stream = torch.cuda.current_stream()
+    for _ in range(2):
+        gsp.gsp_ddplan_search(dd, xd, n_in)
+    gsp.gsp_ddplan_candidates(dd, cap=1)
+    ms = []
+    for _ in range(args.ddplan_steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        gsp.gsp_ddplan_search(dd, xd, n_in)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    _, ncand, _ = gsp.gsp_ddplan_candidates(dd, cap=1)
+    adds = 0.0
+    for lo, step, n, ds in ranges:
+        d1, k1 = gsp.make_desc(nchan, f_lo, f_hi, ts * ds, n_in // ds, ndm=n, dm_lo=lo, dm_step=step)
+        md = int(gsp.gsp_compute_delays(d1)[0].max())
+        adds += float(n) * nchan * (n_in // ds - md)
+    gsp.gsp_ddplan_destroy(dd)
+    del xd
+    torch.cuda.empty_cache()
+    m = float(np.median(ms))
+    return {"plan": "Table 2 (Band1), 8 ranges, 3462 trials", "nchan": nchan,
+            "band_mhz": [f_lo, f_hi], "t_samp_s": ts, "n_in": n_in, "ms_per_search": m,
+            "sky_s_per_s": n_in * ts / (m / 1e3), "adds": adds,
+            "dm_chan_samples_per_s": adds / (m / 1e3), "candidates": int(ncand),
+            "data": "synthetic Gaussian noise (mu 128, sigma 20)"}
+
+
 def run_gsp(args):
     import torch
     from paper_2110_12749_gb300 import gsp, synth
@@ -453,7 +545,11 @@ def run_gsp(args):
     line = None
     stream_res = None
     batch_res = None
-    if args.stream_beams > 0 or args.batch_beams > 0:
+    subband_res = None
+    ddplan_res = None
+    if args.subband_steps > 0 and rank == 0:
+        subband_res = run_subband(args, wl, plan, xd)
+    if args.stream_beams > 0 or args.batch_beams > 0 or args.ddplan_steps > 0:
         if plan is not None:
             gsp.gsp_plan_destroy(plan)
             plan = None
@@ -463,6 +559,8 @@ def run_gsp(args):
         batch_res = run_batch(args, wl)
     if args.stream_beams > 0 and rank == 0:
         stream_res = run_stream(args, wl, delays_fn)
+    if args.ddplan_steps > 0 and rank == 0:
+        ddplan_res = run_ddplan(args)
     if rank == 0:
         cpu = None
         if not args.no_cpu_baseline:
@@ -501,6 +599,10 @@ def run_gsp(args):
             line["cpu_baseline"] = cpu
         if batch_res is not None:
             line["batch"] = batch_res
+        if subband_res is not None:
+            line["subband"] = subband_res
+        if ddplan_res is not None:
+            line["ddplan"] = ddplan_res
         if stream_res is not None:
             line["stream"] = stream_res
             line["p99_chunk_latency_ms"] = stream_res["p99_ms"]

@@ -62,6 +62,8 @@ typedef enum {
 typedef struct gsp_plan_s *gsp_plan_t;
 typedef struct gsp_stream_s *gsp_stream_t;
 typedef struct gsp_batch_s *gsp_batch_t;
+typedef struct gsp_subband_s *gsp_subband_t;
+typedef struct gsp_ddplan_s *gsp_ddplan_t;
 
 /* Batch flags (gsp_batch_create). */
 #define GSP_BATCH_PERSISTENT 1 /* one CTA per SM striding over all beams' work items */
@@ -315,6 +317,93 @@ gsp_status gsp_batch_timing(gsp_batch_t b, float *ms_dedisperse, float *ms_total
 /* The dedispersion variant in use, the autotuner's best batch time (ms, 0 if
  * not tuned) and the kernel launches of the last call (captured ones counted). */
 gsp_status gsp_batch_info(gsp_batch_t b, int32_t *variant, float *tuned_ms, int32_t *launches);
+
+/* ------------------------------------------------------------------------
+ * DDplan ranges and sub-band dedispersion (Sec. 3.1, Tables 2-3; Sec. 2.3).
+ * ------------------------------------------------------------------------ */
+
+/* Time downsampling of a filterbank, as used by the DDplan ranges of Sec. 3.1
+ * (Tables 2-3, column DownSamp): d_out[c][t] = the mean of d_x[c][t*ds ..
+ * t*ds + ds - 1] rounded half up, i.e. floor((2*sum + ds) / (2*ds)), for
+ * t < floor(n_in / ds).  d_x, d_out: device uint8 [nchan][stride];
+ * 1 <= ds <= 2^20.  Asynchronous on stream. */
+gsp_status gsp_downsample(const uint8_t *d_x, int32_t nchan, int64_t n_in, int64_t x_stride,
+                          int32_t ds, uint8_t *d_out, int64_t out_stride, void *stream);
+
+/* One DM range of a survey plan (a row of Tables 2-3): trial DMs
+ * dm_lo + i * dm_step (i < ndm), searched at the sampling time multiplied by
+ * downsamp. */
+typedef struct {
+    double dm_lo;
+    double dm_step;
+    int32_t ndm;
+    int32_t downsamp;
+} gsp_ddplan_range;
+
+/* A DDplan: one plan per range, built from base (band, sampling time,
+ * nsamp_max in input samples, search settings; its DM fields are ignored and
+ * base->delays must be NULL).  Range r's plan has t_samp * downsamp,
+ * nsamp_max / downsamp samples, and its search lengths (block, window,
+ * widths) count downsampled samples.  Each distinct factor owns a device
+ * buffer of nchan x round16(nsamp_max / downsamp) bytes. */
+gsp_status gsp_ddplan_create(gsp_ddplan_t *out, const gsp_plan_desc *base,
+                             const gsp_ddplan_range *ranges, int32_t nranges);
+gsp_status gsp_ddplan_destroy(gsp_ddplan_t d);
+
+/* Search every range: downsample d_x once per distinct factor, then
+ * gsp_search each range's plan on its series (same input rules as
+ * gsp_search; t_offset must be a multiple of every factor).  Asynchronous. */
+gsp_status gsp_ddplan_search(gsp_ddplan_t d, const uint8_t *d_x, int64_t n_in, int64_t x_stride,
+                             int64_t t_offset, void *stream);
+
+/* Candidates of all ranges in range order (each sorted as gsp_candidates):
+ * dm_idx indexes the concatenated trial list, t and width are in input
+ * samples (downsampled index x factor), beam = range index.  Synchronises. */
+gsp_status gsp_ddplan_candidates(gsp_ddplan_t d, gsp_cand *host_out, int64_t cap,
+                                 int64_t *n_total);
+
+/* Two-stage sub-band dedispersion (the algorithm of PRESTO's prepsubband that
+ * GSP accelerates, Sec. 2.3).  The nchan channels (storage order) form nsub
+ * sub-bands of nchan/nsub consecutive channels (nsub must divide nchan); the
+ * reference channel of a sub-band is its highest-frequency channel.  Trials
+ * are taken in groups of `group` (1..16) consecutive trials; the sub-band DM
+ * of group g is trial min(g*group + group/2, ndm - 1).  With Delta_c(DM) the
+ * plan's delay table,
+ *   stage 1: S[s][g][t] = sum_{c in s} X[c][t + d1[g][c]],
+ *            d1[g][c] = Delta_c(sdm_g) - Delta_ref(s)(sdm_g)
+ *   stage 2: D[d][t] = sum_s S[s][g(d)][t + d2[d][s]],  d2[d][s] = Delta_ref(s)(DM_d)
+ * for t < n_out = n_in - max d1 - max d2.  A trial that is its group's
+ * sub-band DM gets exactly the brute-force series; the others are the
+ * sub-band approximation.  desc: as for gsp_plan_create (band and DM grid;
+ * desc->delays must be NULL).  Owns nsub internal plans and a stage-1 buffer of
+ * nsub x nsdm x round4(nsamp_max) int32. */
+gsp_status gsp_subband_create(gsp_subband_t *out, const gsp_plan_desc *desc, int32_t nsub,
+                              int32_t group);
+gsp_status gsp_subband_destroy(gsp_subband_t b);
+
+/* n_out for an input of n_in samples (may be <= 0), -1 for NULL. */
+int64_t gsp_subband_nout(gsp_subband_t b, int64_t n_in);
+
+/* Host copies of d1 [nsdm][nchan], d2 [ndm][nsub] and the sub-band DM trial
+ * indices [nsdm] (any pointer may be NULL). */
+gsp_status gsp_subband_delays(gsp_subband_t b, int32_t *d1, int32_t *d2, int32_t *sdm_idx);
+
+/* Two-stage dedispersion of d_x (device uint8 [nchan][x_stride], d_x and
+ * x_stride 16-byte aligned, else GSP_ERR_ALIGN) into d_out (device int32
+ * [ndm][out_stride], out_stride >= n_out, 4-byte aligned).  Stage 1 is one
+ * persistent launch of the tiled dedispersion kernel over all sub-bands (up
+ * to 32 per launch); stage 2 one launch.  GSP_ERR_TOO_SHORT if n_out <= 0.
+ * Asynchronous on stream; search the result with gsp_search_series. */
+gsp_status gsp_subband_dedisperse(gsp_subband_t b, const uint8_t *d_x, int64_t n_in,
+                                  int64_t x_stride, int32_t *d_out, int64_t out_stride,
+                                  void *stream);
+
+/* Synchronise stream and report GSP_ERR_TIMEOUT if a bounded wait of a stage-1
+ * kernel gave up (the flag is then cleared). */
+gsp_status gsp_subband_finish(gsp_subband_t b, void *stream);
+
+/* Kernel launches of the last gsp_subband_dedisperse call. */
+int32_t gsp_subband_launches(gsp_subband_t b);
 
 /* Static text for a status code. */
 const char *gsp_status_string(gsp_status s);

@@ -119,6 +119,19 @@ def lib():
             "gsp_batch_candidates": ([_vp, _vp, _i64, _vp], ctypes.c_int),
             "gsp_batch_info": ([_vp, _vp, _vp, _vp], ctypes.c_int),
             "gsp_batch_timing": ([_vp, _vp, _vp], ctypes.c_int),
+            "gsp_downsample": ([_vp, ctypes.c_int32, _i64, _i64, ctypes.c_int32, _vp, _i64, _vp],
+                               ctypes.c_int),
+            "gsp_ddplan_create": ([_vp, _vp, _vp, ctypes.c_int32], ctypes.c_int),
+            "gsp_ddplan_destroy": ([_vp], ctypes.c_int),
+            "gsp_ddplan_search": ([_vp, _vp, _i64, _i64, _i64, _vp], ctypes.c_int),
+            "gsp_ddplan_candidates": ([_vp, _vp, _i64, _vp], ctypes.c_int),
+            "gsp_subband_create": ([_vp, _vp, ctypes.c_int32, ctypes.c_int32], ctypes.c_int),
+            "gsp_subband_destroy": ([_vp], ctypes.c_int),
+            "gsp_subband_nout": ([_vp, _i64], _i64),
+            "gsp_subband_delays": ([_vp, _vp, _vp, _vp], ctypes.c_int),
+            "gsp_subband_dedisperse": ([_vp, _vp, _i64, _i64, _vp, _i64, _vp], ctypes.c_int),
+            "gsp_subband_finish": ([_vp, _vp], ctypes.c_int),
+            "gsp_subband_launches": ([_vp], ctypes.c_int32),
             "gsp_status_string": ([ctypes.c_int], ctypes.c_char_p),
             "gsp_last_error_string": ([], ctypes.c_char_p),
             "gsp_version": ([], ctypes.c_int32),
@@ -502,3 +515,127 @@ def gsp_batch_timing(b):
     a, t = ctypes.c_float(0), ctypes.c_float(0)
     _check(lib().gsp_batch_timing(b.handle, ctypes.byref(a), ctypes.byref(t)), "gsp_batch_timing")
     return a.value, t.value
+
+
+
+# ---------------------------------------------------------------------------
+# DDplan ranges and sub-band dedispersion
+
+class gsp_ddplan_range(ctypes.Structure):
+    _fields_ = [("dm_lo", ctypes.c_double), ("dm_step", ctypes.c_double),
+                ("ndm", ctypes.c_int32), ("downsamp", ctypes.c_int32)]
+
+
+def gsp_downsample(x, nchan, n_in, ds, out, stream=None):
+    """x: torch uint8 CUDA [nchan][stride]; out: torch uint8 CUDA [nchan][>= n_in // ds]."""
+    _check(lib().gsp_downsample(_vp(x.data_ptr()), nchan, n_in, x.stride(0), ds,
+                                _vp(out.data_ptr()), out.stride(0), _stream(stream)),
+           "gsp_downsample")
+
+
+class DDPlan:
+    """Owns a gsp_ddplan_t."""
+
+    def __init__(self, handle, ranges):
+        self.handle = handle
+        self.ranges = ranges
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            try:
+                _lib.gsp_ddplan_destroy(self.handle)
+            except Exception:
+                pass
+            self.handle = None
+
+
+def gsp_ddplan_create(base_desc, ranges):
+    """ranges: iterable of (dm_lo, dm_step, ndm, downsamp)."""
+    ranges = list(ranges)
+    arr = (gsp_ddplan_range * len(ranges))()
+    for i, (lo, step, n, ds) in enumerate(ranges):
+        arr[i].dm_lo, arr[i].dm_step, arr[i].ndm, arr[i].downsamp = lo, step, n, ds
+    h = _vp()
+    _check(lib().gsp_ddplan_create(ctypes.byref(h), ctypes.byref(base_desc), arr, len(ranges)),
+           "gsp_ddplan_create")
+    return DDPlan(h, ranges)
+
+
+def gsp_ddplan_destroy(d):
+    if d.handle:
+        st = lib().gsp_ddplan_destroy(d.handle)
+        d.handle = None
+        _check(st, "gsp_ddplan_destroy")
+
+
+def gsp_ddplan_search(d, x, n_in, t_offset=0, stream=None):
+    _check(lib().gsp_ddplan_search(d.handle, _vp(x.data_ptr()), n_in, x.stride(0), t_offset,
+                                   _stream(stream)), "gsp_ddplan_search")
+
+
+def gsp_ddplan_candidates(d, cap=1 << 22):
+    out = np.zeros(max(cap, 1), dtype=CAND_DTYPE)
+    n = ctypes.c_int64(0)
+    st = lib().gsp_ddplan_candidates(d.handle, _np_ptr(out), cap, ctypes.byref(n))
+    if st not in (GSP_OK, GSP_ERR_CAPACITY):
+        _check(st, "gsp_ddplan_candidates")
+    return out[:min(n.value, cap)].copy(), n.value, st
+
+
+class Subband:
+    """Owns a gsp_subband_t."""
+
+    def __init__(self, handle, ndm, nchan, nsub, group):
+        self.handle = handle
+        self.ndm, self.nchan, self.nsub, self.group = ndm, nchan, nsub, group
+        self.nsdm = (ndm + group - 1) // group
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            try:
+                _lib.gsp_subband_destroy(self.handle)
+            except Exception:
+                pass
+            self.handle = None
+
+
+def gsp_subband_create(desc, nsub, group):
+    h = _vp()
+    _check(lib().gsp_subband_create(ctypes.byref(h), ctypes.byref(desc), nsub, group),
+           "gsp_subband_create")
+    return Subband(h, int(desc.ndm), int(desc.nchan), nsub, group)
+
+
+def gsp_subband_destroy(b):
+    if b.handle:
+        st = lib().gsp_subband_destroy(b.handle)
+        b.handle = None
+        _check(st, "gsp_subband_destroy")
+
+
+def gsp_subband_nout(b, n_in):
+    return int(lib().gsp_subband_nout(b.handle, n_in))
+
+
+def gsp_subband_delays(b):
+    d1 = np.zeros((b.nsdm, b.nchan), np.int32)
+    d2 = np.zeros((b.ndm, b.nsub), np.int32)
+    si = np.zeros(b.nsdm, np.int32)
+    _check(lib().gsp_subband_delays(b.handle, _np_ptr(d1), _np_ptr(d2), _np_ptr(si)),
+           "gsp_subband_delays")
+    return d1, d2, si
+
+
+def gsp_subband_dedisperse(b, x, n_in, out, stream=None):
+    """x: torch uint8 CUDA [nchan][stride]; out: torch int32 CUDA [ndm][>= n_out]."""
+    _check(lib().gsp_subband_dedisperse(b.handle, _vp(x.data_ptr()), n_in, x.stride(0),
+                                        _vp(out.data_ptr()), out.stride(0), _stream(stream)),
+           "gsp_subband_dedisperse")
+
+
+def gsp_subband_finish(b, stream=None):
+    _check(lib().gsp_subband_finish(b.handle, _stream(stream)), "gsp_subband_finish")
+
+
+def gsp_subband_launches(b):
+    return int(lib().gsp_subband_launches(b.handle))
