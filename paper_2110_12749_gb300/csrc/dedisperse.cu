@@ -821,6 +821,8 @@ const TiledVariant kVariants[] = {
     {dd_tiled_kernel<1, true, 3, true, 4, 64, false, false, true, 15>, 1, 4, 64, false, 15},
     {dd_tiled_kernel<1, false, 3, false, 4, 64, false, true, true, 15>, 1, 4, 64, true, 15},
     {dd_tiled_kernel<1, false, 3, true, 4, 32, false, false, true, 15>, 1, 4, 32, false, 15},
+    {dd_tiled_kernel<1, false, 3, true, 8, 64, false, true, true, 15>, 1, 8, 64, true, 15},
+    {dd_tiled_kernel<1, false, 3, false, 8, 64, false, true, true, 15>, 1, 8, 64, true, 15},
 };
 constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
 constexpr int kDefaultVariant = 22;
