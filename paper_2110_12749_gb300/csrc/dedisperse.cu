@@ -312,8 +312,9 @@ __device__ __forceinline__ void merged_decode(uint32_t (&acc)[M][4]) {
 // positions (the phase of a (channel, DM) pair is delay & 3 in every tile,
 // since tiles start at multiples of 4 samples), not from a per-stage ballot sort.
 // MF: merged flush of the four phase families (flush_merged).
+// KDM: DM trials per CTA.  UNR: unroll depth of the two-channel loop (A32).
 template <int KW, bool QUAD, int ACC, bool A32 = false, int M = 4, int CB = 32, bool FF = false,
-          bool PRE = false, bool MF = false, int KDM = 16>
+          bool PRE = false, bool MF = false, int KDM = 16, int UNR = 2>
 __global__ void __launch_bounds__((KDM / KW + 1) * 32, 1) dd_tiled_kernel(const TiledArgs a) {
     static_assert(!PRE || (KW == 1 && CB == 64), "precomputed lists: one DM per warp, 64-channel stages");
     static_assert(!MF || (ACC == 3 && !FF), "merged flush: raw + odd views, all families together");
@@ -569,7 +570,7 @@ __global__ void __launch_bounds__((KDM / KW + 1) * 32, 1) dd_tiled_kernel(const 
                             }
                         }
                     }
-#pragma unroll 2
+#pragma unroll UNR
                     for (; j + 2 <= n; j += 2) {
                         const int2 e = *reinterpret_cast<const int2 *>(lp + j);
                         const uint32_t a1 = (uint32_t)e.x + lane4, a2 = (uint32_t)e.y + lane4;
@@ -823,6 +824,8 @@ const TiledVariant kVariants[] = {
     {dd_tiled_kernel<1, false, 3, true, 4, 32, false, false, true, 15>, 1, 4, 32, false, 15},
     {dd_tiled_kernel<1, false, 3, true, 8, 64, false, true, true, 15>, 1, 8, 64, true, 15},
     {dd_tiled_kernel<1, false, 3, false, 8, 64, false, true, true, 15>, 1, 8, 64, true, 15},
+    {dd_tiled_kernel<1, false, 3, true, 4, 64, false, true, true, 15, 4>, 1, 4, 64, true, 15},
+    {dd_tiled_kernel<1, false, 3, true, 4, 64, false, true, true, 15, 1>, 1, 4, 64, true, 15},
 };
 constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
 constexpr int kDefaultVariant = 22;
