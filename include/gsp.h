@@ -405,6 +405,24 @@ gsp_status gsp_subband_finish(gsp_subband_t b, void *stream);
 /* Kernel launches of the last gsp_subband_dedisperse call. */
 int32_t gsp_subband_launches(gsp_subband_t b);
 
+/* ------------------------------------------------------------------------
+ * Candidate ranker building blocks (the project's own design; see the
+ * ranker entry points below).
+ * ------------------------------------------------------------------------ */
+
+/* BF16 GEMM on the tcgen05 tensor cores with FP32 accumulation in tensor
+ * memory: d_C[m][n] = sum_k A[m][k] * B[n][k] (+ d_bias[n], then ReLU if relu),
+ * m < M, n < N.  d_A: device bf16 [M][lda], d_B: device bf16 [N][ldb], both
+ * 16-byte aligned with lda, ldb and K multiples of 8 (else GSP_ERR_ALIGN);
+ * d_C: device float [M][ldc].  splitk > 1 splits K over CTAs that add their
+ * partial tiles atomically into d_C, which must then hold zeros and gets no
+ * bias or ReLU.  d_err (device int32, optional) is set to 1 if a bounded wait
+ * gave up.  Asynchronous on stream. */
+gsp_status gsp_gemm_bf16(const void *d_A, int64_t lda, const void *d_B, int64_t ldb,
+                         float *d_C, int64_t ldc, int32_t M, int32_t N, int32_t K,
+                         const float *d_bias, int32_t relu, int32_t splitk, int32_t *d_err,
+                         void *stream);
+
 /* Static text for a status code. */
 const char *gsp_status_string(gsp_status s);
 

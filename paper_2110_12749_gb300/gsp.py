@@ -132,6 +132,9 @@ def lib():
             "gsp_subband_dedisperse": ([_vp, _vp, _i64, _i64, _vp, _i64, _vp], ctypes.c_int),
             "gsp_subband_finish": ([_vp, _vp], ctypes.c_int),
             "gsp_subband_launches": ([_vp], ctypes.c_int32),
+            "gsp_gemm_bf16": ([_vp, _i64, _vp, _i64, _vp, _i64, ctypes.c_int32, ctypes.c_int32,
+                               ctypes.c_int32, _vp, ctypes.c_int32, ctypes.c_int32, _vp, _vp],
+                              ctypes.c_int),
             "gsp_status_string": ([ctypes.c_int], ctypes.c_char_p),
             "gsp_last_error_string": ([], ctypes.c_char_p),
             "gsp_version": ([], ctypes.c_int32),
@@ -639,3 +642,12 @@ def gsp_subband_finish(b, stream=None):
 
 def gsp_subband_launches(b):
     return int(lib().gsp_subband_launches(b.handle))
+
+
+def gsp_gemm_bf16(A, B, C, M, N, K, bias=None, relu=False, splitk=1, err=None, stream=None):
+    """A: torch bf16 CUDA [M][lda], B: torch bf16 CUDA [N][ldb], C: torch float CUDA [M][ldc]."""
+    _check(lib().gsp_gemm_bf16(_vp(A.data_ptr()), A.stride(0), _vp(B.data_ptr()), B.stride(0),
+                               _vp(C.data_ptr()), C.stride(0), M, N, K,
+                               _vp(bias.data_ptr()) if bias is not None else None, int(relu),
+                               splitk, _vp(err.data_ptr()) if err is not None else None,
+                               _stream(stream)), "gsp_gemm_bf16")
