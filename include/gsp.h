@@ -64,6 +64,7 @@ typedef struct gsp_stream_s *gsp_stream_t;
 typedef struct gsp_batch_s *gsp_batch_t;
 typedef struct gsp_subband_s *gsp_subband_t;
 typedef struct gsp_ddplan_s *gsp_ddplan_t;
+typedef struct gsp_ranker_s *gsp_ranker_t;
 
 /* Batch flags (gsp_batch_create). */
 #define GSP_BATCH_PERSISTENT 1 /* one CTA per SM striding over all beams' work items */
@@ -422,6 +423,60 @@ gsp_status gsp_gemm_bf16(const void *d_A, int64_t lda, const void *d_B, int64_t 
                          float *d_C, int64_t ldc, int32_t M, int32_t N, int32_t K,
                          const float *d_bias, int32_t relu, int32_t splitk, int32_t *d_err,
                          void *stream);
+
+/* Candidate ranker: a small CNN that scores candidates by their 64 x 64
+ * DM-time snippets (the project's own design for the ranking step the paper
+ * motivates in Sec. 1-2; it ranks the threshold output and never replaces it).
+ * Network: three conv 3x3 (pad 1) + bias + ReLU + 2x2 max-pool layers (1 -> 8 ->
+ * 16 -> 32 channels), fc 2048 -> 64 + ReLU, fc 64 -> 2 (class 1 = pulse).  All
+ * products run with bf16 operands (rounded to nearest even) and FP32
+ * accumulation, the convolutions and fc 2048 -> 64 (forward and backward) as
+ * tcgen05 GEMMs.  Parameters are one FP32 vector of gsp_ranker_num_params()
+ * values in the order w1 b1 w2 b2 w3 b3 w4 b4 w5 b5, conv weights as
+ * [co][ci][ky][kx], fc weights as [out][in] with the fc 2048 input index
+ * (y * 8 + x) * 32 + c of the last pooled 8 x 8 x 32 map.  Training is mean
+ * softmax cross-entropy with Adam (beta1 0.9, beta2 0.999, eps 1e-8). */
+int64_t gsp_ranker_num_params(void);
+
+/* Create a ranker for batches of up to max_batch (1..4096) snippets; weights
+ * He-uniform from seed, biases 0.  Allocates all device memory. */
+gsp_status gsp_ranker_create(gsp_ranker_t *out, int32_t max_batch, uint64_t seed);
+gsp_status gsp_ranker_destroy(gsp_ranker_t r);
+
+/* Host copies in and out of the parameter vector; set_params also resets
+ * Adam's moments and step count.  get_params optionally returns the
+ * gradients of the last training step (either pointer may be NULL).
+ * Synchronise the device. */
+gsp_status gsp_ranker_set_params(gsp_ranker_t r, const float *host_params);
+gsp_status gsp_ranker_get_params(gsp_ranker_t r, float *host_params, float *host_grads);
+
+/* Snippets of n device candidates d_cands (as gsp_candidates returns them)
+ * from the series d_D (device int32 [ndm][stride]) of the plan's last search:
+ * d_out[k][i][j] (device float [n][64][64]) = sum over the f = max(1,
+ * width / 4) samples s of time bin j, centred on t + width / 2, of the
+ * normalised series of DM row dm_idx - 32 + i (detrended residual / sigma_ref;
+ * 0 in bad blocks, outside the rows or past the searched length), divided by
+ * sqrt(f).  GSP_ERR_STATE if the plan has not searched.  Asynchronous. */
+gsp_status gsp_ranker_snippets(gsp_plan_t plan, const int32_t *d_D, int64_t stride,
+                               const gsp_cand *d_cands, int32_t n, float *d_out, void *stream);
+
+/* Logits (device float [n][2]) of n snippets (device float [n][64][64]).
+ * Asynchronous. */
+gsp_status gsp_ranker_forward(gsp_ranker_t r, const float *d_x, int32_t n, float *d_logits,
+                              void *stream);
+
+/* One training step on n snippets with labels d_labels (device int32, 0 or
+ * 1): forward, gradients of the mean cross-entropy, one Adam update with
+ * learning rate lr.  d_loss (device float, optional) receives the batch loss.
+ * Asynchronous. */
+gsp_status gsp_ranker_train_step(gsp_ranker_t r, const float *d_x, const int32_t *d_labels,
+                                 int32_t n, float lr, float *d_loss, void *stream);
+
+/* Synchronise stream; GSP_ERR_TIMEOUT if a tensor-core wait gave up. */
+gsp_status gsp_ranker_finish(gsp_ranker_t r, void *stream);
+
+/* Kernel launches of the last forward or training step. */
+int32_t gsp_ranker_launches(gsp_ranker_t r);
 
 /* Static text for a status code. */
 const char *gsp_status_string(gsp_status s);

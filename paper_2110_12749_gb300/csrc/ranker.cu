@@ -1,0 +1,662 @@
+// Candidate ranker: a small CNN over 64 x 64 DM-time snippets of the
+// single-pulse candidates, trained and run on the GPU (the project's own
+// design for the candidate-ranking step the paper motivates, Sec. 1-2: it
+// ranks the plain threshold output, never replaces it).
+//
+// Network: three conv 3x3 (pad 1) + bias + ReLU + 2x2 max-pool layers
+// (1 -> 8 -> 16 -> 32 channels, 64x64 -> 8x8), fc 2048 -> 64 + ReLU, fc 64 -> 2.
+// Activations are NHWC.  Every convolution is an im2col GEMM on the tcgen05
+// tensor cores (tc_gemm.cu), BF16 operands and FP32 accumulation in tensor
+// memory, bias and ReLU fused into the epilogue; fc 2048 -> 64 and the
+// back-propagated products of both fc layers and the convolutions are GEMMs
+// too (weight gradients with split-K over the batch pixels).  The 64 -> 2
+// layer, the loss, pooling, im2col / col2im, bias gradients and Adam are
+// elementwise kernels in FP32.  Every operand of a product is rounded to
+// bf16 (nearest even), at the same points as the CPU oracle.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "gsp_internal.cuh"
+#include "tc_gemm.cuh"
+
+namespace {
+
+using bf16 = __nv_bfloat16;
+
+constexpr int kS = 64;          // snippet side
+constexpr int kFc = 2048;       // 32 x 8 x 8 features
+constexpr int kHid = 64;
+constexpr int kLayers = 3;
+// per conv layer: input channels, output channels, input side
+__host__ __device__ constexpr int cin_of(int l) { return l == 0 ? 1 : (l == 1 ? 8 : 16); }
+__host__ __device__ constexpr int cout_of(int l) { return l == 0 ? 8 : (l == 1 ? 16 : 32); }
+__host__ __device__ constexpr int side_of(int l) { return l == 0 ? 64 : (l == 1 ? 32 : 16); }
+
+__host__ __device__ constexpr int round8(int v) { return (v + 7) & ~7; }
+__host__ __device__ constexpr int kdim(int l) { return 9 * cin_of(l); }         // im2col K
+__host__ __device__ constexpr int kpad(int l) { return round8(kdim(l)); }
+
+// Parameter offsets in the flat FP32 vector (order w1 b1 w2 b2 w3 b3 w4 b4 w5 b5,
+// each in the oracle's layout: conv w[co][ci][ky][kx], fc w[out][in]).
+struct Offsets {
+    int64_t w[5], b[5], total;
+};
+constexpr int kWsize[5] = {8 * 1 * 9, 16 * 8 * 9, 32 * 16 * 9, kHid * kFc, 2 * kHid};
+constexpr int kBsize[5] = {8, 16, 32, kHid, 2};
+Offsets offsets() {
+    Offsets o{};
+    int64_t p = 0;
+    for (int i = 0; i < 5; i++) {
+        o.w[i] = p;
+        p += kWsize[i];
+        o.b[i] = p;
+        p += kBsize[i];
+    }
+    o.total = p;
+    return o;
+}
+
+// ------------------------------------------------------------- elementwise
+
+// im2col of an NHWC activation (layer 0: the FP32 snippets, rounded to bf16
+// here): col[(b, y, x)][(ky * 3 + kx) * Cin + ci] = a[b][y + ky - 1][x + kx - 1][ci],
+// zero outside the image and in the padding columns K..Kp.
+template <typename T>
+__global__ void im2col_kernel(const T *__restrict__ a, int B, int H, int Cin, int Kp,
+                              bf16 *__restrict__ col) {
+    const int64_t total = (int64_t)B * H * H * Kp;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int k = (int)(i % Kp);
+        const int64_t p = i / Kp;
+        const int x = (int)(p % H), y = (int)((p / H) % H);
+        const int64_t b = p / ((int64_t)H * H);
+        float v = 0.0f;
+        if (k < 9 * Cin) {
+            const int tap = k / Cin, ci = k % Cin;
+            const int yy = y + tap / 3 - 1, xx = x + tap % 3 - 1;
+            if (yy >= 0 && yy < H && xx >= 0 && xx < H)
+                v = (float)a[((b * H + yy) * H + xx) * Cin + ci];
+        }
+        col[i] = __float2bfloat16_rn(v);
+    }
+}
+
+// 2x2 max-pool of the ReLU'd pre-activations z (FP32 NHWC [B][H][H][C]):
+// out bf16 [B][H/2][H/2][C], idx = argmax in (0,0), (0,1), (1,0), (1,1) order
+// (first maximum wins).
+__global__ void pool_kernel(const float *__restrict__ z, int B, int H, int C,
+                            bf16 *__restrict__ out, uint8_t *__restrict__ idx) {
+    const int H2 = H / 2;
+    const int64_t total = (int64_t)B * H2 * H2 * C;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int c = (int)(i % C);
+        const int64_t q = i / C;
+        const int x = (int)(q % H2), y = (int)((q / H2) % H2);
+        const int64_t b = q / ((int64_t)H2 * H2);
+        const float *base = z + ((b * H + 2 * y) * H + 2 * x) * C + c;
+        const float v0 = base[0], v1 = base[C], v2 = base[(int64_t)H * C],
+                    v3 = base[(int64_t)H * C + C];
+        float m = v0;
+        int k = 0;
+        if (v1 > m) { m = v1; k = 1; }
+        if (v2 > m) { m = v2; k = 2; }
+        if (v3 > m) { m = v3; k = 3; }
+        out[i] = __float2bfloat16_rn(m);
+        idx[i] = (uint8_t)k;
+    }
+}
+
+// Back through the pool and the ReLU: g[b][y][x][c] = ga[b][y/2][x/2][c] if (y, x)
+// is the window's argmax and z > 0, else 0.  Writes bf16 g as [P][C] and as
+// its transpose [C][P] (P = B*H*H pixels, ldT >= P), and adds FP32 per-channel
+// sums into db.
+__global__ void pool_back_kernel(const float *__restrict__ ga, const uint8_t *__restrict__ idx,
+                                 const float *__restrict__ z, int B, int H, int C,
+                                 bf16 *__restrict__ g, bf16 *__restrict__ gT, int64_t ldT,
+                                 float *__restrict__ db) {
+    extern __shared__ float sdb[];
+    for (int c = threadIdx.x; c < C; c += blockDim.x) sdb[c] = 0.0f;
+    __syncthreads();
+    const int H2 = H / 2;
+    const int64_t P = (int64_t)B * H * H;
+    const int64_t total = P * C;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int c = (int)(i % C);
+        const int64_t p = i / C;
+        const int x = (int)(p % H), y = (int)((p / H) % H);
+        const int64_t b = p / ((int64_t)H * H);
+        const int64_t q = ((b * H2 + y / 2) * H2 + x / 2) * C + c;
+        const int k = (y & 1) * 2 + (x & 1);
+        float v = 0.0f;
+        if (idx[q] == k && z[i] > 0.0f) v = ga[q];
+        g[i] = __float2bfloat16_rn(v);
+        gT[(int64_t)c * ldT + p] = __float2bfloat16_rn(v);
+        if (v != 0.0f) atomicAdd(&sdb[c], v);
+    }
+    __syncthreads();
+    for (int c = threadIdx.x; c < C; c += blockDim.x)
+        if (sdb[c] != 0.0f) atomicAdd(&db[c], sdb[c]);
+}
+
+// col2im (gather form): ga[b][y][x][ci] = sum over taps (ky, kx) of
+// dcol[(b, y - ky + 1, x - kx + 1)][(ky * 3 + kx) * Cin + ci].
+__global__ void col2im_kernel(const float *__restrict__ dcol, int B, int H, int Cin, int Kp,
+                              float *__restrict__ ga) {
+    const int64_t total = (int64_t)B * H * H * Cin;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int ci = (int)(i % Cin);
+        const int64_t p = i / Cin;
+        const int x = (int)(p % H), y = (int)((p / H) % H);
+        const int64_t b = p / ((int64_t)H * H);
+        float s = 0.0f;
+#pragma unroll
+        for (int tap = 0; tap < 9; tap++) {
+            const int yy = y - tap / 3 + 1, xx = x - tap % 3 + 1;
+            if (yy >= 0 && yy < H && xx >= 0 && xx < H)
+                s += dcol[((b * H + yy) * H + xx) * Kp + tap * Cin + ci];
+        }
+        ga[i] = s;
+    }
+}
+
+// bf16 transpose: out[c][r] = in[r][c] for r < R, c < Cc (32 x 32 tiles).
+__global__ void transpose_kernel(const bf16 *__restrict__ in, int64_t ldi, int64_t R, int Cc,
+                                 bf16 *__restrict__ out, int64_t ldo) {
+    __shared__ bf16 t[32][33];
+    const int64_t r0 = (int64_t)blockIdx.x * 32;
+    const int c0 = blockIdx.y * 32;
+    for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+        const int64_t r = r0 + k;
+        const int c = c0 + threadIdx.x;
+        t[k][threadIdx.x] = (r < R && c < Cc) ? in[r * ldi + c] : __float2bfloat16_rn(0.0f);
+    }
+    __syncthreads();
+    for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+        const int c = c0 + k;
+        const int64_t r = r0 + threadIdx.x;
+        if (c < Cc && r < R) out[(int64_t)c * ldo + r] = t[threadIdx.x][k];
+    }
+}
+
+// fc 64 -> 2 (CUDA cores): z5[b][o] = sum_k a4[b][k] * bf16(w5[o][k]) + b5[o].
+__global__ void fc2_kernel(const bf16 *__restrict__ a4, const float *__restrict__ w5,
+                           const float *__restrict__ b5, int B, float *__restrict__ z5) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= B * 2) return;
+    const int b = i / 2, o = i % 2;
+    float s = 0.0f;
+    for (int k = 0; k < kHid; k++)
+        s = fmaf((float)a4[b * kHid + k], __bfloat162float(__float2bfloat16_rn(w5[o * kHid + k])), s);
+    z5[i] = s + b5[o];
+}
+
+// Mean softmax cross-entropy and its gradient g5 = (softmax - onehot) / B, one
+// block; loss_out (optional) receives the mean loss.
+__global__ void loss_kernel(const float *__restrict__ z5, const int32_t *__restrict__ y, int B,
+                            float *__restrict__ g5, float *__restrict__ loss_out) {
+    __shared__ float red[256];
+    float acc = 0.0f;
+    for (int b = threadIdx.x; b < B; b += blockDim.x) {
+        const float z0 = z5[2 * b], z1 = z5[2 * b + 1];
+        const float m = fmaxf(z0, z1);
+        const float e0 = expf(z0 - m), e1 = expf(z1 - m);
+        const float s = e0 + e1;
+        const int lab = y[b] ? 1 : 0;
+        acc += -logf((lab ? e1 : e0) / s);
+        g5[2 * b] = (e0 / s - (lab == 0 ? 1.0f : 0.0f)) / (float)B;
+        g5[2 * b + 1] = (e1 / s - (lab == 1 ? 1.0f : 0.0f)) / (float)B;
+    }
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0 && loss_out) *loss_out = red[0] / (float)B;
+}
+
+// Back through fc 64 -> 2 and the ReLU of fc1 (CUDA cores):
+//   dw5[o][k] = sum_b bf16(g5[b][o]) * a4[b][k],  db5[o] = sum_b g5[b][o]   (block 0)
+//   g4[b][k]  = (sum_o bf16(g5[b][o]) * bf16(w5[o][k])) * [z4[b][k] > 0]
+// g4 is written as bf16 [B][64] and transposed [64][ldT]; db4 += FP32 sums.
+__global__ void fc2_back_kernel(const float *__restrict__ g5, const bf16 *__restrict__ a4,
+                                const float *__restrict__ w5, const float *__restrict__ z4,
+                                int B, float *__restrict__ dw5, float *__restrict__ db5,
+                                bf16 *__restrict__ g4, bf16 *__restrict__ g4T, int64_t ldT,
+                                float *__restrict__ db4) {
+    const int k = threadIdx.x;  // 64 threads: one hidden unit each
+    if (blockIdx.x == 0) {
+        float s0 = 0.0f, s1 = 0.0f, t0 = 0.0f, t1 = 0.0f;
+        for (int b = 0; b < B; b++) {
+            const float a = (float)a4[b * kHid + k];
+            s0 = fmaf(__bfloat162float(__float2bfloat16_rn(g5[2 * b])), a, s0);
+            s1 = fmaf(__bfloat162float(__float2bfloat16_rn(g5[2 * b + 1])), a, s1);
+            t0 += g5[2 * b];
+            t1 += g5[2 * b + 1];
+        }
+        dw5[k] = s0;
+        dw5[kHid + k] = s1;
+        if (k == 0) {
+            db5[0] = t0;
+            db5[1] = t1;
+        }
+    }
+    const float w0 = __bfloat162float(__float2bfloat16_rn(w5[k]));
+    const float w1 = __bfloat162float(__float2bfloat16_rn(w5[kHid + k]));
+    float dsum = 0.0f;
+    for (int b = blockIdx.x; b < B; b += gridDim.x) {
+        const float ga = __bfloat162float(__float2bfloat16_rn(g5[2 * b])) * w0 +
+                         __bfloat162float(__float2bfloat16_rn(g5[2 * b + 1])) * w1;
+        const float v = z4[b * kHid + k] > 0.0f ? ga : 0.0f;
+        g4[b * kHid + k] = __float2bfloat16_rn(v);
+        g4T[(int64_t)k * ldT + b] = __float2bfloat16_rn(v);
+        dsum += v;
+    }
+    atomicAdd(&db4[k], dsum);
+}
+
+// Adam on the flat FP32 parameter vector (step number t >= 1).
+__global__ void adam_kernel(float *__restrict__ p, const float *__restrict__ g,
+                            float *__restrict__ m, float *__restrict__ v, int64_t n, float lr,
+                            float b1, float b2, float eps, float c1, float c2) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const float gi = g[i];
+        const float mi = b1 * m[i] + (1.0f - b1) * gi;
+        const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    }
+}
+
+// bf16 GEMM copies of the conv weights: W[co][(ky*3+kx)*Cin + ci] (padded to
+// Kp) and its transpose WT[k][co] (ld Cout8), from w[co][ci][ky][kx]; and the
+// fc1 weight W4 [64][2048] with its transpose W4T [2048][64].
+__global__ void pack_kernel(const float *__restrict__ params, int64_t w1, int64_t w2, int64_t w3,
+                            int64_t w4, bf16 *__restrict__ W0, bf16 *__restrict__ W0T,
+                            bf16 *__restrict__ W1, bf16 *__restrict__ W1T, bf16 *__restrict__ W2,
+                            bf16 *__restrict__ W2T, bf16 *__restrict__ W4,
+                            bf16 *__restrict__ W4T) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < (int64_t)kHid * kFc) {
+        const bf16 v = __float2bfloat16_rn(params[w4 + i]);
+        W4[i] = v;
+        W4T[(i % kFc) * kHid + i / kFc] = v;
+    }
+    const int64_t woff[3] = {w1, w2, w3};
+    bf16 *Wd[3] = {W0, W1, W2};
+    bf16 *WTd[3] = {W0T, W1T, W2T};
+#pragma unroll
+    for (int l = 0; l < kLayers; l++) {
+        const int Cin = cin_of(l), Cout = cout_of(l), Kp = kpad(l);
+        if (i < (int64_t)Cout * Kp) {
+            const int co = (int)(i / Kp), k = (int)(i % Kp);
+            float v = 0.0f;
+            if (k < 9 * Cin) {
+                const int tap = k / Cin, ci = k % Cin;
+                v = params[woff[l] + ((int64_t)co * Cin + ci) * 9 + tap];
+            }
+            const bf16 b = __float2bfloat16_rn(v);
+            Wd[l][i] = b;
+            WTd[l][(int64_t)k * round8(Cout) + co] = b;
+        }
+    }
+}
+
+// Back to the oracle's conv weight-gradient layout: dw[co][ci][ky][kx] =
+// dW[co][(ky*3+kx)*Cin + ci].
+__global__ void unpack_conv_grad_kernel(const float *__restrict__ dW, int Cin, int Cout, int Kp,
+                                        float *__restrict__ dw) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= Cout * Cin * 9) return;
+    const int tap = i % 9, ci = (i / 9) % Cin, co = i / (9 * Cin);
+    dw[i] = dW[(int64_t)co * Kp + tap * Cin + ci];
+}
+
+}  // namespace
+
+struct gsp_ranker_s {
+    int max_batch = 0;
+    Offsets off{};
+    float *params = nullptr, *grads = nullptr, *m = nullptr, *v = nullptr;
+    int64_t step = 0;
+    // packed bf16 weights
+    bf16 *W[kLayers] = {}, *WT[kLayers] = {}, *W4 = nullptr, *W4T = nullptr;
+    // activations
+    bf16 *col[kLayers] = {}, *colT[kLayers] = {}, *a[kLayers] = {};
+    float *z[kLayers] = {};
+    uint8_t *idx[kLayers] = {};
+    float *z4 = nullptr, *z5 = nullptr, *g5 = nullptr, *ga3 = nullptr, *loss = nullptr;
+    bf16 *a4 = nullptr, *g4 = nullptr, *g4T = nullptr, *a3T = nullptr;
+    // backward scratch
+    bf16 *gz[kLayers] = {}, *gzT[kLayers] = {};
+    float *ga[kLayers] = {};    // gradient w.r.t. the pooled output of layer l
+    float *dcol = nullptr, *dW = nullptr;
+    int *err = nullptr;
+    std::vector<void *> allocs;
+    int32_t launches = 0;
+};
+
+namespace {
+
+template <typename T>
+bool ralloc(gsp_ranker_s *r, T **p, size_t n) {
+    if (cudaMalloc((void **)p, std::max<size_t>(n, 1) * sizeof(T)) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return false;
+    }
+    r->allocs.push_back(*p);
+    return true;
+}
+
+void free_ranker(gsp_ranker_s *r) {
+    if (!r) return;
+    for (void *p : r->allocs) cudaFree(p);
+    delete r;
+}
+
+int blocks_for(int64_t n, int threads = 256) {
+    return (int)std::min<int64_t>((n + threads - 1) / threads, 152 * 16);
+}
+
+#define RK_LAUNCH(...)                                \
+    do {                                              \
+        __VA_ARGS__;                                  \
+        cudaError_t e_ = cudaGetLastError();          \
+        if (e_ != cudaSuccess) return e_;             \
+        r->launches++;                                \
+    } while (0)
+
+cudaError_t pack(gsp_ranker_s *r, cudaStream_t s) {
+    RK_LAUNCH((pack_kernel<<<blocks_for((int64_t)kHid * kFc), 256, 0, s>>>(
+        r->params, r->off.w[0], r->off.w[1], r->off.w[2], r->off.w[3], r->W[0], r->WT[0], r->W[1],
+        r->WT[1], r->W[2], r->WT[2], r->W4, r->W4T)));
+    return cudaSuccess;
+}
+
+cudaError_t gemm(gsp_ranker_s *r, const bf16 *A, int64_t lda, const bf16 *B, int64_t ldb, float *C,
+                 int64_t ldc, bf16 *Cb, int64_t ldcb, int M, int N, int K, const float *bias,
+                 bool relu, int splitk, cudaStream_t s) {
+    cudaError_t e = gsp::launch_gemm_bf16(A, lda, B, ldb, C, ldc, Cb, ldcb, M, N, K, bias, relu,
+                                          splitk, r->err, s);
+    if (e == cudaSuccess) r->launches++;
+    return e;
+}
+
+// Forward pass of n snippets (FP32 [n][64][64]); logits into r->z5.
+cudaError_t forward(gsp_ranker_s *r, const float *x, int n, cudaStream_t s) {
+    for (int l = 0; l < kLayers; l++) {
+        const int H = side_of(l), Cin = cin_of(l), Cout = cout_of(l), Kp = kpad(l);
+        const int64_t P = (int64_t)n * H * H;
+        if (l == 0)
+            RK_LAUNCH((im2col_kernel<float><<<blocks_for(P * Kp), 256, 0, s>>>(x, n, H, Cin, Kp,
+                                                                                r->col[0])));
+        else
+            RK_LAUNCH((im2col_kernel<bf16><<<blocks_for(P * Kp), 256, 0, s>>>(r->a[l - 1], n, H, Cin,
+                                                                               Kp, r->col[l])));
+        cudaError_t e = gemm(r, r->col[l], Kp, r->W[l], Kp, r->z[l], Cout, nullptr, 0, (int)P, Cout,
+                             Kp, r->params + r->off.b[l], true, 1, s);
+        if (e != cudaSuccess) return e;
+        RK_LAUNCH((pool_kernel<<<blocks_for(P / 4 * Cout), 256, 0, s>>>(r->z[l], n, H, Cout, r->a[l],
+                                                                         r->idx[l])));
+    }
+    cudaError_t e = gemm(r, r->a[2], kFc, r->W4, kFc, r->z4, kHid, r->a4, kHid, n, kHid, kFc,
+                         r->params + r->off.b[3], true, 1, s);
+    if (e != cudaSuccess) return e;
+    RK_LAUNCH((fc2_kernel<<<(2 * n + 127) / 128, 128, 0, s>>>(r->a4, r->params + r->off.w[4],
+                                                              r->params + r->off.b[4], n, r->z5)));
+    return cudaSuccess;
+}
+
+// Loss, gradients (into r->grads, the oracle's layout) and one Adam step.
+cudaError_t backward(gsp_ranker_s *r, const int32_t *labels, int n, float lr, cudaStream_t s) {
+    const int n8 = round8(n);
+    cudaError_t e = cudaMemsetAsync(r->grads, 0, (size_t)r->off.total * sizeof(float), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(r->g4T, 0, (size_t)kHid * n8 * sizeof(bf16), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(r->a3T, 0, (size_t)kFc * n8 * sizeof(bf16), s);
+    if (e != cudaSuccess) return e;
+    RK_LAUNCH((loss_kernel<<<1, 256, 0, s>>>(r->z5, labels, n, r->g5, r->loss)));
+    RK_LAUNCH((fc2_back_kernel<<<std::min(n, 152), kHid, 0, s>>>(
+        r->g5, r->a4, r->params + r->off.w[4], r->z4, n, r->grads + r->off.w[4],
+        r->grads + r->off.b[4], r->g4, r->g4T, n8, r->grads + r->off.b[3])));
+    {
+        dim3 grid((unsigned)((n + 31) / 32), (unsigned)(kFc / 32));
+        RK_LAUNCH((transpose_kernel<<<grid, dim3(32, 8), 0, s>>>(r->a[2], kFc, n, kFc, r->a3T, n8)));
+    }
+    e = gemm(r, r->g4T, n8, r->a3T, n8, r->grads + r->off.w[3], kFc, nullptr, 0, kHid, kFc, n8,
+             nullptr, false, 1, s);
+    if (e == cudaSuccess)
+        e = gemm(r, r->g4, kHid, r->W4T, kHid, r->ga[2], kFc, nullptr, 0, n, kFc, kHid, nullptr,
+                 false, 1, s);
+    if (e != cudaSuccess) return e;
+    for (int l = kLayers - 1; l >= 0; l--) {
+        const int H = side_of(l), Cin = cin_of(l), Cout = cout_of(l), Kp = kpad(l);
+        const int64_t P = (int64_t)n * H * H;  // a multiple of 256
+        RK_LAUNCH((pool_back_kernel<<<blocks_for(P * Cout), 256, Cout * sizeof(float), s>>>(
+            r->ga[l], r->idx[l], r->z[l], n, H, Cout, r->gz[l], r->gzT[l], P,
+            r->grads + r->off.b[l])));
+        {
+            dim3 grid((unsigned)((P + 31) / 32), (unsigned)((Kp + 31) / 32));
+            RK_LAUNCH((transpose_kernel<<<grid, dim3(32, 8), 0, s>>>(r->col[l], Kp, P, Kp,
+                                                                      r->colT[l], P)));
+        }
+        e = cudaMemsetAsync(r->dW, 0, (size_t)Cout * Kp * sizeof(float), s);
+        if (e != cudaSuccess) return e;
+        const int ksteps = (int)(P / 64);
+        const int splitk = std::max(1, std::min(ksteps, 4 * 152 / std::max(1, (Kp + 127) / 128)));
+        e = gemm(r, r->gzT[l], P, r->colT[l], P, r->dW, Kp, nullptr, 0, Cout, Kp, (int)P, nullptr,
+                 false, splitk, s);
+        if (e != cudaSuccess) return e;
+        RK_LAUNCH((unpack_conv_grad_kernel<<<(Cout * Cin * 9 + 255) / 256, 256, 0, s>>>(
+            r->dW, Cin, Cout, Kp, r->grads + r->off.w[l])));
+        if (l > 0) {
+            e = gemm(r, r->gz[l], Cout, r->WT[l], round8(Cout), r->dcol, Kp, nullptr, 0, (int)P, Kp,
+                     Cout, nullptr, false, 1, s);
+            if (e != cudaSuccess) return e;
+            RK_LAUNCH((col2im_kernel<<<blocks_for(P * Cin), 256, 0, s>>>(r->dcol, n, H, Cin, Kp,
+                                                                          r->ga[l - 1])));
+        }
+    }
+    r->step++;
+    const double c1 = 1.0 - std::pow(0.9, (double)r->step);
+    const double c2 = 1.0 - std::pow(0.999, (double)r->step);
+    RK_LAUNCH((adam_kernel<<<blocks_for(r->off.total), 256, 0, s>>>(
+        r->params, r->grads, r->m, r->v, r->off.total, lr, 0.9f, 0.999f, 1e-8f, (float)c1,
+        (float)c2)));
+    return pack(r, s);
+}
+
+gsp_status status_of(cudaError_t e, const char *what) {
+    if (e == cudaSuccess) return GSP_OK;
+    gsp::record_error(e, what);
+    return e == cudaErrorInvalidValue ? GSP_ERR_INVALID_ARG : GSP_ERR_CUDA;
+}
+
+// Snippet of candidate blockIdx.x: out[i][j] = sum over the samples s of time
+// bin j (f = max(1, w / 4) samples, bins centred on t + w / 2) of the
+// normalised series of row dm - 32 + i, ((D - m) - (c0 + beta j)) / sigma_ref
+// (0 in bad blocks, rows with sigma_ref = 0, outside the rows or past Ls),
+// divided by sqrt(f).
+__global__ void snippet_kernel(const int32_t *__restrict__ D, int64_t stride, int ndm, int64_t Ls,
+                               int B, const gsp::BlockParam *__restrict__ bp, int64_t nb_max,
+                               const double *__restrict__ sref, const gsp_cand *__restrict__ cands,
+                               float *__restrict__ out) {
+    const gsp_cand c = cands[blockIdx.x];
+    const int f = max(1, c.width / 4);
+    const int64_t tc = c.t + c.width / 2;
+    const float rs = 1.0f / sqrtf((float)f);
+    for (int o = threadIdx.x; o < kS * kS; o += blockDim.x) {
+        const int i = o / kS, j = o % kS;
+        const int r = c.dm_idx - kS / 2 + i;
+        float v = 0.0f;
+        if (r >= 0 && r < ndm && sref[r] > 0.0) {
+            const float inv = (float)(1.0 / sref[r]);
+            const int64_t a = tc + (int64_t)(j - kS / 2) * f;
+            const int64_t s1 = min(a + f, Ls);
+            for (int64_t s = max(a, (int64_t)0); s < s1; s++) {
+                const int64_t b = s / B;
+                const gsp::BlockParam q = bp[(int64_t)r * nb_max + b];
+                if (q.good)
+                    v += ((float)(D[(int64_t)r * stride + s] - q.m) -
+                          (q.c0 + q.beta * (float)(s - b * B))) * inv;
+            }
+        }
+        out[(int64_t)blockIdx.x * kS * kS + o] = v * rs;
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+gsp_status gsp_ranker_snippets(gsp_plan_t p, const int32_t *d_D, int64_t stride,
+                               const gsp_cand *d_cands, int32_t n, float *d_out, void *stream) {
+    if (!p || !d_D || !d_cands || !d_out || n < 0) return GSP_ERR_INVALID_ARG;
+    if (!p->have_search) return GSP_ERR_STATE;
+    if (n == 0) return GSP_OK;
+    const int64_t Ls = p->last_nb * p->desc.block_len;
+    snippet_kernel<<<n, 256, 0, (cudaStream_t)stream>>>(d_D, stride, p->desc.ndm, Ls,
+                                                        p->desc.block_len, p->d_bparam, p->nb_max,
+                                                        p->d_sref, d_cands, d_out);
+    return status_of(cudaGetLastError(), "snippet launch");
+}
+
+int64_t gsp_ranker_num_params(void) { return offsets().total; }
+
+gsp_status gsp_ranker_create(gsp_ranker_t *out, int32_t max_batch, uint64_t seed) {
+    if (!out || max_batch < 1 || max_batch > 4096) return GSP_ERR_INVALID_ARG;
+    *out = nullptr;
+    gsp_ranker_s *r = new (std::nothrow) gsp_ranker_s();
+    if (!r) return GSP_ERR_OOM;
+    r->max_batch = max_batch;
+    r->off = offsets();
+    const int Bm = max_batch, B8 = round8(Bm);
+    const int64_t T = r->off.total;
+    bool ok = ralloc(r, &r->params, T) && ralloc(r, &r->grads, T) && ralloc(r, &r->m, T) &&
+              ralloc(r, &r->v, T) && ralloc(r, &r->W4, (size_t)kHid * kFc) &&
+              ralloc(r, &r->W4T, (size_t)kHid * kFc) && ralloc(r, &r->z4, (size_t)Bm * kHid) &&
+              ralloc(r, &r->a4, (size_t)Bm * kHid) && ralloc(r, &r->z5, (size_t)Bm * 2) &&
+              ralloc(r, &r->g5, (size_t)Bm * 2) && ralloc(r, &r->g4, (size_t)Bm * kHid) &&
+              ralloc(r, &r->g4T, (size_t)kHid * B8) && ralloc(r, &r->a3T, (size_t)kFc * B8) &&
+              ralloc(r, &r->loss, 1) && ralloc(r, &r->err, 1);
+    size_t dcol = 0, dw = 0;
+    for (int l = 0; ok && l < kLayers; l++) {
+        const int H = side_of(l), Cout = cout_of(l), Kp = kpad(l);
+        const int64_t P = (int64_t)Bm * H * H;
+        ok = ralloc(r, &r->W[l], (size_t)Cout * Kp) && ralloc(r, &r->WT[l], (size_t)Kp * round8(Cout)) &&
+             ralloc(r, &r->col[l], (size_t)P * Kp) && ralloc(r, &r->colT[l], (size_t)P * Kp) &&
+             ralloc(r, &r->z[l], (size_t)P * Cout) && ralloc(r, &r->a[l], (size_t)P / 4 * Cout) &&
+             ralloc(r, &r->idx[l], (size_t)P / 4 * Cout) && ralloc(r, &r->gz[l], (size_t)P * Cout) &&
+             ralloc(r, &r->gzT[l], (size_t)P * Cout) && ralloc(r, &r->ga[l], (size_t)P / 4 * Cout);
+        if (l > 0) dcol = std::max(dcol, (size_t)P * Kp);
+        dw = std::max(dw, (size_t)Cout * Kp);
+    }
+    ok = ok && ralloc(r, &r->dcol, dcol) && ralloc(r, &r->dW, dw);
+    if (!ok) {
+        free_ranker(r);
+        return GSP_ERR_OOM;
+    }
+    // He-uniform weights, zero biases, from a 64-bit LCG (host)
+    std::vector<float> h((size_t)T, 0.0f);
+    uint64_t st = seed * 6364136223846793005ull + 1442695040888963407ull;
+    for (int i = 0; i < 5; i++) {
+        const int fan_in = i < 3 ? 9 * cin_of(i) : (i == 3 ? kFc : kHid);
+        const double lim = std::sqrt(6.0 / fan_in);
+        for (int64_t j = 0; j < kWsize[i]; j++) {
+            st = st * 6364136223846793005ull + 1442695040888963407ull;
+            const double u = (double)(st >> 11) * (1.0 / 9007199254740992.0);
+            h[(size_t)(r->off.w[i] + j)] = (float)((2.0 * u - 1.0) * lim);
+        }
+    }
+    cudaError_t e = cudaMemcpy(r->params, h.data(), (size_t)T * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(r->m, 0, (size_t)T * 4);
+    if (e == cudaSuccess) e = cudaMemset(r->v, 0, (size_t)T * 4);
+    if (e == cudaSuccess) e = cudaMemset(r->err, 0, sizeof(int));
+    if (e == cudaSuccess) e = pack(r, 0);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        gsp::record_error(e, "ranker init");
+        free_ranker(r);
+        return GSP_ERR_CUDA;
+    }
+    *out = r;
+    return GSP_OK;
+}
+
+gsp_status gsp_ranker_destroy(gsp_ranker_t r) {
+    if (!r) return GSP_ERR_INVALID_ARG;
+    cudaError_t e = cudaDeviceSynchronize();
+    free_ranker(r);
+    return e == cudaSuccess ? GSP_OK : GSP_ERR_CUDA;
+}
+
+gsp_status gsp_ranker_set_params(gsp_ranker_t r, const float *host_params) {
+    if (!r || !host_params) return GSP_ERR_INVALID_ARG;
+    cudaError_t e = cudaMemcpy(r->params, host_params, (size_t)r->off.total * 4,
+                               cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(r->m, 0, (size_t)r->off.total * 4);
+    if (e == cudaSuccess) e = cudaMemset(r->v, 0, (size_t)r->off.total * 4);
+    if (e == cudaSuccess) e = pack(r, 0);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    r->step = 0;
+    return status_of(e, "ranker set params");
+}
+
+gsp_status gsp_ranker_get_params(gsp_ranker_t r, float *host_params, float *host_grads) {
+    if (!r) return GSP_ERR_INVALID_ARG;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess && host_params)
+        e = cudaMemcpy(host_params, r->params, (size_t)r->off.total * 4, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && host_grads)
+        e = cudaMemcpy(host_grads, r->grads, (size_t)r->off.total * 4, cudaMemcpyDeviceToHost);
+    return status_of(e, "ranker get params");
+}
+
+gsp_status gsp_ranker_forward(gsp_ranker_t r, const float *d_x, int32_t n, float *d_logits,
+                              void *stream) {
+    if (!r || !d_x || n < 1 || n > r->max_batch) return GSP_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    r->launches = 0;
+    cudaError_t e = forward(r, d_x, n, s);
+    if (e == cudaSuccess && d_logits)
+        e = cudaMemcpyAsync(d_logits, r->z5, (size_t)n * 2 * 4, cudaMemcpyDeviceToDevice, s);
+    return status_of(e, "ranker forward");
+}
+
+gsp_status gsp_ranker_train_step(gsp_ranker_t r, const float *d_x, const int32_t *d_labels,
+                                 int32_t n, float lr, float *d_loss, void *stream) {
+    if (!r || !d_x || !d_labels || n < 1 || n > r->max_batch || !(lr >= 0.0f))
+        return GSP_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    r->launches = 0;
+    cudaError_t e = forward(r, d_x, n, s);
+    if (e == cudaSuccess) e = backward(r, d_labels, n, lr, s);
+    if (e == cudaSuccess && d_loss)
+        e = cudaMemcpyAsync(d_loss, r->loss, sizeof(float), cudaMemcpyDeviceToDevice, s);
+    return status_of(e, "ranker train step");
+}
+
+gsp_status gsp_ranker_finish(gsp_ranker_t r, void *stream) {
+    if (!r) return GSP_ERR_INVALID_ARG;
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    int flag = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&flag, r->err, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return status_of(e, "ranker finish");
+    if (flag) {
+        cudaMemset(r->err, 0, sizeof(int));
+        return GSP_ERR_TIMEOUT;
+    }
+    return GSP_OK;
+}
+
+int32_t gsp_ranker_launches(gsp_ranker_t r) { return r ? r->launches : -1; }
+
+}  // extern "C"

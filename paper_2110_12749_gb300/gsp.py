@@ -135,6 +135,17 @@ def lib():
             "gsp_gemm_bf16": ([_vp, _i64, _vp, _i64, _vp, _i64, ctypes.c_int32, ctypes.c_int32,
                                ctypes.c_int32, _vp, ctypes.c_int32, ctypes.c_int32, _vp, _vp],
                               ctypes.c_int),
+            "gsp_ranker_num_params": ([], _i64),
+            "gsp_ranker_create": ([_vp, ctypes.c_int32, ctypes.c_uint64], ctypes.c_int),
+            "gsp_ranker_destroy": ([_vp], ctypes.c_int),
+            "gsp_ranker_set_params": ([_vp, _vp], ctypes.c_int),
+            "gsp_ranker_get_params": ([_vp, _vp, _vp], ctypes.c_int),
+            "gsp_ranker_snippets": ([_vp, _vp, _i64, _vp, ctypes.c_int32, _vp, _vp], ctypes.c_int),
+            "gsp_ranker_forward": ([_vp, _vp, ctypes.c_int32, _vp, _vp], ctypes.c_int),
+            "gsp_ranker_train_step": ([_vp, _vp, _vp, ctypes.c_int32, ctypes.c_float, _vp, _vp],
+                                      ctypes.c_int),
+            "gsp_ranker_finish": ([_vp, _vp], ctypes.c_int),
+            "gsp_ranker_launches": ([_vp], ctypes.c_int32),
             "gsp_status_string": ([ctypes.c_int], ctypes.c_char_p),
             "gsp_last_error_string": ([], ctypes.c_char_p),
             "gsp_version": ([], ctypes.c_int32),
@@ -651,3 +662,83 @@ def gsp_gemm_bf16(A, B, C, M, N, K, bias=None, relu=False, splitk=1, err=None, s
                                _vp(bias.data_ptr()) if bias is not None else None, int(relu),
                                splitk, _vp(err.data_ptr()) if err is not None else None,
                                _stream(stream)), "gsp_gemm_bf16")
+
+
+
+# ---------------------------------------------------------------------------
+# Candidate ranker
+
+class Ranker:
+    """Owns a gsp_ranker_t."""
+
+    def __init__(self, handle, max_batch):
+        self.handle = handle
+        self.max_batch = max_batch
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            try:
+                _lib.gsp_ranker_destroy(self.handle)
+            except Exception:
+                pass
+            self.handle = None
+
+
+def gsp_ranker_num_params():
+    return int(lib().gsp_ranker_num_params())
+
+
+def gsp_ranker_create(max_batch, seed=0):
+    h = _vp()
+    _check(lib().gsp_ranker_create(ctypes.byref(h), max_batch, seed), "gsp_ranker_create")
+    return Ranker(h, max_batch)
+
+
+def gsp_ranker_destroy(r):
+    if r.handle:
+        st = lib().gsp_ranker_destroy(r.handle)
+        r.handle = None
+        _check(st, "gsp_ranker_destroy")
+
+
+def gsp_ranker_set_params(r, params):
+    p = np.ascontiguousarray(params, dtype=np.float32).reshape(-1)
+    assert p.size == gsp_ranker_num_params()
+    _check(lib().gsp_ranker_set_params(r.handle, _np_ptr(p)), "gsp_ranker_set_params")
+
+
+def gsp_ranker_get_params(r):
+    """(parameters, gradients of the last training step), float32 numpy."""
+    n = gsp_ranker_num_params()
+    p = np.zeros(n, np.float32)
+    g = np.zeros(n, np.float32)
+    _check(lib().gsp_ranker_get_params(r.handle, _np_ptr(p), _np_ptr(g)), "gsp_ranker_get_params")
+    return p, g
+
+
+def gsp_ranker_snippets(plan, D, cands, out, stream=None):
+    """D: torch int32 CUDA [ndm][stride]; cands: torch uint8 CUDA holding n
+    records of CAND_DTYPE; out: torch float CUDA [n][64][64]."""
+    n = cands.numel() // CAND_DTYPE.itemsize
+    _check(lib().gsp_ranker_snippets(plan.handle, _vp(D.data_ptr()), D.stride(0),
+                                     _vp(cands.data_ptr()), n, _vp(out.data_ptr()),
+                                     _stream(stream)), "gsp_ranker_snippets")
+
+
+def gsp_ranker_forward(r, x, n, logits, stream=None):
+    _check(lib().gsp_ranker_forward(r.handle, _vp(x.data_ptr()), n, _vp(logits.data_ptr()),
+                                    _stream(stream)), "gsp_ranker_forward")
+
+
+def gsp_ranker_train_step(r, x, labels, n, lr, loss=None, stream=None):
+    _check(lib().gsp_ranker_train_step(r.handle, _vp(x.data_ptr()), _vp(labels.data_ptr()), n,
+                                       float(lr), _vp(loss.data_ptr()) if loss is not None else None,
+                                       _stream(stream)), "gsp_ranker_train_step")
+
+
+def gsp_ranker_finish(r, stream=None):
+    _check(lib().gsp_ranker_finish(r.handle, _stream(stream)), "gsp_ranker_finish")
+
+
+def gsp_ranker_launches(r):
+    return int(lib().gsp_ranker_launches(r.handle))
