@@ -61,6 +61,9 @@ def parse():
     ap.add_argument("--batch-steps", type=int, default=3)
     ap.add_argument("--subband-steps", type=int, default=3,
                     help="timed steps of the two-stage sub-band path on the same beam (0: skip)")
+    ap.add_argument("--ranker-beams", type=int, default=12,
+                    help="training beams of the candidate ranker (0: skip the ranker section)")
+    ap.add_argument("--ranker-steps", type=int, default=600)
     ap.add_argument("--ddplan-steps", type=int, default=3,
                     help="timed steps of the Table 2 (Band1) DDplan search (0: skip)")
     ap.add_argument("--stream-gbs", type=float, default=6.0,
@@ -445,6 +448,43 @@ def run_ddplan(args):
             "data": "synthetic Gaussian noise (mu 128, sigma 20)"}
 
 
+def run_ranker(args):
+    """Candidate ranker: trained on snippets of the candidates the pipeline finds
+    in synthetic CRAFTS-like beams (2^18 samples, 40 injected pulses, 30 RFI
+    channels, 5 DM-0 bursts each), then scoring every candidate of fresh beams."""
+    import torch
+    from paper_2110_12749_gb300 import gsp, ranker, synth
+    wl = ranker.short_crafts(1 << 18)
+    src = ranker.BeamSource(wl)
+    t0 = time.perf_counter()
+    x, y = ranker.build_training_set(src, args.ranker_beams, synth.BASE_SEED + 500)
+    t_data = time.perf_counter() - t0
+    r = gsp.gsp_ranker_create(4096, seed=1)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    losses = ranker.train(r, x, y, args.ranker_steps, batch=256, lr=2e-3, seed=3)
+    e1.record()
+    torch.cuda.synchronize()
+    train_ms = e0.elapsed_time(e1)
+    npos, nneg = int((y == 1).sum()), int((y == 0).sum())
+    del x
+    torch.cuda.empty_cache()
+    ev = ranker.evaluate(r, src, 4, synth.BASE_SEED + 900)
+    gsp.gsp_ranker_destroy(r)
+    gsp.gsp_plan_destroy(src.plan)
+    del src
+    torch.cuda.empty_cache()
+    ev.update({"train_beams": args.ranker_beams, "train_snippets": npos + nneg,
+               "train_positives": npos, "train_steps": args.ranker_steps, "batch": 256,
+               "train_ms": train_ms, "train_steps_per_s": args.ranker_steps / (train_ms / 1e3),
+               "loss_first_last": [losses[0], losses[-1]], "data_s": t_data,
+               "params": gsp.gsp_ranker_num_params(),
+               "eval": "4 fresh beams; recall over injected pulses with S/N >= 8 that the "
+                       "search detects; precision over candidates scored >= 0.5"})
+    return ev
+
+
 def run_gsp(args):
     import torch
     from paper_2110_12749_gb300 import gsp, synth
@@ -549,7 +589,8 @@ def run_gsp(args):
     ddplan_res = None
     if args.subband_steps > 0 and rank == 0:
         subband_res = run_subband(args, wl, plan, xd)
-    if args.stream_beams > 0 or args.batch_beams > 0 or args.ddplan_steps > 0:
+    if args.stream_beams > 0 or args.batch_beams > 0 or args.ddplan_steps > 0 or \
+            args.ranker_beams > 0:
         if plan is not None:
             gsp.gsp_plan_destroy(plan)
             plan = None
@@ -561,6 +602,9 @@ def run_gsp(args):
         stream_res = run_stream(args, wl, delays_fn)
     if args.ddplan_steps > 0 and rank == 0:
         ddplan_res = run_ddplan(args)
+    ranker_res = None
+    if args.ranker_beams > 0 and rank == 0:
+        ranker_res = run_ranker(args)
     if rank == 0:
         cpu = None
         if not args.no_cpu_baseline:
@@ -603,6 +647,8 @@ def run_gsp(args):
             line["subband"] = subband_res
         if ddplan_res is not None:
             line["ddplan"] = ddplan_res
+        if ranker_res is not None:
+            line["ranker"] = ranker_res
         if stream_res is not None:
             line["stream"] = stream_res
             line["p99_chunk_latency_ms"] = stream_res["p99_ms"]
