@@ -63,7 +63,7 @@ def parse():
                     help="timed steps of the two-stage sub-band path on the same beam (0: skip)")
     ap.add_argument("--ranker-beams", type=int, default=12,
                     help="training beams of the candidate ranker (0: skip the ranker section)")
-    ap.add_argument("--ranker-steps", type=int, default=600)
+    ap.add_argument("--ranker-steps", type=int, default=1200)
     ap.add_argument("--ddplan-steps", type=int, default=3,
                     help="timed steps of the Table 2 (Band1) DDplan search (0: skip)")
     ap.add_argument("--stream-gbs", type=float, default=6.0,
@@ -463,7 +463,8 @@ def run_ranker(args):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     e0.record()
-    losses = ranker.train(r, x, y, args.ranker_steps, batch=256, lr=2e-3, seed=3)
+    losses = ranker.fit(r, x, y, steps=(args.ranker_steps // 3, args.ranker_steps - args.ranker_steps // 3),
+                        seed=3)
     e1.record()
     torch.cuda.synchronize()
     train_ms = e0.elapsed_time(e1)
@@ -480,6 +481,9 @@ def run_ranker(args):
                "train_ms": train_ms, "train_steps_per_s": args.ranker_steps / (train_ms / 1e3),
                "loss_first_last": [losses[0], losses[-1]], "data_s": t_data,
                "params": gsp.gsp_ranker_num_params(),
+               "training": "every candidate of the training beams (pulse tracks excluded); "
+                           "1/3 of the steps with uniform negatives, then the 20000 "
+                           "highest-scored negatives over-sampled",
                "eval": "4 fresh beams; recall over injected pulses with S/N >= 8 that the "
                        "search detects; precision over candidates scored >= 0.5"})
     return ev

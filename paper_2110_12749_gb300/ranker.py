@@ -99,44 +99,57 @@ class BeamSource:
         return out
 
 
-def build_training_set(src, beams, seed, neg_per_beam=4000, rng=None):
-    """Snippets and labels: every core candidate and a random sample of label-0
-    candidates of each beam."""
+def build_training_set(src, beams, seed):
+    """Snippets (torch float CUDA) and labels of every candidate labelled 0 or
+    1 in the given number of beams (candidates on a pulse's track excluded)."""
     torch = src.torch
-    rng = rng or np.random.default_rng(seed)
     xs, ys = [], []
     for b in range(beams):
         cands, lab, _, _ = src.search(b, seed)
-        pos = np.nonzero(lab == 1)[0]
-        neg = np.nonzero(lab == 0)[0]
-        if neg.size > neg_per_beam:
-            neg = rng.choice(neg, neg_per_beam, replace=False)
-        sel = np.concatenate([pos, neg])
-        xs.append(src.snippets(cands[sel]))
-        ys.append(np.concatenate([np.ones(pos.size, np.int32), np.zeros(neg.size, np.int32)]))
+        keep = lab >= 0
+        xs.append(src.snippets(cands[keep]))
+        ys.append(lab[keep].astype(np.int32))
     return torch.cat(xs), np.concatenate(ys)
 
 
-def train(ranker, x, y, steps, batch=256, lr=2e-3, seed=0):
-    """Balanced mini-batches (half positives) with Adam; returns the losses."""
+def train(ranker, x, y, steps, batch=256, lr=2e-3, seed=0, hard=None, pos_frac=0.25):
+    """Mini-batches with a fixed share of positives and Adam; negatives are
+    drawn uniformly, or half of them from `hard` (indices of hard negatives)
+    when given.  Returns the losses seen every 50 steps."""
     torch = __import__("torch")
     rng = np.random.default_rng(seed)
     pos = np.nonzero(y == 1)[0]
     neg = np.nonzero(y == 0)[0]
+    npos = max(1, int(round(batch * pos_frac)))
+    nneg = batch - npos
     loss = torch.zeros(1, dtype=torch.float32, device="cuda")
     yd = torch.from_numpy(y).cuda()
     losses = []
     for it in range(steps):
-        idx = np.concatenate([rng.choice(pos, batch // 2), rng.choice(neg, batch - batch // 2)])
-        it_idx = torch.from_numpy(idx).cuda()
-        xb = x.index_select(0, it_idx).contiguous()
-        yb = yd.index_select(0, it_idx).contiguous()
+        if hard is not None and hard.size:
+            negs = np.concatenate([rng.choice(hard, nneg // 2), rng.choice(neg, nneg - nneg // 2)])
+        else:
+            negs = rng.choice(neg, nneg)
+        idx = torch.from_numpy(np.concatenate([rng.choice(pos, npos), negs])).cuda()
+        xb = x.index_select(0, idx).contiguous()
+        yb = yd.index_select(0, idx).contiguous()
         gsp.gsp_ranker_train_step(ranker, xb, yb, batch, lr, loss=loss)
         if it % 50 == 0 or it == steps - 1:
             gsp.gsp_ranker_finish(ranker)
             losses.append(float(loss.item()))
     gsp.gsp_ranker_finish(ranker)
     return losses
+
+
+def fit(ranker, x, y, steps=(400, 800), hard_count=20000, lr=2e-3, seed=0):
+    """Two phases: uniform negatives, then with the highest-scored negatives of
+    the training set (hard-negative mining) over-sampled."""
+    l1 = train(ranker, x, y, steps[0], lr=lr, seed=seed)
+    neg = np.nonzero(y == 0)[0]
+    s = score(ranker, x)
+    hard = neg[np.argsort(-s[neg])[:hard_count]]
+    l2 = train(ranker, x, y, steps[1], lr=lr * 0.5, seed=seed + 1, hard=hard)
+    return l1 + l2
 
 
 def score(ranker, x, chunk=None):
