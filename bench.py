@@ -454,10 +454,9 @@ def run_ranker(args):
     channels, 5 DM-0 bursts each), then scoring every candidate of fresh beams."""
     import torch
     from paper_2110_12749_gb300 import gsp, ranker, synth
-    wl = ranker.short_crafts(1 << 18)
-    src = ranker.BeamSource(wl)
+    src = ranker.BeamSource(ranker.short_crafts(1 << 18, n_pulses=100))
     t0 = time.perf_counter()
-    x, y = ranker.build_training_set(src, args.ranker_beams, synth.BASE_SEED + 500)
+    x, y, pids = ranker.build_training_set(src, args.ranker_beams, synth.BASE_SEED + 500)
     t_data = time.perf_counter() - t0
     r = gsp.gsp_ranker_create(4096, seed=1)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -468,10 +467,14 @@ def run_ranker(args):
     e1.record()
     torch.cuda.synchronize()
     train_ms = e0.elapsed_time(e1)
+    thr = ranker.choose_threshold(r, x, y, pids)
     npos, nneg = int((y == 1).sum()), int((y == 0).sum())
     del x
     torch.cuda.empty_cache()
-    ev = ranker.evaluate(r, src, 4, synth.BASE_SEED + 900)
+    src.wl = ranker.short_crafts(1 << 18, n_pulses=40)    # evaluation beams: the bench recipe
+    ev = ranker.evaluate(r, src, 4, synth.BASE_SEED + 900, threshold=thr)
+    ev["at_0.5"] = {k: v for k, v in ranker.evaluate(r, src, 4, synth.BASE_SEED + 900).items()
+                    if k in ("recall", "precision", "negatives_rejected")}
     gsp.gsp_ranker_destroy(r)
     gsp.gsp_plan_destroy(src.plan)
     del src
@@ -481,7 +484,7 @@ def run_ranker(args):
                "train_ms": train_ms, "train_steps_per_s": args.ranker_steps / (train_ms / 1e3),
                "loss_first_last": [losses[0], losses[-1]], "data_s": t_data,
                "params": gsp.gsp_ranker_num_params(),
-               "training": "every candidate of the training beams (pulse tracks excluded); "
+               "training": "every candidate of 100-pulse training beams (pulse tracks excluded); "
                            "1/3 of the steps with uniform negatives, then the 20000 "
                            "highest-scored negatives over-sampled",
                "eval": "4 fresh beams; recall over injected pulses with S/N >= 8 that the "

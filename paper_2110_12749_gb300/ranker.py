@@ -6,14 +6,18 @@ search, snippet extraction, training and inference all run in libgsp.
 Labels of a candidate (dm_idx d, start t, width w) against the injected
 pulses of its beam (pulse DM trial k = nearest trial, per-channel delays):
   1  core of a pulse: |d - k| <= 3 and |t - t0| <= w_p + smear + 4, where
-     smear = largest delay difference between the pulse and trial k;
+     smear = largest delay difference between the pulse and trial k, and an
+     S/N at least 0.6 of the best core candidate of that pulse (weaker core
+     candidates are labelled -1);
   -1 elsewhere on a pulse's dispersion track (within 60 trials, inside the
      time span the pulse's energy reaches at trial d, +-150 samples): neither
      pulse nor RFI, left out of training and of the precision;
   0  everything else (noise, RFI, DM-0 bursts).
-A pulse is recalled if its best-scored core candidate scores >= 0.5 (softmax
-probability of class 1); precision counts the candidates scoring >= 0.5
-among those labelled 0 or 1.
+A pulse is recalled if its best-scored core candidate scores at least the
+operating threshold (softmax probability of class 1); precision counts the
+candidates scoring at least the threshold among those labelled 0 or 1.  The
+threshold is chosen on the training beams (the score that keeps 99.5% of
+their pulses), never on the evaluation beams.
 """
 from __future__ import annotations
 
@@ -25,9 +29,9 @@ import numpy as np
 from . import gsp, synth
 
 
-def short_crafts(n_in=1 << 18):
+def short_crafts(n_in=1 << 18, n_pulses=40):
     """The CRAFTS-like beam (4096 channels, 2000 trials) cut to n_in samples."""
-    return dataclasses.replace(synth.WORKLOADS["crafts"], n_in=n_in)
+    return dataclasses.replace(synth.WORKLOADS["crafts"], n_in=n_in, n_pulses=n_pulses)
 
 
 def label_candidates(cands, pulses, dl, ndm):
@@ -47,8 +51,11 @@ def label_candidates(cands, pulses, dl, ndm):
         hi = p.t0 + p.width + np.maximum(shift, 0) + 150
         track = (np.abs(d - k) <= 60) & (t >= lo) & (t <= hi)
         lab[track & (lab == 0)] = -1
-        lab[core] = 1
-        pid[core] = i
+        if core.any():
+            strong = core & (cands["snr"] >= 0.6 * cands["snr"][core].max())
+            lab[core] = -1
+            lab[strong] = 1
+            pid[core] = i
     return lab, pid
 
 
@@ -101,15 +108,33 @@ class BeamSource:
 
 def build_training_set(src, beams, seed):
     """Snippets (torch float CUDA) and labels of every candidate labelled 0 or
-    1 in the given number of beams (candidates on a pulse's track excluded)."""
+    1 in the given number of beams (candidates on a pulse's track excluded),
+    and a global pulse id per snippet (-1 for label 0)."""
     torch = src.torch
-    xs, ys = [], []
+    xs, ys, ps = [], [], []
+    base = 0
     for b in range(beams):
-        cands, lab, _, _ = src.search(b, seed)
+        cands, lab, pid, pulses = src.search(b, seed)
         keep = lab >= 0
         xs.append(src.snippets(cands[keep]))
         ys.append(lab[keep].astype(np.int32))
-    return torch.cat(xs), np.concatenate(ys)
+        ps.append(np.where(pid[keep] >= 0, pid[keep] + base, -1))
+        base += len(pulses)
+    return torch.cat(xs), np.concatenate(ys), np.concatenate(ps)
+
+
+def choose_threshold(ranker, x, y, pulse_ids, keep=0.995):
+    """Score that keeps `keep` of the training pulses (each by its best
+    positive snippet), at most 0.5."""
+    pos = np.nonzero(y == 1)[0]
+    s = score(ranker, x[__import__("torch").from_numpy(pos).cuda()])
+    best = {}
+    for i, sc in zip(pulse_ids[pos], s):
+        best[int(i)] = max(best.get(int(i), 0.0), float(sc))
+    v = np.sort(np.array(list(best.values())))
+    if v.size == 0:
+        return 0.5
+    return float(min(0.5, v[int(np.floor((1.0 - keep) * v.size))]))
 
 
 def train(ranker, x, y, steps, batch=256, lr=2e-3, seed=0, hard=None, pos_frac=0.25):
@@ -165,7 +190,7 @@ def score(ranker, x, chunk=None):
     return torch.softmax(logits, dim=1)[:, 1].cpu().numpy()
 
 
-def evaluate(ranker, src, beams, seed, snr_min=8.0, chunk=4096):
+def evaluate(ranker, src, beams, seed, snr_min=8.0, chunk=4096, threshold=0.5):
     """Score every candidate of fresh beams; recall on injected pulses with
     S/N >= snr_min (of those the search detects), precision, and the ranking
     throughput (snippets + forward)."""
@@ -198,13 +223,13 @@ def evaluate(ranker, src, beams, seed, snr_min=8.0, chunk=4096):
             mine = pid == i
             if mine.any():
                 detected += 1
-                recalled += int(scores[mine].max() >= 0.5)
-        hi = scores >= 0.5
+                recalled += int(scores[mine].max() >= threshold)
+        hi = scores >= threshold
         tp += int((hi & (lab == 1)).sum())
         fp += int((hi & (lab == 0)).sum())
         neg_total += int((lab == 0).sum())
         neg_rejected += int((~hi & (lab == 0)).sum())
-    return {"pulses_snr_ge_min": strong, "detected_by_search": detected,
+    return {"threshold": threshold, "pulses_snr_ge_min": strong, "detected_by_search": detected,
             "recall": recalled / max(detected, 1), "precision": tp / max(tp + fp, 1),
             "negatives": neg_total, "negatives_rejected": neg_rejected / max(neg_total, 1),
             "candidates_scored": n_scored, "rank_s": rank_s,
