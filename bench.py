@@ -64,6 +64,8 @@ def parse():
     ap.add_argument("--ranker-beams", type=int, default=12,
                     help="training beams of the candidate ranker (0: skip the ranker section)")
     ap.add_argument("--ranker-steps", type=int, default=1200)
+    ap.add_argument("--ranker-pulses", type=int, default=100,
+                    help="injected pulses per training beam of the ranker")
     ap.add_argument("--ddplan-steps", type=int, default=3,
                     help="timed steps of the Table 2 (Band1) DDplan search (0: skip)")
     ap.add_argument("--stream-gbs", type=float, default=6.0,
@@ -454,9 +456,9 @@ def run_ranker(args):
     channels, 5 DM-0 bursts each), then scoring every candidate of fresh beams."""
     import torch
     from paper_2110_12749_gb300 import gsp, ranker, synth
-    src = ranker.BeamSource(ranker.short_crafts(1 << 18, n_pulses=100))
+    src = ranker.BeamSource(ranker.short_crafts(1 << 18, n_pulses=args.ranker_pulses))
     t0 = time.perf_counter()
-    x, y, pids = ranker.build_training_set(src, args.ranker_beams, synth.BASE_SEED + 500)
+    x, y, pids, psnr = ranker.build_training_set(src, args.ranker_beams, synth.BASE_SEED + 500)
     t_data = time.perf_counter() - t0
     r = gsp.gsp_ranker_create(4096, seed=1)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -467,7 +469,7 @@ def run_ranker(args):
     e1.record()
     torch.cuda.synchronize()
     train_ms = e0.elapsed_time(e1)
-    thr = ranker.choose_threshold(r, x, y, pids)
+    thr = ranker.choose_threshold(r, x, y, pids, psnr)
     npos, nneg = int((y == 1).sum()), int((y == 0).sum())
     del x
     torch.cuda.empty_cache()
@@ -479,12 +481,13 @@ def run_ranker(args):
     gsp.gsp_plan_destroy(src.plan)
     del src
     torch.cuda.empty_cache()
-    ev.update({"train_beams": args.ranker_beams, "train_snippets": npos + nneg,
+    ev.update({"train_beams": args.ranker_beams, "train_pulses_per_beam": args.ranker_pulses,
+               "train_snippets": npos + nneg,
                "train_positives": npos, "train_steps": args.ranker_steps, "batch": 256,
                "train_ms": train_ms, "train_steps_per_s": args.ranker_steps / (train_ms / 1e3),
                "loss_first_last": [losses[0], losses[-1]], "data_s": t_data,
                "params": gsp.gsp_ranker_num_params(),
-               "training": "every candidate of 100-pulse training beams (pulse tracks excluded); "
+               "training": "every candidate of the training beams (pulse tracks excluded); "
                            "1/3 of the steps with uniform negatives, then the 20000 "
                            "highest-scored negatives over-sampled",
                "eval": "4 fresh beams; recall over injected pulses with S/N >= 8 that the "

@@ -109,9 +109,10 @@ class BeamSource:
 def build_training_set(src, beams, seed):
     """Snippets (torch float CUDA) and labels of every candidate labelled 0 or
     1 in the given number of beams (candidates on a pulse's track excluded),
-    and a global pulse id per snippet (-1 for label 0)."""
+    a global pulse id per snippet (-1 for label 0) and the nominal S/N of
+    every pulse (indexed by that id)."""
     torch = src.torch
-    xs, ys, ps = [], [], []
+    xs, ys, ps, snr = [], [], [], []
     base = 0
     for b in range(beams):
         cands, lab, pid, pulses = src.search(b, seed)
@@ -119,18 +120,20 @@ def build_training_set(src, beams, seed):
         xs.append(src.snippets(cands[keep]))
         ys.append(lab[keep].astype(np.int32))
         ps.append(np.where(pid[keep] >= 0, pid[keep] + base, -1))
+        snr.extend(p.snr for p in pulses)
         base += len(pulses)
-    return torch.cat(xs), np.concatenate(ys), np.concatenate(ps)
+    return torch.cat(xs), np.concatenate(ys), np.concatenate(ps), np.array(snr)
 
 
-def choose_threshold(ranker, x, y, pulse_ids, keep=0.995):
-    """Score that keeps `keep` of the training pulses (each by its best
-    positive snippet), at most 0.5."""
+def choose_threshold(ranker, x, y, pulse_ids, pulse_snr, snr_min=8.0, keep=0.995):
+    """Score that keeps `keep` of the training pulses with S/N >= snr_min (each
+    by its best positive snippet), at most 0.5."""
     pos = np.nonzero(y == 1)[0]
     s = score(ranker, x[__import__("torch").from_numpy(pos).cuda()])
     best = {}
     for i, sc in zip(pulse_ids[pos], s):
-        best[int(i)] = max(best.get(int(i), 0.0), float(sc))
+        if pulse_snr[int(i)] >= snr_min:
+            best[int(i)] = max(best.get(int(i), 0.0), float(sc))
     v = np.sort(np.array(list(best.values())))
     if v.size == 0:
         return 0.5
@@ -198,6 +201,7 @@ def evaluate(ranker, src, beams, seed, snr_min=8.0, chunk=4096, threshold=0.5):
     recalled, detected, strong = 0, 0, 0
     tp = fp = neg_total = neg_rejected = 0
     n_scored, rank_s = 0, 0.0
+    per_pulse = []   # (nominal S/N, width, recalled) of detected pulses with S/N >= snr_min
     for b in range(beams):
         cands, lab, pid, pulses = src.search(b, seed)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -223,13 +227,25 @@ def evaluate(ranker, src, beams, seed, snr_min=8.0, chunk=4096, threshold=0.5):
             mine = pid == i
             if mine.any():
                 detected += 1
-                recalled += int(scores[mine].max() >= threshold)
+                ok = bool(scores[mine].max() >= threshold)
+                recalled += int(ok)
+                per_pulse.append((p.snr, p.width, ok))
         hi = scores >= threshold
         tp += int((hi & (lab == 1)).sum())
         fp += int((hi & (lab == 0)).sum())
         neg_total += int((lab == 0).sum())
         neg_rejected += int((~hi & (lab == 0)).sum())
-    return {"threshold": threshold, "pulses_snr_ge_min": strong, "detected_by_search": detected,
+    pp = np.array(per_pulse, dtype=np.float64).reshape(-1, 3)
+
+    def rec(sel):
+        return [int(pp[sel, 2].sum()), int(sel.sum())]
+
+    by_width = {"1-9": rec(pp[:, 1] < 10), "10-49": rec((pp[:, 1] >= 10) & (pp[:, 1] < 50)),
+                "50-100": rec(pp[:, 1] >= 50)}
+    by_snr = {"8-12": rec(pp[:, 0] < 12), "12-20": rec((pp[:, 0] >= 12) & (pp[:, 0] < 20)),
+              "20-30": rec(pp[:, 0] >= 20)}
+    return {"threshold": threshold, "recalled_by_width": by_width, "recalled_by_snr": by_snr,
+            "pulses_snr_ge_min": strong, "detected_by_search": detected,
             "recall": recalled / max(detected, 1), "precision": tp / max(tp + fp, 1),
             "negatives": neg_total, "negatives_rejected": neg_rejected / max(neg_total, 1),
             "candidates_scored": n_scored, "rank_s": rank_s,
