@@ -62,26 +62,45 @@ Offsets offsets() {
 // ------------------------------------------------------------- elementwise
 
 // im2col of an NHWC activation (layer 0: the FP32 snippets, rounded to bf16
-// here): col[(b, y, x)][(ky * 3 + kx) * Cin + ci] = a[b][y + ky - 1][x + kx - 1][ci],
-// zero outside the image and in the padding columns K..Kp.
-template <typename T>
-__global__ void im2col_kernel(const T *__restrict__ a, int B, int H, int Cin, int Kp,
-                              bf16 *__restrict__ col) {
-    const int64_t total = (int64_t)B * H * H * Kp;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const int k = (int)(i % Kp);
-        const int64_t p = i / Kp;
-        const int x = (int)(p % H), y = (int)((p / H) % H);
-        const int64_t b = p / ((int64_t)H * H);
-        float v = 0.0f;
-        if (k < 9 * Cin) {
-            const int tap = k / Cin, ci = k % Cin;
+// here): col[(b, y, x)][(ky * 3 + kx) * CIN + ci] = a[b][y + ky - 1][x + kx - 1][ci],
+// zero outside the image and in the padding columns K..Kp.  One thread per
+// pixel writes its whole row of Kp values in 16-byte pieces (consecutive
+// threads write consecutive rows); channel taps are read 16 bytes at a time
+// when CIN is a multiple of 8.
+template <typename T, int CIN>
+__global__ void __launch_bounds__(256) im2col_kernel(const T *__restrict__ a, int B, int H,
+                                                     bf16 *__restrict__ col) {
+    constexpr int K = 9 * CIN, KP = (K + 7) & ~7;
+    const int64_t npix = (int64_t)B * H * H;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < npix;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t b = p / (H * H);
+        const int rem = (int)(p - b * H * H);
+        const int y = rem / H, x = rem - (rem / H) * H;
+        __align__(16) bf16 row[KP];
+#pragma unroll
+        for (int tap = 0; tap < 9; tap++) {
             const int yy = y + tap / 3 - 1, xx = x + tap % 3 - 1;
-            if (yy >= 0 && yy < H && xx >= 0 && xx < H)
-                v = (float)a[((b * H + yy) * H + xx) * Cin + ci];
+            const bool in = yy >= 0 && yy < H && xx >= 0 && xx < H;
+            const T *src = a + ((b * H + yy) * H + xx) * CIN;
+            if constexpr (CIN % 8 == 0 && sizeof(T) == 2) {
+#pragma unroll
+                for (int c8 = 0; c8 < CIN / 8; c8++) {
+                    uint4 v = make_uint4(0u, 0u, 0u, 0u);
+                    if (in) v = __ldg(reinterpret_cast<const uint4 *>(src) + c8);
+                    *reinterpret_cast<uint4 *>(&row[tap * CIN + c8 * 8]) = v;
+                }
+            } else {
+#pragma unroll
+                for (int ci = 0; ci < CIN; ci++)
+                    row[tap * CIN + ci] = __float2bfloat16_rn(in ? (float)src[ci] : 0.0f);
+            }
         }
-        col[i] = __float2bfloat16_rn(v);
+#pragma unroll
+        for (int k = K; k < KP; k++) row[k] = __float2bfloat16_rn(0.0f);
+        uint4 *dst = reinterpret_cast<uint4 *>(col + p * KP);
+#pragma unroll
+        for (int q = 0; q < KP / 8; q++) dst[q] = *reinterpret_cast<const uint4 *>(&row[q * 8]);
     }
 }
 
@@ -396,12 +415,13 @@ cudaError_t forward(gsp_ranker_s *r, const float *x, int n, cudaStream_t s) {
     for (int l = 0; l < kLayers; l++) {
         const int H = side_of(l), Cin = cin_of(l), Cout = cout_of(l), Kp = kpad(l);
         const int64_t P = (int64_t)n * H * H;
+        (void)Cin;
         if (l == 0)
-            RK_LAUNCH((im2col_kernel<float><<<blocks_for(P * Kp), 256, 0, s>>>(x, n, H, Cin, Kp,
-                                                                                r->col[0])));
+            RK_LAUNCH((im2col_kernel<float, 1><<<blocks_for(P), 256, 0, s>>>(x, n, H, r->col[0])));
+        else if (l == 1)
+            RK_LAUNCH((im2col_kernel<bf16, 8><<<blocks_for(P), 256, 0, s>>>(r->a[0], n, H, r->col[1])));
         else
-            RK_LAUNCH((im2col_kernel<bf16><<<blocks_for(P * Kp), 256, 0, s>>>(r->a[l - 1], n, H, Cin,
-                                                                               Kp, r->col[l])));
+            RK_LAUNCH((im2col_kernel<bf16, 16><<<blocks_for(P), 256, 0, s>>>(r->a[1], n, H, r->col[2])));
         cudaError_t e = gemm(r, r->col[l], Kp, r->W[l], Kp, r->z[l], Cout, nullptr, 0, (int)P, Cout,
                              Kp, r->params + r->off.b[l], true, 1, s);
         if (e != cudaSuccess) return e;
@@ -500,13 +520,21 @@ __global__ void snippet_kernel(const int32_t *__restrict__ D, int64_t stride, in
         if (r >= 0 && r < ndm && sref[r] > 0.0) {
             const float inv = (float)(1.0 / sref[r]);
             const int64_t a = tc + (int64_t)(j - kS / 2) * f;
-            const int64_t s1 = min(a + f, Ls);
-            for (int64_t s = max(a, (int64_t)0); s < s1; s++) {
-                const int64_t b = s / B;
-                const gsp::BlockParam q = bp[(int64_t)r * nb_max + b];
-                if (q.good)
-                    v += ((float)(D[(int64_t)r * stride + s] - q.m) -
-                          (q.c0 + q.beta * (float)(s - b * B))) * inv;
+            const int64_t s0 = max(a, (int64_t)0), s1 = min(a + f, Ls);
+            if (s0 < s1) {
+                int64_t b = s0 / B;
+                int jb = (int)(s0 - b * B);           // position inside block b
+                gsp::BlockParam q = bp[(int64_t)r * nb_max + b];
+                const int32_t *drow = D + (int64_t)r * stride;
+                for (int64_t s = s0; s < s1; s++, jb++) {
+                    if (jb == B) {
+                        b++;
+                        jb = 0;
+                        q = bp[(int64_t)r * nb_max + b];
+                    }
+                    if (q.good)
+                        v += ((float)(drow[s] - q.m) - (q.c0 + q.beta * (float)jb)) * inv;
+                }
             }
         }
         out[(int64_t)blockIdx.x * kS * kS + o] = v * rs;
