@@ -106,27 +106,43 @@ __global__ void __launch_bounds__(256) im2col_kernel(const T *__restrict__ a, in
 
 // 2x2 max-pool of the ReLU'd pre-activations z (FP32 NHWC [B][H][H][C]):
 // out bf16 [B][H/2][H/2][C], idx = argmax in (0,0), (0,1), (1,0), (1,1) order
-// (first maximum wins).
-__global__ void pool_kernel(const float *__restrict__ z, int B, int H, int C,
-                            bf16 *__restrict__ out, uint8_t *__restrict__ idx) {
+// (first maximum wins).  One thread per pooled pixel, all C channels (float4
+// loads).
+template <int C>
+__global__ void __launch_bounds__(256) pool_kernel(const float *__restrict__ z, int B, int H,
+                                                   bf16 *__restrict__ out,
+                                                   uint8_t *__restrict__ idx) {
     const int H2 = H / 2;
-    const int64_t total = (int64_t)B * H2 * H2 * C;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const int c = (int)(i % C);
-        const int64_t q = i / C;
-        const int x = (int)(q % H2), y = (int)((q / H2) % H2);
-        const int64_t b = q / ((int64_t)H2 * H2);
-        const float *base = z + ((b * H + 2 * y) * H + 2 * x) * C + c;
-        const float v0 = base[0], v1 = base[C], v2 = base[(int64_t)H * C],
-                    v3 = base[(int64_t)H * C + C];
-        float m = v0;
-        int k = 0;
-        if (v1 > m) { m = v1; k = 1; }
-        if (v2 > m) { m = v2; k = 2; }
-        if (v3 > m) { m = v3; k = 3; }
-        out[i] = __float2bfloat16_rn(m);
-        idx[i] = (uint8_t)k;
+    const int64_t total = (int64_t)B * H2 * H2;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t b = q / (H2 * H2);
+        const int rem = (int)(q - b * H2 * H2);
+        const int y = rem / H2, x = rem - (rem / H2) * H2;
+        const float *p0 = z + ((b * H + 2 * y) * H + 2 * x) * C;
+        const float *src[4] = {p0, p0 + C, p0 + (int64_t)H * C, p0 + (int64_t)H * C + C};
+#pragma unroll
+        for (int c4 = 0; c4 < C / 4; c4++) {
+            float4 v[4];
+#pragma unroll
+            for (int k = 0; k < 4; k++) v[k] = __ldg(reinterpret_cast<const float4 *>(src[k]) + c4);
+            float m[4] = {v[0].x, v[0].y, v[0].z, v[0].w};
+            uint32_t kk[4] = {0, 0, 0, 0};
+#pragma unroll
+            for (int k = 1; k < 4; k++) {
+                const float w[4] = {v[k].x, v[k].y, v[k].z, v[k].w};
+#pragma unroll
+                for (int e = 0; e < 4; e++)
+                    if (w[e] > m[e]) {
+                        m[e] = w[e];
+                        kk[e] = (uint32_t)k;
+                    }
+            }
+            const int64_t o = q * C + c4 * 4;
+#pragma unroll
+            for (int e = 0; e < 4; e++) out[o + e] = __float2bfloat16_rn(m[e]);
+            *reinterpret_cast<uint32_t *>(idx + o) = kk[0] | (kk[1] << 8) | (kk[2] << 16) | (kk[3] << 24);
+        }
     }
 }
 
@@ -425,8 +441,12 @@ cudaError_t forward(gsp_ranker_s *r, const float *x, int n, cudaStream_t s) {
         cudaError_t e = gemm(r, r->col[l], Kp, r->W[l], Kp, r->z[l], Cout, nullptr, 0, (int)P, Cout,
                              Kp, r->params + r->off.b[l], true, 1, s);
         if (e != cudaSuccess) return e;
-        RK_LAUNCH((pool_kernel<<<blocks_for(P / 4 * Cout), 256, 0, s>>>(r->z[l], n, H, Cout, r->a[l],
-                                                                         r->idx[l])));
+        if (l == 0)
+            RK_LAUNCH((pool_kernel<8><<<blocks_for(P / 4), 256, 0, s>>>(r->z[0], n, H, r->a[0], r->idx[0])));
+        else if (l == 1)
+            RK_LAUNCH((pool_kernel<16><<<blocks_for(P / 4), 256, 0, s>>>(r->z[1], n, H, r->a[1], r->idx[1])));
+        else
+            RK_LAUNCH((pool_kernel<32><<<blocks_for(P / 4), 256, 0, s>>>(r->z[2], n, H, r->a[2], r->idx[2])));
     }
     cudaError_t e = gemm(r, r->a[2], kFc, r->W4, kFc, r->z4, kHid, r->a4, kHid, n, kHid, kFc,
                          r->params + r->off.b[3], true, 1, s);

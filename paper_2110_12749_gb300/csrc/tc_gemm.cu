@@ -20,8 +20,9 @@ __device__ int g_gemm_err;  // fallback error flag when the caller passes none
 // columns >= kend read as zero (kend is a multiple of 8).
 template <int ROWS>
 __device__ __forceinline__ void stage_tile(uint8_t *dst, const __nv_bfloat16 *__restrict__ src,
-                                           int64_t ld, int row0, int nrows, int k0, int kend) {
-    for (int idx = threadIdx.x; idx < ROWS * 8; idx += 128) {
+                                           int64_t ld, int row0, int nrows, int k0, int kend,
+                                           int nc8) {
+    for (int idx = threadIdx.x; idx < ROWS * nc8; idx += 128) {
         const int r = idx % ROWS, c8 = idx / ROWS;
         const int gr = row0 + r, gk = k0 + c8 * 8;
         uint4 v = make_uint4(0u, 0u, 0u, 0u);
@@ -44,9 +45,10 @@ __global__ void __launch_bounds__(128) gemm_bf16_kernel(
     constexpr uint32_t kCols = BN < 32 ? 32u : (uint32_t)BN;
     constexpr uint32_t kIdesc = tc::idesc_bf16(kBM, BN);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int m0 = blockIdx.x * kBM, n0 = blockIdx.y * BN;
+    const int n0 = blockIdx.y * BN;
     const int kbeg = blockIdx.z * kchunk;
     const int kend = min(K, kbeg + kchunk);
+    const int mtiles = (M + kBM - 1) / kBM;
     const uint32_t bar = tc::smem_u32(&mbar);
     if (warp == 0) tc::tmem_alloc(tc::smem_u32(&tmem_base), kCols);
     if (tid == 0) tc::mbar_init1(bar);
@@ -58,33 +60,40 @@ __global__ void __launch_bounds__(128) gemm_bf16_kernel(
     uint32_t phase = 0;
     bool ok = true;
     bool pending = false;  // MMAs committed and not yet waited for
-    for (int k0 = kbeg; k0 < kend; k0 += kBK) {
-        stage_tile<kBM>(sA, A, lda, m0, M, k0, kend);
-        stage_tile<BN>(sB, B, ldb, n0, N, k0, kend);
-        tc::fence_proxy_async();  // generic-proxy smem writes -> tensor-core reads
-        __syncthreads();
-        if (tid == 0) {
-            tc::fence_after();
-#pragma unroll
-            for (int kk = 0; kk < kBK / 16; kk++) {
-                // K = 16 per MMA: two core matrices along K (256 bytes)
-                const uint64_t ad = tc::smem_desc(aaddr + kk * 256, 128, 1024);
-                const uint64_t bd = tc::smem_desc(baddr + kk * 256, 128, 1024);
-                tc::mma_bf16(tmem, ad, bd, kIdesc, (k0 > kbeg || kk > 0) ? 1u : 0u);
+    // CTAs stride over the M tiles; tensor memory and the barrier are reused
+    for (int mt = blockIdx.x; mt < mtiles && ok; mt += gridDim.x) {
+        const int m0 = mt * kBM;
+        for (int k0 = kbeg; k0 < kend; k0 += kBK) {
+            const int nk = min(kBK, kend - k0);       // a multiple of 8
+            const int nc8 = nk / 8;                   // 16-byte chunks per row
+            const int nmma = (nk + 15) / 16;          // K = 16 per MMA
+            stage_tile<kBM>(sA, A, lda, m0, M, k0, kend, (nmma * 16) / 8);
+            stage_tile<BN>(sB, B, ldb, n0, N, k0, kend, (nmma * 16) / 8);
+            (void)nc8;
+            tc::fence_proxy_async();  // generic-proxy smem writes -> tensor-core reads
+            tc::fence_before();
+            __syncthreads();
+            if (tid == 0) {
+                tc::fence_after();
+                for (int kk = 0; kk < nmma; kk++) {
+                    // two core matrices along K (256 bytes) per MMA
+                    const uint64_t ad = tc::smem_desc(aaddr + kk * 256, 128, 1024);
+                    const uint64_t bd = tc::smem_desc(baddr + kk * 256, 128, 1024);
+                    tc::mma_bf16(tmem, ad, bd, kIdesc, (k0 > kbeg || kk > 0) ? 1u : 0u);
+                }
+                tc::mma_commit(bar);
             }
-            tc::mma_commit(bar);
+            pending = true;
+            const bool done = tc::mbar_wait_bounded(bar, phase, kGemmBudget);
+            phase ^= 1u;
+            if (!__syncthreads_and(done)) {
+                ok = false;
+                break;
+            }
+            pending = false;
+            tc::fence_after();
         }
-        pending = true;
-        const bool done = tc::mbar_wait_bounded(bar, phase, kGemmBudget);
-        phase ^= 1u;
-        if (!__syncthreads_and(done)) {
-            ok = false;
-            break;
-        }
-        pending = false;
-        tc::fence_after();
-    }
-    if (ok && kbeg < kend) {
+        if (!ok || kbeg >= kend) break;
         const int row = m0 + warp * 32 + lane;
         const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
 #pragma unroll 1
@@ -108,6 +117,10 @@ __global__ void __launch_bounds__(128) gemm_bf16_kernel(
                 }
             }
         }
+        // every lane's tensor-memory reads are complete before the next tile's MMAs
+        tc::fence_before();
+        __syncthreads();
+        tc::fence_after();
     }
     if (!ok) {
         if (tid == 0) atomicExch(err, 1);
@@ -137,7 +150,10 @@ cudaError_t launch_gemm_bf16(const __nv_bfloat16 *A, int64_t lda, const __nv_bfl
     const int kchunk = ((ksteps + splitk - 1) / splitk) * kBK;
     splitk = (K + kchunk - 1) / kchunk;
     const int BN = N <= 16 ? 16 : N <= 32 ? 32 : N <= 64 ? 64 : 128;
-    dim3 grid((unsigned)((M + kBM - 1) / kBM), (unsigned)((N + BN - 1) / BN), (unsigned)splitk);
+    // up to 4 CTAs per SM in total; each strides over the M tiles
+    const int mtiles = (M + kBM - 1) / kBM, ntiles = (N + BN - 1) / BN;
+    const int mgrid = std::max(1, std::min(mtiles, (4 * 152 + ntiles * splitk - 1) / (ntiles * splitk)));
+    dim3 grid((unsigned)mgrid, (unsigned)ntiles, (unsigned)splitk);
     const int r = relu ? 1 : 0;
     switch (BN) {
         case 16:

@@ -25,6 +25,8 @@ def gsp():
     (300, 130, 512, 1, True, True),       # several tiles in M and N
     (64, 9, 4096, 8, False, False),       # split-K (weight-gradient shape)
     (1024, 64, 2048, 1, True, True),      # fully connected layer shape
+    (89600, 8, 16, 1, True, True),        # first conv layer shape: CTAs loop over M tiles
+    (40000, 72, 32, 1, False, False),     # conv input-gradient shape
 ])
 def test_gemm_matches_float64(gsp, M, N, K, splitk, bias, relu):
     g = torch.Generator().manual_seed(M * 7 + N * 3 + K)
