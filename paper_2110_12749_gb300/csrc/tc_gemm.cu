@@ -150,16 +150,11 @@ cudaError_t launch_gemm_bf16(const __nv_bfloat16 *A, int64_t lda, const __nv_bfl
     const int kchunk = ((ksteps + splitk - 1) / splitk) * kBK;
     splitk = (K + kchunk - 1) / kchunk;
     const int BN = N <= 16 ? 16 : N <= 32 ? 32 : N <= 64 ? 64 : 128;
-    // as many CTAs as tensor memory holds (512 columns per SM; 32 for BN <= 32),
-    // at most 16 per SM; each strides over the M tiles
-    const int cols = BN < 32 ? 32 : BN;
-    const int per_sm = std::min(16, 512 / cols);
-    int dev = 0, nsm = 152;
-    if (cudaGetDevice(&dev) == cudaSuccess)
-        (void)cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    // one CTA per M tile: with one synchronous stage -> MMA -> epilogue chain
+    // per tile, many short CTAs overlap better than fewer CTAs striding over
+    // the tiles (measured); the kernel still strides if the grid is capped
     const int mtiles = (M + kBM - 1) / kBM, ntiles = (N + BN - 1) / BN;
-    const int slots = std::max(1, nsm * per_sm / (ntiles * splitk));
-    const int mgrid = std::max(1, std::min(mtiles, slots));
+    const int mgrid = std::max(1, std::min(mtiles, 1 << 30));
     dim3 grid((unsigned)mgrid, (unsigned)ntiles, (unsigned)splitk);
     const int r = relu ? 1 : 0;
     switch (BN) {
