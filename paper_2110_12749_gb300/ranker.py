@@ -16,8 +16,8 @@ pulses of its beam (pulse DM trial k = nearest trial, per-channel delays):
 A pulse is recalled if its best-scored core candidate scores at least the
 operating threshold (softmax probability of class 1); precision counts the
 candidates scoring at least the threshold among those labelled 0 or 1.  The
-threshold is chosen on the training beams (the score that keeps 99.5% of
-their pulses), never on the evaluation beams.
+threshold is chosen on the training beams (the score that keeps 99% of
+their pulses with S/N >= 8), never on the evaluation beams.
 """
 from __future__ import annotations
 
@@ -125,7 +125,7 @@ def build_training_set(src, beams, seed):
     return torch.cat(xs), np.concatenate(ys), np.concatenate(ps), np.array(snr)
 
 
-def choose_threshold(ranker, x, y, pulse_ids, pulse_snr, snr_min=8.0, keep=0.995):
+def choose_threshold(ranker, x, y, pulse_ids, pulse_snr, snr_min=8.0, keep=0.99):
     """Score that keeps `keep` of the training pulses with S/N >= snr_min (each
     by its best positive snippet), at most 0.5."""
     pos = np.nonzero(y == 1)[0]
