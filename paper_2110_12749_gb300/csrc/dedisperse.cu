@@ -313,8 +313,9 @@ __device__ __forceinline__ void merged_decode(uint32_t (&acc)[M][4]) {
 // since tiles start at multiples of 4 samples), not from a per-stage ballot sort.
 // MF: merged flush of the four phase families (flush_merged).
 // KDM: DM trials per CTA.  UNR: unroll depth of the two-channel loop (A32).
+// IMA: per-channel address adds as x * 1 + y on the multiply-add pipe (A32).
 template <int KW, bool QUAD, int ACC, bool A32 = false, int M = 4, int CB = 32, bool FF = false,
-          bool PRE = false, bool MF = false, int KDM = 16, int UNR = 2>
+          bool PRE = false, bool MF = false, int KDM = 16, int UNR = 2, bool IMA = false>
 __global__ void __launch_bounds__((KDM / KW + 1) * 32, 1) dd_tiled_kernel(const TiledArgs a) {
     static_assert(!PRE || (KW == 1 && CB == 64), "precomputed lists: one DM per warp, 64-channel stages");
     static_assert(!MF || (ACC == 3 && !FF), "merged flush: raw + odd views, all families together");
@@ -573,7 +574,10 @@ __global__ void __launch_bounds__((KDM / KW + 1) * 32, 1) dd_tiled_kernel(const 
 #pragma unroll UNR
                     for (; j + 2 <= n; j += 2) {
                         const int2 e = *reinterpret_cast<const int2 *>(lp + j);
-                        const uint32_t a1 = (uint32_t)e.x + lane4, a2 = (uint32_t)e.y + lane4;
+                        const uint32_t a1 = IMA ? ptx::imadd((uint32_t)e.x, one, lane4)
+                                                : (uint32_t)e.x + lane4;
+                        const uint32_t a2 = IMA ? ptx::imadd((uint32_t)e.y, one, lane4)
+                                                : (uint32_t)e.y + lane4;
                         uint32_t w1[kM], w2[kM];
                         ptx::lds_words<kM>(a1, w1);
                         ptx::lds_words<kM>(a2, w2);
@@ -586,7 +590,10 @@ __global__ void __launch_bounds__((KDM / KW + 1) * 32, 1) dd_tiled_kernel(const 
 #pragma unroll
                         for (int k = 0; k < kM; k++) {
                             E[i][P][k] += ACC == 3 ? w1[k] : (w1[k] & 0x00ff00ffu);
-                            O[i][P][k] += __byte_perm(w1[k], 0, 0x4341);
+                            if (IMA)
+                                O[i][P][k] = ptx::imadd(__byte_perm(w1[k], 0, 0x4341), one, O[i][P][k]);
+                            else
+                                O[i][P][k] += __byte_perm(w1[k], 0, 0x4341);
                         }
                     }
                 }
@@ -826,6 +833,7 @@ const TiledVariant kVariants[] = {
     {dd_tiled_kernel<1, false, 3, false, 8, 64, false, true, true, 15>, 1, 8, 64, true, 15},
     {dd_tiled_kernel<1, false, 3, true, 4, 64, false, true, true, 15, 4>, 1, 4, 64, true, 15},
     {dd_tiled_kernel<1, false, 3, true, 4, 64, false, true, true, 15, 1>, 1, 4, 64, true, 15},
+    {dd_tiled_kernel<1, false, 3, true, 4, 64, false, true, true, 15, 2, true>, 1, 4, 64, true, 15},
 };
 constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
 constexpr int kDefaultVariant = 22;
