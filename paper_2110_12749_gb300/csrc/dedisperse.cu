@@ -835,6 +835,9 @@ const TiledVariant kVariants[] = {
     {dd_tiled_kernel<1, false, 3, true, 4, 64, false, true, true, 15, 1>, 1, 4, 64, true, 15},
     {dd_tiled_kernel<1, false, 3, true, 4, 64, false, true, true, 15, 2, true>, 1, 4, 64, true, 15},
     {dd_tiled_kernel<1, false, 3, true, 6, 64, false, true, true, 15, 2, true>, 1, 6, 64, true, 15},
+    {dd_tiled_kernel<1, false, 3, true, 6, 64, false, true, true, 15, 1, true>, 1, 6, 64, true, 15},
+    {dd_tiled_kernel<1, false, 3, true, 6, 32, false, false, true, 15, 2, true>, 1, 6, 32, false, 15},
+    {dd_tiled_kernel<1, false, 3, true, 7, 64, false, true, true, 15, 2, true>, 1, 7, 64, true, 15},
 };
 constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
 constexpr int kDefaultVariant = 22;
