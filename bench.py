@@ -33,7 +33,7 @@ if ROOT not in sys.path:
 # capture size rule keeping full-size multi-pass captures off the GPU; traffic grows
 # with the number of time tiles, i.e. in proportion to the adds.
 DD_TRAFFIC_BYTES_PER_ADD = (1.5677e9 + 0.6673e9) / 6.899e11
-DD_TRAFFIC_VARIANT = "default"
+DD_TRAFFIC_VARIANT = "22"  # re-measured for the new default below
 
 NOMINAL_SMS = 152
 INT_LANES_PER_SM = 128          # issue slots per SM per clock (4 schedulers x 32 lanes)

@@ -840,8 +840,8 @@ const TiledVariant kVariants[] = {
     {dd_tiled_kernel<1, false, 3, true, 7, 64, false, true, true, 15, 2, true>, 1, 7, 64, true, 15},
 };
 constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
-constexpr int kDefaultVariant = 22;
-constexpr int kFallbackVariant = 21;  // default when the precomputed lists are unavailable
+constexpr int kDefaultVariant = 32;
+constexpr int kFallbackVariant = 34;  // default when the precomputed lists are unavailable
 
 }  // namespace
 
@@ -954,7 +954,7 @@ bool plan_dedisperse_tiled(gsp_plan_s *p, std::vector<int32_t> (&blkmin)[kNumKdm
 int dedisperse_num_variants() { return kNumVariants; }
 
 // Variants the batch autotuner times (the fastest family on this GPU).
-const int kTuneList[] = {22, 25, 21, 23};
+const int kTuneList[] = {32, 35, 31, 22};
 int dedisperse_tune_candidates(const int **list) {
     *list = kTuneList;
     return (int)(sizeof(kTuneList) / sizeof(kTuneList[0]));
