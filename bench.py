@@ -28,12 +28,12 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 # DRAM bytes (read + write) per algorithmic add of the default dedispersion kernel
-# (variant 22): ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch on the
-# CRAFTS-like beam cut to 131072 samples (1.568 GB + 0.667 GB for 6.899e11 adds), the
+# (variant 32): ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch on the
+# CRAFTS-like beam cut to 131072 samples (1.598 GB + 0.666 GB for 6.899e11 adds), the
 # capture size rule keeping full-size multi-pass captures off the GPU; traffic grows
 # with the number of time tiles, i.e. in proportion to the adds.
-DD_TRAFFIC_BYTES_PER_ADD = (1.5677e9 + 0.6673e9) / 6.899e11
-DD_TRAFFIC_VARIANT = "22"  # re-measured for the new default below
+DD_TRAFFIC_BYTES_PER_ADD = (1.5984e9 + 0.6663e9) / 6.899e11
+DD_TRAFFIC_VARIANT = "default"
 
 NOMINAL_SMS = 152
 INT_LANES_PER_SM = 128          # issue slots per SM per clock (4 schedulers x 32 lanes)
