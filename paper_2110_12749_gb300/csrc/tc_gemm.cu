@@ -13,11 +13,12 @@ constexpr long long kGemmBudget = 2000000000ll;  // ~1 s of SM clock per wait
 
 __device__ int g_gemm_err;  // fallback error flag when the caller passes none
 
-// Copy one 128 x 64 (or BN x 64) bf16 tile of a K-contiguous matrix into the
-// core-matrix layout: element (r, c) at byte (r/8)*1024 + (c/8)*128 + (r%8)*16
-// + (c%8)*2.  Consecutive threads take consecutive rows of one 8-column chunk,
-// so each quarter warp writes 128 contiguous bytes.  Rows >= nrows and
-// columns >= kend read as zero (kend is a multiple of 8).
+// Copy the first nc8 8-column chunks of one 128 x 64 (or BN x 64) bf16 tile of a
+// K-contiguous matrix into the core-matrix layout: element (r, c) at byte
+// (r/8)*1024 + (c/8)*128 + (r%8)*16 + (c%8)*2.  Consecutive threads take
+// consecutive rows of one chunk, so each quarter warp writes 128 contiguous
+// bytes.  Rows >= nrows and columns >= kend read as zero (kend is a multiple
+// of 8).
 template <int ROWS>
 __device__ __forceinline__ void stage_tile(uint8_t *dst, const __nv_bfloat16 *__restrict__ src,
                                            int64_t ld, int row0, int nrows, int k0, int kend,
@@ -65,11 +66,10 @@ __global__ void __launch_bounds__(128) gemm_bf16_kernel(
         const int m0 = mt * kBM;
         for (int k0 = kbeg; k0 < kend; k0 += kBK) {
             const int nk = min(kBK, kend - k0);       // a multiple of 8
-            const int nc8 = nk / 8;                   // 16-byte chunks per row
             const int nmma = (nk + 15) / 16;          // K = 16 per MMA
-            stage_tile<kBM>(sA, A, lda, m0, M, k0, kend, (nmma * 16) / 8);
-            stage_tile<BN>(sB, B, ldb, n0, N, k0, kend, (nmma * 16) / 8);
-            (void)nc8;
+            // stage the 16-byte chunks the MMAs read (2 per MMA; zeros past kend)
+            stage_tile<kBM>(sA, A, lda, m0, M, k0, kend, 2 * nmma);
+            stage_tile<BN>(sB, B, ldb, n0, N, k0, kend, 2 * nmma);
             tc::fence_proxy_async();  // generic-proxy smem writes -> tensor-core reads
             tc::fence_before();
             __syncthreads();
