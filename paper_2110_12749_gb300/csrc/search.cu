@@ -304,15 +304,31 @@ __global__ void __launch_bounds__(kBoxThreads) boxcar_kernel(
             const uint32_t p0 = sP[i];
             float bsnr = -FLT_MAX;
             int bw = 0;
-            if (kDefaultW && !kWriteSnr && t + 150 <= Ls) {
-                // default widths: the maximum S/N first (one max per width); the
-                // width that reaches it is recovered only when it passes the
-                // threshold (rare).  Boxcars running into block b + 1 take its line.
-                BlockParam q2 = q;
-                if (150 > rem && b + 1 < nb) q2 = bp[b + 1];
+            if (kDefaultW && !kWriteSnr && t + 150 <= Ls && 150 <= rem) {
+                // default widths inside block b: the maximum S/N first (one max per
+                // width); the width that reaches it is recovered only when it
+                // passes the threshold (rare)
+                float v[kNumDefaultWidths];
+#pragma unroll
+                for (int iw = 0; iw < kNumDefaultWidths; iw++) {
+                    const int w = default_width(iw);
+                    const int32_t Y = (int32_t)(sP[i + w] - p0);
+                    const float cr = (float)w * g + beta1 * (0.5f * (float)w * (float)(w - 1));
+                    v[iw] = ((float)Y - cr) * sc[iw];
+                    bsnr = fmaxf(bsnr, v[iw]);
+                }
+                if (bsnr >= threshold) {
+                    // first width reaching the maximum (ties: the smaller width)
+#pragma unroll
+                    for (int iw = kNumDefaultWidths - 1; iw >= 0; iw--)
+                        if (v[iw] == bsnr) bw = default_width(iw);
+                }
+            } else if (kDefaultW && !kWriteSnr && t + 150 <= Ls) {
+                // default widths near the end of block b: boxcars longer than the
+                // samples left run into block b + 1 and take its line there
+                const BlockParam q2 = bp[b + 1];
                 const float c02 = q2.good ? q2.c0 : 0.0f;
                 const float beta2 = q2.good ? q2.beta : 0.0f;
-                float v[kNumDefaultWidths];
 #pragma unroll
                 for (int iw = 0; iw < kNumDefaultWidths; iw++) {
                     const int w = default_width(iw);
@@ -325,14 +341,11 @@ __global__ void __launch_bounds__(kBoxThreads) boxcar_kernel(
                         cr = (float)n1 * g + beta1 * (0.5f * (float)n1 * (float)(n1 - 1)) +
                              (float)n2 * c02 + beta2 * (0.5f * (float)n2 * (float)(n2 - 1));
                     }
-                    v[iw] = ((float)Y - cr) * sc[iw];
-                    bsnr = fmaxf(bsnr, v[iw]);
-                }
-                if (bsnr >= threshold) {
-                    // first width reaching the maximum (ties: the smaller width)
-#pragma unroll
-                    for (int iw = kNumDefaultWidths - 1; iw >= 0; iw--)
-                        if (v[iw] == bsnr) bw = default_width(iw);
+                    const float v = ((float)Y - cr) * sc[iw];
+                    if (v > bsnr) {
+                        bsnr = v;
+                        bw = w;
+                    }
                 }
             } else if (kDefaultW && t + 150 <= Ls && 150 <= rem) {
                 // default widths, every boxcar inside block b
