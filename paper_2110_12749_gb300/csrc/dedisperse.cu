@@ -838,6 +838,9 @@ const TiledVariant kVariants[] = {
     {dd_tiled_kernel<1, false, 3, true, 6, 64, false, true, true, 15, 1, true>, 1, 6, 64, true, 15},
     {dd_tiled_kernel<1, false, 3, true, 6, 32, false, false, true, 15, 2, true>, 1, 6, 32, false, 15},
     {dd_tiled_kernel<1, false, 3, true, 7, 64, false, true, true, 15, 2, true>, 1, 7, 64, true, 15},
+    {dd_tiled_kernel<1, false, 3, true, 6, 64, false, true, true, 15, 3, true>, 1, 6, 64, true, 15},
+    {dd_tiled_kernel<1, false, 3, true, 6, 64, false, true, true, 15, 4, true>, 1, 6, 64, true, 15},
+    {dd_tiled_kernel<1, false, 3, true, 5, 64, false, true, true, 15, 2, true>, 1, 5, 64, true, 15},
 };
 constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
 constexpr int kDefaultVariant = 32;
