@@ -105,6 +105,9 @@ void free_plan(gsp_plan_s *p) {
     cudaFree(p->d_xstage);
     for (auto &e : p->ev)
         if (e) cudaEventDestroy(e);
+    for (auto &e : p->h2d_ev)
+        if (e) cudaEventDestroy(e);
+    if (p->h2d_stream) cudaStreamDestroy(p->h2d_stream);
     delete p;
 }
 
@@ -517,6 +520,15 @@ gsp_status gsp_candidates(gsp_plan_t p, gsp_cand *host_out, int64_t cap, int64_t
     return ((int64_t)n > m) ? GSP_ERR_CAPACITY : GSP_OK;
 }
 
+// Host input in time chunks: the copy of chunk k + 1 (on a second stream)
+// overlaps the dedispersion of chunk k.  Chunk boundaries are multiples of
+// lcm(block_len, 16) output samples, so every chunk's input starts 16-byte
+// aligned and its block sums land in whole blocks; chunk k needs the input
+// columns [a_k, a_{k+1} + max_delay), and its copy brings the columns not yet
+// on the device.  The series are exact integer sums, so the result does not
+// depend on the chunking.
+constexpr int kHostChunks = 4;
+
 gsp_status gsp_search_host(gsp_plan_t p, const uint8_t *h_x, int64_t n_in, int64_t x_stride,
                            int64_t t_offset, gsp_cand *host_out, int64_t cap, int64_t *n_total,
                            void *stream) {
@@ -535,14 +547,64 @@ gsp_status gsp_search_host(gsp_plan_t p, const uint8_t *h_x, int64_t n_in, int64
         p->d_xstage_bytes = full;
     }
     cudaStream_t s = (cudaStream_t)stream;
-    if (x_stride == dstride) {
-        GSP_CK(cudaMemcpyAsync(p->d_xstage, h_x, need, cudaMemcpyHostToDevice, s));
-    } else {
-        GSP_CK(cudaMemcpy2DAsync(p->d_xstage, dstride, h_x, x_stride, n_in, p->desc.nchan,
-                                 cudaMemcpyHostToDevice, s));
+    const int64_t n_out = n_in - p->max_delay;
+    const int64_t B = p->desc.block_len;
+    int64_t unit = B;
+    while (unit % 16) unit += B;  // lcm(B, 16)
+    const bool pipelined = !p->simple_dd && n_out >= kHostChunks * unit;
+    if (!pipelined) {
+        if (x_stride == dstride) {
+            GSP_CK(cudaMemcpyAsync(p->d_xstage, h_x, need, cudaMemcpyHostToDevice, s));
+        } else {
+            GSP_CK(cudaMemcpy2DAsync(p->d_xstage, dstride, h_x, x_stride, n_in, p->desc.nchan,
+                                     cudaMemcpyHostToDevice, s));
+        }
+        gsp_status st = gsp_search(p, p->d_xstage, n_in, dstride, t_offset, nullptr, 0, stream);
+        if (st != GSP_OK) return st;
+        return gsp_candidates(p, host_out, cap, n_total);
     }
-    gsp_status st = gsp_search(p, p->d_xstage, n_in, dstride, t_offset, nullptr, 0, stream);
+    if (!p->h2d_stream) GSP_CK(cudaStreamCreateWithFlags(&p->h2d_stream, cudaStreamNonBlocking));
+    for (auto &e : p->h2d_ev)
+        if (!e) GSP_CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    int64_t a[kHostChunks + 1];
+    for (int k = 0; k <= kHostChunks; k++) a[k] = (n_out * k / kHostChunks) / unit * unit;
+    a[kHostChunks] = n_out;
+    // the copies start after the caller's earlier work on s (which may still
+    // read the staging buffer)
+    GSP_CK(cudaEventRecord(p->h2d_ev[kHostChunks], s));
+    GSP_CK(cudaStreamWaitEvent(p->h2d_stream, p->h2d_ev[kHostChunks], 0));
+    int64_t copied = 0;
+    for (int k = 0; k < kHostChunks; k++) {
+        const int64_t upto = std::min(n_in, a[k + 1] + p->max_delay);
+        if (upto > copied)
+            GSP_CK(cudaMemcpy2DAsync(p->d_xstage + copied, dstride, h_x + copied, x_stride,
+                                     upto - copied, p->desc.nchan, cudaMemcpyHostToDevice,
+                                     p->h2d_stream));
+        copied = std::max(copied, upto);
+        GSP_CK(cudaEventRecord(p->h2d_ev[k], p->h2d_stream));
+    }
+    gsp_status st = ensure_scratch_D(p, n_out);
     if (st != GSP_OK) return st;
+    int32_t *D = p->d_D;
+    const int64_t stride = (n_out + 3) & ~(int64_t)3;
+    p->launches = 0;
+    unsigned long long *bsum = nullptr;
+    if (fused_stats(p) && n_out / B > 0) {
+        bsum = p->d_bsum;
+        GSP_CK(cudaMemsetAsync(bsum, 0, (size_t)p->desc.ndm * p->nb_max * 3 * sizeof(*bsum), s));
+    }
+    if (p->timed) GSP_CK(cudaEventRecord(p->ev[0], s));
+    for (int k = 0; k < kHostChunks; k++) {
+        GSP_CK(cudaStreamWaitEvent(s, p->h2d_ev[k], 0));
+        const int64_t len = a[k + 1] - a[k];
+        st = run_dedisperse(p, p->d_xstage + a[k], len + p->max_delay, dstride, len, D + a[k],
+                            stride, bsum ? bsum + (a[k] / B) * 3 : nullptr, s);
+        if (st != GSP_OK) return st;
+    }
+    if (p->timed) GSP_CK(cudaEventRecord(p->ev[1], s));
+    st = run_search(p, D, n_out, stride, t_offset, nullptr, bsum, s);
+    if (st != GSP_OK) return st;
+    if (p->timed) GSP_CK(cudaEventRecord(p->ev[2], s));
     return gsp_candidates(p, host_out, cap, n_total);
 }
 

@@ -87,6 +87,9 @@ struct gsp_plan_s {
     gsp::DDGeom geom;
 
     cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+    // host-input pipeline (gsp_search_host): copy stream and its events, created on first use
+    cudaStream_t h2d_stream = nullptr;
+    cudaEvent_t h2d_ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
     bool timed = false;
     cudaStream_t last_stream = nullptr;
     int64_t last_nout = -1;

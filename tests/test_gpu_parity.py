@@ -200,3 +200,40 @@ def test_custom_widths_blocks_windows_offset(gsp, orc, tiny):
     ncmp, bad = compare_candidates(cands, ora, thr, L, off, contenders)
     assert not bad, bad[:10]
     assert ncmp >= 10
+
+
+def test_host_input_in_chunks_equals_device_search(gsp, orc):
+    # gsp_search_host copies the input in time chunks that overlap the
+    # dedispersion; block_len 1000 makes the chunk unit lcm(1000, 16) = 2000, and
+    # the host rows have a stride that is not a multiple of 16
+    rng = np.random.default_rng(21)
+    nchan, n_in = 96, 30000
+    dms = np.arange(0.0, 40.0, 0.5)
+    x = rng.integers(0, 256, (nchan, n_in + 7), dtype=np.uint8)
+    x[:, 12000:12004] = 255
+    desc, keep = gsp.make_desc(nchan, 1200.0, 1500.0, 1e-4, n_in, dms=dms, block_len=1000,
+                               threshold=4.0, flags=gsp.GSP_FLAG_TIMING)
+    plan = gsp.gsp_plan_create(desc, keep)
+    c1, n1, _ = gsp.gsp_search_host(plan, x, n_in, t_offset=4000)
+    assert n1 > 0
+    launches = gsp.gsp_plan_launches(plan)
+    assert launches >= 4 + 5                   # four dedispersion chunks + the search
+    dd_ms, se_ms = gsp.gsp_plan_timing(plan)
+    assert dd_ms > 0 and se_ms > 0
+    xd = torch.zeros((nchan, (n_in + 15) // 16 * 16), dtype=torch.uint8)
+    xd[:, :n_in] = torch.from_numpy(x[:, :n_in])
+    gsp.gsp_search(plan, xd.cuda(), n_in, t_offset=4000)
+    c2, n2, _ = gsp.gsp_candidates(plan)
+    assert n1 == n2 and (c1 == c2).all()
+    # and the oracle on the same input
+    dl, _ = orc.delays(nchan, 1200.0, 1500.0, 1e-4, dms)
+    D = orc.dedisperse(np.ascontiguousarray(x[:, :n_in]), n_in, dl)
+    cont, ora = {}, []
+    for r in range(len(dms)):
+        det = orc.search_row(D[r], dm_idx=r, block_len=1000, threshold=4.0, t_offset=4000,
+                             detail=True)
+        cont[r] = window_contenders(det, 1024, 4000, 4.0)
+        ora.append(det["cands"])
+    ncmp, bad = compare_candidates(c1, np.concatenate(ora), 4.0, 1024, 4000, cont)
+    assert not bad, bad[:5]
+    assert ncmp > 0
