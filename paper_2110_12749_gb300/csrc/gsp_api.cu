@@ -527,7 +527,7 @@ gsp_status gsp_candidates(gsp_plan_t p, gsp_cand *host_out, int64_t cap, int64_t
 // columns [a_k, a_{k+1} + max_delay), and its copy brings the columns not yet
 // on the device.  The series are exact integer sums, so the result does not
 // depend on the chunking.
-constexpr int kHostChunks = 4;
+constexpr int kHostChunks = 8;
 
 gsp_status gsp_search_host(gsp_plan_t p, const uint8_t *h_x, int64_t n_in, int64_t x_stride,
                            int64_t t_offset, gsp_cand *host_out, int64_t cap, int64_t *n_total,

@@ -89,7 +89,7 @@ struct gsp_plan_s {
     cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
     // host-input pipeline (gsp_search_host): copy stream and its events, created on first use
     cudaStream_t h2d_stream = nullptr;
-    cudaEvent_t h2d_ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    cudaEvent_t h2d_ev[9] = {};  // one per chunk + one for the caller's stream
     bool timed = false;
     cudaStream_t last_stream = nullptr;
     int64_t last_nout = -1;

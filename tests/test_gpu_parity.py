@@ -217,7 +217,7 @@ def test_host_input_in_chunks_equals_device_search(gsp, orc):
     c1, n1, _ = gsp.gsp_search_host(plan, x, n_in, t_offset=4000)
     assert n1 > 0
     launches = gsp.gsp_plan_launches(plan)
-    assert launches >= 4 + 5                   # four dedispersion chunks + the search
+    assert launches >= 8 + 5                   # eight dedispersion chunks + the search
     dd_ms, se_ms = gsp.gsp_plan_timing(plan)
     assert dd_ms > 0 and se_ms > 0
     xd = torch.zeros((nchan, (n_in + 15) // 16 * 16), dtype=torch.uint8)
