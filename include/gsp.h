@@ -200,7 +200,13 @@ gsp_status gsp_candidates(gsp_plan_t plan, gsp_cand *host_out, int64_t cap,
 
 /* End-to-end call on HOST data: copies h_x (host, pinned or pageable,
  * x_stride bytes per channel) to plan-owned device memory, runs gsp_search
- * and returns the candidates as gsp_candidates does.  Synchronises. */
+ * and returns the candidates as gsp_candidates does.  Synchronises.  With the
+ * tiled kernel the input is copied in time chunks (8 by default; environment
+ * variable GSP_HOST_CHUNKS = 1..8, 1 = copy everything first) on a second
+ * stream, each chunk's dedispersion starting when its columns have arrived,
+ * so that the copy of chunk k + 1 overlaps the dedispersion of chunk k
+ * (overlap needs pinned host memory).  The result does not depend on the
+ * chunking. */
 gsp_status gsp_search_host(gsp_plan_t plan, const uint8_t *h_x, int64_t n_in,
                            int64_t x_stride, int64_t t_offset, gsp_cand *host_out,
                            int64_t cap, int64_t *n_total, void *stream);

@@ -526,8 +526,17 @@ gsp_status gsp_candidates(gsp_plan_t p, gsp_cand *host_out, int64_t cap, int64_t
 // aligned and its block sums land in whole blocks; chunk k needs the input
 // columns [a_k, a_{k+1} + max_delay), and its copy brings the columns not yet
 // on the device.  The series are exact integer sums, so the result does not
-// depend on the chunking.
+// depend on the chunking.  GSP_HOST_CHUNKS (1..8) sets the number of chunks;
+// 1 copies everything first.
 constexpr int kHostChunks = 8;
+
+int host_chunks() {
+    if (const char *v = std::getenv("GSP_HOST_CHUNKS")) {
+        const int k = std::atoi(v);
+        if (k >= 1 && k <= kHostChunks) return k;
+    }
+    return kHostChunks;
+}
 
 gsp_status gsp_search_host(gsp_plan_t p, const uint8_t *h_x, int64_t n_in, int64_t x_stride,
                            int64_t t_offset, gsp_cand *host_out, int64_t cap, int64_t *n_total,
@@ -551,7 +560,8 @@ gsp_status gsp_search_host(gsp_plan_t p, const uint8_t *h_x, int64_t n_in, int64
     const int64_t B = p->desc.block_len;
     int64_t unit = B;
     while (unit % 16) unit += B;  // lcm(B, 16)
-    const bool pipelined = !p->simple_dd && n_out >= kHostChunks * unit;
+    const int nch = host_chunks();
+    const bool pipelined = nch > 1 && !p->simple_dd && n_out >= nch * unit;
     if (!pipelined) {
         if (x_stride == dstride) {
             GSP_CK(cudaMemcpyAsync(p->d_xstage, h_x, need, cudaMemcpyHostToDevice, s));
@@ -567,14 +577,14 @@ gsp_status gsp_search_host(gsp_plan_t p, const uint8_t *h_x, int64_t n_in, int64
     for (auto &e : p->h2d_ev)
         if (!e) GSP_CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     int64_t a[kHostChunks + 1];
-    for (int k = 0; k <= kHostChunks; k++) a[k] = (n_out * k / kHostChunks) / unit * unit;
-    a[kHostChunks] = n_out;
+    for (int k = 0; k <= nch; k++) a[k] = (n_out * k / nch) / unit * unit;
+    a[nch] = n_out;
     // the copies start after the caller's earlier work on s (which may still
     // read the staging buffer)
     GSP_CK(cudaEventRecord(p->h2d_ev[kHostChunks], s));
     GSP_CK(cudaStreamWaitEvent(p->h2d_stream, p->h2d_ev[kHostChunks], 0));
     int64_t copied = 0;
-    for (int k = 0; k < kHostChunks; k++) {
+    for (int k = 0; k < nch; k++) {
         const int64_t upto = std::min(n_in, a[k + 1] + p->max_delay);
         if (upto > copied)
             GSP_CK(cudaMemcpy2DAsync(p->d_xstage + copied, dstride, h_x + copied, x_stride,
@@ -594,7 +604,7 @@ gsp_status gsp_search_host(gsp_plan_t p, const uint8_t *h_x, int64_t n_in, int64
         GSP_CK(cudaMemsetAsync(bsum, 0, (size_t)p->desc.ndm * p->nb_max * 3 * sizeof(*bsum), s));
     }
     if (p->timed) GSP_CK(cudaEventRecord(p->ev[0], s));
-    for (int k = 0; k < kHostChunks; k++) {
+    for (int k = 0; k < nch; k++) {
         GSP_CK(cudaStreamWaitEvent(s, p->h2d_ev[k], 0));
         const int64_t len = a[k + 1] - a[k];
         st = run_dedisperse(p, p->d_xstage + a[k], len + p->max_delay, dstride, len, D + a[k],
