@@ -346,7 +346,7 @@ def gsp_candidates(plan, cap=None):
     """Returns (candidates sorted by (dm_idx, t, width), true count, status)."""
     if cap is None:
         cap = int(plan.desc.max_cands)
-    out = np.zeros(max(cap, 1), dtype=CAND_DTYPE)
+    out = np.empty(max(cap, 1), dtype=CAND_DTYPE)   # only the first n records are read
     n = ctypes.c_int64(0)
     st = lib().gsp_candidates(plan.handle, _np_ptr(out), cap, ctypes.byref(n))
     if st not in (GSP_OK, GSP_ERR_CAPACITY):
@@ -358,7 +358,7 @@ def gsp_search_host(plan, x_host, n_in, t_offset=0, cap=None, stream=None):
     """x_host: numpy uint8 [nchan][stride] or a (pinned) CPU torch tensor."""
     if cap is None:
         cap = int(plan.desc.max_cands)
-    out = np.zeros(max(cap, 1), dtype=CAND_DTYPE)
+    out = np.empty(max(cap, 1), dtype=CAND_DTYPE)   # only the first n records are read
     n = ctypes.c_int64(0)
     if isinstance(x_host, np.ndarray):
         ptr, stride = _np_ptr(x_host), x_host.strides[0]
@@ -453,7 +453,7 @@ def gsp_stream_results(s, cap=None):
     """(candidates with absolute t and the beam label, true count, status, t_abs0)."""
     if cap is None:
         cap = int(s.plan.desc.max_cands)
-    out = np.zeros(max(cap, 1), dtype=CAND_DTYPE)
+    out = np.empty(max(cap, 1), dtype=CAND_DTYPE)   # only the first n records are read
     n, t0 = ctypes.c_int64(0), ctypes.c_int64(0)
     st = lib().gsp_stream_results(s.handle, _np_ptr(out), cap, ctypes.byref(n), ctypes.byref(t0))
     if st not in (GSP_OK, GSP_ERR_CAPACITY):
@@ -510,7 +510,7 @@ def gsp_batch_search(b, xs, n_ins, t_offsets=None, stream=None):
 
 
 def gsp_batch_candidates(b, cap=1 << 22):
-    out = np.zeros(max(cap, 1), dtype=CAND_DTYPE)
+    out = np.empty(max(cap, 1), dtype=CAND_DTYPE)   # only the first n records are read
     n = ctypes.c_int64(0)
     st = lib().gsp_batch_candidates(b.handle, _np_ptr(out), cap, ctypes.byref(n))
     if st not in (GSP_OK, GSP_ERR_CAPACITY):
@@ -588,7 +588,7 @@ def gsp_ddplan_search(d, x, n_in, t_offset=0, stream=None):
 
 
 def gsp_ddplan_candidates(d, cap=1 << 22):
-    out = np.zeros(max(cap, 1), dtype=CAND_DTYPE)
+    out = np.empty(max(cap, 1), dtype=CAND_DTYPE)   # only the first n records are read
     n = ctypes.c_int64(0)
     st = lib().gsp_ddplan_candidates(d.handle, _np_ptr(out), cap, ctypes.byref(n))
     if st not in (GSP_OK, GSP_ERR_CAPACITY):
