@@ -220,17 +220,27 @@ def run_stream(args, wl, delays_fn):
     import threading
     import torch
     from paper_2110_12749_gb300 import gsp, synth
-    B, K, chunk = args.stream_beams, args.stream_chunks, 1 << 18
+    K, chunk = args.stream_chunks, 1 << 18
     plans, streams, cstreams = [], [], []
     md = None
-    for b in range(B):
+    admitted_bytes = 0
+    # admit beams by memory: a beam joins while its plan and stream buffers fit in
+    # 80% of the device memory that is free
+    for b in range(args.stream_beams):
         desc, keep = gsp.make_desc(wl.nchan, wl.f_lo, wl.f_hi, wl.t_samp, 1 << 20, ndm=wl.ndm,
                                    dm_lo=wl.dm_lo, dm_step=wl.dm_step)
         plan = gsp.gsp_plan_create(desc, keep)
+        free, _ = torch.cuda.mem_get_info()
+        need = gsp.gsp_stream_bytes(plan, chunk)
+        if need > 0.8 * free:
+            gsp.gsp_plan_destroy(plan)
+            break
         md = gsp.gsp_plan_max_delay(plan)
         plans.append(plan)
         streams.append(gsp.gsp_stream_create(plan, chunk, beam=b))
         cstreams.append(torch.cuda.Stream())
+        admitted_bytes += need
+    B = len(plans)
     # one primed chunk of synthetic data, repeated for every chunk of every beam
     import dataclasses
     wl1 = dataclasses.replace(wl, n_in=md + chunk)
@@ -290,7 +300,10 @@ def run_stream(args, wl, delays_fn):
         gsp.gsp_plan_destroy(p)
     lat_sorted = sorted(lat)
     span = max(done_at) - t_start
-    return {"beams": B, "chunk_samples": chunk, "chunk_sky_s": chunk * wl.t_samp,
+    return {"beams": B, "beams_requested": args.stream_beams,
+            "admission": "by memory: a beam joins while gsp_stream_bytes fits in 80% of free "
+                         "device memory", "admitted_bytes": int(admitted_bytes),
+            "chunk_samples": chunk, "chunk_sky_s": chunk * wl.t_samp,
             "arrival_gbs": args.stream_gbs, "chunks_timed": n_items,
             "p50_ms": float(np.percentile(lat_sorted, 50)),
             "p99_ms": float(np.percentile(lat_sorted, 99)), "max_ms": float(lat_sorted[-1]),

@@ -270,6 +270,12 @@ gsp_status gsp_search_series_static(const int32_t *d_D, int32_t ndm, int64_t n_o
  * (sigma_ref) is per chunk. */
 gsp_status gsp_stream_create(gsp_stream_t *out, gsp_plan_t plan, int64_t chunk_out, int32_t beam);
 
+/* Device bytes a new stream of chunk_out samples on this plan will allocate:
+ * its two input buffers, plus the plan's series scratch if the plan has not
+ * searched yet.  For admitting beams by memory (compare with cudaMemGetInfo).
+ * -1 for a NULL plan or chunk_out <= 0.  Host only. */
+int64_t gsp_stream_bytes(gsp_plan_t plan, int64_t chunk_out);
+
 /* Free the stream's buffers (synchronises the device; the plan is not freed). */
 gsp_status gsp_stream_destroy(gsp_stream_t s);
 

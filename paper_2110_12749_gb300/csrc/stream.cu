@@ -5,6 +5,7 @@
 // is the device-resident form of the overlapping read blocks of Alg. 2 /
 // Alg. 3 (lastdata + data), and of the half-overlap merge of adjacent files
 // in Sec. 2.1, for an unbounded stream.
+#include <algorithm>
 #include <cstring>
 #include <new>
 
@@ -60,6 +61,19 @@ gsp_status gsp_stream_destroy(gsp_stream_t s) {
     cudaFree(s->buf[1]);
     delete s;
     return e == cudaSuccess ? GSP_OK : GSP_ERR_CUDA;
+}
+
+int64_t gsp_stream_bytes(gsp_plan_t plan, int64_t chunk_out) {
+    if (!plan || chunk_out <= 0) return -1;
+    const int64_t stride = (chunk_out + gsp_plan_max_delay(plan) + 15) & ~(int64_t)15;
+    int64_t bytes = 2 * stride * (int64_t)plan->desc.nchan;
+    // the plan's series scratch, allocated on its first search for nsamp_max samples
+    if (!plan->d_D) {
+        const int64_t row = (std::max<int64_t>(plan->desc.nsamp_max - plan->max_delay, chunk_out) + 3) &
+                            ~(int64_t)3;
+        bytes += (int64_t)plan->desc.ndm * row * (int64_t)sizeof(int32_t);
+    }
+    return bytes;
 }
 
 int64_t gsp_stream_need(gsp_stream_t s) {

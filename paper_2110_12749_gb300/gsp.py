@@ -111,6 +111,7 @@ def lib():
             "gsp_stream_create": ([_vp, _vp, _i64, ctypes.c_int32], ctypes.c_int),
             "gsp_stream_destroy": ([_vp], ctypes.c_int),
             "gsp_stream_need": ([_vp], _i64),
+            "gsp_stream_bytes": ([_vp, _i64], _i64),
             "gsp_stream_push": ([_vp, _vp, _i64, _i64, _vp], ctypes.c_int),
             "gsp_stream_results": ([_vp, _vp, _i64, _vp, _vp], ctypes.c_int),
             "gsp_batch_create": ([_vp, _vp, ctypes.c_int32, ctypes.c_int32], ctypes.c_int),
@@ -434,6 +435,10 @@ def gsp_stream_destroy(s):
         st = lib().gsp_stream_destroy(s.handle)
         s.handle = None
         _check(st, "gsp_stream_destroy")
+
+
+def gsp_stream_bytes(plan, chunk_out):
+    return int(lib().gsp_stream_bytes(plan.handle, chunk_out))
 
 
 def gsp_stream_need(s):

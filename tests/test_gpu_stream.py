@@ -77,3 +77,24 @@ def test_stream_chunks_equal_one_shot_spans(gsp, orc):
     with pytest.raises(gsp.GspError):
         gsp.gsp_stream_push(s, np.zeros((nchan, chunk + 16), np.uint8), chunk + 16)
     gsp.gsp_stream_destroy(s)
+
+
+def test_stream_bytes_for_admission(gsp, orc):
+    nchan, chunk = 64, 4096
+    desc, keep = gsp.make_desc(nchan, 1200.0, 1500.0, 1e-4, 1 << 16, ndm=32, dm_lo=0.0,
+                               dm_step=1.0)
+    plan = gsp.gsp_plan_create(desc, keep)
+    md = gsp.gsp_plan_max_delay(plan)
+    bufs = 2 * ((chunk + md + 15) // 16 * 16) * nchan
+    scratch = 32 * (((1 << 16) - md + 3) // 4 * 4) * 4
+    assert gsp.gsp_stream_bytes(plan, chunk) == bufs + scratch   # plan not searched yet
+    free0, _ = torch.cuda.mem_get_info()
+    s = gsp.gsp_stream_create(plan, chunk)
+    free1, _ = torch.cuda.mem_get_info()
+    assert free0 - free1 >= bufs                                   # the stream's buffers
+    x = np.zeros((nchan, chunk + md), np.uint8)
+    gsp.gsp_stream_push(s, x, gsp.gsp_stream_need(s))
+    gsp.gsp_stream_results(s)
+    assert gsp.gsp_stream_bytes(plan, chunk) == bufs               # scratch now exists
+    assert gsp.gsp_stream_bytes(plan, 0) == -1
+    gsp.gsp_stream_destroy(s)
