@@ -169,7 +169,7 @@ __device__ __forceinline__ void fail(int *err) { atomicExch(err, 1); }
 // pipe of the additions: 0 = IADD3 on the integer ALU, 1 = E on the ALU and
 // O as x * 1 + acc on the multiply-add pipe, 2 = both on the multiply-add
 // pipe.  For ACC 3, E is the raw sum of the words (IADD3, no extraction) and
-// O is summed on the multiply-add pipe; since w = (b0 + 2^16 b2) + 2^8 O(w),
+// O is summed on the multiply-add pipe (ACC 4: O with IADD3 on the ALU too); since w = (b0 + 2^16 b2) + 2^8 O(w),
 // the even-byte sums are E - (O << 8) mod 2^32, exact while the 16-bit lanes
 // cannot overflow.
 // Flush one phase family P into the int32 accumulators: recover the four
@@ -185,7 +185,7 @@ __device__ __forceinline__ void flush_family(uint32_t (&E)[M], uint32_t (&O)[M],
     for (int k = 0; k < M; k++) {
         sp[k][0] = sp[k][1] = sp[k][2] = 0;
         const uint32_t o = O[k];
-        const uint32_t e = ACC == 3 ? E[k] - (o << 8) : E[k];
+        const uint32_t e = ACC >= 3 ? E[k] - (o << 8) : E[k];
         const uint32_t b[4] = {e & 0xffffu, o & 0xffffu, e >> 16, o >> 16};
 #pragma unroll
         for (int q = 0; q < 4; q++) {
@@ -231,6 +231,10 @@ __device__ __forceinline__ void acc_pair(uint32_t &E, uint32_t &O, uint32_t w1, 
         // raw view: E holds sum w; the even bytes are recovered at the flush
         E += w1 + w2;
         O = ptx::imadd(o1, one, ptx::imadd(o2, one, O));
+    } else if (ACC == 4) {
+        // raw view, both sums as three-input adds on the integer ALU
+        E += w1 + w2;
+        O += o1 + o2;
     } else if (ACC == 0) {
         E += e1 + e2;
         O += o1 + o2;
@@ -318,7 +322,7 @@ template <int KW, bool QUAD, int ACC, bool A32 = false, int M = 4, int CB = 32, 
           bool PRE = false, bool MF = false, int KDM = 16, int UNR = 2, bool IMA = false>
 __global__ void __launch_bounds__((KDM / KW + 1) * 32, 1) dd_tiled_kernel(const TiledArgs a) {
     static_assert(!PRE || (KW == 1 && CB == 64), "precomputed lists: one DM per warp, 64-channel stages");
-    static_assert(!MF || (ACC == 3 && !FF), "merged flush: raw + odd views, all families together");
+    static_assert(!MF || (ACC >= 3 && !FF), "merged flush: raw + odd views, all families together");
     constexpr int kCB = CB;
     constexpr int kH = CB / 32;                  // channels per lane per stage
     constexpr int kFlushStages = 256 / kCB;      // stages between SWAR flushes (256 channels)
@@ -589,7 +593,7 @@ __global__ void __launch_bounds__((KDM / KW + 1) * 32, 1) dd_tiled_kernel(const 
                         ptx::lds_words<kM>((uint32_t)lp[j] + lane4, w1);
 #pragma unroll
                         for (int k = 0; k < kM; k++) {
-                            E[i][P][k] += ACC == 3 ? w1[k] : (w1[k] & 0x00ff00ffu);
+                            E[i][P][k] += ACC >= 3 ? w1[k] : (w1[k] & 0x00ff00ffu);
                             if (IMA)
                                 O[i][P][k] = ptx::imadd(__byte_perm(w1[k], 0, 0x4341), one, O[i][P][k]);
                             else
@@ -645,7 +649,7 @@ __global__ void __launch_bounds__((KDM / KW + 1) * 32, 1) dd_tiled_kernel(const 
 #pragma unroll
                     for (int k = 0; k < kM; k++) {
                         const uint32_t w1 = p1[32 * k];
-                        E[i][P][k] += ACC == 3 ? w1 : (w1 & 0x00ff00ffu);
+                        E[i][P][k] += ACC >= 3 ? w1 : (w1 & 0x00ff00ffu);
                         O[i][P][k] += __byte_perm(w1, 0, 0x4341);
                     }
                 }
@@ -679,7 +683,7 @@ __global__ void __launch_bounds__((KDM / KW + 1) * 32, 1) dd_tiled_kernel(const 
 #pragma unroll
                     for (int P = 0; P < 4; P++) {
                         const uint32_t o = O[i][P][k];
-                        const uint32_t e = ACC == 3 ? E[i][P][k] - (o << 8) : E[i][P][k];
+                        const uint32_t e = ACC >= 3 ? E[i][P][k] - (o << 8) : E[i][P][k];
                         uint32_t b[4];
                         b[0] = e & 0xffffu;
                         b[1] = o & 0xffffu;
@@ -841,6 +845,7 @@ const TiledVariant kVariants[] = {
     {dd_tiled_kernel<1, false, 3, true, 6, 64, false, true, true, 15, 3, true>, 1, 6, 64, true, 15},
     {dd_tiled_kernel<1, false, 3, true, 6, 64, false, true, true, 15, 4, true>, 1, 6, 64, true, 15},
     {dd_tiled_kernel<1, false, 3, true, 5, 64, false, true, true, 15, 2, true>, 1, 5, 64, true, 15},
+    {dd_tiled_kernel<1, false, 4, true, 6, 64, false, true, true, 15, 2, true>, 1, 6, 64, true, 15},
 };
 constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
 constexpr int kDefaultVariant = 32;
