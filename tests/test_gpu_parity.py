@@ -202,22 +202,26 @@ def test_custom_widths_blocks_windows_offset(gsp, orc, tiny):
     assert ncmp >= 10
 
 
-def test_host_input_in_chunks_equals_device_search(gsp, orc):
+@pytest.mark.parametrize("chunks,flags", [("8", 0), ("3", 0), ("1", 0), ("8", 2)])
+def test_host_input_in_chunks_equals_device_search(gsp, orc, monkeypatch, chunks, flags):
     # gsp_search_host copies the input in time chunks that overlap the
     # dedispersion; block_len 1000 makes the chunk unit lcm(1000, 16) = 2000, and
-    # the host rows have a stride that is not a multiple of 16
+    # the host rows have a stride that is not a multiple of 16.  One chunk and
+    # the simple kernel (flags 2) take the copy-first path.
+    monkeypatch.setenv("GSP_HOST_CHUNKS", chunks)
     rng = np.random.default_rng(21)
     nchan, n_in = 96, 30000
     dms = np.arange(0.0, 40.0, 0.5)
     x = rng.integers(0, 256, (nchan, n_in + 7), dtype=np.uint8)
     x[:, 12000:12004] = 255
     desc, keep = gsp.make_desc(nchan, 1200.0, 1500.0, 1e-4, n_in, dms=dms, block_len=1000,
-                               threshold=4.0, flags=gsp.GSP_FLAG_TIMING)
+                               threshold=4.0, flags=gsp.GSP_FLAG_TIMING | flags)
     plan = gsp.gsp_plan_create(desc, keep)
     c1, n1, _ = gsp.gsp_search_host(plan, x, n_in, t_offset=4000)
     assert n1 > 0
     launches = gsp.gsp_plan_launches(plan)
-    assert launches >= 8 + 5                   # eight dedispersion chunks + the search
+    if flags == 0:
+        assert launches >= int(chunks) + 5     # one dedispersion launch per chunk + the search
     dd_ms, se_ms = gsp.gsp_plan_timing(plan)
     assert dd_ms > 0 and se_ms > 0
     xd = torch.zeros((nchan, (n_in + 15) // 16 * 16), dtype=torch.uint8)
