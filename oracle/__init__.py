@@ -42,7 +42,8 @@ def lib():
         L.oracle_subband_delays.argtypes = [i64, dbl, dbl, ctypes.c_int, dbl, i64, vp, i64, i64,
                                             vp, vp, vp]
         L.oracle_subband_delays.restype = ctypes.c_int
-        L.oracle_subband_dedisperse.argtypes = [vp, i64, i64, i64, i64, i64, vp, vp, i64, i64, vp]
+        L.oracle_subband_dedisperse.argtypes = [vp, i64, i64, i64, i64, i64, vp, vp, i64, vp, i64,
+                                                i64, vp]
         L.oracle_subband_dedisperse.restype = ctypes.c_int
         L.oracle_num_threads.argtypes = []
         L.oracle_num_threads.restype = ctypes.c_int
@@ -223,8 +224,9 @@ def subband_nout(n_in, d1, d2):
     return n_in - max_delay(d1) - max_delay(d2)
 
 
-def subband_dedisperse(x, n_in, d1, d2, group, n_out=None):
-    """int64 D [ndm][n_out] of the two-stage sub-band dedispersion."""
+def subband_dedisperse(x, n_in, d1, d2, group, n_out=None, rows=None):
+    """int64 D [nrows][n_out] of the two-stage sub-band dedispersion (rows: the
+    trial indices to compute, default all)."""
     x = np.ascontiguousarray(x, dtype=np.uint8)
     d1 = np.ascontiguousarray(d1, dtype=np.int32)
     d2 = np.ascontiguousarray(d2, dtype=np.int32)
@@ -232,9 +234,14 @@ def subband_dedisperse(x, n_in, d1, d2, group, n_out=None):
     ndm, nsub = d2.shape
     if n_out is None:
         n_out = subband_nout(n_in, d1, d2)
-    out = np.empty((ndm, max(n_out, 0)), dtype=np.int64)
+    if rows is None:
+        r, nrows = None, ndm
+    else:
+        r = np.ascontiguousarray(np.asarray(rows, dtype=np.int64).reshape(-1))
+        nrows = r.size
+    out = np.empty((nrows, max(n_out, 0)), dtype=np.int64)
     rc = lib().oracle_subband_dedisperse(_ptr(x), nchan, n_in, stride, nsub, int(group),
-                                         _ptr(d1), _ptr(d2), ndm, n_out, _ptr(out))
+                                         _ptr(d1), _ptr(d2), ndm, _ptr(r), nrows, n_out, _ptr(out))
     if rc != 0:
         raise ValueError("oracle_subband_dedisperse failed (%d)" % rc)
     return out

@@ -416,44 +416,73 @@ int oracle_subband_delays(int64_t nchan, double f_lo, double f_hi, int descendin
  *   stage 1: S[g][s][t] = sum_{c in sub-band s} X[c][t + d1[g][c]],  t < n1
  *   stage 2: D[d][t]    = sum_s S[group(d)][s][t + d2[d][s]],        t < n_out
  * with n1 = n_in - max d1 and n_out <= n1 - max d2; group(d) = d / group.
- * out: int64 [ndm][n_out]. */
+ * rows: the trial indices to compute (NULL = all ndm, nrows = ndm); stage 1
+ * is computed only for the groups those rows use.
+ * out: int64 [nrows][n_out]. */
 int oracle_subband_dedisperse(const uint8_t *x, int64_t nchan, int64_t n_in,
                               int64_t x_stride, int64_t nsub, int64_t group,
                               const int32_t *d1, const int32_t *d2, int64_t ndm,
-                              int64_t n_out, int64_t *out) {
+                              const int64_t *rows, int64_t nrows, int64_t n_out,
+                              int64_t *out) {
     if (!x || !d1 || !d2 || !out || nchan <= 0 || nsub <= 0 || nchan % nsub != 0 ||
         group <= 0 || ndm <= 0 || n_out < 0 || x_stride < n_in)
         return ORACLE_EINVAL;
+    if (rows == NULL) nrows = ndm;
     int64_t cs = nchan / nsub;
     int64_t nsdm = (ndm + group - 1) / group;
     int64_t max1 = oracle_max_delay(d1, nsdm, nchan);
     int64_t max2 = oracle_max_delay(d2, ndm, nsub);
     int64_t n1 = n_in - max1;
     if (n1 < 0 || n_out + max2 > n1) return ORACLE_EINVAL;
-    int64_t *S = (int64_t *)calloc((size_t)(nsdm * nsub * (n1 > 0 ? n1 : 1)), sizeof(int64_t));
-    if (!S) return ORACLE_ENOMEM;
-    int64_t gs;
+    /* the groups the selected rows use, and a slot for each */
+    int64_t *slot = (int64_t *)malloc((size_t)nsdm * sizeof(int64_t));
+    if (!slot) return ORACLE_ENOMEM;
+    for (int64_t g = 0; g < nsdm; g++) slot[g] = -1;
+    int64_t nused = 0;
+    for (int64_t r = 0; r < nrows; r++) {
+        int64_t d = rows ? rows[r] : r;
+        if (d < 0 || d >= ndm) {
+            free(slot);
+            return ORACLE_EINVAL;
+        }
+        if (slot[d / group] < 0) slot[d / group] = nused++;
+    }
+    int64_t *gl = (int64_t *)malloc((size_t)(nused > 0 ? nused : 1) * sizeof(int64_t));
+    int64_t *S = (int64_t *)calloc((size_t)((nused > 0 ? nused : 1) * nsub * (n1 > 0 ? n1 : 1)),
+                                   sizeof(int64_t));
+    if (!gl || !S) {
+        free(slot);
+        free(gl);
+        free(S);
+        return ORACLE_ENOMEM;
+    }
+    for (int64_t g = 0; g < nsdm; g++)
+        if (slot[g] >= 0) gl[slot[g]] = g;
+    int64_t us;
 #pragma omp parallel for schedule(dynamic, 1)
-    for (gs = 0; gs < nsdm * nsub; gs++) {
-        int64_t g = gs / nsub, s = gs % nsub;
-        int64_t *o = S + gs * n1;
+    for (us = 0; us < nused * nsub; us++) {
+        int64_t u = us / nsub, s = us % nsub, g = gl[u];
+        int64_t *o = S + us * n1;
         for (int64_t c = s * cs; c < s * cs + cs; c++) {
             const uint8_t *xc = x + c * x_stride + d1[g * nchan + c];
             for (int64_t t = 0; t < n1; t++) o[t] += (int64_t)xc[t];
         }
     }
-    int64_t d;
+    int64_t r;
 #pragma omp parallel for schedule(dynamic, 1)
-    for (d = 0; d < ndm; d++) {
-        int64_t g = d / group;
-        int64_t *o = out + d * n_out;
+    for (r = 0; r < nrows; r++) {
+        int64_t d = rows ? rows[r] : r;
+        int64_t u = slot[d / group];
+        int64_t *o = out + r * n_out;
         for (int64_t t = 0; t < n_out; t++) o[t] = 0;
         for (int64_t s = 0; s < nsub; s++) {
-            const int64_t *Ss = S + (g * nsub + s) * n1 + d2[d * nsub + s];
+            const int64_t *Ss = S + (u * nsub + s) * n1 + d2[d * nsub + s];
             for (int64_t t = 0; t < n_out; t++) o[t] += Ss[t];
         }
     }
     free(S);
+    free(gl);
+    free(slot);
     return ORACLE_OK;
 }
 

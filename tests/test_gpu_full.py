@@ -139,3 +139,52 @@ def test_full_size_parity(gsp, orc, name):
                   (np.abs(cands["t"] - p.t0) <= p.width + smear + 4)]
         found += int(len(m) > 0)
     assert strong > 0 and found >= 0.8 * strong, (found, strong)
+
+
+def test_full_size_subband_parity(gsp, orc):
+    # The two-stage sub-band path on the CRAFTS-like beam in the bench's
+    # configuration (64 sub-bands of 64 channels, groups of 16 trials): every row
+    # through the prefix-sum identities with the effective per-channel delays
+    # d1[g][c] + d2[d][s(c)], and sampled rows bit-exactly against the oracle.
+    from paper_2110_12749_gb300 import synth
+    wl = synth.WORKLOADS["crafts"]
+    nsub, group = 64, 16
+    dl, _ = orc.delays(wl.nchan, wl.f_lo, wl.f_hi, wl.t_samp, wl.dms)
+    d1, d2, si = orc.subband_delays(wl.nchan, wl.f_lo, wl.f_hi, wl.t_samp, wl.dms, nsub, group)
+    n_out = orc.subband_nout(wl.n_in, d1, d2)
+    x, _, _, pulses = synth.workload_filterbank(
+        wl, lambda dm: orc.delays(wl.nchan, wl.f_lo, wl.f_hi, wl.t_samp, [dm])[0][0],
+        wl.n_in - orc.max_delay(dl))
+    desc, keep = gsp.make_desc(wl.nchan, wl.f_lo, wl.f_hi, wl.t_samp, wl.n_in, ndm=wl.ndm,
+                               dm_lo=wl.dm_lo, dm_step=wl.dm_step)
+    sb = gsp.gsp_subband_create(desc, nsub, group)
+    g1, g2, gsi = gsp.gsp_subband_delays(sb)
+    assert (g1 == d1).all() and (g2 == d2).all() and (gsi == si).all()
+    assert gsp.gsp_subband_nout(sb, wl.n_in) == n_out
+    D = torch.empty((wl.ndm, (n_out + 3) // 4 * 4), dtype=torch.int32, device="cuda")
+    xd = torch.from_numpy(x).cuda()
+    gsp.gsp_subband_dedisperse(sb, xd, wl.n_in, D)
+    gsp.gsp_subband_finish(sb)
+    del xd
+    gsp.gsp_subband_destroy(sb)
+    torch.cuda.empty_cache()
+    # (1) every row
+    cs = wl.nchan // nsub
+    eff = d1[np.arange(wl.ndm) // group] + np.repeat(d2, cs, axis=1)
+    g0, gs1 = _gpu_row_sums(D, n_out)
+    e0, e1 = _prefix_expect(x, eff, n_out)
+    assert (g0 == e0).all(), np.nonzero(g0 != e0)[0][:10]
+    assert (gs1 == e1).all(), np.nonzero(gs1 != e1)[0][:10]
+    # (2) sampled rows: sub-band DM trials, trials next to pulses, random ones
+    rng = np.random.default_rng(321)
+    rows = {int(si[0]), int(si[-1]), 0, wl.ndm - 1}
+    rows |= set(int(r) for r in rng.choice(wl.ndm, 3, replace=False))
+    for p in pulses[:2]:
+        rows.add(min(max(int(round((p.dm - wl.dm_lo) / wl.dm_step)), 0), wl.ndm - 1))
+    rows = np.array(sorted(rows))
+    Dref = orc.subband_dedisperse(x, wl.n_in, d1, d2, group, rows=rows)
+    Dg = D[torch.from_numpy(rows).cuda()][:, :n_out].cpu().numpy().astype(np.int64)
+    assert (Dg == Dref).all()
+    # the sub-band DM trials equal brute force
+    brute = orc.dedisperse(x, wl.n_in, dl, rows=[int(si[0]), int(si[-1])], n_out=n_out)
+    assert (Dg[np.searchsorted(rows, [int(si[0]), int(si[-1])])] == brute).all()

@@ -195,3 +195,14 @@ def test_subband_pulse_smearing_bound(orc):
     lo, hi = np.nonzero(D[i])[0][[0, -1]]
     spread = int(np.abs(d1[i // group] + np.repeat(d2[i], nchan // nsub) - dl[i]).max())
     assert t0 - spread <= lo and hi <= t0 + w - 1 + spread
+
+
+def test_subband_row_selection(orc):
+    rng = np.random.default_rng(13)
+    nchan, n_in = 64, 2500
+    dms = np.arange(0.0, 30.0, 1.0)
+    d1, d2, _ = orc.subband_delays(nchan, 1200.0, 1500.0, 1e-4, dms, 8, 4)
+    x = rng.integers(0, 256, (nchan, n_in), dtype=np.uint8)
+    full = orc.subband_dedisperse(x, n_in, d1, d2, 4)
+    rows = [29, 3, 3, 17, 0]
+    assert (orc.subband_dedisperse(x, n_in, d1, d2, 4, rows=rows) == full[rows]).all()
