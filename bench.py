@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--batch-beams", type=int, default=19,
                     help="beams of the batched multi-beam measurement (0: skip)")
     ap.add_argument("--batch-steps", type=int, default=3)
+    ap.add_argument("--ingest-steps", type=int, default=3,
+                    help="timed steps of the ingest transpose of the beam (0: skip)")
     ap.add_argument("--subband-steps", type=int, default=3,
                     help="timed steps of the two-stage sub-band path on the same beam (0: skip)")
     ap.add_argument("--ranker-beams", type=int, default=12,
@@ -375,6 +377,43 @@ def run_batch(args, wl):
                       "the per-beam search kernels"}
 
 
+def measured_hbm_gbs():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def run_ingest(args, wl, xd):
+    """Ingest transpose of the beam from time-major [N][C] (PSRFITS order) to the
+    channel-major layout: read + write bytes per second against the HBM copy peak."""
+    import torch
+    from paper_2110_12749_gb300 import gsp
+    x_tc = xd[:, :wl.n_in].t().contiguous()          # set-up, not timed
+    out = torch.empty_like(xd)
+    stream = torch.cuda.current_stream()
+    for _ in range(2):
+        gsp.gsp_ingest_transpose(x_tc, wl.n_in, wl.nchan, out)
+    ms = []
+    for _ in range(args.ingest_steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        gsp.gsp_ingest_transpose(x_tc, wl.n_in, wl.nchan, out)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    ok = bool(torch.equal(out[:, :wl.n_in], xd[:, :wl.n_in]))
+    del x_tc, out
+    torch.cuda.empty_cache()
+    m = float(np.median(ms))
+    nbytes = 2.0 * wl.nchan * wl.n_in
+    peak, basis = measured_hbm_gbs()
+    return {"ms": m, "bytes": nbytes, "gbs": nbytes / (m / 1e3) / 1e9, "peak_gbs": peak,
+            "peak_basis": basis, "frac": nbytes / (m / 1e3) / 1e9 / peak,
+            "round_trip_identical": ok}
+
+
 def run_subband(args, wl, plan, xd, n_sub=64, group=16):
     """Two-stage sub-band dedispersion (Sec. 2.3) of the same beam and DM grid,
     then the same search; CUDA events around each part."""
@@ -610,6 +649,9 @@ def run_gsp(args):
     batch_res = None
     subband_res = None
     ddplan_res = None
+    ingest_res = None
+    if args.ingest_steps > 0 and rank == 0:
+        ingest_res = run_ingest(args, wl, xd)
     if args.subband_steps > 0 and rank == 0:
         subband_res = run_subband(args, wl, plan, xd)
     if args.stream_beams > 0 or args.batch_beams > 0 or args.ddplan_steps > 0 or \
@@ -666,6 +708,8 @@ def run_gsp(args):
             line["cpu_baseline"] = cpu
         if batch_res is not None:
             line["batch"] = batch_res
+        if ingest_res is not None:
+            line["ingest"] = ingest_res
         if subband_res is not None:
             line["subband"] = subband_res
         if ddplan_res is not None:

@@ -331,6 +331,16 @@ gsp_status gsp_batch_timing(gsp_batch_t b, float *ms_dedisperse, float *ms_total
  * not tuned) and the kernel launches of the last call (captured ones counted). */
 gsp_status gsp_batch_info(gsp_batch_t b, int32_t *variant, float *tuned_ms, int32_t *launches);
 
+/* Ingest transpose (the optional first step of the path): time-major 8-bit
+ * samples d_in[t][c] (the order of PSRFITS files and of Alg. 2's numpts x
+ * numchan input matrix, Sec. 2.3), t < n_samp, c < nchan, row stride in_stride
+ * >= nchan bytes, into the channel-major d_out[c][t] the other entry points
+ * read (row stride out_stride >= n_samp bytes; a multiple of 16 for them).
+ * Device pointers; asynchronous on stream. */
+gsp_status gsp_ingest_transpose(const uint8_t *d_in, int64_t n_samp, int32_t nchan,
+                                int64_t in_stride, uint8_t *d_out, int64_t out_stride,
+                                void *stream);
+
 /* ------------------------------------------------------------------------
  * DDplan ranges and sub-band dedispersion (Sec. 3.1, Tables 2-3; Sec. 2.3).
  * ------------------------------------------------------------------------ */

@@ -245,3 +245,14 @@ def subband_dedisperse(x, n_in, d1, d2, group, n_out=None, rows=None):
     if rc != 0:
         raise ValueError("oracle_subband_dedisperse failed (%d)" % rc)
     return out
+
+
+def ingest_transpose(x_tc):
+    """Channel-major copy x[c][t] of time-major samples x_tc[t][c] (the input
+    layout of Alg. 2, numpts x numchan, Sec. 2.3)."""
+    x_tc = np.asarray(x_tc, dtype=np.uint8)
+    n, c = x_tc.shape
+    out = np.empty((c, n), np.uint8)
+    for ch in range(c):
+        out[ch, :] = x_tc[:, ch]
+    return out

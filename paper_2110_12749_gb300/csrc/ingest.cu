@@ -1,0 +1,81 @@
+// Ingest transpose: time-major 8-bit samples [N][C] (the order of PSRFITS
+// files and of Alg. 2's numpts x numchan input matrix, Sec. 2.3) into the
+// channel-major [C][N] layout the dedispersion kernels read.  HBM-bound: one
+// read and one write per byte.  A CTA moves a 64 x 64 byte tile through shared
+// memory; each thread loads and stores 4-byte words (16 threads per 64-byte
+// row), with a padded tile so that the column reads are conflict-free.
+#include "gsp_internal.cuh"
+
+namespace {
+
+constexpr int kTile = 64;
+
+__global__ void __launch_bounds__(256) ingest_transpose_kernel(const uint8_t *__restrict__ in,
+                                                               int64_t in_stride, int64_t N, int C,
+                                                               uint8_t *__restrict__ out,
+                                                               int64_t out_stride, bool words) {
+    __shared__ uint8_t tile[kTile][kTile + 4];
+    const int64_t t0 = (int64_t)blockIdx.x * kTile;   // time
+    const int c0 = blockIdx.y * kTile;                // channel
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;  // 16 x 16 threads
+    // load: rows are times, 4 channels per thread
+    for (int r = ty; r < kTile; r += 16) {
+        const int64_t t = t0 + r;
+        const int c = c0 + 4 * tx;
+        uint32_t v = 0;
+        if (t < N) {
+            const uint8_t *src = in + t * in_stride + c;
+            if (words && c + 3 < C) {
+                v = __ldg(reinterpret_cast<const uint32_t *>(src));
+            } else {
+                for (int k = 0; k < 4; k++)
+                    if (c + k < C) v |= (uint32_t)__ldg(src + k) << (8 * k);
+            }
+        }
+        tile[r][4 * tx + 0] = (uint8_t)v;
+        tile[r][4 * tx + 1] = (uint8_t)(v >> 8);
+        tile[r][4 * tx + 2] = (uint8_t)(v >> 16);
+        tile[r][4 * tx + 3] = (uint8_t)(v >> 24);
+    }
+    __syncthreads();
+    // store: rows are channels, 4 times per thread
+    for (int r = ty; r < kTile; r += 16) {
+        const int c = c0 + r;
+        if (c >= C) continue;
+        const int64_t t = t0 + 4 * tx;
+        const uint32_t v = (uint32_t)tile[4 * tx + 0][r] | ((uint32_t)tile[4 * tx + 1][r] << 8) |
+                           ((uint32_t)tile[4 * tx + 2][r] << 16) |
+                           ((uint32_t)tile[4 * tx + 3][r] << 24);
+        uint8_t *dst = out + (int64_t)c * out_stride + t;
+        if (words && t + 3 < N) {
+            *reinterpret_cast<uint32_t *>(dst) = v;
+        } else {
+            for (int k = 0; k < 4; k++)
+                if (t + k < N) dst[k] = (uint8_t)(v >> (8 * k));
+        }
+    }
+}
+
+}  // namespace
+
+extern "C" gsp_status gsp_ingest_transpose(const uint8_t *d_in, int64_t n_samp, int32_t nchan,
+                                           int64_t in_stride, uint8_t *d_out, int64_t out_stride,
+                                           void *stream) {
+    if (!d_in || !d_out || n_samp < 0 || nchan <= 0 || in_stride < nchan || out_stride < n_samp)
+        return GSP_ERR_INVALID_ARG;
+    if (n_samp == 0) return GSP_OK;
+    const int64_t tiles_t = (n_samp + kTile - 1) / kTile;
+    const int tiles_c = (nchan + kTile - 1) / kTile;
+    if (tiles_c > 65535 || tiles_t > 0x7fffffffll) return GSP_ERR_INVALID_ARG;
+    const bool words = ((((uintptr_t)d_in | (uintptr_t)d_out) & 3) == 0) && (in_stride % 4 == 0) &&
+                       (out_stride % 4 == 0);
+    dim3 grid((unsigned)tiles_t, (unsigned)tiles_c);
+    ingest_transpose_kernel<<<grid, 256, 0, (cudaStream_t)stream>>>(d_in, in_stride, n_samp, nchan,
+                                                                    d_out, out_stride, words);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        gsp::record_error(e, "ingest transpose launch");
+        return GSP_ERR_CUDA;
+    }
+    return GSP_OK;
+}

@@ -120,6 +120,7 @@ def lib():
             "gsp_batch_candidates": ([_vp, _vp, _i64, _vp], ctypes.c_int),
             "gsp_batch_info": ([_vp, _vp, _vp, _vp], ctypes.c_int),
             "gsp_batch_timing": ([_vp, _vp, _vp], ctypes.c_int),
+            "gsp_ingest_transpose": ([_vp, _i64, ctypes.c_int32, _i64, _vp, _i64, _vp], ctypes.c_int),
             "gsp_downsample": ([_vp, ctypes.c_int32, _i64, _i64, ctypes.c_int32, _vp, _i64, _vp],
                                ctypes.c_int),
             "gsp_ddplan_create": ([_vp, _vp, _vp, ctypes.c_int32], ctypes.c_int),
@@ -543,6 +544,14 @@ def gsp_batch_timing(b):
 class gsp_ddplan_range(ctypes.Structure):
     _fields_ = [("dm_lo", ctypes.c_double), ("dm_step", ctypes.c_double),
                 ("ndm", ctypes.c_int32), ("downsamp", ctypes.c_int32)]
+
+
+def gsp_ingest_transpose(x_tc, n_samp, nchan, out, stream=None):
+    """x_tc: torch uint8 CUDA [n_samp][>= nchan] (time-major); out: torch uint8 CUDA
+    [nchan][>= n_samp] (channel-major)."""
+    _check(lib().gsp_ingest_transpose(_vp(x_tc.data_ptr()), n_samp, nchan, x_tc.stride(0),
+                                      _vp(out.data_ptr()), out.stride(0), _stream(stream)),
+           "gsp_ingest_transpose")
 
 
 def gsp_downsample(x, nchan, n_in, ds, out, stream=None):

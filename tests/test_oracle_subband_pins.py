@@ -206,3 +206,11 @@ def test_subband_row_selection(orc):
     full = orc.subband_dedisperse(x, n_in, d1, d2, 4)
     rows = [29, 3, 3, 17, 0]
     assert (orc.subband_dedisperse(x, n_in, d1, d2, 4, rows=rows) == full[rows]).all()
+
+
+def test_ingest_transpose_definition(orc):
+    x = np.random.default_rng(2).integers(0, 256, (13, 5), dtype=np.uint8)
+    out = orc.ingest_transpose(x)
+    for t in range(13):
+        for c in range(5):
+            assert out[c, t] == x[t, c]
