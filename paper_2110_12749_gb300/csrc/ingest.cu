@@ -2,8 +2,8 @@
 // files and of Alg. 2's numpts x numchan input matrix, Sec. 2.3) into the
 // channel-major [C][N] layout the dedispersion kernels read.  HBM-bound: one
 // read and one write per byte.  A CTA moves a 64 x 64 byte tile through shared
-// memory; each thread loads and stores 4-byte words (16 threads per 64-byte
-// row), with a padded tile so that the column reads are conflict-free.
+// memory, with 16-byte global accesses when pointers and strides allow
+// (ingest_transpose16_kernel), else 4-byte or byte accesses.
 #include "gsp_internal.cuh"
 
 namespace {
@@ -56,6 +56,64 @@ __global__ void __launch_bounds__(256) ingest_transpose_kernel(const uint8_t *__
     }
 }
 
+// The same with 16-byte global accesses (pointers and strides 16-byte
+// aligned): thread (r, q) loads bytes [16q, 16q + 16) of time row r into
+// 4-byte words of a padded tile (17 words per row), and thread (c, q) gathers
+// the byte c of rows 16q .. 16q + 15 into one 16-byte store of channel row c.
+// Edge tiles fall back to byte accesses.
+__global__ void __launch_bounds__(256) ingest_transpose16_kernel(const uint8_t *__restrict__ in,
+                                                                 int64_t in_stride, int64_t N,
+                                                                 int C, uint8_t *__restrict__ out,
+                                                                 int64_t out_stride) {
+    __shared__ uint32_t tile[kTile][17];
+    const int64_t t0 = (int64_t)blockIdx.x * kTile;
+    const int c0 = blockIdx.y * kTile;
+    const int r = threadIdx.x >> 2, q = threadIdx.x & 3;
+    {
+        const int64_t t = t0 + r;
+        const int c = c0 + 16 * q;
+        uint4 v = make_uint4(0u, 0u, 0u, 0u);
+        if (t < N) {
+            const uint8_t *src = in + t * in_stride + c;
+            if (c + 15 < C) {
+                v = __ldg(reinterpret_cast<const uint4 *>(src));
+            } else {
+                uint32_t w[4] = {0u, 0u, 0u, 0u};
+                for (int k = 0; k < 16; k++)
+                    if (c + k < C) w[k >> 2] |= (uint32_t)__ldg(src + k) << (8 * (k & 3));
+                v = make_uint4(w[0], w[1], w[2], w[3]);
+            }
+        }
+        tile[r][4 * q + 0] = v.x;
+        tile[r][4 * q + 1] = v.y;
+        tile[r][4 * q + 2] = v.z;
+        tile[r][4 * q + 3] = v.w;
+    }
+    __syncthreads();
+    {
+        const int cl = threadIdx.x >> 2;   // channel inside the tile
+        const int c = c0 + cl;
+        if (c >= C) return;
+        const int64_t t = t0 + 16 * q;
+        const uint32_t sel = (uint32_t)(cl & 3);
+        uint32_t w[4];
+#pragma unroll
+        for (int g = 0; g < 4; g++) {
+            uint32_t b[4];
+#pragma unroll
+            for (int k = 0; k < 4; k++) b[k] = (tile[16 * q + 4 * g + k][cl >> 2] >> (8 * sel)) & 0xffu;
+            w[g] = b[0] | (b[1] << 8) | (b[2] << 16) | (b[3] << 24);
+        }
+        uint8_t *dst = out + (int64_t)c * out_stride + t;
+        if (t + 15 < N) {
+            *reinterpret_cast<uint4 *>(dst) = make_uint4(w[0], w[1], w[2], w[3]);
+        } else {
+            for (int k = 0; k < 16; k++)
+                if (t + k < N) dst[k] = (uint8_t)(w[k >> 2] >> (8 * (k & 3)));
+        }
+    }
+}
+
 }  // namespace
 
 extern "C" gsp_status gsp_ingest_transpose(const uint8_t *d_in, int64_t n_samp, int32_t nchan,
@@ -70,8 +128,15 @@ extern "C" gsp_status gsp_ingest_transpose(const uint8_t *d_in, int64_t n_samp, 
     const bool words = ((((uintptr_t)d_in | (uintptr_t)d_out) & 3) == 0) && (in_stride % 4 == 0) &&
                        (out_stride % 4 == 0);
     dim3 grid((unsigned)tiles_t, (unsigned)tiles_c);
-    ingest_transpose_kernel<<<grid, 256, 0, (cudaStream_t)stream>>>(d_in, in_stride, n_samp, nchan,
-                                                                    d_out, out_stride, words);
+    const bool v16 = ((((uintptr_t)d_in | (uintptr_t)d_out) & 15) == 0) && (in_stride % 16 == 0) &&
+                     (out_stride % 16 == 0);
+    if (v16)
+        ingest_transpose16_kernel<<<grid, 256, 0, (cudaStream_t)stream>>>(d_in, in_stride, n_samp,
+                                                                          nchan, d_out, out_stride);
+    else
+        ingest_transpose_kernel<<<grid, 256, 0, (cudaStream_t)stream>>>(d_in, in_stride, n_samp,
+                                                                        nchan, d_out, out_stride,
+                                                                        words);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
         gsp::record_error(e, "ingest transpose launch");

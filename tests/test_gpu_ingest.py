@@ -19,7 +19,7 @@ def gsp():
     return g
 
 
-@pytest.mark.parametrize("n,c,in_pad,out_pad", [(1013, 77, 3, 5), (4096, 256, 0, 0),
+@pytest.mark.parametrize("n,c,in_pad,out_pad", [(1013, 77, 3, 5), (4096, 256, 0, 0), (1000, 200, 8, 24),
                                                 (70, 1, 0, 2), (130, 4096, 4, 16)])
 def test_transpose_bit_exact(gsp, orc, n, c, in_pad, out_pad):
     rng = np.random.default_rng(n + c)
