@@ -57,19 +57,25 @@ __global__ void __launch_bounds__(256) ingest_transpose_kernel(const uint8_t *__
 }
 
 // The same with 16-byte global accesses (pointers and strides 16-byte
-// aligned): thread (r, q) loads bytes [16q, 16q + 16) of time row r into
-// 4-byte words of a padded tile (17 words per row), and thread (c, q) gathers
-// the byte c of rows 16q .. 16q + 15 into one 16-byte store of channel row c.
-// Edge tiles fall back to byte accesses.
+// aligned) on 256 (time) x 64 (channel) tiles: thread (r, q) loads bytes
+// [16q, 16q + 16) of time rows r, r + 64, r + 128, r + 192 into 4-byte words of a
+// padded tile (17 words per row); thread (c, q) then gathers byte c of the
+// 16-sample groups q, q + 4, q + 8, q + 12 into 16-byte stores of channel row c.
+// Four loads and four stores per thread keep more bytes in flight.  Edge
+// tiles fall back to byte accesses.
+constexpr int kTileT16 = 256;
+
 __global__ void __launch_bounds__(256) ingest_transpose16_kernel(const uint8_t *__restrict__ in,
                                                                  int64_t in_stride, int64_t N,
                                                                  int C, uint8_t *__restrict__ out,
                                                                  int64_t out_stride) {
-    __shared__ uint32_t tile[kTile][17];
-    const int64_t t0 = (int64_t)blockIdx.x * kTile;
+    __shared__ uint32_t tile[kTileT16][17];
+    const int64_t t0 = (int64_t)blockIdx.x * kTileT16;
     const int c0 = blockIdx.y * kTile;
-    const int r = threadIdx.x >> 2, q = threadIdx.x & 3;
-    {
+    const int q = threadIdx.x & 3;
+#pragma unroll
+    for (int i = 0; i < kTileT16 / 64; i++) {
+        const int r = (threadIdx.x >> 2) + 64 * i;
         const int64_t t = t0 + r;
         const int c = c0 + 16 * q;
         uint4 v = make_uint4(0u, 0u, 0u, 0u);
@@ -90,18 +96,20 @@ __global__ void __launch_bounds__(256) ingest_transpose16_kernel(const uint8_t *
         tile[r][4 * q + 3] = v.w;
     }
     __syncthreads();
-    {
-        const int cl = threadIdx.x >> 2;   // channel inside the tile
-        const int c = c0 + cl;
-        if (c >= C) return;
-        const int64_t t = t0 + 16 * q;
-        const uint32_t sel = (uint32_t)(cl & 3);
+    const int cl = threadIdx.x >> 2;   // channel inside the tile
+    const int c = c0 + cl;
+    if (c >= C) return;
+    const uint32_t sh = 8u * (uint32_t)(cl & 3);
+#pragma unroll
+    for (int j = 0; j < kTileT16 / 64; j++) {
+        const int grp = q + 4 * j;       // 16-sample group inside the tile
+        const int64_t t = t0 + 16 * grp;
         uint32_t w[4];
 #pragma unroll
         for (int g = 0; g < 4; g++) {
             uint32_t b[4];
 #pragma unroll
-            for (int k = 0; k < 4; k++) b[k] = (tile[16 * q + 4 * g + k][cl >> 2] >> (8 * sel)) & 0xffu;
+            for (int k = 0; k < 4; k++) b[k] = (tile[16 * grp + 4 * g + k][cl >> 2] >> sh) & 0xffu;
             w[g] = b[0] | (b[1] << 8) | (b[2] << 16) | (b[3] << 24);
         }
         uint8_t *dst = out + (int64_t)c * out_stride + t;
@@ -130,9 +138,11 @@ extern "C" gsp_status gsp_ingest_transpose(const uint8_t *d_in, int64_t n_samp, 
     dim3 grid((unsigned)tiles_t, (unsigned)tiles_c);
     const bool v16 = ((((uintptr_t)d_in | (uintptr_t)d_out) & 15) == 0) && (in_stride % 16 == 0) &&
                      (out_stride % 16 == 0);
-    if (v16)
-        ingest_transpose16_kernel<<<grid, 256, 0, (cudaStream_t)stream>>>(d_in, in_stride, n_samp,
-                                                                          nchan, d_out, out_stride);
+    if (v16) {
+        dim3 grid16((unsigned)((n_samp + kTileT16 - 1) / kTileT16), (unsigned)tiles_c);
+        ingest_transpose16_kernel<<<grid16, 256, 0, (cudaStream_t)stream>>>(
+            d_in, in_stride, n_samp, nchan, d_out, out_stride);
+    }
     else
         ingest_transpose_kernel<<<grid, 256, 0, (cudaStream_t)stream>>>(d_in, in_stride, n_samp,
                                                                         nchan, d_out, out_stride,
