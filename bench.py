@@ -528,7 +528,8 @@ def run_ranker(args):
     src.wl = ranker.short_crafts(1 << 18, n_pulses=40)    # evaluation beams: the bench recipe
     ev = ranker.evaluate(r, src, 4, synth.BASE_SEED + 900, threshold=thr)
     ev["at_0.5"] = {k: v for k, v in ranker.evaluate(r, src, 4, synth.BASE_SEED + 900).items()
-                    if k in ("recall", "precision", "negatives_rejected")}
+                    if k in ("recall", "recall_detected_snr_ge_min", "precision",
+                             "negatives_rejected")}
     gsp.gsp_ranker_destroy(r)
     gsp.gsp_plan_destroy(src.plan)
     del src
@@ -542,8 +543,9 @@ def run_ranker(args):
                "training": "every candidate of the training beams (pulse tracks excluded); "
                            "1/3 of the steps with uniform negatives, then the 20000 "
                            "highest-scored negatives over-sampled",
-               "eval": "4 fresh beams; recall over injected pulses with S/N >= 8 that the "
-                       "search detects; precision over candidates scored >= 0.5"})
+               "eval": "4 fresh beams; recall over injected pulses of nominal S/N >= 8 that the "
+                       "search detects, and over those it detects at S/N >= 8; precision over "
+                       "candidates scored >= the threshold"})
     return ev
 
 
