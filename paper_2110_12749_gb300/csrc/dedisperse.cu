@@ -320,7 +320,8 @@ __device__ __forceinline__ void merged_decode(uint32_t (&acc)[M][4]) {
 // IMA: per-channel address adds as x * 1 + y on the multiply-add pipe (A32).
 template <int KW, bool QUAD, int ACC, bool A32 = false, int M = 4, int CB = 32, bool FF = false,
           bool PRE = false, bool MF = false, int KDM = 16, int UNR = 2, bool IMA = false>
-__global__ void __launch_bounds__((KDM / KW + 1) * 32, 1) dd_tiled_kernel(const TiledArgs a) {
+__global__ void __launch_bounds__((KDM / KW + 1) * 32, (KDM / KW + 1) * 32 <= 256 ? 2 : 1)
+    dd_tiled_kernel(const TiledArgs a) {
     static_assert(!PRE || (KW == 1 && CB == 64), "precomputed lists: one DM per warp, 64-channel stages");
     static_assert(!MF || (ACC >= 3 && !FF), "merged flush: raw + odd views, all families together");
     constexpr int kCB = CB;
@@ -846,8 +847,17 @@ const TiledVariant kVariants[] = {
     {dd_tiled_kernel<1, false, 3, true, 6, 64, false, true, true, 15, 4, true>, 1, 6, 64, true, 15},
     {dd_tiled_kernel<1, false, 3, true, 5, 64, false, true, true, 15, 2, true>, 1, 5, 64, true, 15},
     {dd_tiled_kernel<1, false, 4, true, 6, 64, false, true, true, 15, 2, true>, 1, 6, 64, true, 15},
+    {dd_tiled_kernel<1, false, 3, true, 6, 32, false, false, true, 7, 2, true>, 1, 6, 32, false, 7},
+    {dd_tiled_kernel<1, false, 3, true, 4, 32, false, false, true, 7, 2, true>, 1, 4, 32, false, 7},
 };
 constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
+
+// Shared memory a CTA of variant v may use: all of an SM's 227 KB, or half of
+// it (less the per-CTA reserve) for CTAs of at most 8 warps, two per SM.
+int ctas_per_sm(const TiledVariant &v) { return (v.kdm / v.kw + 1) * 32 <= 256 ? 2 : 1; }
+int64_t smem_budget(const TiledVariant &v) {
+    return ctas_per_sm(v) == 2 ? 112 * 1024 : 227 * 1024;
+}
 constexpr int kDefaultVariant = 32;
 constexpr int kFallbackVariant = 34;  // default when the precomputed lists are unavailable
 
@@ -943,7 +953,7 @@ bool plan_dedisperse_tiled(gsp_plan_s *p, std::vector<int32_t> (&blkmin)[kNumKdm
     const int kT = 128 * v.m;
     const int64_t win = (kT + 15 + g.spread[o] + 15) & ~(int64_t)15;
     const int64_t fixed = (int64_t)v.kdm * 4 * v.cb * 4 + 2 * 8 * 8;
-    const int64_t stages = std::min<int64_t>(8, (227 * 1024 - fixed) / ((int64_t)v.cb * win));
+    const int64_t stages = std::min<int64_t>(8, (smem_budget(v) - fixed) / ((int64_t)v.cb * win));
     if (stages < 2) {
         for (auto &b : blkmin) b.clear();
         return false;
@@ -985,7 +995,7 @@ cudaError_t launch_dedisperse_batch(const BeamLaunch *beams, int nbeams, int var
         win = std::max<int64_t>(win, (t_cta + 15 + p->geom.spread[o] + 15) & ~(int64_t)15);
     }
     const int64_t fixed = (int64_t)v.kdm * 4 * v.cb * 4 + 2 * 8 * 8;
-    const int64_t stages = std::min<int64_t>(8, (227 * 1024 - fixed) / ((int64_t)v.cb * win));
+    const int64_t stages = std::min<int64_t>(8, (smem_budget(v) - fixed) / ((int64_t)v.cb * win));
     if (stages < 2) return cudaErrorInvalidValue;
     const int smem = (int)(stages * v.cb * win + fixed);
     static int configured_smem[kNumVariants] = {0};
@@ -1031,7 +1041,7 @@ cudaError_t launch_dedisperse_batch(const BeamLaunch *beams, int nbeams, int var
     a.one = 1u;
     a.err = err;
     a.items = items;
-    int64_t grid = persistent ? std::min<int64_t>(items, num_sms) : items;
+    int64_t grid = persistent ? std::min<int64_t>(items, (int64_t)num_sms * ctas_per_sm(v)) : items;
     if (grid < 1 || grid > 0x7fffffffll) return cudaErrorInvalidConfiguration;
     v.fn<<<(unsigned)grid, (v.kdm / v.kw + 1) * 32, smem, s>>>(a);
     *nlaunch += 1;

@@ -13,12 +13,13 @@ namespace gsp {
 constexpr int kMaxWidths = 32;
 
 // DM trials per CTA of the tiled dedispersion kernel (one per consumer warp):
-// 16, or 15 so that the CTA (15 consumer warps + 1 producer) is 16 warps and
-// each thread may hold up to 128 registers.  Plans keep the DM-block tables
-// of both sizes so that any tile variant can run on any plan.
-constexpr int kNumKdm = 2;
-constexpr int kKdmSizes[kNumKdm] = {16, 15};
-inline int kdm_index(int kdm) { return kdm == 15 ? 1 : 0; }
+// 16; 15 so that the CTA (15 consumer warps + 1 producer) is 16 warps and each
+// thread may hold up to 128 registers; or 7 for two 8-warp CTAs per SM at the
+// same register budget.  Plans keep the DM-block tables of every size so that
+// any tile variant can run on any plan.
+constexpr int kNumKdm = 3;
+constexpr int kKdmSizes[kNumKdm] = {16, 15, 7};
+inline int kdm_index(int kdm) { return kdm == 15 ? 1 : (kdm == 7 ? 2 : 0); }
 
 // Per-block parameters consumed by the boxcar kernel, derived in FP64 from
 // exact integer block sums and rounded once to FP32:
@@ -43,9 +44,9 @@ struct DDGeom {
     int stages = 0;    // pipeline depth
     int smem = 0;      // dynamic shared memory bytes
     // per DM-block size kKdmSizes[o]:
-    int nblk[kNumKdm] = {0, 0};        // DM blocks
-    int grp[kNumKdm] = {1, 1};         // DM blocks per launch group
-    int64_t spread[kNumKdm] = {0, 0};  // largest delay spread inside a DM block
+    int nblk[kNumKdm] = {};            // DM blocks
+    int grp[kNumKdm] = {1, 1, 1};      // DM blocks per launch group
+    int64_t spread[kNumKdm] = {};      // largest delay spread inside a DM block
     int variant = 0;   // template variant index
 };
 
@@ -63,7 +64,7 @@ struct gsp_plan_s {
 
     // device memory owned by the plan
     int32_t *d_delays = nullptr;     // [ndm][nchan]
-    int32_t *d_blkmin[gsp::kNumKdm] = {nullptr, nullptr};  // [nblk][nchan] min delay per DM block
+    int32_t *d_blkmin[gsp::kNumKdm] = {};  // [nblk][nchan] min delay per DM block
     int32_t *d_dpos = nullptr;       // [ndm][nchan] (delay << 8) | phase-list position
     uint32_t *d_fcnt = nullptr;      // [ndm][ceil(nchan / 64)] phase family sizes
     int *d_err = nullptr;            // set by a kernel whose bounded wait gave up
