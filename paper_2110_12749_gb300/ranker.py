@@ -16,8 +16,9 @@ pulses of its beam (pulse DM trial k = nearest trial, per-channel delays):
 A pulse is recalled if its best-scored core candidate scores at least the
 operating threshold (softmax probability of class 1); precision counts the
 candidates scoring at least the threshold among those labelled 0 or 1.  The
-threshold is chosen on the training beams (the score that keeps 99% of
-their pulses with S/N >= 8), never on the evaluation beams.
+threshold is chosen on held-out validation beams (the score that keeps 99.5%
+of their pulses the search detects at S/N >= 8), never on the training or
+the evaluation beams.
 """
 from __future__ import annotations
 
@@ -125,16 +126,55 @@ def build_training_set(src, beams, seed):
     return torch.cat(xs), np.concatenate(ys), np.concatenate(ps), np.array(snr)
 
 
-def choose_threshold(ranker, x, y, pulse_ids, pulse_snr, snr_min=8.0, keep=0.99):
-    """Score that keeps `keep` of the training pulses with S/N >= snr_min (each
-    by its best positive snippet), at most 0.5."""
-    pos = np.nonzero(y == 1)[0]
-    s = score(ranker, x[__import__("torch").from_numpy(pos).cuda()])
-    best = {}
-    for i, sc in zip(pulse_ids[pos], s):
-        if pulse_snr[int(i)] >= snr_min:
-            best[int(i)] = max(best.get(int(i), 0.0), float(sc))
-    v = np.sort(np.array(list(best.values())))
+def pulse_scores(ranker, src, beams, seed, chunk=4096):
+    """Score every candidate of the given beams.  Returns a dict with, per
+    injected pulse that ends inside the searched blocks, its nominal S/N and
+    width, its best detected S/N and its best score (both -1 if the search finds none of
+    its core candidates); the scores of the candidates labelled 0 and 1; the
+    candidates scored and the seconds spent on snippets + forward passes."""
+    torch = src.torch
+    nominal, width, det, best, neg, pos = [], [], [], [], [], []
+    n_scored, rank_s = 0, 0.0
+    for b in range(beams):
+        cands, lab, pid, pulses = src.search(b, seed)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        scores = np.empty(cands.size, np.float32)
+        for i in range(0, cands.size, chunk):
+            sub = cands[i:i + chunk]
+            torch.cuda.synchronize()
+            e0.record()
+            x = src.snippets(sub)
+            logits = torch.empty((sub.size, 2), dtype=torch.float32, device="cuda")
+            gsp.gsp_ranker_forward(ranker, x, sub.size, logits)
+            e1.record()
+            gsp.gsp_ranker_finish(ranker)
+            rank_s += e0.elapsed_time(e1) / 1e3
+            scores[i:i + sub.size] = torch.softmax(logits, dim=1)[:, 1].cpu().numpy()
+            del x
+        n_scored += cands.size
+        Ls = (src.n_out // 1024) * 1024
+        for i, p in enumerate(pulses):
+            if p.t0 + p.width > Ls:
+                continue
+            mine = pid == i
+            nominal.append(p.snr)
+            width.append(p.width)
+            det.append(float(cands["snr"][mine].max()) if mine.any() else -1.0)
+            best.append(float(scores[mine].max()) if mine.any() else -1.0)
+        neg.append(scores[lab == 0])
+        pos.append(scores[lab == 1])
+    return {"nominal": np.array(nominal), "width": np.array(width), "detected": np.array(det),
+            "best": np.array(best),
+            "neg": np.concatenate(neg), "pos": np.concatenate(pos), "n_scored": n_scored,
+            "rank_s": rank_s}
+
+
+def choose_threshold(ranker, src, beams, seed, snr_min=8.0, keep=0.995):
+    """Operating threshold from validation beams: the score that keeps `keep`
+    of their pulses the search detects at S/N >= snr_min (each by its best
+    core candidate), at most 0.5."""
+    ps = pulse_scores(ranker, src, beams, seed)
+    v = np.sort(ps["best"][ps["detected"] >= snr_min])
     if v.size == 0:
         return 0.5
     return float(min(0.5, v[int(np.floor((1.0 - keep) * v.size))]))
@@ -193,70 +233,45 @@ def score(ranker, x, chunk=None):
     return torch.softmax(logits, dim=1)[:, 1].cpu().numpy()
 
 
-def evaluate(ranker, src, beams, seed, snr_min=8.0, chunk=4096, threshold=0.5):
-    """Score every candidate of fresh beams; recall on injected pulses with
-    S/N >= snr_min (of those the search detects), precision, and the ranking
-    throughput (snippets + forward)."""
-    torch = src.torch
-    recalled, detected, strong = 0, 0, 0
-    det8, rec8 = 0, 0      # pulses whose best detected S/N (not the nominal one) is >= snr_min
-    tp = fp = neg_total = neg_rejected = 0
-    n_scored, rank_s = 0, 0.0
-    per_pulse = []   # (nominal S/N, width, recalled) of detected pulses with S/N >= snr_min
-    for b in range(beams):
-        cands, lab, pid, pulses = src.search(b, seed)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        scores = np.empty(cands.size, np.float32)
-        for i in range(0, cands.size, chunk):
-            sub = cands[i:i + chunk]
-            torch.cuda.synchronize()
-            e0.record()
-            x = src.snippets(sub)
-            logits = torch.empty((sub.size, 2), dtype=torch.float32, device="cuda")
-            gsp.gsp_ranker_forward(ranker, x, sub.size, logits)
-            e1.record()
-            gsp.gsp_ranker_finish(ranker)
-            rank_s += e0.elapsed_time(e1) / 1e3
-            scores[i:i + sub.size] = torch.softmax(logits, dim=1)[:, 1].cpu().numpy()
-            del x
-        n_scored += cands.size
-        Ls = (src.n_out // 1024) * 1024
-        for i, p in enumerate(pulses):
-            if p.snr < snr_min or p.t0 + p.width > Ls:
-                continue
-            strong += 1
-            mine = pid == i
-            if mine.any():
-                detected += 1
-                ok = bool(scores[mine].max() >= threshold)
-                recalled += int(ok)
-                per_pulse.append((p.snr, p.width, ok))
-        # the same over the pulses the search detects at S/N >= snr_min: DM-trial
-        # smearing can leave a pulse of nominal S/N >= snr_min near the threshold
-        for i, p in enumerate(pulses):
-            mine = pid == i
-            if p.t0 + p.width > Ls or not mine.any() or cands["snr"][mine].max() < snr_min:
-                continue
-            det8 += 1
-            rec8 += int(scores[mine].max() >= threshold)
-        hi = scores >= threshold
-        tp += int((hi & (lab == 1)).sum())
-        fp += int((hi & (lab == 0)).sum())
-        neg_total += int((lab == 0).sum())
-        neg_rejected += int((~hi & (lab == 0)).sum())
-    pp = np.array(per_pulse, dtype=np.float64).reshape(-1, 3)
+def evaluate(ranker, src, beams, seed, snr_min=8.0, thresholds=(0.5,)):
+    """Score every candidate of fresh beams.  At each threshold: recall on
+    the injected pulses the search detects at S/N >= snr_min, recall on those
+    of nominal S/N >= snr_min that it detects at all, precision and the share
+    of negatives rejected; for the first threshold also [recalled, pulses]
+    by width and by detected S/N, and the missed pulses detected at S/N >=
+    snr_min ([nominal S/N, width, detected S/N, score], at most 10).  Plus
+    the ranking throughput (snippets + forward)."""
+    ps = pulse_scores(ranker, src, beams, seed)
+    nom, wid, det, best = ps["nominal"], ps["width"], ps["detected"], ps["best"]
+    d8 = det >= snr_min                       # detected at S/N >= snr_min
+    n8 = (nom >= snr_min) & (det >= 0)        # nominal S/N >= snr_min, detected
+    at = {}
+    for t in thresholds:
+        tp, fp = int((ps["pos"] >= t).sum()), int((ps["neg"] >= t).sum())
+        at[t] = {"recall": float((best[d8] >= t).mean()) if d8.any() else 0.0,
+                 "recall_nominal": float((best[n8] >= t).mean()) if n8.any() else 0.0,
+                 "precision": tp / max(tp + fp, 1),
+                 "negatives_rejected": 1.0 - fp / max(ps["neg"].size, 1)}
+    t0 = thresholds[0]
+    ok = best >= t0
 
     def rec(sel):
-        return [int(pp[sel, 2].sum()), int(sel.sum())]
+        sel = sel & d8
+        return [int((ok & sel).sum()), int(sel.sum())]
 
-    by_width = {"1-9": rec(pp[:, 1] < 10), "10-49": rec((pp[:, 1] >= 10) & (pp[:, 1] < 50)),
-                "50-100": rec(pp[:, 1] >= 50)}
-    by_snr = {"8-12": rec(pp[:, 0] < 12), "12-20": rec((pp[:, 0] >= 12) & (pp[:, 0] < 20)),
-              "20-30": rec(pp[:, 0] >= 20)}
-    return {"threshold": threshold, "recalled_by_width": by_width, "recalled_by_snr": by_snr,
-            "pulses_detected_at_snr_ge_min": det8, "recall_detected_snr_ge_min": rec8 / max(det8, 1),
-            "pulses_snr_ge_min": strong, "detected_by_search": detected,
-            "recall": recalled / max(detected, 1), "precision": tp / max(tp + fp, 1),
-            "negatives": neg_total, "negatives_rejected": neg_rejected / max(neg_total, 1),
-            "candidates_scored": n_scored, "rank_s": rank_s,
-            "candidates_per_s": n_scored / max(rank_s, 1e-9)}
+    out = dict(at[t0])
+    out.update({
+        "threshold": t0,
+        "pulses_detected_snr_ge_min": int(d8.sum()),
+        "pulses_nominal_snr_ge_min": int((nom >= snr_min).sum()),
+        "nominal_snr_ge_min_detected": int(n8.sum()),
+        "recalled_by_width": {"1-9": rec(wid < 10), "10-49": rec((wid >= 10) & (wid < 50)),
+                              "50-150": rec(wid >= 50)},
+        "recalled_by_snr": {"8-12": rec(det < 12), "12-20": rec((det >= 12) & (det < 20)),
+                            ">=20": rec(det >= 20)},
+        "negatives": int(ps["neg"].size), "candidates_scored": ps["n_scored"],
+        "rank_s": ps["rank_s"], "candidates_per_s": ps["n_scored"] / max(ps["rank_s"], 1e-9),
+        "missed": [[round(float(nom[i]), 2), int(wid[i]), round(float(det[i]), 2),
+                    round(float(best[i]), 4)] for i in np.nonzero(d8 & ~ok)[0][:10]],
+        "at": {"%.4g" % t: at[t] for t in thresholds[1:]}})
+    return out
