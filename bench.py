@@ -508,8 +508,8 @@ def run_ranker(args):
     """Candidate ranker: trained on snippets of the candidates the pipeline finds
     in synthetic CRAFTS-like beams (2^18 samples, --ranker-pulses injected
     pulses, 30 RFI channels, 5 DM-0 bursts each), its threshold set on held-out
-    beams of the same recipe, then scoring every candidate of fresh beams with
-    40 injected pulses each."""
+    beams with 40 injected pulses each, then scoring every candidate of fresh
+    beams of that recipe."""
     import torch
     from paper_2110_12749_gb300 import gsp, ranker, synth
     src = ranker.BeamSource(ranker.short_crafts(1 << 18, n_pulses=args.ranker_pulses))
@@ -528,10 +528,10 @@ def run_ranker(args):
     npos, nneg = int((y == 1).sum()), int((y == 0).sum())
     del x
     torch.cuda.empty_cache()
-    # operating threshold from held-out validation beams (training recipe, own seed)
+    # validation and evaluation beams: the bench recipe (40 pulses), own seeds
+    src.wl = ranker.short_crafts(1 << 18, n_pulses=40)
     thr = ranker.choose_threshold(r, src, args.ranker_val_beams, synth.BASE_SEED + 700)
-    src.wl = ranker.short_crafts(1 << 18, n_pulses=40)    # evaluation beams: the bench recipe
-    ev = ranker.evaluate(r, src, 4, synth.BASE_SEED + 900, thresholds=(thr, 0.5))
+    ev = ranker.evaluate(r, src, 4, synth.BASE_SEED + 900, thresholds=(thr, 0.05, 0.5))
     gsp.gsp_ranker_destroy(r)
     gsp.gsp_plan_destroy(src.plan)
     del src
@@ -545,8 +545,8 @@ def run_ranker(args):
                "training": "every candidate of the training beams (pulse tracks excluded); "
                            "1/3 of the steps with uniform negatives, then the 20000 "
                            "highest-scored negatives over-sampled",
-               "validation": "%d beams of the training recipe (own seed) set the threshold: "
-                             "the score keeping 99.5%% of their pulses detected at S/N >= 8"
+               "validation": "%d beams of the bench recipe (own seed) set the threshold: "
+                             "the score keeping 99%% of their pulses detected at S/N >= 8"
                              % args.ranker_val_beams,
                "eval": "4 fresh beams of the bench recipe; recall over injected pulses the "
                        "search detects at S/N >= 8 (recall_nominal: over those of nominal "

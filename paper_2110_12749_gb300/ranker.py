@@ -16,7 +16,7 @@ pulses of its beam (pulse DM trial k = nearest trial, per-channel delays):
 A pulse is recalled if its best-scored core candidate scores at least the
 operating threshold (softmax probability of class 1); precision counts the
 candidates scoring at least the threshold among those labelled 0 or 1.  The
-threshold is chosen on held-out validation beams (the score that keeps 99.5%
+threshold is chosen on held-out validation beams (the score that keeps 99%
 of their pulses the search detects at S/N >= 8), never on the training or
 the evaluation beams.
 """
@@ -169,7 +169,7 @@ def pulse_scores(ranker, src, beams, seed, chunk=4096):
             "rank_s": rank_s}
 
 
-def choose_threshold(ranker, src, beams, seed, snr_min=8.0, keep=0.995):
+def choose_threshold(ranker, src, beams, seed, snr_min=8.0, keep=0.99):
     """Operating threshold from validation beams: the score that keeps `keep`
     of their pulses the search detects at S/N >= snr_min (each by its best
     core candidate), at most 0.5."""
