@@ -453,6 +453,9 @@ gsp_status gsp_gemm_bf16(const void *d_A, int64_t lda, const void *d_B, int64_t 
  * 16 -> 32 channels), fc 2048 -> 64 + ReLU, fc 64 -> 2 (class 1 = pulse).  All
  * products run with bf16 operands (rounded to nearest even) and FP32
  * accumulation, the convolutions and fc 2048 -> 64 (forward and backward) as
+ * tcgen05 GEMMs.  An inference pass (gsp_ranker_forward) fuses each conv
+ * layer with its bias, ReLU and pool at the same rounding points: the
+ * one-input-channel first layer on the CUDA cores, the other two as implicit
  * tcgen05 GEMMs.  Parameters are one FP32 vector of gsp_ranker_num_params()
  * values in the order w1 b1 w2 b2 w3 b3 w4 b4 w5 b5, conv weights as
  * [co][ci][ky][kx], fc weights as [out][in] with the fc 2048 input index

@@ -5,9 +5,13 @@
 //
 // Network: three conv 3x3 (pad 1) + bias + ReLU + 2x2 max-pool layers
 // (1 -> 8 -> 16 -> 32 channels, 64x64 -> 8x8), fc 2048 -> 64 + ReLU, fc 64 -> 2.
-// Activations are NHWC.  Every convolution is an im2col GEMM on the tcgen05
-// tensor cores (tc_gemm.cu), BF16 operands and FP32 accumulation in tensor
-// memory, bias and ReLU fused into the epilogue; fc 2048 -> 64 and the
+// Activations are NHWC.  Every convolution of a training pass is an im2col
+// GEMM on the tcgen05 tensor cores (tc_gemm.cu), BF16 operands and FP32
+// accumulation in tensor memory, bias and ReLU fused into the epilogue.  An
+// inference pass fuses each conv layer with its bias, ReLU and pool at the
+// same rounding points: layer 0 (one input channel, K = 9) on the CUDA cores,
+// layers 1 and 2 as implicit GEMMs on the tensor cores that gather their taps
+// straight from the activations.  fc 2048 -> 64 and the
 // back-propagated products of both fc layers and the convolutions are GEMMs
 // too (weight gradients with split-K over the batch pixels).  The 64 -> 2
 // layer, the loss, pooling, im2col / col2im, bias gradients and Adam are
@@ -101,6 +105,66 @@ __global__ void __launch_bounds__(256) im2col_kernel(const T *__restrict__ a, in
         uint4 *dst = reinterpret_cast<uint4 *>(col + p * KP);
 #pragma unroll
         for (int q = 0; q < KP / 8; q++) dst[q] = *reinterpret_cast<const uint4 *>(&row[q * 8]);
+    }
+}
+
+// Layer 0 of an inference pass: conv 3x3 (1 -> 8, pad 1) + bias + ReLU + 2x2
+// max-pool straight from the FP32 snippets, on the CUDA cores: with one input
+// channel the product has K = 9, too short for the tensor pipe to pay for its
+// staging.  The rounding points are those of the im2col + GEMM + pool path:
+// inputs and weights in bf16, the nine products and the bias summed in FP32,
+// the pooled maximum rounded to bf16.  One thread per pooled pixel reads its
+// 4 x 4 input patch, computes its 2 x 2 conv outputs for all 8 channels and
+// writes the 8 bf16 results as one 16-byte store (NHWC, as pool_kernel<8>).
+__global__ void __launch_bounds__(256) conv0_pool_kernel(const float *__restrict__ x, int B,
+                                                         const bf16 *__restrict__ W0,
+                                                         const float *__restrict__ b0,
+                                                         bf16 *__restrict__ a0) {
+    constexpr int C = 8, KP = kpad(0), H = kS, H2 = kS / 2;
+    __shared__ float sw[C][9];
+    __shared__ float sb[C];
+    for (int i = threadIdx.x; i < C * 9; i += blockDim.x)
+        sw[i / 9][i % 9] = __bfloat162float(W0[(i / 9) * KP + i % 9]);
+    for (int i = threadIdx.x; i < C; i += blockDim.x) sb[i] = b0[i];
+    __syncthreads();
+    const int64_t total = (int64_t)B * H2 * H2;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t b = q / (H2 * H2);
+        const int rem = (int)(q - b * H2 * H2);
+        const int y2 = rem / H2, x2 = rem - (rem / H2) * H2;
+        const float *img = x + b * H * H;
+        float v[4][4];
+#pragma unroll
+        for (int r = 0; r < 4; r++) {
+            const int yy = 2 * y2 - 1 + r;
+#pragma unroll
+            for (int c = 0; c < 4; c++) {
+                const int xx = 2 * x2 - 1 + c;
+                const bool in = yy >= 0 && yy < H && xx >= 0 && xx < H;
+                v[r][c] = in ? __bfloat162float(__float2bfloat16_rn(__ldg(img + yy * H + xx)))
+                             : 0.0f;
+            }
+        }
+        __align__(16) bf16 out[C];
+#pragma unroll
+        for (int co = 0; co < C; co++) {
+            float m = 0.0f;  // ReLU outputs are >= 0
+#pragma unroll
+            for (int dy = 0; dy < 2; dy++)
+#pragma unroll
+                for (int dx = 0; dx < 2; dx++) {
+                    float z = 0.0f;
+#pragma unroll
+                    for (int ky = 0; ky < 3; ky++)
+#pragma unroll
+                        for (int kx = 0; kx < 3; kx++)
+                            z = fmaf(v[dy + ky][dx + kx], sw[co][ky * 3 + kx], z);
+                    m = fmaxf(m, z + sb[co]);
+                }
+            out[co] = __float2bfloat16_rn(m);
+        }
+        *reinterpret_cast<uint4 *>(a0 + q * C) = *reinterpret_cast<const uint4 *>(out);
     }
 }
 
@@ -358,6 +422,245 @@ __global__ void unpack_conv_grad_kernel(const float *__restrict__ dW, int Cin, i
 
 }  // namespace
 
+namespace {
+
+// ------------------------------------------- fused conv layers for inference
+
+namespace tc = gsp::tc;
+
+constexpr long long kConvBudget = 2000000000ll;  // ~1 s of SM clock per wait
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src, uint32_t src_bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src),
+                 "r"(src_bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// Layers 1 and 2 of an inference pass: conv 3x3 (CIN -> COUT, pad 1) as an
+// implicit GEMM on the tcgen05 tensor cores, + bias + ReLU + 2x2 max-pool in
+// the epilogue, from the bf16 NHWC activation act [B][SIDE][SIDE][CIN] to the
+// pooled bf16 NHWC output out [B][SIDE/2][SIDE/2][COUT].  The products and
+// their rounding points are those of the im2col + GEMM + pool path (the same
+// K order and K = 16 steps, FP32 accumulation in tensor memory, bias after
+// the accumulation, the pooled maximum rounded to bf16).
+//
+// Persistent CTAs of 4 warps stride over 128-pixel M tiles (a tile is 128 /
+// SIDE whole image rows, so every 2x2 pooling window lies inside it).  Each
+// thread gathers the 9 taps of its pixel straight from act with 16-byte
+// cp.async copies (zero-filled outside the image) into the K-major
+// core-matrix layout; two A buffers and two tensor-memory accumulators let
+// the gather of tile k+1 and the MMAs of tile k run under the epilogue of
+// tile k-1.  The weights are staged once per CTA.  Every wait is bounded; on
+// a timeout the kernel sets *err, waits (bounded) for its MMAs in flight and
+// releases its tensor memory.
+template <int CIN, int COUT, int SIDE>
+__global__ void __launch_bounds__(128) conv_pool_tc_kernel(const bf16 *__restrict__ act, int B,
+                                                           const bf16 *__restrict__ W,
+                                                           const float *__restrict__ bias,
+                                                           bf16 *__restrict__ out, int *err) {
+    static_assert(CIN % 8 == 0 && COUT % 16 == 0 && COUT <= 32, "shapes of layers 1 and 2");
+    static_assert((SIDE * SIDE) % 128 == 0 && 128 % (2 * SIDE) == 0, "tiles of whole row pairs");
+    constexpr int K = 9 * CIN;                  // im2col K (a multiple of 8)
+    constexpr int NK16 = (K + 15) / 16;         // MMAs per tile
+    constexpr int KC = K / 8;                   // 16-byte K chunks carrying data
+    constexpr int KCS = NK16 * 2;               // staged K chunks (zero past KC)
+    constexpr uint32_t SBO = KCS * 128;         // bytes between 8-row groups
+    constexpr int A_BYTES = 128 * KCS * 16;
+    constexpr int B_BYTES = COUT * KCS * 16;
+    constexpr int LDZ = COUT + 4;               // padded FP32 row of the epilogue tile
+    constexpr uint32_t kCols = 2 * COUT < 32 ? 32u : (uint32_t)(2 * COUT);
+    constexpr uint32_t kIdesc = tc::idesc_bf16(128, COUT);
+    constexpr int PW = SIDE / 2;
+    constexpr int KP = (K + 7) & ~7;            // row length of W
+    extern __shared__ __align__(1024) uint8_t smem[];
+    uint8_t *sA0 = smem, *sA1 = smem + A_BYTES, *sB = smem + 2 * A_BYTES;
+    float *sz = reinterpret_cast<float *>(smem + 2 * A_BYTES + B_BYTES);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sz + 128 * LDZ);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2);
+    __shared__ float sbias[COUT];
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int64_t ntiles = (int64_t)B * SIDE * SIDE / 128;
+    const int64_t my = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+
+    if (warp == 0) tc::tmem_alloc(tc::smem_u32(tmem_slot), kCols);
+    if (tid == 0) {
+        tc::mbar_init1(tc::smem_u32(bars));
+        tc::mbar_init1(tc::smem_u32(bars + 1));
+    }
+    for (int i = tid; i < COUT; i += 128) sbias[i] = bias[i];
+    // weights once: W[n][k] into the core-matrix layout, zero past K
+    for (int idx = tid; idx < COUT * KCS; idx += 128) {
+        const int n = idx % COUT, q = idx / COUT;
+        uint4 v = make_uint4(0u, 0u, 0u, 0u);
+        if (q < KC) v = __ldg(reinterpret_cast<const uint4 *>(W + (int64_t)n * KP) + q);
+        *reinterpret_cast<uint4 *>(sB + (n >> 3) * SBO + q * 128 + (n & 7) * 16) = v;
+    }
+    // the zero K chunks of both A buffers (never written by the gathers)
+    for (int idx = tid; idx < 128 * (KCS - KC); idx += 128) {
+        const int r = idx & 127, q = KC + (idx >> 7);
+        const uint32_t o = (r >> 3) * SBO + q * 128 + (r & 7) * 16;
+        *reinterpret_cast<uint4 *>(sA0 + o) = make_uint4(0u, 0u, 0u, 0u);
+        *reinterpret_cast<uint4 *>(sA1 + o) = make_uint4(0u, 0u, 0u, 0u);
+    }
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    const uint32_t tmem = *tmem_slot;
+    const uint32_t a_addr0 = tc::smem_u32(sA0), a_addr1 = tc::smem_u32(sA1);
+    const uint32_t b_addr = tc::smem_u32(sB);
+    const uint32_t bar0 = tc::smem_u32(bars), bar1 = tc::smem_u32(bars + 1);
+    auto a_addr = [&](int j) { return j ? a_addr1 : a_addr0; };
+    auto bar = [&](int j) { return j ? bar1 : bar0; };
+
+    // this thread's row of tile `tile`: pixel m0 + tid, all 9 taps
+    auto gather = [&](int64_t tile, uint32_t dst_base) {
+        const int64_t p = tile * 128 + tid;
+        const int64_t b = p / (SIDE * SIDE);
+        const int rem = (int)(p - b * SIDE * SIDE);
+        const int y = rem / SIDE, x = rem % SIDE;
+        const uint32_t dst = dst_base + (tid >> 3) * SBO + (tid & 7) * 16;
+#pragma unroll
+        for (int tap = 0; tap < 9; tap++) {
+            const int yy = y + tap / 3 - 1, xx = x + tap % 3 - 1;
+            const bool in = yy >= 0 && yy < SIDE && xx >= 0 && xx < SIDE;
+            const bf16 *src = in ? act + ((b * SIDE + yy) * SIDE + xx) * CIN : act;
+#pragma unroll
+            for (int j = 0; j < CIN / 8; j++)
+                cp_async16(dst + (tap * (CIN / 8) + j) * 128, in ? src + j * 8 : act, in ? 16u : 0u);
+        }
+    };
+    // bias + ReLU + 2x2 max-pool of the tile in accumulator `acc`
+    auto epilogue = [&](int64_t tile, int acc) {
+        const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(acc * COUT);
+        float *zr = sz + (warp * 32 + lane) * LDZ;
+#pragma unroll
+        for (int c0 = 0; c0 < COUT; c0 += 16) {
+            float v[16];
+            tc::tmem_ld16(taddr + (uint32_t)c0, v);
+#pragma unroll
+            for (int c = 0; c < 16; c += 4) {
+                float4 o;
+                o.x = fmaxf(v[c] + sbias[c0 + c], 0.0f);
+                o.y = fmaxf(v[c + 1] + sbias[c0 + c + 1], 0.0f);
+                o.z = fmaxf(v[c + 2] + sbias[c0 + c + 2], 0.0f);
+                o.w = fmaxf(v[c + 3] + sbias[c0 + c + 3], 0.0f);
+                *reinterpret_cast<float4 *>(zr + c0 + c) = o;
+            }
+        }
+        __syncthreads();
+        const int64_t m0 = tile * 128;
+        const int64_t b = m0 / (SIDE * SIDE);
+        const int y0 = (int)(m0 - b * SIDE * SIDE) / SIDE;
+        const int64_t pbase = b * PW * PW + (int64_t)(y0 / 2) * PW;
+        for (int it = tid; it < 32 * (COUT / 4); it += 128) {
+            const int pp = it / (COUT / 4), c4 = it % (COUT / 4);
+            const int py = pp / PW, px = pp % PW;
+            const int r00 = 2 * py * SIDE + 2 * px;
+            const float4 q0 = *reinterpret_cast<const float4 *>(sz + r00 * LDZ + c4 * 4);
+            const float4 q1 = *reinterpret_cast<const float4 *>(sz + (r00 + 1) * LDZ + c4 * 4);
+            const float4 q2 = *reinterpret_cast<const float4 *>(sz + (r00 + SIDE) * LDZ + c4 * 4);
+            const float4 q3 = *reinterpret_cast<const float4 *>(sz + (r00 + SIDE + 1) * LDZ + c4 * 4);
+            __align__(8) bf16 o[4];
+            o[0] = __float2bfloat16_rn(fmaxf(fmaxf(q0.x, q1.x), fmaxf(q2.x, q3.x)));
+            o[1] = __float2bfloat16_rn(fmaxf(fmaxf(q0.y, q1.y), fmaxf(q2.y, q3.y)));
+            o[2] = __float2bfloat16_rn(fmaxf(fmaxf(q0.z, q1.z), fmaxf(q2.z, q3.z)));
+            o[3] = __float2bfloat16_rn(fmaxf(fmaxf(q0.w, q1.w), fmaxf(q2.w, q3.w)));
+            *reinterpret_cast<uint2 *>(out + (pbase + pp) * COUT + c4 * 4) =
+                *reinterpret_cast<const uint2 *>(o);
+        }
+    };
+
+    // per accumulator j: parity of its barrier's next phase, MMAs in flight
+    uint32_t ph0 = 0u, ph1 = 0u;
+    bool pend0 = false, pend1 = false;
+    auto flip = [&](int j) {
+        if (j) ph1 ^= 1u; else ph0 ^= 1u;
+    };
+    auto set_pend = [&](int j, bool v) {
+        if (j) pend1 = v; else pend0 = v;
+    };
+    bool ok = true;
+    if (my > 0) {
+        gather(blockIdx.x, a_addr(0));
+        cp_async_commit();
+    }
+    for (int64_t k = 0; k < my; k++) {
+        const int cur = (int)(k & 1), nxt = cur ^ 1;
+        const int64_t tile = blockIdx.x + k * gridDim.x;
+        if (k >= 1) {
+            // MMAs of tile k-1 done: its A buffer may be refilled, its accumulator read
+            const bool done = tc::mbar_wait_bounded(bar(nxt), nxt ? ph1 : ph0, kConvBudget);
+            if (!__syncthreads_and(done)) {
+                ok = false;
+                break;
+            }
+            flip(nxt);
+            set_pend(nxt, false);
+            tc::fence_after();
+        }
+        if (k + 1 < my) {
+            gather(tile + gridDim.x, a_addr(nxt));
+            cp_async_commit();
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
+        }
+        tc::fence_proxy_async();  // this thread's copies -> tensor-core reads
+        tc::fence_before();
+        __syncthreads();
+        tc::fence_after();
+        if (tid == 0) {
+#pragma unroll
+            for (int kk = 0; kk < NK16; kk++) {
+                const uint64_t ad = tc::smem_desc(a_addr(cur) + kk * 256, 128, SBO);
+                const uint64_t bd = tc::smem_desc(b_addr + kk * 256, 128, SBO);
+                tc::mma_bf16(tmem + (uint32_t)(cur * COUT), ad, bd, kIdesc, kk > 0 ? 1u : 0u);
+            }
+            tc::mma_commit(bar(cur));
+        }
+        set_pend(cur, true);
+        if (k >= 1) epilogue(tile - gridDim.x, nxt);
+    }
+    if (ok && my > 0) {
+        const int last = (int)((my - 1) & 1);
+        const bool done = tc::mbar_wait_bounded(bar(last), last ? ph1 : ph0, kConvBudget);
+        if (__syncthreads_and(done)) {
+            flip(last);
+            set_pend(last, false);
+            tc::fence_after();
+            epilogue(blockIdx.x + (my - 1) * gridDim.x, last);
+        } else {
+            ok = false;
+        }
+    }
+    cp_async_wait<0>();
+    if (!ok) {
+        if (tid == 0) atomicExch(err, 1);
+        // never release tensor memory under MMAs still in flight (bounded)
+        if (pend0) (void)tc::mbar_wait_bounded(bar0, ph0, kConvBudget);
+        if (pend1) (void)tc::mbar_wait_bounded(bar1, ph1, kConvBudget);
+    }
+    tc::fence_before();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, kCols);
+}
+
+template <int CIN, int COUT, int SIDE>
+constexpr int conv_pool_smem() {
+    return 2 * (128 * ((9 * CIN + 15) / 16) * 2 * 16) + COUT * ((9 * CIN + 15) / 16) * 2 * 16 +
+           128 * (COUT + 4) * 4 + 2 * 8 + 16;
+}
+
+}  // namespace
+
 struct gsp_ranker_s {
     int max_batch = 0;
     Offsets off{};
@@ -426,12 +729,55 @@ cudaError_t gemm(gsp_ranker_s *r, const bf16 *A, int64_t lda, const bf16 *B, int
     return e;
 }
 
-// Forward pass of n snippets (FP32 [n][64][64]); logits into r->z5.
-cudaError_t forward(gsp_ranker_s *r, const float *x, int n, cudaStream_t s) {
+template <int CIN, int COUT, int SIDE>
+cudaError_t launch_conv_pool(gsp_ranker_s *r, const bf16 *act, int n, const bf16 *W,
+                             const float *bias, bf16 *out, cudaStream_t s) {
+    constexpr int smem = conv_pool_smem<CIN, COUT, SIDE>();
+    static int blocks_per_sm = 0;
+    if (blocks_per_sm == 0) {
+        cudaError_t e = cudaFuncSetAttribute(conv_pool_tc_kernel<CIN, COUT, SIDE>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                &blocks_per_sm, conv_pool_tc_kernel<CIN, COUT, SIDE>, 128, smem);
+        if (e != cudaSuccess) return e;
+        // at most 512 tensor-memory columns per SM (2 accumulators of COUT columns)
+        blocks_per_sm = std::max(1, std::min(blocks_per_sm, 512 / std::max(32, 2 * COUT)));
+    }
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    const int64_t ntiles = (int64_t)n * SIDE * SIDE / 128;
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(ntiles, (int64_t)sms * blocks_per_sm));
+    RK_LAUNCH((conv_pool_tc_kernel<CIN, COUT, SIDE><<<grid, 128, smem, s>>>(act, n, W, bias, out,
+                                                                           r->err)));
+    return cudaSuccess;
+}
+
+// Forward pass of n snippets (FP32 [n][64][64]); logits into r->z5.  A
+// training pass keeps what the backward pass needs (im2col matrices,
+// pre-activations, pool argmaxes); an inference pass runs each conv layer as
+// one fused conv + bias + ReLU + pool kernel.
+cudaError_t forward(gsp_ranker_s *r, const float *x, int n, bool train, cudaStream_t s) {
     for (int l = 0; l < kLayers; l++) {
         const int H = side_of(l), Cin = cin_of(l), Cout = cout_of(l), Kp = kpad(l);
         const int64_t P = (int64_t)n * H * H;
         (void)Cin;
+        if (!train) {
+            cudaError_t e = cudaSuccess;
+            if (l == 0)
+                RK_LAUNCH((conv0_pool_kernel<<<blocks_for(P / 4), 256, 0, s>>>(
+                    x, n, r->W[0], r->params + r->off.b[0], r->a[0])));
+            else if (l == 1)
+                e = launch_conv_pool<8, 16, 32>(r, r->a[0], n, r->W[1], r->params + r->off.b[1],
+                                                r->a[1], s);
+            else
+                e = launch_conv_pool<16, 32, 16>(r, r->a[1], n, r->W[2], r->params + r->off.b[2],
+                                                 r->a[2], s);
+            if (e != cudaSuccess) return e;
+            continue;
+        }
         if (l == 0)
             RK_LAUNCH((im2col_kernel<float, 1><<<blocks_for(P), 256, 0, s>>>(x, n, H, r->col[0])));
         else if (l == 1)
@@ -673,7 +1019,7 @@ gsp_status gsp_ranker_forward(gsp_ranker_t r, const float *d_x, int32_t n, float
     if (!r || !d_x || n < 1 || n > r->max_batch) return GSP_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     r->launches = 0;
-    cudaError_t e = forward(r, d_x, n, s);
+    cudaError_t e = forward(r, d_x, n, false, s);
     if (e == cudaSuccess && d_logits)
         e = cudaMemcpyAsync(d_logits, r->z5, (size_t)n * 2 * 4, cudaMemcpyDeviceToDevice, s);
     return status_of(e, "ranker forward");
@@ -685,7 +1031,7 @@ gsp_status gsp_ranker_train_step(gsp_ranker_t r, const float *d_x, const int32_t
         return GSP_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     r->launches = 0;
-    cudaError_t e = forward(r, d_x, n, s);
+    cudaError_t e = forward(r, d_x, n, true, s);
     if (e == cudaSuccess) e = backward(r, d_labels, n, lr, s);
     if (e == cudaSuccess && d_loss)
         e = cudaMemcpyAsync(d_loss, r->loss, sizeof(float), cudaMemcpyDeviceToDevice, s);

@@ -87,13 +87,34 @@ def test_forward_matches_oracle(gsp, n):
     logits = torch.zeros((n, 2), dtype=torch.float32, device="cuda")
     gsp.gsp_ranker_forward(r, torch.from_numpy(x).cuda(), n, logits)
     gsp.gsp_ranker_finish(r)
-    assert gsp.gsp_ranker_launches(r) == 11      # 3 x (im2col, GEMM, pool), fc1 GEMM, fc2
+    # three fused conv + pool layers, fc1 GEMM, fc2
+    assert gsp.gsp_ranker_launches(r) == 5
     got = logits.cpu().numpy().astype(np.float64)
     ref, _ = R.forward(p, x.astype(np.float64))
     err = np.abs(got - ref)
     # FP32 vs FP64 accumulation; a bf16 rounding flip changes one operand by 2^-8
     assert np.median(err) < 1e-4 * max(1.0, np.abs(ref).max())
     assert err.max() < 1e-2 * max(1.0, np.abs(ref).max())
+
+
+def test_inference_and_training_passes_agree(gsp):
+    """The fused inference pass and the im2col training pass round at the same
+    points: the cross-entropy of the inference logits equals the training
+    step's loss (lr 0) up to FP32 summation order."""
+    p = R.init_params(14)
+    n = 200
+    x, y = _batch(n, 8)
+    r = gsp.gsp_ranker_create(256, seed=6)
+    gsp.gsp_ranker_set_params(r, _flat(p))
+    xd, yd = torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda()
+    logits = torch.zeros((n, 2), dtype=torch.float32, device="cuda")
+    gsp.gsp_ranker_forward(r, xd, n, logits)
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+    gsp.gsp_ranker_train_step(r, xd, yd, n, 0.0, loss=loss)
+    gsp.gsp_ranker_finish(r)
+    ce = float(torch.nn.functional.cross_entropy(logits.double().cpu(),
+                                                 torch.from_numpy(y).long()))
+    assert abs(ce - float(loss.item())) <= 1e-4 * max(1.0, ce), (ce, float(loss.item()))
 
 
 def test_gradients_match_oracle(gsp):
