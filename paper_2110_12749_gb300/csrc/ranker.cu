@@ -879,12 +879,19 @@ __global__ void snippet_kernel(const int32_t *__restrict__ D, int64_t stride, in
     const int f = max(1, c.width / 4);
     const int64_t tc = c.t + c.width / 2;
     const float rs = 1.0f / sqrtf((float)f);
+    // 1 / sigma_ref of the snippet's rows, once per row (0: row left blank)
+    __shared__ float s_inv[kS];
+    for (int i = threadIdx.x; i < kS; i += blockDim.x) {
+        const int r = c.dm_idx - kS / 2 + i;
+        s_inv[i] = (r >= 0 && r < ndm && sref[r] > 0.0) ? (float)(1.0 / sref[r]) : 0.0f;
+    }
+    __syncthreads();
     for (int o = threadIdx.x; o < kS * kS; o += blockDim.x) {
         const int i = o / kS, j = o % kS;
         const int r = c.dm_idx - kS / 2 + i;
         float v = 0.0f;
-        if (r >= 0 && r < ndm && sref[r] > 0.0) {
-            const float inv = (float)(1.0 / sref[r]);
+        const float inv = s_inv[i];
+        if (inv != 0.0f) {
             const int64_t a = tc + (int64_t)(j - kS / 2) * f;
             const int64_t s0 = max(a, (int64_t)0), s1 = min(a + f, Ls);
             if (s0 < s1) {
