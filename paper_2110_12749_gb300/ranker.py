@@ -169,15 +169,19 @@ def pulse_scores(ranker, src, beams, seed, chunk=4096):
             "rank_s": rank_s}
 
 
-def choose_threshold(ranker, src, beams, seed, snr_min=8.0, keep=0.99):
-    """Operating threshold from validation beams: the score that keeps `keep`
-    of their pulses the search detects at S/N >= snr_min (each by its best
-    core candidate), at most 0.5."""
-    ps = pulse_scores(ranker, src, beams, seed)
+def threshold_for(ps, snr_min=8.0, keep=0.99):
+    """The score that keeps `keep` of the pulses in pulse_scores output `ps`
+    that the search detects at S/N >= snr_min (each by its best core
+    candidate), at most 0.5; 0.5 if there are none."""
     v = np.sort(ps["best"][ps["detected"] >= snr_min])
     if v.size == 0:
         return 0.5
     return float(min(0.5, v[int(np.floor((1.0 - keep) * v.size))]))
+
+
+def choose_threshold(ranker, src, beams, seed, snr_min=8.0, keep=0.99):
+    """Operating threshold from validation beams (threshold_for over them)."""
+    return threshold_for(pulse_scores(ranker, src, beams, seed), snr_min, keep)
 
 
 def train(ranker, x, y, steps, batch=256, lr=2e-3, seed=0, hard=None, pos_frac=0.25):
@@ -234,14 +238,18 @@ def score(ranker, x, chunk=None):
 
 
 def evaluate(ranker, src, beams, seed, snr_min=8.0, thresholds=(0.5,)):
-    """Score every candidate of fresh beams.  At each threshold: recall on
-    the injected pulses the search detects at S/N >= snr_min, recall on those
-    of nominal S/N >= snr_min that it detects at all, precision and the share
-    of negatives rejected; for the first threshold also [recalled, pulses]
-    by width and by detected S/N, and the missed pulses detected at S/N >=
-    snr_min ([nominal S/N, width, detected S/N, score], at most 10).  Plus
-    the ranking throughput (snippets + forward)."""
-    ps = pulse_scores(ranker, src, beams, seed)
+    """Score every candidate of fresh beams and summarise (see summarise)."""
+    return summarise(pulse_scores(ranker, src, beams, seed), snr_min, thresholds)
+
+
+def summarise(ps, snr_min=8.0, thresholds=(0.5,)):
+    """Quality of the scores in pulse_scores output `ps`.  At each threshold:
+    recall on the injected pulses the search detects at S/N >= snr_min,
+    recall on those of nominal S/N >= snr_min that it detects at all,
+    precision and the share of negatives rejected; for the first threshold
+    also [recalled, pulses] by width and by detected S/N, and the missed
+    pulses detected at S/N >= snr_min ([nominal S/N, width, detected S/N,
+    score], at most 10).  Plus the ranking throughput (snippets + forward)."""
     nom, wid, det, best = ps["nominal"], ps["width"], ps["detected"], ps["best"]
     d8 = det >= snr_min                       # detected at S/N >= snr_min
     n8 = (nom >= snr_min) & (det >= 0)        # nominal S/N >= snr_min, detected

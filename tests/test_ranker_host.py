@@ -49,3 +49,44 @@ def test_short_crafts_recipe():
     assert wl.n_in == 1 << 18 and wl.n_pulses == 100
     assert (wl.nchan, wl.ndm, wl.dm_step, wl.t_samp) == (base.nchan, base.ndm, base.dm_step,
                                                          base.t_samp)
+
+
+def _ps():
+    # five pulses: detected S/N 9, 15, 25 (>= 8); 7.5 (below 8, nominal 10); one undetected
+    return {"nominal": np.array([9.0, 16.0, 30.0, 10.0, 12.0]),
+            "width": np.array([2, 20, 80, 1, 3]),
+            "detected": np.array([9.0, 15.0, 25.0, 7.5, -1.0]),
+            "best": np.array([0.9, 0.2, 0.6, 0.05, -1.0]),
+            "neg": np.array([0.01, 0.3, 0.7, 0.02]),
+            "pos": np.array([0.9, 0.6, 0.2]),
+            "n_scored": 12, "rank_s": 0.5}
+
+
+def test_summarise_counts():
+    out = ranker.summarise(_ps(), thresholds=(0.5, 0.1))
+    assert out["pulses_detected_snr_ge_min"] == 3
+    assert out["pulses_nominal_snr_ge_min"] == 5
+    assert out["nominal_snr_ge_min_detected"] == 4
+    assert abs(out["recall"] - 2 / 3) < 1e-12                 # 0.9 and 0.6 pass 0.5
+    assert abs(out["recall_nominal"] - 2 / 4) < 1e-12
+    assert abs(out["precision"] - 2 / 3) < 1e-12              # pos 0.9, 0.6; neg 0.7
+    assert abs(out["negatives_rejected"] - 3 / 4) < 1e-12
+    assert out["recalled_by_width"] == {"1-9": [1, 1], "10-49": [0, 1], "50-150": [1, 1]}
+    assert out["recalled_by_snr"] == {"8-12": [1, 1], "12-20": [0, 1], ">=20": [1, 1]}
+    assert out["missed"] == [[16.0, 20, 15.0, 0.2]]
+    at = out["at"]["0.1"]
+    assert at["recall"] == 1.0 and abs(at["recall_nominal"] - 3 / 4) < 1e-12
+    assert abs(out["candidates_per_s"] - 24.0) < 1e-12
+
+
+def test_threshold_for_keeps_the_share():
+    ps = _ps()
+    assert ranker.threshold_for(ps, keep=1.0) == 0.2          # the weakest detected >= 8
+    assert ranker.threshold_for(ps, keep=0.5) == 0.5          # capped at 0.5
+    ps["best"] = np.linspace(0.0, 0.45, 201)
+    ps["detected"] = np.full(201, 9.0)
+    # keep 99% of 201 pulses: floor(0.01 * 201) = 2 may fall below the threshold
+    t = ranker.threshold_for(ps, keep=0.99)
+    assert t == ps["best"][2] and (ps["best"] >= t).mean() >= 0.99
+    ps["detected"][:] = 7.0
+    assert ranker.threshold_for(ps) == 0.5                    # none detected at >= 8
