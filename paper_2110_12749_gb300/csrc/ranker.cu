@@ -893,21 +893,25 @@ __global__ void snippet_kernel(const int32_t *__restrict__ D, int64_t stride, in
         const float inv = s_inv[i];
         if (inv != 0.0f) {
             const int64_t a = tc + (int64_t)(j - kS / 2) * f;
-            const int64_t s0 = max(a, (int64_t)0), s1 = min(a + f, Ls);
-            if (s0 < s1) {
-                int64_t b = s0 / B;
-                int jb = (int)(s0 - b * B);           // position inside block b
-                gsp::BlockParam q = bp[(int64_t)r * nb_max + b];
-                const int32_t *drow = D + (int64_t)r * stride;
-                for (int64_t s = s0; s < s1; s++, jb++) {
-                    if (jb == B) {
-                        b++;
-                        jb = 0;
-                        q = bp[(int64_t)r * nb_max + b];
-                    }
-                    if (q.good)
-                        v += ((float)(drow[s] - q.m) - (q.c0 + q.beta * (float)jb)) * inv;
+            int64_t s0 = max(a, (int64_t)0);
+            const int64_t s1 = min(a + f, Ls);
+            const int32_t *drow = D + (int64_t)r * stride;
+            // the bin in runs of samples inside one block (at most two runs, f <= B):
+            // sum over the run of (D - m) - (c0 + beta jb) = (sum D - n m) - (n c0 + beta sum jb)
+            while (s0 < s1) {
+                const int64_t b = s0 / B;
+                const int jb0 = (int)(s0 - b * B);
+                const int64_t e = min(s1, (b + 1) * (int64_t)B);
+                const int n = (int)(e - s0);
+                const gsp::BlockParam q = bp[(int64_t)r * nb_max + b];
+                if (q.good) {
+                    int64_t sd = 0;  // exact
+                    for (int64_t t = s0; t < e; t++) sd += drow[t];
+                    const int64_t sj = (int64_t)n * jb0 + (int64_t)n * (n - 1) / 2;
+                    v += ((float)(sd - (int64_t)n * q.m) - ((float)n * q.c0 + q.beta * (float)sj)) *
+                         inv;
                 }
+                s0 = e;
             }
         }
         out[(int64_t)blockIdx.x * kS * kS + o] = v * rs;
