@@ -90,3 +90,15 @@ def test_threshold_for_keeps_the_share():
     assert t == ps["best"][2] and (ps["best"] >= t).mean() >= 0.99
     ps["detected"][:] = 7.0
     assert ranker.threshold_for(ps) == 0.5                    # none detected at >= 8
+
+
+def test_bench_entry_points_wrap_the_host_summary(monkeypatch):
+    # the GPU scoring pass replaced by fixed per-pulse arrays
+    monkeypatch.setattr(ranker, "pulse_scores", lambda r, src, beams, seed: _ps())
+    thr = ranker.choose_threshold(None, None, 8, 0)
+    assert thr == ranker.threshold_for(_ps())
+    ev = ranker.evaluate(None, None, 4, 0, thresholds=(thr, 0.05, 0.5))
+    assert ev == ranker.summarise(_ps(), 8.0, (thr, 0.05, 0.5))
+    assert set(ev["at"]) == {"0.05", "0.5"}
+    import json
+    json.dumps(ev)      # the bench line must serialise
