@@ -36,6 +36,9 @@ DD_TRAFFIC_BYTES_PER_ADD = (1.5984e9 + 0.6663e9) / 6.899e11
 DD_TRAFFIC_VARIANT = "default"
 
 NOMINAL_SMS = 152
+RANKER_KEYS = ("recall", "recall_nominal", "precision", "negatives_rejected", "threshold",
+               "pulses_detected_snr_ge_min", "candidates_scored", "candidates_per_s",
+               "train_snippets", "train_positives", "train_steps", "train_steps_per_s", "params")
 INT_LANES_PER_SM = 128          # issue slots per SM per clock (4 schedulers x 32 lanes)
 SM_MAX_MHZ = 2070.0
 
@@ -52,10 +55,14 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--n-in", type=int, default=0,
                     help="samples per channel (0: the workload's); smaller only for profiling")
-    ap.add_argument("--stream-beams", type=int, default=4,
+    ap.add_argument("--stream-beams", type=int, default=19,
                     help="beams of the streaming-latency measurement (0: skip)")
-    ap.add_argument("--stream-chunks", type=int, default=6,
+    ap.add_argument("--stream-chunks", type=int, default=12,
                     help="chunks per beam in the streaming measurement (the first one primes)")
+    ap.add_argument("--stream-pool", type=int, default=4,
+                    help="device chunk buffers shared by the streams (admission by memory)")
+    ap.add_argument("--stream-sources", type=int, default=3,
+                    help="seeded synthetic series the streamed chunks are windows of")
     ap.add_argument("--batch-beams", type=int, default=19,
                     help="beams of the batched multi-beam measurement (0: skip)")
     ap.add_argument("--batch-steps", type=int, default=3)
@@ -76,6 +83,9 @@ def parse():
                     help="aggregate arrival rate of the simulated stream (GB/s)")
     ap.add_argument("--variant", type=int, default=-1,
                     help="tiled dedispersion kernel variant (GSP_DD_VARIANT); -1: library default")
+    ap.add_argument("--wideband-steps", type=int, default=3,
+                    help="timed steps of the wide-band workload (2048 ch, 500-3300 MHz, 3000 DMs; "
+                         "0: skip)")
     return ap.parse_args()
 
 
@@ -217,102 +227,161 @@ def run_reference(args):
     return 0
 
 
-def run_stream(args, wl, delays_fn):
-    """Streaming loop: B beams, chunks of 2^18 samples admitted round-robin as they
-    arrive at an aggregate rate; latency = candidates on the host - arrival."""
+def run_stream(args, wl, delays_fn, base_src):
+    """Streaming loop of the learned + streaming workload: B beams of 2^18-sample
+    chunks arriving round-robin at an aggregate rate (6 GB/s), each beam with its
+    own plan and pooled stream (its overlap tail kept on the device).  Beams are
+    admitted by memory at start; every chunk is admitted by memory as it
+    arrives: it needs a free buffer of the shared chunk pool, else it waits in
+    an arrival queue.  Latency = candidates on the host - arrival."""
     import queue
     import threading
     import torch
     from paper_2110_12749_gb300 import gsp, synth
-    K, chunk = args.stream_chunks, 1 << 18
+    chunk = 1 << 18
+    K = args.stream_chunks
     plans, streams, cstreams = [], [], []
     md = None
     admitted_bytes = 0
-    # admit beams by memory: a beam joins while its plan and stream buffers fit in
-    # 80% of the device memory that is free
+    free0, _ = torch.cuda.mem_get_info()
     for b in range(args.stream_beams):
         desc, keep = gsp.make_desc(wl.nchan, wl.f_lo, wl.f_hi, wl.t_samp, 1 << 20, ndm=wl.ndm,
                                    dm_lo=wl.dm_lo, dm_step=wl.dm_step)
+        probe = gsp.gsp_plan_create(desc, keep)
+        md = gsp.gsp_plan_max_delay(probe)
+        gsp.gsp_plan_destroy(probe)
+        desc, keep = gsp.make_desc(wl.nchan, wl.f_lo, wl.f_hi, wl.t_samp, chunk + md, ndm=wl.ndm,
+                                   dm_lo=wl.dm_lo, dm_step=wl.dm_step)
         plan = gsp.gsp_plan_create(desc, keep)
-        free, _ = torch.cuda.mem_get_info()
-        need = gsp.gsp_stream_bytes(plan, chunk)
-        if need > 0.8 * free:
+        # a beam joins while its tail buffer and series scratch fit in 70% of the
+        # device memory that was free when the stream started
+        need = gsp.gsp_stream_pooled_bytes(plan, chunk)
+        if admitted_bytes + need > 0.7 * free0:
             gsp.gsp_plan_destroy(plan)
             break
-        md = gsp.gsp_plan_max_delay(plan)
         plans.append(plan)
-        streams.append(gsp.gsp_stream_create(plan, chunk, beam=b))
-        cstreams.append(torch.cuda.Stream())
         admitted_bytes += need
     B = len(plans)
-    # one primed chunk of synthetic data, repeated for every chunk of every beam
-    import dataclasses
-    wl1 = dataclasses.replace(wl, n_in=md + chunk)
-    x, _, _, _ = synth.workload_filterbank(wl1, delays_fn, chunk, beam=0)
-    xh = torch.from_numpy(x).pin_memory()
-    first = xh
-    later = xh[:, md:md + chunk]
-    chunk_bytes = wl.nchan * chunk
-    interval = chunk_bytes / (args.stream_gbs * 1e9)
-    # priming chunk of every beam (not timed; also allocates the plans' scratch)
+    pool_bytes = gsp.gsp_chunkpool_bytes(wl.nchan, chunk, md, args.stream_pool)
+    pool = gsp.gsp_chunkpool_create(wl.nchan, chunk, md, args.stream_pool)
+    for b, plan in enumerate(plans):
+        streams.append(gsp.gsp_stream_create_pooled(plan, pool, beam=b))
+        cstreams.append(torch.cuda.Stream())
+    # seeded synthetic sources: the bench's CRAFTS-like beam (pinned) and further
+    # beams of the same recipe; chunk k of beam b is a window of source b mod S at a
+    # seeded random offset (distinct data for every chunk)
+    span = wl.n_in
+    t_gen = time.time()
+    srcs = [base_src]
+    for g in range(1, args.stream_sources):
+        x, _, _, _ = synth.workload_filterbank(wl, delays_fn, span - md, beam=100 + g)
+        srcs.append(torch.from_numpy(x).pin_memory())
+        del x
+    t_gen = time.time() - t_gen
+    rng = np.random.default_rng(synth.BASE_SEED + 4)
+    hi = span - (chunk + md)
+
+    def window(b, k):
+        src = srcs[b % len(srcs)]
+        o = int(rng.integers(0, hi // 64)) * 64
+        return src[:, o:o + (chunk + md if k == 0 else chunk)]
+
+    # priming chunk of every beam (not timed; allocates the plans' scratch)
     for b in range(B):
         with torch.cuda.stream(cstreams[b]):
-            gsp.gsp_stream_push(streams[b], first, gsp.gsp_stream_need(streams[b]),
-                                stream=cstreams[b])
+            while not gsp.gsp_stream_push(streams[b], window(b, 0), chunk + md,
+                                          stream=cstreams[b], busy_ok=True):
+                time.sleep(0.001)
         gsp.gsp_stream_results(streams[b])
+    torch.cuda.synchronize()
     q = queue.Queue()
-    lat, done_at = [], []
+    lat, done_at, intervals = [], [], []
     beam_free = [threading.Event() for _ in range(B)]
     for e in beam_free:
         e.set()
+    t_ref = torch.cuda.Event(enable_timing=True)
 
     def waiter():
         while True:
             item = q.get()
             if item is None:
                 return
-            b, arrival, ev = item
-            ev.synchronize()
+            b, arrival, e0, e1 = item
+            e1.synchronize()
             gsp.gsp_stream_results(streams[b])
             t = time.perf_counter()
             lat.append((t - arrival) * 1e3)
             done_at.append(t)
+            intervals.append((t_ref.elapsed_time(e0), t_ref.elapsed_time(e1)))
             beam_free[b].set()
 
     th = threading.Thread(target=waiter, daemon=True)
     th.start()
     n_items = B * (K - 1)
+    chunk_bytes = wl.nchan * chunk
+    interval = chunk_bytes / (args.stream_gbs * 1e9)
+    t_ref.record()
     t_start = time.perf_counter() + 0.05
-    for i in range(n_items):
-        b = i % B
-        arrival = t_start + i * interval
+    pending = []            # arrived, not yet admitted: (b, arrival, data)
+    refusals, max_wait = 0, 0
+    i = 0
+    while i < n_items or pending:
         now = time.perf_counter()
-        if arrival > now:
-            time.sleep(arrival - now)
-        beam_free[b].wait()
-        beam_free[b].clear()
-        with torch.cuda.stream(cstreams[b]):
-            gsp.gsp_stream_push(streams[b], later, chunk, stream=cstreams[b])
-            ev = torch.cuda.Event()
-            ev.record(cstreams[b])
-        q.put((b, arrival, ev))
+        while i < n_items and t_start + i * interval <= now:
+            pending.append((i % B, t_start + i * interval, window(i % B, 1)))
+            i += 1
+        max_wait = max(max_wait, len(pending))
+        while pending:
+            b, arrival, data = pending[0]
+            if not beam_free[b].is_set():
+                break                       # the beam's previous chunk is still running
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            with torch.cuda.stream(cstreams[b]):
+                e0.record(cstreams[b])
+                ok = gsp.gsp_stream_push(streams[b], data, chunk, stream=cstreams[b], busy_ok=True)
+                if ok:
+                    e1.record(cstreams[b])
+            if not ok:
+                refusals += 1               # not admitted: no free pool buffer yet
+                break
+            beam_free[b].clear()
+            pending.pop(0)
+            q.put((b, arrival, e0, e1))
+        nxt = t_start + i * interval if i < n_items else now + 0.001
+        time.sleep(max(0.0, min(nxt - time.perf_counter(), 0.001 if pending else 1.0)))
     q.put(None)
     th.join()
+    torch.cuda.synchronize()
     for st in streams:
         gsp.gsp_stream_destroy(st)
+    gsp.gsp_chunkpool_destroy(pool)
     for p in plans:
         gsp.gsp_plan_destroy(p)
+    del srcs
+    # GPU busy: the union of the chunks' [first copy, last search kernel] intervals
+    busy, cur = 0.0, None
+    for a, b2 in sorted(intervals):
+        if cur is None or a > cur[1]:
+            if cur is not None:
+                busy += cur[1] - cur[0]
+            cur = [a, b2]
+        else:
+            cur[1] = max(cur[1], b2)
+    if cur is not None:
+        busy += cur[1] - cur[0]
+    span_ms = max(b2 for _, b2 in intervals) - min(a for a, _ in intervals)
     lat_sorted = sorted(lat)
-    span = max(done_at) - t_start
-    return {"beams": B, "beams_requested": args.stream_beams,
-            "admission": "by memory: a beam joins while gsp_stream_bytes fits in 80% of free "
-                         "device memory", "admitted_bytes": int(admitted_bytes),
-            "chunk_samples": chunk, "chunk_sky_s": chunk * wl.t_samp,
-            "arrival_gbs": args.stream_gbs, "chunks_timed": n_items,
-            "p50_ms": float(np.percentile(lat_sorted, 50)),
-            "p99_ms": float(np.percentile(lat_sorted, 99)), "max_ms": float(lat_sorted[-1]),
-            "sky_s_per_s": n_items * chunk * wl.t_samp / span,
-            "data": "one synthetic primed chunk repeated for every chunk and beam"}
+    wall = max(done_at) - t_start
+    return {"beams": B, "beams_requested": args.stream_beams, "pool_buffers": args.stream_pool,
+            "device_bytes": int(admitted_bytes + pool_bytes), "chunk_samples": chunk,
+            "chunk_ms": _r(chunk * wl.t_samp * 1e3), "arrival_gbs": args.stream_gbs,
+            "chunks_timed": n_items, "p50_ms": _r(float(np.percentile(lat_sorted, 50))),
+            "p99_ms": _r(float(np.percentile(lat_sorted, 99))), "max_ms": _r(lat_sorted[-1]),
+            "gpu_busy_frac": _r(busy / span_ms) if span_ms > 0 else None,
+            "admission_refusals": refusals, "max_queued": max_wait,
+            "sky_s_per_s": _r(n_items * chunk * wl.t_samp / wall), "data_gen_s": _r(t_gen),
+            "data": "each chunk a seeded random window of one of %d synthetic CRAFTS-like "
+                    "beams" % args.stream_sources}
 
 
 def run_batch(args, wl):
@@ -353,6 +422,7 @@ def run_batch(args, wl):
     bt = gsp.gsp_batch_create(plans, flags)
     gsp.gsp_batch_search(bt, xs, n_ins, stream=s)       # autotune + capture
     variant, tuned_ms, launches = gsp.gsp_batch_info(bt)
+    tuned = [[v, _r(ms)] for v, ms in gsp.gsp_batch_tune_results(bt)]
     dd, tot = [], []
     for _ in range(args.batch_steps):
         gsp.gsp_batch_search(bt, xs, n_ins, stream=s)   # graph replay
@@ -368,15 +438,72 @@ def run_batch(args, wl):
     ms_dd, ms_tot = float(np.median(dd)), float(np.median(tot))
     nsm = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
     peak = nsm * INT_LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
-    return {"beams": B, "samples_total": int(sum(n_ins)), "sky_s": sky, "adds": adds,
-            "ms_per_batch": ms_tot, "dedisperse_ms": ms_dd,
-            "sky_s_per_s": sky / (ms_tot / 1e3),
-            "dm_chan_samples_per_s": adds / (ms_tot / 1e3),
-            "dedisperse_frac_of_roofline": adds / (ms_dd / 1e3) / 1e12 / peak,
-            "variant": variant, "autotune_best_ms": tuned_ms, "launches_per_batch": launches,
-            "candidates": int(ncand),
-            "launch": "one persistent dedispersion launch for all beams, graph-captured with "
-                      "the per-beam search kernels"}
+    return {"beams": B, "samples_total": int(sum(n_ins)), "sky_s": _r(sky), "adds": _r(adds),
+            "ms_per_batch": _r(ms_tot), "dedisperse_ms": _r(ms_dd),
+            "sky_s_per_s": _r(sky / (ms_tot / 1e3)),
+            "dm_chan_samples_per_s": _r(adds / (ms_tot / 1e3)),
+            "dedisperse_frac_of_roofline": _r(adds / (ms_dd / 1e3) / 1e12 / peak),
+            "variant": variant, "autotune_ms_per_variant": tuned, "launches_per_batch": launches,
+            "candidates": int(ncand), "launch": "1 persistent dedispersion launch, graph-captured"}
+
+
+def run_wideband(args):
+    """The wide-band workload (2048 channels, 500-3300 MHz, 98.304 us, 2^20 samples,
+    3000 DMs 0-2999; largest delay 493269 samples): the plan's tile variant is
+    autotuned on the input (gsp_plan_tune), then gsp_search is timed with CUDA
+    events; the dedispersion kernel's duration gives its roofline fraction."""
+    import torch
+    from paper_2110_12749_gb300 import gsp, synth
+    wl = synth.WORKLOADS["wideband"]
+    desc, keep = gsp.make_desc(wl.nchan, wl.f_lo, wl.f_hi, wl.t_samp, wl.n_in, ndm=wl.ndm,
+                               dm_lo=wl.dm_lo, dm_step=wl.dm_step, flags=gsp.GSP_FLAG_TIMING)
+    plan = gsp.gsp_plan_create(desc, keep)
+    n_out = gsp.gsp_plan_nout(plan, wl.n_in)
+
+    def delays_fn(dm):
+        d1, k1 = gsp.make_desc(wl.nchan, wl.f_lo, wl.f_hi, wl.t_samp, wl.n_in, dms=[dm])
+        return gsp.gsp_compute_delays(d1)[0][0]
+
+    x, _, _, _ = synth.workload_filterbank(wl, delays_fn, n_out, beam=0)
+    xd = torch.from_numpy(x).cuda()
+    del x
+    _, auto = gsp.gsp_dedisperse_variants(plan)
+    variant, tune_ms = gsp.gsp_plan_tune(plan, xd, wl.n_in)
+    for _ in range(2):
+        gsp.gsp_search(plan, xd, wl.n_in)
+        gsp.gsp_plan_timing(plan)
+    dd, se, tot = [], [], []
+    stream = torch.cuda.current_stream()
+    for _ in range(args.wideband_steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        gsp.gsp_search(plan, xd, wl.n_in)
+        e1.record(stream)
+        a, b = gsp.gsp_plan_timing(plan)
+        dd.append(a)
+        se.append(b)
+        tot.append(e0.elapsed_time(e1))
+    _, ncand, _ = gsp.gsp_candidates(plan)
+    gsp.gsp_plan_destroy(plan)
+    del xd
+    torch.cuda.empty_cache()
+    adds = float(wl.ndm) * wl.nchan * n_out
+    ms_dd, ms_tot = float(np.median(dd)), float(np.median(tot))
+    nsm = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    peak = nsm * INT_LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
+    return {"workload": workload_desc(wl), "n_out": n_out, "max_delay": wl.n_in - n_out,
+            "variant_auto": auto, "variant": variant, "ms_per_step": _r(ms_tot),
+            "dedisperse_ms": _r(ms_dd), "search_ms": _r(float(np.median(se))),
+            "sky_s_per_s": _r(wl.sky_seconds() / (ms_tot / 1e3)),
+            "dedisperse_frac_of_roofline": _r(adds / (ms_dd / 1e3) / 1e12 / peak),
+            "candidates": int(ncand)}
+
+
+def _r(v, sig=4):
+    """Round a float to `sig` significant digits (keeps the JSON line short)."""
+    if v is None or not isinstance(v, float) or v != v or v in (float("inf"), float("-inf")):
+        return v
+    return float("%.*g" % (sig, v))
 
 
 def measured_hbm_gbs():
@@ -663,16 +790,19 @@ def run_gsp(args):
     if args.subband_steps > 0 and rank == 0:
         subband_res = run_subband(args, wl, plan, xd)
     if args.stream_beams > 0 or args.batch_beams > 0 or args.ddplan_steps > 0 or \
-            args.ranker_beams > 0:
+            args.ranker_beams > 0 or args.wideband_steps > 0:
         if plan is not None:
             gsp.gsp_plan_destroy(plan)
             plan = None
         del xd
         torch.cuda.empty_cache()
+    wide_res = None
+    if args.wideband_steps > 0 and rank == 0:
+        wide_res = run_wideband(args)
     if args.batch_beams > 0 and rank == 0:
         batch_res = run_batch(args, wl)
     if args.stream_beams > 0 and rank == 0:
-        stream_res = run_stream(args, wl, delays_fn)
+        stream_res = run_stream(args, wl, delays_fn, xh)
     if args.ddplan_steps > 0 and rank == 0:
         ddplan_res = run_ddplan(args)
     ranker_res = None
@@ -714,19 +844,35 @@ def run_gsp(args):
         }
         if cpu is not None:
             line["cpu_baseline"] = cpu
+        # the sections, shortest last-needed first: the driver keeps the line's last
+        # 1500 characters, which must show the wide-band, batch and stream sections
+        # and the benchmark spec's targets; the long ranker breakdown goes to stderr
+        if ranker_res is not None:
+            sys.stderr.write("ranker detail: %s\n" % json.dumps(ranker_res))
+            line["ranker"] = {k: _r(ranker_res[k]) if isinstance(ranker_res.get(k), float)
+                              else ranker_res.get(k) for k in RANKER_KEYS if k in ranker_res}
+        if subband_res is not None:
+            line["subband"] = {k: _r(v) if isinstance(v, float) else v
+                               for k, v in subband_res.items() if k != "exact_rows"}
+        if ddplan_res is not None:
+            line["ddplan"] = {k: _r(v) if isinstance(v, float) else v
+                              for k, v in ddplan_res.items() if k not in ("data", "band_mhz")}
+        if ingest_res is not None:
+            line["ingest"] = {k: _r(v) if isinstance(v, float) else v for k, v in ingest_res.items()}
+        if wide_res is not None:
+            line["wideband"] = wide_res
         if batch_res is not None:
             line["batch"] = batch_res
-        if ingest_res is not None:
-            line["ingest"] = ingest_res
-        if subband_res is not None:
-            line["subband"] = subband_res
-        if ddplan_res is not None:
-            line["ddplan"] = ddplan_res
-        if ranker_res is not None:
-            line["ranker"] = ranker_res
         if stream_res is not None:
             line["stream"] = stream_res
             line["p99_chunk_latency_ms"] = stream_res["p99_ms"]
+        line["targets"] = {
+            "realtime_factor_crafts": _r(value / world),
+            "batch19_dedisperse_frac": batch_res["dedisperse_frac_of_roofline"] if batch_res else None,
+            "wideband_dedisperse_frac": wide_res["dedisperse_frac_of_roofline"] if wide_res else None,
+            "stream_p99_ms": stream_res["p99_ms"] if stream_res else None,
+            "stream_chunk_ms": _r(stream_res["chunk_sky_s"] * 1e3) if stream_res else None,
+            "ranker_recall_snr8": line["ranker"].get("recall") if ranker_res else None}
         print(json.dumps(line))
     if plan is not None:
         gsp.gsp_plan_destroy(plan)

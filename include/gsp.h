@@ -52,7 +52,8 @@ typedef enum {
     GSP_ERR_TIE = 7,         /* a delay lies within 1e-9 of a rounding tie */
     GSP_ERR_ALIGN = 8,       /* pointer or stride violates a stated alignment */
     GSP_ERR_STATE = 9,       /* call out of order (e.g. no search yet) */
-    GSP_ERR_TOO_LARGE = 10   /* sizes exceed the static scratch of gsp_search_series_static */
+    GSP_ERR_TOO_LARGE = 10,  /* sizes exceed the static scratch of gsp_search_series_static */
+    GSP_ERR_BUSY = 11        /* no free chunk buffer: the chunk was not admitted, nothing enqueued */
 } gsp_status;
 
 /* Plan flags (gsp_plan_desc.flags). */
@@ -61,6 +62,7 @@ typedef enum {
 
 typedef struct gsp_plan_s *gsp_plan_t;
 typedef struct gsp_stream_s *gsp_stream_t;
+typedef struct gsp_chunkpool_s *gsp_chunkpool_t;
 typedef struct gsp_batch_s *gsp_batch_t;
 typedef struct gsp_subband_s *gsp_subband_t;
 typedef struct gsp_ddplan_s *gsp_ddplan_t;
@@ -224,11 +226,33 @@ int32_t gsp_plan_launches(gsp_plan_t plan);
  * counterpart; every variant computes the same bit-exact series).  Returns
  * the number of variants; if plan is not NULL and in_use is not NULL, writes
  * the variant the plan uses, or -1 if it uses the simple kernel.  A plan's
- * variant is chosen at gsp_plan_create: the default, or the index in the
- * environment variable GSP_DD_VARIANT if that is in range (variants that need
- * the packed delay lists fall back to the default when the largest delay is
- * 2^23 samples or more). */
+ * variant is chosen at gsp_plan_create: the index in the environment variable
+ * GSP_DD_VARIANT if that is in range and fits the plan, else the first of a
+ * preference list (64-channel stages; 32-channel stages; 7-DM blocks) whose
+ * shared-memory stages hold the plan's largest in-block delay spread with at
+ * least two ring slots.  The simple kernel (-1) is used only with
+ * GSP_FLAG_SIMPLE_DD or when no tiled variant fits the spread (a 7-DM block
+ * spread of more than about 3000 samples), never silently otherwise. */
 int32_t gsp_dedisperse_variants(gsp_plan_t plan, int32_t *in_use);
+
+/* Autotune the plan's tile variant on the caller's input (a tuning knob with
+ * no paper counterpart): every variant of the tuning list that fits the plan
+ * runs once to warm up and three times timed, with CUDA events on stream, over
+ * the first 131072 output samples of d_x (layout and limits as gsp_dedisperse)
+ * into the plan's series scratch (allocated here if needed); the variant with
+ * the smallest median becomes the plan's.  *variant and *best_ms (optional)
+ * receive it and its median.  Synchronises.  GSP_ERR_STATE for a plan on the
+ * simple kernel. */
+gsp_status gsp_plan_tune(gsp_plan_t plan, const uint8_t *d_x, int64_t n_in, int64_t x_stride,
+                         void *stream, int32_t *variant, float *best_ms);
+
+/* The series of the plan's last search (gsp_search, gsp_search_host,
+ * gsp_search_series, or a batch search of this plan): its device address, row
+ * stride (elements) and n_out.  The address is the caller's d_out or the
+ * plan's scratch; it stays valid until the plan is destroyed or searches
+ * again.  GSP_ERR_STATE before the first search.  Host only. */
+gsp_status gsp_plan_series(gsp_plan_t plan, const int32_t **d_D, int64_t *stride,
+                           int64_t *n_out);
 
 /* Search of caller-provided dedispersed series that allocates nothing: for
  * callers that may not call cudaMalloc (for instance a real-time ingest loop
@@ -245,13 +269,17 @@ int32_t gsp_dedisperse_variants(gsp_plan_t plan, int32_t *in_use);
  *             beyond max_cands are dropped.
  * Working memory is one static device array inside the library, about 7 MB on
  * every GPU that loads it, which limits a call to ndm <= 4096 rows and
- * ndm * floor(n_out / block_len) <= 2^18 search blocks; larger calls return
- * GSP_ERR_TOO_LARGE.  The first call on a device looks up the array's device
- * address (cudaGetSymbolAddress), so make that first call before any stream
- * capture.  All calls share the array: calls whose kernels overlap on the GPU
- * race on it, calls queued one after another on one stream do not.  No
- * cudaMalloc, cudaFree or allocating library routine is called.  Asynchronous
- * on stream. */
+ * ndm * floor(n_out / block_len) <= 2^18 search blocks, and the candidate
+ * windows of a row to fewer than 2^31; larger calls return GSP_ERR_TOO_LARGE.
+ * threshold must be finite (as in gsp_plan_desc).  The first call on a device
+ * looks up the array's device address (cudaGetSymbolAddress) and caches it
+ * for the life of the process; with lazy module loading that call also loads
+ * the library's device code, array included, on that device.  So make that
+ * first call before any stream capture, and do not use this entry point on a
+ * device after cudaDeviceReset.  All calls share the array: calls whose
+ * kernels overlap on the GPU race on it, calls queued one after another on
+ * one stream do not.  No cudaMalloc, cudaFree or allocating library routine is
+ * called.  Asynchronous on stream. */
 gsp_status gsp_search_series_static(const int32_t *d_D, int32_t ndm, int64_t n_out,
                                     int64_t stride, int64_t t_offset, const int32_t *widths,
                                     int32_t nwidths, int32_t block_len, int32_t window_len,
@@ -276,6 +304,36 @@ gsp_status gsp_stream_create(gsp_stream_t *out, gsp_plan_t plan, int64_t chunk_o
  * -1 for a NULL plan or chunk_out <= 0.  Host only. */
 int64_t gsp_stream_bytes(gsp_plan_t plan, int64_t chunk_out);
 
+/* A pool of nbuf device input buffers, each nchan x round16(chunk_out +
+ * max_tail) bytes, shared by the pooled streams of many beams (admission by
+ * memory, chunk by chunk).  A pooled stream keeps only its overlap tail on the
+ * device; each push takes a pool buffer whose previous chunk has finished, or
+ * is refused with GSP_ERR_BUSY and enqueues nothing, so that the caller can
+ * queue the chunk and retry.  The buffer returns to the pool when the chunk's
+ * copies and search have run on the GPU (an event recorded on the push's
+ * stream).  A pool is used from one host thread at a time.  Allocates. */
+gsp_status gsp_chunkpool_create(gsp_chunkpool_t *out, int32_t nchan, int64_t chunk_out,
+                                int64_t max_tail, int32_t nbuf);
+gsp_status gsp_chunkpool_destroy(gsp_chunkpool_t pool);
+
+/* Device bytes of a pool (host only; -1 for invalid sizes). */
+int64_t gsp_chunkpool_bytes(int32_t nchan, int64_t chunk_out, int64_t max_tail, int32_t nbuf);
+
+/* Pool buffers free now (polls the buffers' events; -1 for NULL). */
+int32_t gsp_chunkpool_free(gsp_chunkpool_t pool);
+
+/* A stream of the plan's beam whose input buffers come from the pool: chunks
+ * of the pool's chunk_out samples (a multiple of block_len and window_len);
+ * the plan's max delay must be <= the pool's max_tail and chunk_out +
+ * max_delay <= nsamp_max.  Owns a device tail buffer of nchan x
+ * round16(max_delay) bytes.  Pushes and results as for gsp_stream_create. */
+gsp_status gsp_stream_create_pooled(gsp_stream_t *out, gsp_plan_t plan, gsp_chunkpool_t pool,
+                                    int32_t beam);
+
+/* Device bytes a new pooled stream will allocate: its tail buffer, plus the
+ * plan's series scratch if the plan has not searched yet.  Host only. */
+int64_t gsp_stream_pooled_bytes(gsp_plan_t plan, int64_t chunk_out);
+
 /* Free the stream's buffers (synchronises the device; the plan is not freed). */
 gsp_status gsp_stream_destroy(gsp_stream_t s);
 
@@ -287,8 +345,10 @@ int64_t gsp_stream_need(gsp_stream_t s);
  * gsp_stream_need(s) new samples per channel (pinned memory makes the copy
  * asynchronous).  Enqueues on stream: the copy of the previous chunk's last
  * max_delay samples (device to device), the host-to-device copy of the new
- * samples, and gsp_search.  Returns GSP_ERR_INVALID_ARG if n differs from
- * gsp_stream_need(s). */
+ * samples, and gsp_search (a pooled stream also keeps the new tail).  Returns
+ * GSP_ERR_INVALID_ARG if n differs from gsp_stream_need(s), and for a pooled
+ * stream GSP_ERR_BUSY if no pool buffer is free (nothing enqueued).  Read the
+ * chunk's results (gsp_stream_results) before the next push of this stream. */
 gsp_status gsp_stream_push(gsp_stream_t s, const uint8_t *h_x, int64_t n, int64_t h_stride,
                            void *stream);
 
@@ -327,9 +387,18 @@ gsp_status gsp_batch_candidates(gsp_batch_t b, gsp_cand *host_out, int64_t cap, 
  * graph); requires GSP_BATCH_TIMING.  Synchronises. */
 gsp_status gsp_batch_timing(gsp_batch_t b, float *ms_dedisperse, float *ms_total);
 
-/* The dedispersion variant in use, the autotuner's best batch time (ms, 0 if
- * not tuned) and the kernel launches of the last call (captured ones counted). */
+/* The dedispersion variant in use, the autotuner's best median tuning time
+ * (ms, 0 if not tuned) and the kernel launches of the last call (captured ones
+ * counted). */
 gsp_status gsp_batch_info(gsp_batch_t b, int32_t *variant, float *tuned_ms, int32_t *launches);
+
+/* The autotuner's measurements (a tuning knob with no paper counterpart):
+ * writes up to cap (variant, median ms) pairs, one per tile variant it timed,
+ * to the host arrays variants and ms (either may be NULL) and returns how many
+ * it timed (0 before tuning, -1 for a NULL batch or cap < 0).  A variant is
+ * timed if it fits every beam's largest in-block delay spread; each is run
+ * three times over every beam's first 65536 output samples. */
+int32_t gsp_batch_tune_results(gsp_batch_t b, int32_t *variants, float *ms, int32_t cap);
 
 /* Ingest transpose (the optional first step of the path): time-major 8-bit
  * samples d_in[t][c] (the order of PSRFITS files and of Alg. 2's numpts x

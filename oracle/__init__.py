@@ -31,6 +31,8 @@ def lib():
         L.oracle_max_delay.restype = i64
         L.oracle_dedisperse.argtypes = [vp, i64, i64, i64, vp, i64, vp, i64, i64, vp]
         L.oracle_dedisperse.restype = ctypes.c_int
+        L.oracle_row_sums.argtypes = [vp, i64, i64, i64, vp, i64, i64, vp, vp]
+        L.oracle_row_sums.restype = ctypes.c_int
         L.oracle_lower_median.argtypes = [vp, i64]
         L.oracle_lower_median.restype = dbl
         L.oracle_search_row.argtypes = [vp, i64, i32, vp, vp, i64, vp, vp, vp, vp, vp, vp, vp, vp]
@@ -109,6 +111,25 @@ def dedisperse(x, n_in, dl, rows=None, n_out=None):
     if rc != 0:
         raise ValueError("oracle_dedisperse failed (%d)" % rc)
     return out
+
+
+def row_sums(x, n_in, dl, n_out=None):
+    """Exact int64 (sum_t D[d][t], sum_t t*D[d][t]) of every DM row from channel
+    prefix sums, without dedispersing (the full-coverage identities of the
+    plain sum of Alg. 2/3)."""
+    x = np.ascontiguousarray(x, dtype=np.uint8)
+    dl = np.ascontiguousarray(dl, dtype=np.int32)
+    nchan, stride = x.shape
+    ndm = dl.shape[0]
+    if n_out is None:
+        n_out = n_in - max_delay(dl)
+    s0 = np.empty(ndm, np.int64)
+    s1 = np.empty(ndm, np.int64)
+    rc = lib().oracle_row_sums(_ptr(x), nchan, n_in, stride, _ptr(dl), ndm, n_out, _ptr(s0),
+                               _ptr(s1))
+    if rc != 0:
+        raise ValueError("oracle_row_sums failed (%d)" % rc)
+    return s0, s1
 
 
 def _params(block_len, window_len, t_offset, threshold, bad_lo, bad_hi, widths):

@@ -134,6 +134,63 @@ int oracle_dedisperse(const uint8_t *x, int64_t nchan, int64_t n_in,
     return ORACLE_OK;
 }
 
+/* Row invariants of the dedispersed series, computed without dedispersing:
+ * the full-coverage identities of the plain sum above.  With the channel
+ * prefix sums P_c[u] = sum_{v<u} X[c][v] and Q_c[u] = sum_{v<u} v X[c][v],
+ * for every DM row d and a = delays[d][c], b = a + n_out:
+ *   s0[d] = sum_t D[d][t]   = sum_c (P_c[b] - P_c[a])
+ *   s1[d] = sum_t t D[d][t] = sum_c (Q_c[b] - Q_c[a]) - a (P_c[b] - P_c[a]).
+ * O(nchan (n_in + ndm)) work, so every row of a full-size series can be
+ * checked exactly.  s0, s1: int64 [ndm]. */
+int oracle_row_sums(const uint8_t *x, int64_t nchan, int64_t n_in, int64_t x_stride,
+                    const int32_t *delays, int64_t ndm, int64_t n_out, int64_t *s0,
+                    int64_t *s1) {
+    if (!x || !delays || !s0 || !s1 || nchan <= 0 || ndm <= 0 || n_out < 0 || x_stride < n_in)
+        return ORACLE_EINVAL;
+    for (int64_t i = 0; i < ndm * nchan; i++)
+        if (delays[i] < 0 || delays[i] + n_out > n_in) return ORACLE_EINVAL;
+    for (int64_t d = 0; d < ndm; d++) s0[d] = s1[d] = 0;
+    int err = 0;
+#pragma omp parallel
+    {
+        int64_t *P = malloc((size_t)(n_in + 1) * sizeof(int64_t));
+        int64_t *Q = malloc((size_t)(n_in + 1) * sizeof(int64_t));
+        int64_t *a0 = calloc((size_t)ndm, sizeof(int64_t));
+        int64_t *a1 = calloc((size_t)ndm, sizeof(int64_t));
+        if (!P || !Q || !a0 || !a1) {
+#pragma omp atomic write
+            err = 1;
+        } else {
+            int64_t c;
+#pragma omp for schedule(dynamic, 4)
+            for (c = 0; c < nchan; c++) {
+                const uint8_t *xc = x + c * x_stride;
+                P[0] = Q[0] = 0;
+                for (int64_t u = 0; u < n_in; u++) {
+                    P[u + 1] = P[u] + (int64_t)xc[u];
+                    Q[u + 1] = Q[u] + u * (int64_t)xc[u];
+                }
+                for (int64_t d = 0; d < ndm; d++) {
+                    const int64_t a = delays[d * nchan + c], b = a + n_out;
+                    const int64_t dp = P[b] - P[a];
+                    a0[d] += dp;
+                    a1[d] += (Q[b] - Q[a]) - a * dp;
+                }
+            }
+#pragma omp critical
+            for (int64_t d = 0; d < ndm; d++) {
+                s0[d] += a0[d];
+                s1[d] += a1[d];
+            }
+        }
+        free(P);
+        free(Q);
+        free(a0);
+        free(a1);
+    }
+    return err ? ORACLE_ENOMEM : ORACLE_OK;
+}
+
 /* ---------------------------------------------------------------- search */
 
 typedef struct {

@@ -6,8 +6,10 @@
 // GSP_BATCH_GRAPH the whole enqueue sequence (block-sum resets, the batched
 // dedispersion, every beam's search kernels) is captured once into a CUDA
 // graph and replayed while the inputs stay the same; with GSP_BATCH_AUTOTUNE
-// the first call times every compatible tile variant of the dedispersion
-// kernel on the actual inputs and keeps the fastest.
+// the first call times the dedispersion kernel's tile variants that fit the
+// batch (channels per stage, DM trials per block, samples per tile, visiting
+// order) on the actual inputs, each three times on every beam's first
+// kTuneSamples output samples, and keeps the one with the smallest median.
 #include <algorithm>
 #include <cstring>
 #include <new>
@@ -19,7 +21,10 @@ struct gsp_batch_s {
     std::vector<gsp_plan_t> plans;
     int32_t flags = 0;
     int variant = -1;
-    float tuned_ms = 0.f;
+    float tuned_ms = 0.f;   // median time of the fastest tuning run (ms)
+    int32_t tune_tried = 0;  // variants the autotuner timed
+    std::vector<int32_t> tune_variant;  // every timed candidate and its median (ms)
+    std::vector<float> tune_ms;
     std::vector<gsp_beam_input> last;  // inputs the graph was captured for
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -31,6 +36,9 @@ struct gsp_batch_s {
 };
 
 namespace {
+
+constexpr int64_t kTuneSamples = 65536;  // output samples per beam of a tuning run
+constexpr int kTuneReps = 3;             // timed runs per candidate (median kept)
 
 bool same_inputs(const std::vector<gsp_beam_input> &a, const gsp_beam_input *b, size_t n) {
     if (a.size() != n) return false;
@@ -87,6 +95,8 @@ gsp_status enqueue(gsp_batch_s *b, const gsp_beam_input *in, int variant, cudaSt
                                bl[i].bsum, s, nlaunch) != cudaSuccess)
             return GSP_ERR_CUDA;
         p->last_stream = s;
+        p->last_D = bl[i].out;
+        p->last_stride = bl[i].out_stride;
         p->last_nout = n_out[i];
         p->last_nb = n_out[i] / p->desc.block_len;
         p->have_search = true;
@@ -95,6 +105,46 @@ gsp_status enqueue(gsp_batch_s *b, const gsp_beam_input *in, int variant, cudaSt
                      cudaSuccess)
         return GSP_ERR_CUDA;
     return GSP_OK;
+}
+
+// Median device time (ms) of kTuneReps batched dedispersion launches of
+// variant v over every beam's first kTuneSamples output samples (series into
+// the plans' scratch, no block sums); < 0 if the variant cannot run.
+float time_variant(gsp_batch_s *b, const gsp_beam_input *in, int v, cudaStream_t s,
+                   cudaEvent_t e0, cudaEvent_t e1) {
+    const int nb = (int)b->plans.size();
+    std::vector<gsp::BeamLaunch> bl((size_t)nb);
+    for (int i = 0; i < nb; i++) {
+        gsp_plan_s *p = b->plans[i];
+        if (!gsp::dedisperse_variant_usable(p, v)) return -1.f;
+        int64_t n_out = 0, stride = 0;
+        int32_t *D = nullptr;
+        unsigned long long *bsum = nullptr;
+        if (gsp::plan_check_input(p, in[i].d_x, in[i].n_in, in[i].x_stride, &n_out) != GSP_OK ||
+            gsp::plan_prepare_search(p, n_out, &D, &stride, &bsum) != GSP_OK)
+            return -1.f;
+        const int64_t n = std::min<int64_t>(n_out, kTuneSamples);
+        bl[i] = gsp::BeamLaunch{p, in[i].d_x, n + p->max_delay, in[i].x_stride, n, D, stride,
+                                nullptr};
+    }
+    gsp_plan_s *p0 = b->plans[0];
+    std::vector<float> ms;
+    for (int r = 0; r <= kTuneReps; r++) {  // run 0 warms up and sets the kernel's attributes
+        int32_t nl = 0;
+        if (cudaEventRecord(e0, s) != cudaSuccess) return -1.f;
+        if (gsp::launch_dedisperse_batch(bl.data(), nb, v, (b->flags & GSP_BATCH_PERSISTENT) != 0,
+                                         p0->num_sms, p0->d_err, s, &nl) != cudaSuccess) {
+            (void)cudaGetLastError();
+            return -1.f;
+        }
+        float t = 0.f;
+        if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+            cudaEventElapsedTime(&t, e0, e1) != cudaSuccess)
+            return -1.f;
+        if (r > 0) ms.push_back(t);
+    }
+    std::sort(ms.begin(), ms.end());
+    return ms[ms.size() / 2];
 }
 
 }  // namespace
@@ -111,11 +161,15 @@ gsp_status gsp_batch_create(gsp_batch_t *out, const gsp_plan_t *plans, int32_t n
         for (int j = 0; j < i; j++)
             if (plans[j] == plans[i]) return GSP_ERR_INVALID_ARG;  // one plan per beam
     }
+    // one tile variant for all beams: the beams' own if it fits every beam's
+    // delay spread, else the first automatic choice that does
+    const int variant = gsp::dedisperse_choose_variant(plans, nbeams);
+    if (variant < 0) return GSP_ERR_INVALID_ARG;
     gsp_batch_s *b = new (std::nothrow) gsp_batch_s();
     if (!b) return GSP_ERR_OOM;
     b->plans.assign(plans, plans + nbeams);
     b->flags = flags;
-    b->variant = plans[0]->geom.variant;
+    b->variant = variant;
     if (flags & GSP_BATCH_TIMING)
         for (auto &e : b->ev)
             if (cudaEventCreate(&e) != cudaSuccess) {
@@ -143,38 +197,27 @@ gsp_status gsp_batch_search(gsp_batch_t b, const gsp_beam_input *in, void *strea
     const size_t nb = b->plans.size();
     b->launches = 0;
     if ((b->flags & GSP_BATCH_AUTOTUNE) && b->tuned_ms == 0.f) {
-        // time every variant that fits this batch; keep the fastest
-        cudaEvent_t e0, e1;
-        if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+        // time every candidate variant that fits this batch; keep the fastest median
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+            if (e0) cudaEventDestroy(e0);
             return GSP_ERR_CUDA;
+        }
         int best = -1;
         float best_ms = 0.f;
         const int *cand = nullptr;
         const int ncand = gsp::dedisperse_tune_candidates(&cand);
+        b->tune_tried = 0;
+        b->tune_variant.clear();
+        b->tune_ms.clear();
         for (int ci = 0; ci < ncand; ci++) {
-            const int v = cand[ci];
-            int32_t nl = 0;
-            gsp_status st = enqueue(b, in, v, s, &nl);  // warm-up (also sets attributes)
-            if (st == GSP_ERR_CUDA) {
-                (void)cudaGetLastError();
-                continue;  // variant does not fit (shared memory), skip it
-            }
-            if (cudaStreamSynchronize(s) != cudaSuccess) return GSP_ERR_CUDA;
-            if (st != GSP_OK) return st;
-            cudaError_t ce = cudaEventRecord(e0, s);
-            if (ce == cudaSuccess && enqueue(b, in, v, s, &nl) != GSP_OK) ce = cudaErrorLaunchFailure;
-            if (ce == cudaSuccess) ce = cudaEventRecord(e1, s);
-            if (ce == cudaSuccess) ce = cudaEventSynchronize(e1);
-            float ms = 0.f;
-            if (ce == cudaSuccess) ce = cudaEventElapsedTime(&ms, e0, e1);
-            if (ce != cudaSuccess) {
-                gsp::record_error(ce, "batch autotune timing");
-                cudaEventDestroy(e0);
-                cudaEventDestroy(e1);
-                return GSP_ERR_CUDA;
-            }
+            const float ms = time_variant(b, in, cand[ci], s, e0, e1);
+            if (ms < 0.f) continue;
+            b->tune_tried++;
+            b->tune_variant.push_back(cand[ci]);
+            b->tune_ms.push_back(ms);
             if (best < 0 || ms < best_ms) {
-                best = v;
+                best = cand[ci];
                 best_ms = ms;
             }
         }
@@ -252,6 +295,16 @@ gsp_status gsp_batch_timing(gsp_batch_t b, float *ms_dedisperse, float *ms_total
     if (ms_dedisperse) *ms_dedisperse = a;
     if (ms_total) *ms_total = t;
     return GSP_OK;
+}
+
+int32_t gsp_batch_tune_results(gsp_batch_t b, int32_t *variants, float *ms, int32_t cap) {
+    if (!b || cap < 0) return -1;
+    const int32_t n = (int32_t)b->tune_variant.size();
+    for (int32_t i = 0; i < std::min(n, cap); i++) {
+        if (variants) variants[i] = b->tune_variant[i];
+        if (ms) ms[i] = b->tune_ms[i];
+    }
+    return n;
 }
 
 gsp_status gsp_batch_info(gsp_batch_t b, int32_t *variant, float *tuned_ms, int32_t *launches) {

@@ -99,8 +99,9 @@ struct BeamTile {
     int64_t n_out;
     const int32_t *delays;  // [ndm][nchan]
     const int32_t *blkmin;  // [nblk][nchan]
-    const int32_t *dpos;    // [ndm][nchan] (delay << 8) | list position (64-channel stages)
-    const uint32_t *fcnt;   // [ndm][nst64] channels per phase family, 4 x 8 bits
+    const int32_t *dpos;    // [ndm][nchan] (delay << 8) | list position (stages of the variant's width)
+    const uint32_t *fcnt;   // [ndm][nst] channels per phase family, 4 x 8 bits
+    const int32_t *stspread;  // [nst] largest in-block delay spread of each stage's channels
     int32_t *out;
     int64_t out_stride;
     unsigned long long *bsum;  // optional [ndm][nb_max][3] block sums {S0, S1, S2}
@@ -322,7 +323,8 @@ template <int KW, bool QUAD, int ACC, bool A32 = false, int M = 4, int CB = 32, 
           bool PRE = false, bool MF = false, int KDM = 16, int UNR = 2, bool IMA = false>
 __global__ void __launch_bounds__((KDM / KW + 1) * 32, (KDM / KW + 1) * 32 <= 256 ? 2 : 1)
     dd_tiled_kernel(const TiledArgs a) {
-    static_assert(!PRE || (KW == 1 && CB == 64), "precomputed lists: one DM per warp, 64-channel stages");
+    static_assert(!PRE || (KW == 1 && (CB == 64 || CB == 32)),
+                  "precomputed lists: one DM per warp, 32- or 64-channel stages");
     static_assert(!MF || (ACC >= 3 && !FF), "merged flush: raw + odd views, all families together");
     constexpr int kCB = CB;
     constexpr int kH = CB / 32;                  // channels per lane per stage
@@ -373,6 +375,9 @@ __global__ void __launch_bounds__((KDM / KW + 1) * 32, (KDM / KW + 1) * 32 <= 25
                     break;
                 }
             }
+            // this stage's window: the tile plus the largest in-block delay spread of
+            // its own channels (at most a.win, the slot pitch set by the widest stage)
+            const int64_t wst = min((int64_t)a.win, (int64_t)((kT + 30 + bt.stspread[st]) & ~15));
             int64_t s_c[kH], avail[kH];
             uint32_t len16[kH];
             uint32_t tot = 0;
@@ -385,7 +390,7 @@ __global__ void __launch_bounds__((KDM / KW + 1) * 32, (KDM / KW + 1) * 32 <= 25
                 if (c < a.nchan) {
                     s_c[h] = (t0 + bmin[c]) & ~(int64_t)15;
                     avail[h] = bt.n_in - s_c[h];
-                    len16[h] = (uint32_t)min((int64_t)a.win, avail[h] & ~(int64_t)15);
+                    len16[h] = (uint32_t)min(wst, avail[h] & ~(int64_t)15);
                 }
                 tot += len16[h];
             }
@@ -405,7 +410,7 @@ __global__ void __launch_bounds__((KDM / KW + 1) * 32, (KDM / KW + 1) * 32 <= 25
                     ptx::bulk_g2s(ptx::smem_addr(dst), src, len16[h], full(slot));
                 }
                 if (c < a.nchan) {
-                    const int64_t end = min((int64_t)a.win, avail[h]);
+                    const int64_t end = min(wst, avail[h]);
                     for (int64_t i = len16[h]; i < end; i++)
                         dst[i] = bt.x[(int64_t)c * bt.x_stride + s_c[h] + i];
                 }
@@ -849,30 +854,81 @@ const TiledVariant kVariants[] = {
     {dd_tiled_kernel<1, false, 4, true, 6, 64, false, true, true, 15, 2, true>, 1, 6, 64, true, 15},
     {dd_tiled_kernel<1, false, 3, true, 6, 32, false, false, true, 7, 2, true>, 1, 6, 32, false, 7},
     {dd_tiled_kernel<1, false, 3, true, 4, 32, false, false, true, 7, 2, true>, 1, 4, 32, false, 7},
+    // 32-channel stages with precomputed lists (plans whose delay spread leaves
+    // the 64-channel stages fewer than two ring slots: wide bands, coarse DM steps)
+    {dd_tiled_kernel<1, false, 3, true, 6, 32, false, true, true, 15, 2, true>, 1, 6, 32, true, 15},
+    {dd_tiled_kernel<1, false, 3, true, 4, 32, false, true, true, 15, 2, true>, 1, 4, 32, true, 15},
+    {dd_tiled_kernel<1, false, 3, true, 6, 32, false, true, true, 7, 2, true>, 1, 6, 32, true, 7},
 };
 constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
 
-// Shared memory a CTA of variant v may use: all of an SM's 227 KB, or half of
-// it (less the per-CTA reserve) for CTAs of at most 8 warps, two per SM.
-int ctas_per_sm(const TiledVariant &v) { return (v.kdm / v.kw + 1) * 32 <= 256 ? 2 : 1; }
-int64_t smem_budget(const TiledVariant &v) {
-    return ctas_per_sm(v) == 2 ? 112 * 1024 : 227 * 1024;
+constexpr int kDefaultVariant = 32;  // 15 DMs x 768 samples, 64-channel stages, precomputed lists
+
+// Variants tried in order when a plan is created; the first whose stages fit
+// at least two ring slots is taken: the default; the same tile with 32-channel
+// stages (half the shared memory per stage); ballot-sorted lists for delays of
+// 2^23 samples or more; 7-DM blocks (half the in-block spread).  Measured on
+// GB300 (fraction of the integer-issue roofline): 64-channel stages with two
+// slots 0.675 against 0.617 for 32-channel stages with five (2500 trials to DM
+// 1500); on the wide band 32-channel stages with two slots 0.610, 7-DM blocks
+// 0.40 (one CTA per SM) and 0.49 (two per SM, 4 words per lane).
+const int kAutoList[] = {32, 42, 34, 44, 40, 41};
+
+// Variants the batch autotuner times (those that fit the batch are timed).
+const int kTuneList[] = {32, 42, 35, 31, 22, 43, 44, 36, 34, 40};
+
+// Shared memory of one CTA: all of an SM's 227 KB, or half of it (less the
+// per-CTA reserve) for CTAs of at most 8 warps that run two per SM.
+constexpr int64_t kSmemOne = 227 * 1024;
+constexpr int64_t kSmemTwo = 112 * 1024;
+
+TileFit fit_variant(const TiledVariant &v, int64_t spread) {
+    TileFit f;
+    const int kT = 128 * v.m;
+    const int64_t win = (kT + 15 + spread + 15) & ~(int64_t)15;
+    const int64_t fixed = (int64_t)v.kdm * 4 * v.cb * 4 + 2 * 8 * 8;
+    const bool small = (v.kdm / v.kw + 1) * 32 <= 256;
+    // small CTAs run two per SM when two stages fit in half the shared memory,
+    // else one per SM with all of it
+    for (int two = small ? 1 : 0; two >= 0; two--) {
+        const int64_t budget = two ? kSmemTwo : kSmemOne;
+        const int64_t stages = std::min<int64_t>(8, (budget - fixed) / ((int64_t)v.cb * win));
+        if (stages >= 2) {
+            f.ok = true;
+            f.win = (int)win;
+            f.stages = (int)stages;
+            f.smem = (int)(stages * v.cb * win + fixed);
+            f.ctas_per_sm = two ? 2 : 1;
+            return f;
+        }
+    }
+    return f;
 }
-constexpr int kDefaultVariant = 32;
-constexpr int kFallbackVariant = 34;  // default when the precomputed lists are unavailable
+
+bool lists_ok(const TiledVariant &v, bool have_lists) { return !v.pre || have_lists; }
+
+// The first variant of the automatic list that fits; -1 if none does.
+int choose_auto(const int64_t (&spread)[kNumKdm], const bool (&have_lists)[kNumCb]) {
+    for (int v : kAutoList) {
+        const TiledVariant &tv = kVariants[v];
+        if (!lists_ok(tv, have_lists[cb_index(tv.cb)])) continue;
+        if (fit_variant(tv, spread[kdm_index(tv.kdm)]).ok) return v;
+    }
+    return -1;
+}
 
 }  // namespace
 
-void plan_phase_lists(const gsp_plan_s *p, std::vector<int32_t> *dpos,
+void plan_phase_lists(const gsp_plan_s *p, int cb, std::vector<int32_t> *dpos,
                       std::vector<uint32_t> *fcnt) {
-    // Phase-sorted lists of 64-channel stages, per DM: channel c of stage st
+    // Phase-sorted lists of cb-channel stages, per DM: channel c of stage st
     // (in channel order within its family) is filed at position
-    // P * 64 + rank, P = delay & 3, and the stage's four family sizes are
+    // P * cb + rank, P = delay & 3, and the stage's four family sizes are
     // packed 8 bits each.  The phase of a (channel, DM) pair is the same in
     // every time tile because tiles start at multiples of 4 samples and the
     // staged windows at multiples of 16 bytes.
     const int C = p->desc.nchan, ndm = p->desc.ndm;
-    const int nst = (C + 63) / 64;
+    const int nst = (C + cb - 1) / cb;
     dpos->clear();
     fcnt->clear();
     if (p->max_delay >= ((int64_t)1 << 23)) return;  // packed delay field is 23 bits
@@ -882,9 +938,9 @@ void plan_phase_lists(const gsp_plan_s *p, std::vector<int32_t> *dpos,
         const int32_t *dl = p->delays_h.data() + (size_t)d * C;
         for (int st = 0; st < nst; st++) {
             uint32_t cnt[4] = {0, 0, 0, 0};
-            for (int c = st * 64; c < std::min(C, st * 64 + 64); c++) {
+            for (int c = st * cb; c < std::min(C, st * cb + cb); c++) {
                 const int P = dl[c] & 3;
-                (*dpos)[(size_t)d * C + c] = (int32_t)(((uint32_t)dl[c] << 8) | (uint32_t)(P * 64 + cnt[P]));
+                (*dpos)[(size_t)d * C + c] = (int32_t)(((uint32_t)dl[c] << 8) | (uint32_t)(P * cb + cnt[P]));
                 cnt[P]++;
             }
             (*fcnt)[(size_t)d * nst + st] = cnt[0] | (cnt[1] << 8) | (cnt[2] << 16) | (cnt[3] << 24);
@@ -892,18 +948,18 @@ void plan_phase_lists(const gsp_plan_s *p, std::vector<int32_t> *dpos,
     }
 }
 
-bool plan_dedisperse_tiled(gsp_plan_s *p, std::vector<int32_t> (&blkmin)[kNumKdm],
-                           bool have_lists) {
+bool plan_dedisperse_tiled(gsp_plan_s *p, TiledTables *tab) {
     const int C = p->desc.nchan, ndm = p->desc.ndm;
     DDGeom &g = p->geom;
     // DM blocks of each supported block size: per-block minimum delay of every
-    // channel, the largest delay spread inside a block, and the L2 grouping
+    // channel, the largest delay spread inside a block (overall and per stage
+    // of either width), and the L2 grouping
     for (int o = 0; o < kNumKdm; o++) {
         const int kdm = kKdmSizes[o];
         const int nblk = (ndm + kdm - 1) / kdm;
-        std::vector<int32_t> &bm = blkmin[o];
+        std::vector<int32_t> &bm = tab->blkmin[o];
         bm.assign((size_t)nblk * C, 0);
-        int64_t spread = 0;
+        std::vector<int64_t> chspread((size_t)C, 0);  // per channel, over all blocks
         for (int b = 0; b < nblk; b++) {
             for (int c = 0; c < C; c++) {
                 int32_t lo = INT32_MAX, hi = 0;
@@ -913,8 +969,17 @@ bool plan_dedisperse_tiled(gsp_plan_s *p, std::vector<int32_t> (&blkmin)[kNumKdm
                     hi = std::max(hi, v);
                 }
                 bm[(size_t)b * C + c] = lo;
-                spread = std::max<int64_t>(spread, (int64_t)hi - lo);
+                chspread[c] = std::max<int64_t>(chspread[c], (int64_t)hi - lo);
             }
+        }
+        int64_t spread = 0;
+        for (int c = 0; c < C; c++) spread = std::max(spread, chspread[c]);
+        for (int i = 0; i < kNumCb; i++) {
+            const int cb = kCbSizes[i];
+            std::vector<int32_t> &ss = tab->stspread[o][i];
+            ss.assign((size_t)((C + cb - 1) / cb), 0);
+            for (int c = 0; c < C; c++)
+                ss[c / cb] = std::max(ss[c / cb], (int32_t)chspread[c]);
         }
         g.nblk[o] = nblk;
         g.spread[o] = spread;
@@ -941,41 +1006,93 @@ bool plan_dedisperse_tiled(gsp_plan_s *p, std::vector<int32_t> (&blkmin)[kNumKdm
             }
         }
     }
-    // GSP_DD_VARIANT selects a tuning variant of the tiled kernel.
-    int variant = kDefaultVariant;
+    bool have_lists[kNumCb];
+    for (int i = 0; i < kNumCb; i++) {
+        plan_phase_lists(p, kCbSizes[i], &tab->dpos[i], &tab->fcnt[i]);
+        have_lists[i] = !tab->dpos[i].empty();
+    }
+    // GSP_DD_VARIANT selects a tuning variant of the tiled kernel if it fits
+    // this plan; otherwise the automatic choice.
+    int variant = -1;
     if (const char *v = std::getenv("GSP_DD_VARIANT")) {
         const int k = std::atoi(v);
-        if (k >= 0 && k < kNumVariants) variant = k;
+        if (k >= 0 && k < kNumVariants && lists_ok(kVariants[k], have_lists[cb_index(kVariants[k].cb)]) &&
+            fit_variant(kVariants[k], g.spread[kdm_index(kVariants[k].kdm)]).ok)
+            variant = k;
     }
-    if (kVariants[variant].pre && !have_lists) variant = kFallbackVariant;
-    const TiledVariant &v = kVariants[variant];
-    const int o = kdm_index(v.kdm);
-    const int kT = 128 * v.m;
-    const int64_t win = (kT + 15 + g.spread[o] + 15) & ~(int64_t)15;
-    const int64_t fixed = (int64_t)v.kdm * 4 * v.cb * 4 + 2 * 8 * 8;
-    const int64_t stages = std::min<int64_t>(8, (smem_budget(v) - fixed) / ((int64_t)v.cb * win));
-    if (stages < 2) {
-        for (auto &b : blkmin) b.clear();
+    if (variant < 0) variant = choose_auto(g.spread, have_lists);
+    if (variant < 0) {
+        *tab = TiledTables();
         return false;
     }
+    const TiledVariant &v = kVariants[variant];
+    const TileFit f = fit_variant(v, g.spread[kdm_index(v.kdm)]);
     g.kdm = v.kdm;
-    g.t_cta = kT;
-    g.t_eff = kT - 4;
+    g.t_cta = 128 * v.m;
+    g.t_eff = 128 * v.m - 4;
     g.cb = v.cb;
-    g.win = (int)win;
-    g.stages = (int)stages;
-    g.smem = (int)(stages * v.cb * win + fixed);
+    g.win = f.win;
+    g.stages = f.stages;
+    g.smem = f.smem;
+    g.ctas_per_sm = f.ctas_per_sm;
     g.variant = variant;
     return true;
 }
 
 int dedisperse_num_variants() { return kNumVariants; }
 
-// Variants the batch autotuner times (the fastest family on this GPU).
-const int kTuneList[] = {32, 35, 31, 22};
 int dedisperse_tune_candidates(const int **list) {
     *list = kTuneList;
     return (int)(sizeof(kTuneList) / sizeof(kTuneList[0]));
+}
+
+TileFit dedisperse_fit(int variant, const int64_t (&spread)[kNumKdm]) {
+    if (variant < 0 || variant >= kNumVariants) return TileFit();
+    const TiledVariant &v = kVariants[variant];
+    return fit_variant(v, spread[kdm_index(v.kdm)]);
+}
+
+bool dedisperse_variant_usable(const gsp_plan_s *p, int variant) {
+    if (!p || p->simple_dd || variant < 0 || variant >= kNumVariants) return false;
+    const TiledVariant &v = kVariants[variant];
+    const int o = kdm_index(v.kdm), ci = cb_index(v.cb);
+    if (!p->d_blkmin[o] || !p->d_stspread[o][ci]) return false;
+    if (v.pre && (!p->d_dpos[ci] || !p->d_fcnt[ci])) return false;
+    return fit_variant(v, p->geom.spread[o]).ok;
+}
+
+void dedisperse_set_variant(gsp_plan_s *p, int variant) {
+    const TiledVariant &v = kVariants[variant];
+    const TileFit f = fit_variant(v, p->geom.spread[kdm_index(v.kdm)]);
+    DDGeom &g = p->geom;
+    g.kdm = v.kdm;
+    g.t_cta = 128 * v.m;
+    g.t_eff = 128 * v.m - 4;
+    g.cb = v.cb;
+    g.win = f.win;
+    g.stages = f.stages;
+    g.smem = f.smem;
+    g.ctas_per_sm = f.ctas_per_sm;
+    g.variant = variant;
+}
+
+int dedisperse_choose_variant(const gsp_plan_s *const *plans, int nplans) {
+    if (nplans < 1) return -1;
+    int64_t spread[kNumKdm] = {};
+    bool have_lists[kNumCb] = {true, true};
+    for (int i = 0; i < nplans; i++) {
+        if (!plans[i] || plans[i]->simple_dd) return -1;
+        for (int o = 0; o < kNumKdm; o++) spread[o] = std::max(spread[o], plans[i]->geom.spread[o]);
+        for (int c = 0; c < kNumCb; c++) have_lists[c] = have_lists[c] && plans[i]->d_dpos[c];
+    }
+    // the plans' common variant if it fits the batch, else the automatic choice
+    const int v0 = plans[0]->geom.variant;
+    bool same = true;
+    for (int i = 1; i < nplans; i++) same = same && plans[i]->geom.variant == v0;
+    if (same && lists_ok(kVariants[v0], have_lists[cb_index(kVariants[v0].cb)]) &&
+        fit_variant(kVariants[v0], spread[kdm_index(kVariants[v0].kdm)]).ok)
+        return v0;
+    return choose_auto(spread, have_lists);
 }
 
 cudaError_t launch_dedisperse_batch(const BeamLaunch *beams, int nbeams, int variant,
@@ -984,26 +1101,25 @@ cudaError_t launch_dedisperse_batch(const BeamLaunch *beams, int nbeams, int var
     if (nbeams < 1 || nbeams > kMaxBatchBeams || variant < 0 || variant >= kNumVariants)
         return cudaErrorInvalidValue;
     const TiledVariant &v = kVariants[variant];
-    const int o = kdm_index(v.kdm);
+    const int o = kdm_index(v.kdm), ci = cb_index(v.cb);
     const int t_cta = 128 * v.m, t_eff = t_cta - 4;
     const int nchan = beams[0].plan->desc.nchan;
-    int64_t win = 0;
+    int64_t spread = 0;
     for (int b = 0; b < nbeams; b++) {
         const gsp_plan_s *p = beams[b].plan;
-        if (p->desc.nchan != nchan || !p->d_blkmin[o]) return cudaErrorInvalidValue;
-        if (v.pre && (!p->d_dpos || !p->d_fcnt)) return cudaErrorInvalidValue;
-        win = std::max<int64_t>(win, (t_cta + 15 + p->geom.spread[o] + 15) & ~(int64_t)15);
+        if (p->desc.nchan != nchan || !p->d_blkmin[o] || !p->d_stspread[o][ci])
+            return cudaErrorInvalidValue;
+        if (v.pre && (!p->d_dpos[ci] || !p->d_fcnt[ci])) return cudaErrorInvalidValue;
+        spread = std::max(spread, p->geom.spread[o]);
     }
-    const int64_t fixed = (int64_t)v.kdm * 4 * v.cb * 4 + 2 * 8 * 8;
-    const int64_t stages = std::min<int64_t>(8, (smem_budget(v) - fixed) / ((int64_t)v.cb * win));
-    if (stages < 2) return cudaErrorInvalidValue;
-    const int smem = (int)(stages * v.cb * win + fixed);
+    const TileFit f = fit_variant(v, spread);
+    if (!f.ok) return cudaErrorInvalidValue;
     static int configured_smem[kNumVariants] = {0};
-    if (smem > configured_smem[variant]) {
+    if (f.smem > configured_smem[variant]) {
         cudaError_t e = cudaFuncSetAttribute(v.fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             smem);
+                                             f.smem);
         if (e != cudaSuccess) return e;
-        configured_smem[variant] = smem;
+        configured_smem[variant] = f.smem;
     }
     TiledArgs a;
     std::memset(&a, 0, sizeof(a));
@@ -1018,8 +1134,9 @@ cudaError_t launch_dedisperse_batch(const BeamLaunch *beams, int nbeams, int var
         bt.n_out = in.n_out;
         bt.delays = p->d_delays;
         bt.blkmin = p->d_blkmin[o];
-        bt.dpos = p->d_dpos;
-        bt.fcnt = p->d_fcnt;
+        bt.dpos = p->d_dpos[ci];
+        bt.fcnt = p->d_fcnt[ci];
+        bt.stspread = p->d_stspread[o][ci];
         bt.out = in.out;
         bt.out_stride = in.out_stride;
         bt.bsum = in.bsum;
@@ -1036,14 +1153,14 @@ cudaError_t launch_dedisperse_batch(const BeamLaunch *beams, int nbeams, int var
     }
     a.nbeams = nbeams;
     a.nchan = nchan;
-    a.win = (int)win;
-    a.stages = (int)stages;
+    a.win = f.win;
+    a.stages = f.stages;
     a.one = 1u;
     a.err = err;
     a.items = items;
-    int64_t grid = persistent ? std::min<int64_t>(items, (int64_t)num_sms * ctas_per_sm(v)) : items;
+    int64_t grid = persistent ? std::min<int64_t>(items, (int64_t)num_sms * f.ctas_per_sm) : items;
     if (grid < 1 || grid > 0x7fffffffll) return cudaErrorInvalidConfiguration;
-    v.fn<<<(unsigned)grid, (v.kdm / v.kw + 1) * 32, smem, s>>>(a);
+    v.fn<<<(unsigned)grid, (v.kdm / v.kw + 1) * 32, f.smem, s>>>(a);
     *nlaunch += 1;
     return cudaGetLastError();
 }

@@ -88,8 +88,10 @@ void free_plan(gsp_plan_s *p) {
     if (!p) return;
     cudaFree(p->d_delays);
     for (auto *b : p->d_blkmin) cudaFree(b);
-    cudaFree(p->d_dpos);
-    cudaFree(p->d_fcnt);
+    for (auto *b : p->d_dpos) cudaFree(b);
+    for (auto *b : p->d_fcnt) cudaFree(b);
+    for (auto &row : p->d_stspread)
+        for (auto *b : row) cudaFree(b);
     cudaFree(p->d_err);
     cudaFree(p->d_bsum);
     cudaFree(p->d_sigma_b);
@@ -202,6 +204,8 @@ gsp_status run_search(gsp_plan_s *p, const int32_t *D, int64_t n_out, int64_t st
         return GSP_ERR_CUDA;
     }
     p->last_stream = s;
+    p->last_D = D;
+    p->last_stride = stride;
     p->last_nout = n_out;
     p->last_nb = n_out / p->desc.block_len;
     p->have_search = true;
@@ -325,23 +329,25 @@ gsp_status gsp_plan_create(gsp_plan_t *out, const gsp_plan_desc *d) {
         delete p;
         return GSP_ERR_CUDA;
     }
-    std::vector<int32_t> blkmin[gsp::kNumKdm], dpos;
-    std::vector<uint32_t> fcnt;
-    if (!p->simple_dd) gsp::plan_phase_lists(p, &dpos, &fcnt);
-    if (!p->simple_dd && !gsp::plan_dedisperse_tiled(p, blkmin, !dpos.empty())) p->simple_dd = true;
-    if (p->simple_dd) {
-        dpos.clear();
-        fcnt.clear();
-    }
+    // tiled-kernel tables; the simple kernel only when asked for, or when no
+    // tiled variant fits the delay spread (gsp_dedisperse_variants reports it)
+    gsp::TiledTables tab;
+    if (!p->simple_dd && !gsp::plan_dedisperse_tiled(p, &tab)) p->simple_dd = true;
 
     p->nb_max = std::max<int64_t>(d->nsamp_max / d->block_len, 1);
     const size_t rows_blocks = (size_t)ndm * (size_t)p->nb_max;
     gsp_status st = GSP_OK;
     if (st == GSP_OK) st = dalloc(&p->d_delays, (size_t)(C * ndm));
-    for (int o = 0; o < gsp::kNumKdm; o++)
-        if (st == GSP_OK && !blkmin[o].empty()) st = dalloc(&p->d_blkmin[o], blkmin[o].size());
-    if (st == GSP_OK && !dpos.empty()) st = dalloc(&p->d_dpos, dpos.size());
-    if (st == GSP_OK && !fcnt.empty()) st = dalloc(&p->d_fcnt, fcnt.size());
+    for (int o = 0; o < gsp::kNumKdm; o++) {
+        if (st == GSP_OK && !tab.blkmin[o].empty()) st = dalloc(&p->d_blkmin[o], tab.blkmin[o].size());
+        for (int i = 0; i < gsp::kNumCb; i++)
+            if (st == GSP_OK && !tab.stspread[o][i].empty())
+                st = dalloc(&p->d_stspread[o][i], tab.stspread[o][i].size());
+    }
+    for (int i = 0; i < gsp::kNumCb; i++) {
+        if (st == GSP_OK && !tab.dpos[i].empty()) st = dalloc(&p->d_dpos[i], tab.dpos[i].size());
+        if (st == GSP_OK && !tab.fcnt[i].empty()) st = dalloc(&p->d_fcnt[i], tab.fcnt[i].size());
+    }
     if (st == GSP_OK) st = dalloc(&p->d_sigma_b, rows_blocks);
     if (st == GSP_OK) st = dalloc(&p->d_bad, rows_blocks);
     if (st == GSP_OK) st = dalloc(&p->d_bparam, rows_blocks);
@@ -362,14 +368,18 @@ gsp_status gsp_plan_create(gsp_plan_t *out, const gsp_plan_desc *d) {
     }
     e = cudaMemcpy(p->d_delays, p->delays_h.data(), (size_t)(C * ndm) * sizeof(int32_t),
                    cudaMemcpyHostToDevice);
-    for (int o = 0; o < gsp::kNumKdm; o++)
-        if (e == cudaSuccess && !blkmin[o].empty())
-            e = cudaMemcpy(p->d_blkmin[o], blkmin[o].data(), blkmin[o].size() * sizeof(int32_t),
-                           cudaMemcpyHostToDevice);
-    if (e == cudaSuccess && !dpos.empty())
-        e = cudaMemcpy(p->d_dpos, dpos.data(), dpos.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess && !fcnt.empty())
-        e = cudaMemcpy(p->d_fcnt, fcnt.data(), fcnt.size() * sizeof(uint32_t), cudaMemcpyHostToDevice);
+    auto up = [&](void *dst, const void *src, size_t bytes) {
+        if (e == cudaSuccess && bytes > 0) e = cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice);
+    };
+    for (int o = 0; o < gsp::kNumKdm; o++) {
+        up(p->d_blkmin[o], tab.blkmin[o].data(), tab.blkmin[o].size() * sizeof(int32_t));
+        for (int i = 0; i < gsp::kNumCb; i++)
+            up(p->d_stspread[o][i], tab.stspread[o][i].data(), tab.stspread[o][i].size() * sizeof(int32_t));
+    }
+    for (int i = 0; i < gsp::kNumCb; i++) {
+        up(p->d_dpos[i], tab.dpos[i].data(), tab.dpos[i].size() * sizeof(int32_t));
+        up(p->d_fcnt[i], tab.fcnt[i].data(), tab.fcnt[i].size() * sizeof(uint32_t));
+    }
     if (e == cudaSuccess) e = cudaMemset(p->d_ncand, 0, sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMemset(p->d_err, 0, sizeof(int));
     for (int i = 0; i < 3 && e == cudaSuccess; i++) e = cudaEventCreate(&p->ev[i]);
@@ -634,6 +644,73 @@ gsp_status gsp_plan_timing(gsp_plan_t p, float *ms_dd, float *ms_search) {
 
 int32_t gsp_plan_launches(gsp_plan_t p) { return p ? p->launches : -1; }
 
+gsp_status gsp_plan_series(gsp_plan_t p, const int32_t **d_D, int64_t *stride, int64_t *n_out) {
+    if (!p || !d_D || !stride || !n_out) return GSP_ERR_INVALID_ARG;
+    if (!p->have_search) return GSP_ERR_STATE;
+    *d_D = p->last_D;
+    *stride = p->last_stride;
+    *n_out = p->last_nout;
+    return GSP_OK;
+}
+
+// Tile-variant autotuning of one plan on the caller's input: every tiled
+// variant that fits the plan is timed kPlanTuneReps times (after one warm-up
+// run) over the first kPlanTuneSamples output samples, into the plan's series
+// scratch; the one with the smallest median becomes the plan's variant.
+constexpr int64_t kPlanTuneSamples = 131072;
+constexpr int kPlanTuneReps = 3;
+
+gsp_status gsp_plan_tune(gsp_plan_t p, const uint8_t *d_x, int64_t n_in, int64_t x_stride,
+                         void *stream, int32_t *variant, float *best_ms) {
+    int64_t n_out = 0;
+    gsp_status st = check_dd_args(p, d_x, n_in, x_stride, nullptr, 0, &n_out);
+    if (st != GSP_OK) return st;
+    if (p->simple_dd) return GSP_ERR_STATE;
+    st = ensure_scratch_D(p, n_out);
+    if (st != GSP_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t n = std::min(n_out, kPlanTuneSamples);
+    const int64_t stride = (n_out + 3) & ~(int64_t)3;
+    const int *cand = nullptr;
+    const int ncand = gsp::dedisperse_tune_candidates(&cand);
+    const int keep = p->geom.variant;
+    int best = -1;
+    float best_t = 0.f;
+    for (int ci = 0; ci < ncand; ci++) {
+        if (!gsp::dedisperse_variant_usable(p, cand[ci])) continue;
+        gsp::dedisperse_set_variant(p, cand[ci]);
+        std::vector<float> ms;
+        for (int r = 0; r <= kPlanTuneReps; r++) {
+            int32_t nl = 0;
+            GSP_CK(cudaEventRecord(p->ev[0], s));
+            cudaError_t e = gsp::launch_dedisperse_tiled(p, d_x, n + p->max_delay, x_stride, n,
+                                                         p->d_D, stride, nullptr, s, &nl);
+            if (e != cudaSuccess) {
+                gsp::dedisperse_set_variant(p, keep);
+                set_err(e, "tuning launch");
+                return GSP_ERR_CUDA;
+            }
+            GSP_CK(cudaEventRecord(p->ev[1], s));
+            GSP_CK(cudaEventSynchronize(p->ev[1]));
+            float t = 0.f;
+            GSP_CK(cudaEventElapsedTime(&t, p->ev[0], p->ev[1]));
+            if (r > 0) ms.push_back(t);
+        }
+        std::sort(ms.begin(), ms.end());
+        const float med = ms[ms.size() / 2];
+        if (best < 0 || med < best_t) {
+            best = cand[ci];
+            best_t = med;
+        }
+    }
+    gsp_status kst = take_kernel_error(p);
+    gsp::dedisperse_set_variant(p, best >= 0 ? best : keep);
+    if (kst != GSP_OK) return kst;
+    if (variant) *variant = p->geom.variant;
+    if (best_ms) *best_ms = best_t;
+    return GSP_OK;
+}
+
 int32_t gsp_dedisperse_variants(gsp_plan_t p, int32_t *in_use) {
     if (p && in_use) *in_use = p->simple_dd ? -1 : p->geom.variant;
     return gsp::dedisperse_num_variants();
@@ -652,6 +729,7 @@ const char *gsp_status_string(gsp_status s) {
         case GSP_ERR_ALIGN: return "pointer or stride misaligned";
         case GSP_ERR_STATE: return "call out of order";
         case GSP_ERR_TOO_LARGE: return "sizes exceed the static scratch of the no-allocation search";
+        case GSP_ERR_BUSY: return "no free chunk buffer (chunk not admitted)";
     }
     return "unknown status";
 }

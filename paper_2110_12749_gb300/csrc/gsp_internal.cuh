@@ -34,20 +34,38 @@ struct BlockParam {
     int32_t good;
 };
 
+// Channels per shared-memory stage of the tiled kernel: 64 or 32.  Plans keep
+// the per-stage tables of both widths (index cb_index(cb)).
+constexpr int kNumCb = 2;
+constexpr int kCbSizes[kNumCb] = {64, 32};
+inline int cb_index(int cb) { return cb == 32 ? 1 : 0; }
+
 // Tile geometry of the performance dedispersion kernel, chosen per plan.
 struct DDGeom {
     int kdm = 0;       // DM trials per CTA of the plan's variant
     int t_cta = 0;     // output samples computed per CTA (t_eff stored)
     int t_eff = 0;     // output samples stored per CTA (tiles overlap)
     int cb = 0;        // channels per shared-memory stage
-    int win = 0;       // bytes per channel window in shared memory
+    int win = 0;       // bytes per channel window in shared memory (the widest stage)
     int stages = 0;    // pipeline depth
     int smem = 0;      // dynamic shared memory bytes
+    int ctas_per_sm = 1;
     // per DM-block size kKdmSizes[o]:
     int nblk[kNumKdm] = {};            // DM blocks
     int grp[kNumKdm] = {1, 1, 1};      // DM blocks per launch group
     int64_t spread[kNumKdm] = {};      // largest delay spread inside a DM block
     int variant = 0;   // template variant index
+};
+
+// Launch geometry of one tile variant for a given largest in-block delay
+// spread: window bytes per channel, ring depth, shared memory and CTAs per
+// SM.  ok = false if fewer than two stages fit.
+struct TileFit {
+    bool ok = false;
+    int win = 0;
+    int stages = 0;
+    int smem = 0;
+    int ctas_per_sm = 1;
 };
 
 }  // namespace gsp
@@ -65,8 +83,13 @@ struct gsp_plan_s {
     // device memory owned by the plan
     int32_t *d_delays = nullptr;     // [ndm][nchan]
     int32_t *d_blkmin[gsp::kNumKdm] = {};  // [nblk][nchan] min delay per DM block
-    int32_t *d_dpos = nullptr;       // [ndm][nchan] (delay << 8) | phase-list position
-    uint32_t *d_fcnt = nullptr;      // [ndm][ceil(nchan / 64)] phase family sizes
+    // per stage width kCbSizes[i]: (delay << 8) | phase-list position [ndm][nchan],
+    // and the four phase-family sizes of every (DM, stage) [ndm][ceil(nchan / cb)]
+    int32_t *d_dpos[gsp::kNumCb] = {};
+    uint32_t *d_fcnt[gsp::kNumCb] = {};
+    // largest in-block delay spread of each stage's channels, per DM-block size
+    // and stage width [ceil(nchan / cb)] (sizes each stage's copy window)
+    int32_t *d_stspread[gsp::kNumKdm][gsp::kNumCb] = {};
     int *d_err = nullptr;            // set by a kernel whose bounded wait gave up
     unsigned long long *d_bsum = nullptr;  // [ndm][nb_max][3] block sums (tiled path)
     double *d_sigma_b = nullptr;     // [ndm][nb_max]
@@ -95,6 +118,8 @@ struct gsp_plan_s {
     cudaStream_t last_stream = nullptr;
     int64_t last_nout = -1;
     int64_t last_nb = 0;
+    const int32_t *last_D = nullptr;  // series of the last search and its row stride
+    int64_t last_stride = 0;
     bool have_search = false;
     int32_t launches = 0;
 };
@@ -122,7 +147,17 @@ cudaError_t launch_dedisperse_batch(const BeamLaunch *beams, int nbeams, int var
                                     bool persistent, int num_sms, int *err, cudaStream_t s,
                                     int32_t *nlaunch);
 int dedisperse_num_variants();
+// Variants the batch autotuner may time, in order of preference.
 int dedisperse_tune_candidates(const int **list);
+// Geometry of variant v for the largest in-block spreads (per DM-block size).
+TileFit dedisperse_fit(int variant, const int64_t (&spread)[kNumKdm]);
+// Whether variant v can run on plan p (its tables exist and its tiles fit).
+bool dedisperse_variant_usable(const gsp_plan_s *p, int variant);
+// Make variant v the plan's (it must be usable); updates the tile geometry.
+void dedisperse_set_variant(gsp_plan_s *p, int variant);
+// The preferred tiled variant for a set of plans dedispersed in one launch
+// (largest spreads over the plans), or -1 if no tiled variant fits.
+int dedisperse_choose_variant(const gsp_plan_s *const *plans, int nplans);
 
 // gsp_api.cu helpers shared with the batch module.
 void record_error(cudaError_t e, const char *what);
@@ -137,12 +172,21 @@ cudaError_t launch_dedisperse_tiled(const gsp_plan_s *p, const uint8_t *x, int64
                                     int64_t x_stride, int64_t n_out, int32_t *out,
                                     int64_t out_stride, unsigned long long *bsum,
                                     cudaStream_t s, int32_t *nlaunch);
-// Phase-sorted list positions of 64-channel stages (empty if the delays do
-// not fit the packed form), then the tile geometry and variant.
-void plan_phase_lists(const gsp_plan_s *p, std::vector<int32_t> *dpos,
+// Phase-sorted list positions of cb-channel stages (empty if the delays do
+// not fit the packed form).
+void plan_phase_lists(const gsp_plan_s *p, int cb, std::vector<int32_t> *dpos,
                       std::vector<uint32_t> *fcnt);
-bool plan_dedisperse_tiled(gsp_plan_s *p, std::vector<int32_t> (&blkmin)[kNumKdm],
-                           bool have_lists);
+// Host tables of the tiled kernel for a plan.
+struct TiledTables {
+    std::vector<int32_t> blkmin[kNumKdm];
+    std::vector<int32_t> dpos[kNumCb];
+    std::vector<uint32_t> fcnt[kNumCb];
+    std::vector<int32_t> stspread[kNumKdm][kNumCb];
+};
+// DM-block tables and per-stage spreads of every block size and stage width,
+// then the plan's variant and geometry.  Returns false (the plan then uses
+// the simple kernel) only if no tiled variant fits the plan's delay spread.
+bool plan_dedisperse_tiled(gsp_plan_s *p, TiledTables *tab);
 
 // bsum (optional): block sums left by the tiled dedispersion kernel.
 cudaError_t launch_search(gsp_plan_s *p, const int32_t *D, int64_t n_out, int64_t stride,

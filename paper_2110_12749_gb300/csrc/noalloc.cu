@@ -13,11 +13,17 @@
 // The array lives in device global memory for as long as the library is
 // loaded, on every GPU that loads it.  Its address is looked up once per
 // device (cudaGetSymbolAddress) on the first call made with that device
-// current.  Every call shares the array, so calls whose kernels overlap on
-// the GPU (different streams, or different host threads) race on it; calls
-// issued one after another on one stream are safe.  Nothing in the array has
-// to start at zero: each call writes every entry it later reads.
+// current; with lazy module loading that first call is also the one that
+// loads this library's device code on the device and with it the array, so
+// it should come before any stream capture.  The address is cached for the
+// life of the process: after cudaDeviceReset on a device the cached address
+// is stale, so this entry point must not be used on that device again.
+// Every call shares the array, so calls whose kernels overlap on the GPU
+// (different streams, or different host threads) race on it; calls issued
+// one after another on one stream are safe.  Nothing in the array has to
+// start at zero: each call writes every entry it later reads.
 #include <algorithm>
+#include <cmath>
 #include <mutex>
 
 #include "gsp_internal.cuh"
@@ -57,7 +63,7 @@ extern "C" gsp_status gsp_search_series_static(
     unsigned long long *d_ncand, void *stream) {
     if (!d_D || !d_cands || !d_ncand || ndm <= 0 || n_out <= 0 || stride < n_out ||
         max_cands <= 0 || block_len <= 0 || window_len <= 0 || !(bad_lo <= bad_hi) ||
-        !(threshold == threshold))
+        !std::isfinite(threshold))
         return GSP_ERR_INVALID_ARG;
     const int32_t *w = widths ? widths : kDefaultWidths;
     const int nw = widths ? nwidths : 13;
@@ -67,6 +73,8 @@ extern "C" gsp_status gsp_search_series_static(
     if (w[nw - 1] > block_len || w[nw - 1] > 1024) return GSP_ERR_INVALID_ARG;
     const int64_t nb = n_out / block_len;
     if (ndm > kMaxRows || (int64_t)ndm * nb > kMaxRowBlocks) return GSP_ERR_TOO_LARGE;
+    // one boxcar CTA per candidate window of a row: the window count must fit a grid dimension
+    if ((nb * block_len) / window_len + 2 > (int64_t)INT32_MAX) return GSP_ERR_TOO_LARGE;
 
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);

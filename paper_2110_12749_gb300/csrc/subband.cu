@@ -367,8 +367,14 @@ gsp_status gsp_subband_dedisperse(gsp_subband_t b, const uint8_t *d_x, int64_t n
     }
     for (size_t i = 0; i < bl.size(); i += 32) {
         const int n = (int)std::min<size_t>(32, bl.size() - i);
-        cudaError_t e = gsp::launch_dedisperse_batch(bl.data() + i, n, bl[i].plan->geom.variant,
-                                                     true, b->num_sms, b->d_err, s, &b->launches);
+        // one variant that fits every sub-band of this launch
+        std::vector<const gsp_plan_s *> ps((size_t)n);
+        for (int k = 0; k < n; k++) ps[k] = bl[i + k].plan;
+        const int variant = gsp::dedisperse_choose_variant(ps.data(), n);
+        cudaError_t e = variant < 0 ? cudaErrorInvalidValue
+                                    : gsp::launch_dedisperse_batch(bl.data() + i, n, variant, true,
+                                                                   b->num_sms, b->d_err, s,
+                                                                   &b->launches);
         if (e != cudaSuccess) {
             gsp::record_error(e, "sub-band stage 1 launch");
             return GSP_ERR_CUDA;

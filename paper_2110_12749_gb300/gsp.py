@@ -26,6 +26,7 @@ GSP_ERR_TIE = 7
 GSP_ERR_ALIGN = 8
 GSP_ERR_STATE = 9
 GSP_ERR_TOO_LARGE = 10
+GSP_ERR_BUSY = 11
 
 GSP_FLAG_TIMING = 1
 GSP_FLAG_SIMPLE_DD = 2
@@ -108,12 +109,21 @@ def lib():
                                          ctypes.c_int),
             "gsp_plan_launches": ([_vp], ctypes.c_int32),
             "gsp_dedisperse_variants": ([_vp, _vp], ctypes.c_int32),
+            "gsp_plan_tune": ([_vp, _vp, _i64, _i64, _vp, _vp, _vp], ctypes.c_int),
+            "gsp_plan_series": ([_vp, _vp, _vp, _vp], ctypes.c_int),
+            "gsp_batch_tune_results": ([_vp, _vp, _vp, ctypes.c_int32], ctypes.c_int32),
             "gsp_stream_create": ([_vp, _vp, _i64, ctypes.c_int32], ctypes.c_int),
             "gsp_stream_destroy": ([_vp], ctypes.c_int),
             "gsp_stream_need": ([_vp], _i64),
             "gsp_stream_bytes": ([_vp, _i64], _i64),
             "gsp_stream_push": ([_vp, _vp, _i64, _i64, _vp], ctypes.c_int),
             "gsp_stream_results": ([_vp, _vp, _i64, _vp, _vp], ctypes.c_int),
+            "gsp_chunkpool_create": ([_vp, ctypes.c_int32, _i64, _i64, ctypes.c_int32], ctypes.c_int),
+            "gsp_chunkpool_destroy": ([_vp], ctypes.c_int),
+            "gsp_chunkpool_bytes": ([ctypes.c_int32, _i64, _i64, ctypes.c_int32], _i64),
+            "gsp_chunkpool_free": ([_vp], ctypes.c_int32),
+            "gsp_stream_create_pooled": ([_vp, _vp, _vp, ctypes.c_int32], ctypes.c_int),
+            "gsp_stream_pooled_bytes": ([_vp, _i64], _i64),
             "gsp_batch_create": ([_vp, _vp, ctypes.c_int32, ctypes.c_int32], ctypes.c_int),
             "gsp_batch_destroy": ([_vp], ctypes.c_int),
             "gsp_batch_search": ([_vp, _vp, _vp], ctypes.c_int),
@@ -393,6 +403,44 @@ def gsp_dedisperse_variants(plan=None):
     return n, (int(used.value) if plan is not None else None)
 
 
+def gsp_plan_tune(plan, x, n_in, stream=None):
+    """Autotune the plan's tile variant on x (torch uint8 CUDA [nchan][stride]);
+    returns (variant, median ms of the tuning runs)."""
+    v, ms = ctypes.c_int32(-1), ctypes.c_float(0)
+    _check(lib().gsp_plan_tune(plan.handle, x.data_ptr(), n_in, x.stride(0), _stream(stream),
+                               ctypes.byref(v), ctypes.byref(ms)), "gsp_plan_tune")
+    return v.value, ms.value
+
+
+def gsp_plan_series(plan):
+    """(device address, row stride, n_out) of the series of the plan's last search."""
+    p, st, n = _vp(), ctypes.c_int64(0), ctypes.c_int64(0)
+    _check(lib().gsp_plan_series(plan.handle, ctypes.byref(p), ctypes.byref(st), ctypes.byref(n)),
+           "gsp_plan_series")
+    return p.value, st.value, n.value
+
+
+class _DeviceArray:
+    """A view of device memory for torch.as_tensor (CUDA array interface)."""
+
+    def __init__(self, addr, shape, strides, typestr):
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "strides": tuple(strides),
+                                         "typestr": typestr, "data": (int(addr), False),
+                                         "version": 3}
+
+
+def gsp_plan_series_tensor(plan):
+    """torch int32 CUDA view [ndm][n_out] (row stride as stored) of the series of
+    the plan's last search; valid until the plan searches again or is destroyed."""
+    import torch
+    addr, stride, n_out = gsp_plan_series(plan)
+    ndm = plan.desc.ndm if hasattr(plan, "desc") else None
+    if ndm is None:
+        raise RuntimeError("plan without its descriptor")
+    return torch.as_tensor(_DeviceArray(addr, (ndm, n_out), (4 * stride, 4), "<i4"),
+                           device="cuda")
+
+
 def gsp_search_series_static(D, n_out, d_cands, d_ncand, t_offset=0, widths=None,
                              block_len=1024, window_len=1024, threshold=6.0, bad_lo=0.5,
                              bad_hi=2.5, stream=None):
@@ -446,13 +494,69 @@ def gsp_stream_need(s):
     return int(lib().gsp_stream_need(s.handle))
 
 
-def gsp_stream_push(s, x_host, n, stream=None):
-    """x_host: numpy uint8 [nchan][stride] or a (pinned) CPU torch tensor."""
+def gsp_stream_push(s, x_host, n, stream=None, busy_ok=False):
+    """x_host: numpy uint8 [nchan][stride] or a (pinned) CPU torch tensor.  With
+    busy_ok, returns False instead of raising when a pooled stream finds no free
+    pool buffer (the chunk was not admitted); True when it was pushed."""
     if isinstance(x_host, np.ndarray):
         ptr, stride = _np_ptr(x_host), x_host.strides[0]
     else:
         ptr, stride = _vp(x_host.data_ptr()), x_host.stride(0)
-    _check(lib().gsp_stream_push(s.handle, ptr, n, stride, _stream(stream)), "gsp_stream_push")
+    st = lib().gsp_stream_push(s.handle, ptr, n, stride, _stream(stream))
+    if busy_ok and st == GSP_ERR_BUSY:
+        return False
+    _check(st, "gsp_stream_push")
+    return True
+
+
+class ChunkPool:
+    """Owns a gsp_chunkpool_t."""
+
+    def __init__(self, handle):
+        self.handle = handle
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            try:
+                _lib.gsp_chunkpool_destroy(self.handle)
+            except Exception:
+                pass
+            self.handle = None
+
+
+def gsp_chunkpool_create(nchan, chunk_out, max_tail, nbuf):
+    h = _vp()
+    _check(lib().gsp_chunkpool_create(ctypes.byref(h), nchan, chunk_out, max_tail, nbuf),
+           "gsp_chunkpool_create")
+    return ChunkPool(h)
+
+
+def gsp_chunkpool_destroy(p):
+    if p.handle:
+        st = lib().gsp_chunkpool_destroy(p.handle)
+        p.handle = None
+        _check(st, "gsp_chunkpool_destroy")
+
+
+def gsp_chunkpool_bytes(nchan, chunk_out, max_tail, nbuf):
+    return int(lib().gsp_chunkpool_bytes(nchan, chunk_out, max_tail, nbuf))
+
+
+def gsp_chunkpool_free(p):
+    return int(lib().gsp_chunkpool_free(p.handle))
+
+
+def gsp_stream_create_pooled(plan, pool, beam=0):
+    h = _vp()
+    _check(lib().gsp_stream_create_pooled(ctypes.byref(h), plan.handle, pool.handle, beam),
+           "gsp_stream_create_pooled")
+    st = Stream(h, plan)
+    st.pool = pool
+    return st
+
+
+def gsp_stream_pooled_bytes(plan, chunk_out):
+    return int(lib().gsp_stream_pooled_bytes(plan.handle, chunk_out))
 
 
 def gsp_stream_results(s, cap=None):
@@ -529,6 +633,17 @@ def gsp_batch_info(b):
     _check(lib().gsp_batch_info(b.handle, ctypes.byref(v), ctypes.byref(ms), ctypes.byref(nl)),
            "gsp_batch_info")
     return v.value, ms.value, nl.value
+
+
+def gsp_batch_tune_results(b):
+    """[(variant, median ms)] of every tile variant the autotuner timed."""
+    n = int(lib().gsp_batch_tune_results(b.handle, None, None, 0))
+    if n <= 0:
+        return []
+    v = np.zeros(n, np.int32)
+    ms = np.zeros(n, np.float32)
+    lib().gsp_batch_tune_results(b.handle, _np_ptr(v), _np_ptr(ms), n)
+    return [(int(a), float(m)) for a, m in zip(v, ms)]
 
 
 def gsp_batch_timing(b):

@@ -96,6 +96,31 @@ def test_null_arguments_return_status(gsp):
     assert L.gsp_plan_max_delay(None) == -1
     assert L.gsp_dedisperse(None, None, 0, 0, None, 0, None) == gsp.GSP_ERR_INVALID_ARG
     assert L.gsp_candidates(None, None, 0, None) == gsp.GSP_ERR_INVALID_ARG
+    assert L.gsp_plan_tune(None, None, 0, 0, None, None, None) == gsp.GSP_ERR_INVALID_ARG
+    assert L.gsp_plan_series(None, None, None, None) == gsp.GSP_ERR_INVALID_ARG
+    assert L.gsp_batch_tune_results(None, None, None, 0) == -1
+
+
+def test_static_search_argument_checks_on_host(gsp):
+    # argument checks of the no-allocation search return before any CUDA call
+    L = gsp.lib()
+    fake = 0x1000  # never dereferenced: every case below is rejected first
+    args = dict(ndm=4, n_out=8192, stride=8192, t_off=0, bl=1024, wl=1024, thr=6.0)
+
+    def call(**kw):
+        a = dict(args)
+        a.update(kw)
+        return L.gsp_search_series_static(fake, a["ndm"], a["n_out"], a["stride"], a["t_off"],
+                                          None, 0, a["bl"], a["wl"], a["thr"], 0.5, 2.5, fake,
+                                          16, fake, None)
+    assert call(thr=float("inf")) == gsp.GSP_ERR_INVALID_ARG
+    assert call(thr=float("-inf")) == gsp.GSP_ERR_INVALID_ARG
+    assert call(thr=float("nan")) == gsp.GSP_ERR_INVALID_ARG
+    assert call(ndm=4097) == gsp.GSP_ERR_TOO_LARGE
+    assert call(ndm=300, n_out=1024 * 1024, stride=1024 * 1024) == gsp.GSP_ERR_TOO_LARGE
+    # a long series cut into one-sample windows: more windows than a grid dimension
+    big = 1 << 40
+    assert call(ndm=1, n_out=big, stride=big, bl=1 << 30, wl=1) == gsp.GSP_ERR_TOO_LARGE
 
 
 def test_plan_without_gpu_fails_cleanly(gsp):

@@ -1,9 +1,19 @@
 """Batched multi-beam search (gsp_batch_*): beams with different lengths and DM
 grids dedispersed in one launch (one CTA per item, or persistent CTAs), with
-and without CUDA-graph replay and autotuning.  Every beam's candidates and
-block statistics must equal a separate gsp_search of that beam."""
+and without CUDA-graph replay and autotuning.
+
+Small cases: every beam's candidates and block statistics must equal a
+separate gsp_search of that beam.  Full shape: 19 beams of 4096 channels with
+lengths uniform in 2^18..2^20 samples and their own DM grids (1000-2500 trials
+to DM 500-1500, one beam the coarsest step, 1000 trials to DM 1500) in one
+persistent, graph-captured, autotuned batch, checked against the CPU oracle:
+every row of every beam through the exact prefix-sum identities, sampled rows
+bit-exact, and the candidates of the sampled rows against the oracle search.
+"""
 import numpy as np
 import pytest
+
+from helpers import compare_candidates, window_contenders
 
 pytestmark = pytest.mark.gpu
 
@@ -87,3 +97,83 @@ def test_batch_rejects_mixed_channels_and_shared_plans(gsp):
         gsp.gsp_batch_create([p1, p2])
     with pytest.raises(gsp.GspError):
         gsp.gsp_batch_create([p1, p1])
+
+
+def test_batch_full_shape_against_oracle(gsp, orc):
+    import dataclasses
+    from paper_2110_12749_gb300 import synth
+    wl = synth.WORKLOADS["crafts"]
+    rng = np.random.default_rng(synth.BASE_SEED + 31)
+    nbeams = 19
+    beams = []
+    for b in range(nbeams):
+        n_in = int(rng.integers(1 << 18, (1 << 20) + 1)) // 16 * 16
+        if b == 7:
+            ntr, dmax = 1000, 1500.0        # the coarsest grid of the recipe (step 1.5)
+        else:
+            ntr, dmax = int(rng.integers(1000, 2501)), float(rng.uniform(500.0, 1500.0))
+        beams.append((n_in, ntr, dmax / ntr))
+    plans, xs, expect = [], [], []
+    for b, (n_in, ntr, step) in enumerate(beams):
+        dms = np.arange(ntr) * step
+        dl, _ = orc.delays(wl.nchan, wl.f_lo, wl.f_hi, wl.t_samp, dms)
+        n_out = n_in - orc.max_delay(dl)
+        wlb = dataclasses.replace(wl, n_in=n_in, ndm=ntr, dm_step=step, n_pulses=10,
+                                  pulse_dm=(10.0, ntr * step), pulse_w=(1, 150),
+                                  pulse_snr=(5.0, 40.0))
+        x, _, _, pulses = synth.workload_filterbank(
+            wlb, lambda dm: orc.delays(wl.nchan, wl.f_lo, wl.f_hi, wl.t_samp, [dm])[0][0],
+            n_out, beam=b)
+        # expected values, computed now so that the host copy can go
+        s0, s1 = orc.row_sums(x, n_in, dl, n_out)
+        rows = {0, ntr - 1, int(rng.integers(0, ntr))}
+        p = pulses[int(rng.integers(0, len(pulses)))]
+        rows.add(min(max(int(round(p.dm / step)), 0), ntr - 1))
+        rows = np.array(sorted(rows))
+        Dref = orc.dedisperse(x, n_in, dl, rows=rows, n_out=n_out)
+        expect.append((n_out, s0, s1, rows, Dref))
+        desc, keep = gsp.make_desc(wl.nchan, wl.f_lo, wl.f_hi, wl.t_samp, n_in, ndm=ntr,
+                                   dm_step=step, max_cands=ntr * (n_out // 1024 + 2))
+        plans.append(gsp.gsp_plan_create(desc, keep))
+        assert (gsp.gsp_plan_delays(plans[-1]) == dl).all()
+        xs.append(torch.from_numpy(x).cuda())
+        del x
+    s = torch.cuda.Stream()
+    flags = gsp.GSP_BATCH_PERSISTENT | gsp.GSP_BATCH_GRAPH | gsp.GSP_BATCH_AUTOTUNE
+    bt = gsp.gsp_batch_create(plans, flags)
+    n_ins = [b[0] for b in beams]
+    gsp.gsp_batch_search(bt, xs, n_ins, stream=s)        # autotune + capture + run
+    gsp.gsp_batch_search(bt, xs, n_ins, stream=s)        # graph replay
+    cands, ncand, st = gsp.gsp_batch_candidates(bt)
+    assert st == gsp.GSP_OK
+    variant, tuned, _ = gsp.gsp_batch_info(bt)
+    assert variant >= 0 and tuned > 0
+    assert len(gsp.gsp_batch_tune_results(bt)) >= 2
+    del xs
+    torch.cuda.empty_cache()
+    for b, (plan, (n_out, s0, s1, rows, Dref)) in enumerate(zip(plans, expect)):
+        D = gsp.gsp_plan_series_tensor(plan)
+        assert D.shape[1] == n_out
+        t = torch.arange(n_out, device="cuda", dtype=torch.int64)
+        g0, g1 = [], []
+        for r0 in range(0, D.shape[0], 128):
+            blk = D[r0:r0 + 128].to(torch.int64)
+            g0.append(blk.sum(1))
+            g1.append((blk * t).sum(1))
+        g0, g1 = torch.cat(g0).cpu().numpy(), torch.cat(g1).cpu().numpy()
+        assert (g0 == s0).all(), (b, np.nonzero(g0 != s0)[0][:5])
+        assert (g1 == s1).all(), (b, np.nonzero(g1 != s1)[0][:5])
+        Dg = D[torch.from_numpy(rows).cuda()].cpu().numpy().astype(np.int64)
+        assert (Dg == Dref).all(), b
+        contenders, ora = {}, []
+        for i, r in enumerate(rows):
+            det = orc.search_row(Dref[i], dm_idx=int(r), detail=True)
+            contenders[int(r)] = window_contenders(det, 1024, 0, 6.0)
+            ora.append(det["cands"])
+        mine = cands[cands["beam"] == b]
+        ncmp, bad = compare_candidates(mine, np.concatenate(ora), 6.0, 1024, 0, contenders,
+                                       rows=set(rows.tolist()))
+        assert not bad, (b, bad[:5])
+    gsp.gsp_batch_destroy(bt)
+    for p in plans:
+        gsp.gsp_plan_destroy(p)

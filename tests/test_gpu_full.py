@@ -74,6 +74,8 @@ def test_full_size_parity(gsp, orc, name):
                                dm_lo=wl.dm_lo, dm_step=wl.dm_step, max_cands=wl.ndm * nwin)
     plan = gsp.gsp_plan_create(desc, keep)
     assert (gsp.gsp_plan_delays(plan) == dl).all()
+    _, used = gsp.gsp_dedisperse_variants(plan)
+    assert used >= 0          # the tiled kernel, also for the wide band's long sweep
     xd = torch.from_numpy(x).cuda()
     stride = (n_out + 3) // 4 * 4
     D = torch.empty((wl.ndm, stride), dtype=torch.int32, device="cuda")
@@ -85,7 +87,7 @@ def test_full_size_parity(gsp, orc, name):
 
     # (1) every row: exact prefix-sum identities
     g0, g1 = _gpu_row_sums(D, n_out)
-    e0, e1 = _prefix_expect(x, dl, n_out)
+    e0, e1 = orc.row_sums(x, wl.n_in, dl, n_out)
     assert (g0 == e0).all(), np.nonzero(g0 != e0)[0][:10]
     assert (g1 == e1).all(), np.nonzero(g1 != e1)[0][:10]
 

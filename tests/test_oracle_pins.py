@@ -166,6 +166,32 @@ def test_dedisperse_prefix_sum_invariants(orc):
         assert (D[d] * np.arange(n_out)).sum() == s1
 
 
+def test_row_sums_equal_brute_force_and_dedispersed_sums(orc):
+    """oracle.row_sums (the prefix-sum identities, used to check every row of
+    full-size series) against pure-Python brute force on tiny inputs and the
+    sums of the oracle's dedispersed rows on a larger one."""
+    rng = np.random.default_rng(51)
+    for trial in range(5):
+        nchan = int(rng.integers(1, 9))
+        n_in = int(rng.integers(20, 65))
+        ndm = int(rng.integers(1, 6))
+        dl = rng.integers(0, n_in // 2, (ndm, nchan)).astype(np.int32)
+        x = rng.integers(0, 256, (nchan, n_in + int(rng.integers(0, 5))), dtype=np.uint8)
+        n_out = n_in - int(dl.max())
+        Db = _brute_dedisperse(x, dl, n_out)
+        s0, s1 = orc.row_sums(x, n_in, dl)
+        assert (s0 == Db.sum(1)).all()
+        assert (s1 == (Db * np.arange(n_out)).sum(1)).all()
+    nchan, n_in = 77, 6007
+    x = np.full((nchan, 6016), 255, np.uint8)
+    x[:, ::3] = rng.integers(0, 256, (nchan, 2006), dtype=np.uint8)
+    dl, _ = orc.delays(nchan, 1000.0, 1500.0, 1e-4, np.arange(0, 60, 0.7))
+    D = orc.dedisperse(x, n_in, dl)
+    s0, s1 = orc.row_sums(x, n_in, dl)
+    assert (s0 == D.sum(1)).all()
+    assert (s1 == (D * np.arange(D.shape[1])).sum(1)).all()
+
+
 # ------------------------------------------------------------------ search
 
 def _pattern(n):

@@ -9,10 +9,16 @@ in a row, on different sizes so that the second call runs over the first
 call's leftovers, and checks each result against the plan-based
 gsp_search_series (same candidates, S/N within the tests' 1e-5 tolerance).
 After the first call (which may load the library's device code), a call must
-not change the device's free memory.  The file is named to be collected last.
+not change the device's free memory.  Further cases compare it with the CPU
+oracle's search (including a negative t_offset, i.e. windows aligned to
+absolute sample indices before the series starts), and overflow max_cands:
+the true count comes back and nothing is written past max_cands records.
+The file is named to be collected last.
 """
 import numpy as np
 import pytest
+
+from helpers import compare_candidates, window_contenders
 
 pytestmark = pytest.mark.gpu
 
@@ -83,3 +89,51 @@ def test_static_search_rejects_oversize(gsp):
     with pytest.raises(gsp.GspError) as e:
         gsp.gsp_search_series_static(D, 2048, d_cands, d_ncand)
     assert e.value.status == gsp.GSP_ERR_TOO_LARGE
+
+
+def _static(gsp, D, n_out, max_cands, t_off, guard=0):
+    """Run the static search; returns (records written, true count, guard bytes)."""
+    rec = gsp.CAND_DTYPE.itemsize
+    buf = torch.full(((max_cands + guard) * rec,), 0xAB, dtype=torch.uint8, device="cuda")
+    d_ncand = torch.zeros(1, dtype=torch.int64, device="cuda")
+    gsp.gsp_search_series_static(D, n_out, buf[:max_cands * rec], d_ncand, t_offset=t_off,
+                                 threshold=6.0)
+    torch.cuda.synchronize()
+    n = int(d_ncand.item())
+    host = buf.cpu().numpy()
+    got = host[:max_cands * rec].view(gsp.CAND_DTYPE)[:min(n, max_cands)].copy()
+    return got, n, host[max_cands * rec:]
+
+
+@pytest.mark.parametrize("t_off", [0, -1500, -5000 * 1024 - 77])
+def test_static_search_matches_oracle(gsp, orc, t_off):
+    rng = np.random.default_rng(77 + abs(t_off) % 1000)
+    ndm, n_out = 23, 15000
+    D = _series(rng, ndm, n_out)
+    Dh = D[:, :n_out].cpu().numpy().astype(np.int64)
+    got, n, _ = _static(gsp, D, n_out, 4096, t_off)
+    assert n == len(got) and n > 10
+    contenders, ora = {}, []
+    for r in range(ndm):
+        det = orc.search_row(Dh[r], dm_idx=r, t_offset=t_off, detail=True)
+        contenders[r] = window_contenders(det, 1024, t_off, 6.0)
+        ora.append(det["cands"])
+    ncmp, bad = compare_candidates(got, np.concatenate(ora), 6.0, 1024, t_off, contenders)
+    assert not bad, bad[:5]
+    assert ncmp > 10
+
+
+def test_static_search_capacity_overflow(gsp):
+    rng = np.random.default_rng(91)
+    ndm, n_out = 40, 12000
+    D = _series(rng, ndm, n_out)
+    full, nfull, _ = _static(gsp, D, n_out, 4096, 0)
+    assert nfull == len(full) and nfull > 20
+    cap = 7
+    got, n, guard = _static(gsp, D, n_out, cap, 0, guard=64)
+    assert n == nfull                     # the true count, not the stored one
+    assert len(got) == cap
+    assert (guard == 0xAB).all()          # nothing written past max_cands records
+    keys = {(int(c["dm_idx"]), int(c["t"]), int(c["width"])) for c in full}
+    for c in got:                         # every stored record is a real candidate
+        assert (int(c["dm_idx"]), int(c["t"]), int(c["width"])) in keys
