@@ -37,8 +37,9 @@ DD_TRAFFIC_VARIANT = "default"
 
 NOMINAL_SMS = 152
 RANKER_KEYS = ("recall", "recall_nominal", "precision", "negatives_rejected", "threshold",
-               "pulses_detected_snr_ge_min", "candidates_scored", "candidates_per_s",
-               "train_snippets", "train_positives", "train_steps", "train_steps_per_s", "params")
+               "runs", "pulses_detected_snr_ge_min", "candidates_scored", "candidates_per_s",
+               "train_snippets", "train_positives", "train_steps", "train_steps_per_s", "params",
+               "recipe")
 INT_LANES_PER_SM = 128          # issue slots per SM per clock (4 schedulers x 32 lanes)
 SM_MAX_MHZ = 2070.0
 
@@ -70,11 +71,19 @@ def parse():
                     help="timed steps of the ingest transpose of the beam (0: skip)")
     ap.add_argument("--subband-steps", type=int, default=3,
                     help="timed steps of the two-stage sub-band path on the same beam (0: skip)")
-    ap.add_argument("--ranker-beams", type=int, default=24,
+    ap.add_argument("--ranker-beams", type=int, default=32,
                     help="training beams of the candidate ranker (0: skip the ranker section)")
     ap.add_argument("--ranker-steps", type=int, default=3600)
+    ap.add_argument("--ranker-snippets", type=int, default=200000,
+                    help="snippets in the ranker's training set")
+    ap.add_argument("--ranker-runs", type=int, default=3,
+                    help="independent trainings of the ranker")
+    ap.add_argument("--ranker-keep", type=float, default=0.995,
+                    help="share of validation pulses detected at S/N >= 8 the threshold keeps")
     ap.add_argument("--ranker-val-beams", type=int, default=8,
                     help="validation beams that set the ranker's operating threshold")
+    ap.add_argument("--ranker-eval-beams", type=int, default=8,
+                    help="fresh evaluation beams of the ranker")
     ap.add_argument("--ranker-pulses", type=int, default=100,
                     help="injected pulses per training beam of the ranker")
     ap.add_argument("--ddplan-steps", type=int, default=3,
@@ -632,54 +641,66 @@ def run_ddplan(args):
 
 
 def run_ranker(args):
-    """Candidate ranker: trained on snippets of the candidates the pipeline finds
-    in synthetic CRAFTS-like beams (2^18 samples, --ranker-pulses injected
-    pulses, 30 RFI channels, 5 DM-0 bursts each), its threshold set on held-out
-    beams with 40 injected pulses each, then scoring every candidate of fresh
-    beams of that recipe."""
+    """Candidate ranker on the learned + streaming workload's recipe: beams of 2^18
+    samples (4096 channels, 2000 trials to DM 1499.25) with pulses injected at DM
+    10-1500, width 1-150, S/N 5-40, plus 30 RFI channels and 5 DM-0 bursts.  The
+    training set is --ranker-snippets snippets of the candidates the pipeline finds
+    in --ranker-beams beams (every pulse core candidate, seeded negatives); then
+    --ranker-runs independent trainings (own initialisation and batch order), each
+    with its threshold set on the same held-out validation beams (the score that
+    keeps --ranker-keep of their pulses detected at S/N >= 8) and scored on the same
+    fresh evaluation beams."""
     import torch
     from paper_2110_12749_gb300 import gsp, ranker, synth
-    src = ranker.BeamSource(ranker.short_crafts(1 << 18, n_pulses=args.ranker_pulses))
+    src = ranker.BeamSource(ranker.learned_crafts(1 << 18, n_pulses=args.ranker_pulses))
     t0 = time.perf_counter()
-    x, y, _, _ = ranker.build_training_set(src, args.ranker_beams, synth.BASE_SEED + 500)
+    x, y, pid, _ = ranker.build_training_set(src, args.ranker_beams, synth.BASE_SEED + 500)
+    x, y, pid = ranker.subsample(x, y, pid, args.ranker_snippets, synth.BASE_SEED + 501)
+    src.wl = ranker.learned_crafts(1 << 18, n_pulses=40)
+    val = ranker.ScoredBeams(src, args.ranker_val_beams, synth.BASE_SEED + 700)
+    ev = ranker.ScoredBeams(src, args.ranker_eval_beams, synth.BASE_SEED + 900)
     t_data = time.perf_counter() - t0
-    r = gsp.gsp_ranker_create(4096, seed=1)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    e0.record()
-    losses = ranker.fit(r, x, y, steps=(args.ranker_steps // 3, args.ranker_steps - args.ranker_steps // 3),
-                        seed=3)
-    e1.record()
-    torch.cuda.synchronize()
-    train_ms = e0.elapsed_time(e1)
-    npos, nneg = int((y == 1).sum()), int((y == 0).sum())
-    del x
-    torch.cuda.empty_cache()
-    # validation and evaluation beams: the bench recipe (40 pulses), own seeds
-    src.wl = ranker.short_crafts(1 << 18, n_pulses=40)
-    thr = ranker.choose_threshold(r, src, args.ranker_val_beams, synth.BASE_SEED + 700)
-    ev = ranker.evaluate(r, src, 4, synth.BASE_SEED + 900, thresholds=(thr, 0.05, 0.5))
-    gsp.gsp_ranker_destroy(r)
+    steps = (args.ranker_steps // 3, args.ranker_steps - args.ranker_steps // 3)
+    runs, detail = [], []
+    for k in range(args.ranker_runs):
+        r = gsp.gsp_ranker_create(4096, seed=1 + 17 * k)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        losses = ranker.fit(r, x, y, steps=steps, seed=3 + 17 * k)
+        e1.record()
+        torch.cuda.synchronize()
+        train_ms = e0.elapsed_time(e1)
+        thr = ranker.threshold_for(val.scores(r), 8.0, args.ranker_keep)
+        res = ranker.summarise(ev.scores(r), 8.0, (thr, 0.5))
+        res.update({"train_ms": train_ms, "train_steps_per_s": args.ranker_steps / (train_ms / 1e3),
+                    "loss_first_last": [losses[0], losses[-1]]})
+        detail.append(res)
+        runs.append({"recall": _r(res["recall"]), "recall_nominal": _r(res["recall_nominal"]),
+                     "precision": _r(res["precision"]),
+                     "negatives_rejected": _r(res["negatives_rejected"]),
+                     "threshold": _r(thr), "missed": res["missed"][:3]})
+        gsp.gsp_ranker_destroy(r)
     gsp.gsp_plan_destroy(src.plan)
-    del src
+    npos, nneg = int((y == 1).sum()), int((y == 0).sum())
+    del x, src, val, ev
     torch.cuda.empty_cache()
-    ev.update({"train_beams": args.ranker_beams, "train_pulses_per_beam": args.ranker_pulses,
-               "train_snippets": npos + nneg,
-               "train_positives": npos, "train_steps": args.ranker_steps, "batch": 256,
-               "train_ms": train_ms, "train_steps_per_s": args.ranker_steps / (train_ms / 1e3),
-               "loss_first_last": [losses[0], losses[-1]], "data_s": t_data,
-               "params": gsp.gsp_ranker_num_params(),
-               "training": "every candidate of the training beams (pulse tracks excluded); "
-                           "1/3 of the steps with uniform negatives, then the 20000 "
-                           "highest-scored negatives over-sampled",
-               "validation": "%d beams of the bench recipe (own seed) set the threshold: "
-                             "the score keeping 99%% of their pulses detected at S/N >= 8"
-                             % args.ranker_val_beams,
-               "eval": "4 fresh beams of the bench recipe; recall over injected pulses the "
-                       "search detects at S/N >= 8 (recall_nominal: over those of nominal "
-                       "S/N >= 8 it detects at all); precision over candidates scored >= the "
-                       "threshold"})
-    return ev
+    last = detail[-1]
+    out = {"recall": min(d["recall"] for d in detail),
+           "recall_nominal": min(d["recall_nominal"] for d in detail),
+           "precision": min(d["precision"] for d in detail),
+           "negatives_rejected": min(d["negatives_rejected"] for d in detail),
+           "threshold": runs[-1]["threshold"], "runs": runs,
+           "pulses_detected_snr_ge_min": last["pulses_detected_snr_ge_min"],
+           "candidates_scored": last["candidates_scored"],
+           "candidates_per_s": last["candidates_per_s"], "train_snippets": npos + nneg,
+           "train_positives": npos, "train_steps": args.ranker_steps,
+           "train_steps_per_s": last["train_steps_per_s"], "params": gsp.gsp_ranker_num_params(),
+           "data_s": t_data, "detail": detail,
+           "recipe": "pulses DM 10-1500, width 1-150, S/N 5-40; grid 2000 trials to DM 1499.25; "
+                     "%d training beams, %d validation, %d evaluation"
+                     % (args.ranker_beams, args.ranker_val_beams, args.ranker_eval_beams)}
+    return out
 
 
 def run_gsp(args):
@@ -871,7 +892,7 @@ def run_gsp(args):
             "batch19_dedisperse_frac": batch_res["dedisperse_frac_of_roofline"] if batch_res else None,
             "wideband_dedisperse_frac": wide_res["dedisperse_frac_of_roofline"] if wide_res else None,
             "stream_p99_ms": stream_res["p99_ms"] if stream_res else None,
-            "stream_chunk_ms": _r(stream_res["chunk_sky_s"] * 1e3) if stream_res else None,
+            "stream_chunk_ms": stream_res["chunk_ms"] if stream_res else None,
             "ranker_recall_snr8": line["ranker"].get("recall") if ranker_res else None}
         print(json.dumps(line))
     if plan is not None:

@@ -519,9 +519,10 @@ gsp_status gsp_gemm_bf16(const void *d_A, int64_t lda, const void *d_B, int64_t 
  * DM-time snippets (the project's own design for the ranking step the paper
  * motivates in Sec. 1-2; it ranks the threshold output and never replaces it).
  * Network: three conv 3x3 (pad 1) + bias + ReLU + 2x2 max-pool layers (1 -> 8 ->
- * 16 -> 32 channels), fc 2048 -> 64 + ReLU, fc 64 -> 2 (class 1 = pulse).  All
+ * 16 -> 32 channels), fc 2048 -> 96 + ReLU, fc 96 -> 2 (class 1 = pulse),
+ * 202,786 parameters.  All
  * products run with bf16 operands (rounded to nearest even) and FP32
- * accumulation, the convolutions and fc 2048 -> 64 (forward and backward) as
+ * accumulation, the convolutions and fc 2048 -> 96 (forward and backward) as
  * tcgen05 GEMMs.  An inference pass (gsp_ranker_forward) fuses each conv
  * layer with its bias, ReLU and pool at the same rounding points: the
  * one-input-channel first layer on the CUDA cores, the other two as implicit

@@ -18,8 +18,8 @@ Network (NCHW here; the GPU's layout is its own):
     conv 3x3 pad 1 (1 -> 8) + bias, ReLU, max-pool 2x2      64x64 -> 32x32
     conv 3x3 pad 1 (8 -> 16) + bias, ReLU, max-pool 2x2     -> 16x16
     conv 3x3 pad 1 (16 -> 32) + bias, ReLU, max-pool 2x2    -> 8x8
-    fc 2048 -> 64 + bias, ReLU   (feature index (y * 8 + x) * 32 + c)
-    fc 64 -> 2 + bias            (logits; class 1 = astrophysical pulse)
+    fc 2048 -> 96 + bias, ReLU   (feature index (y * 8 + x) * 32 + c)
+    fc 96 -> 2 + bias            (logits; class 1 = astrophysical pulse)
 Rounding points (the GPU rounds at the same places): every operand of a
 product (weights, activations, back-propagated gradients) is rounded to
 bfloat16 (round to nearest even); sums, bias, ReLU, pooling, softmax and the
@@ -34,8 +34,8 @@ import numpy as np
 
 SNIP = 64
 SHAPES = {"w1": (8, 1, 3, 3), "b1": (8,), "w2": (16, 8, 3, 3), "b2": (16,),
-          "w3": (32, 16, 3, 3), "b3": (32,), "w4": (64, 2048), "b4": (64,),
-          "w5": (2, 64), "b5": (2,)}
+          "w3": (32, 16, 3, 3), "b3": (32,), "w4": (96, 2048), "b4": (96,),
+          "w5": (2, 96), "b5": (2,)}
 ORDER = ("w1", "b1", "w2", "b2", "w3", "b3", "w4", "b4", "w5", "b5")
 
 

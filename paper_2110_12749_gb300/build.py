@@ -68,5 +68,19 @@ def build(force=False, verbose=False, extra=()):
     return LIB
 
 
+def run_pipe_probe():
+    """Build and run the pipe throughput probe (csrc/probe/pipe_probe.cu), which
+    measures the integer, FP32 and shared-load throughput behind the
+    dedispersion kernel's roofline; returns its report."""
+    os.makedirs(BUILD, exist_ok=True)
+    exe = os.path.join(BUILD, "pipe_probe")
+    src = os.path.join(CSRC, "probe", "pipe_probe.cu")
+    subprocess.run([NVCC, *ARCH, "-O3", "-o", exe, src], check=True)
+    return subprocess.run([exe], check=True, capture_output=True, text=True).stdout
+
+
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))
+    if "--probe" in sys.argv:
+        print(run_pipe_probe())
+    else:
+        print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))

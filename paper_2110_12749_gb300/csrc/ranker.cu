@@ -4,16 +4,16 @@
 // ranks the plain threshold output, never replaces it).
 //
 // Network: three conv 3x3 (pad 1) + bias + ReLU + 2x2 max-pool layers
-// (1 -> 8 -> 16 -> 32 channels, 64x64 -> 8x8), fc 2048 -> 64 + ReLU, fc 64 -> 2.
+// (1 -> 8 -> 16 -> 32 channels, 64x64 -> 8x8), fc 2048 -> 96 + ReLU, fc 96 -> 2.
 // Activations are NHWC.  Every convolution of a training pass is an im2col
 // GEMM on the tcgen05 tensor cores (tc_gemm.cu), BF16 operands and FP32
 // accumulation in tensor memory, bias and ReLU fused into the epilogue.  An
 // inference pass fuses each conv layer with its bias, ReLU and pool at the
 // same rounding points: layer 0 (one input channel, K = 9) on the CUDA cores,
 // layers 1 and 2 as implicit GEMMs on the tensor cores that gather their taps
-// straight from the activations.  fc 2048 -> 64 and the
+// straight from the activations.  fc 2048 -> 96 and the
 // back-propagated products of both fc layers and the convolutions are GEMMs
-// too (weight gradients with split-K over the batch pixels).  The 64 -> 2
+// too (weight gradients with split-K over the batch pixels).  The 96 -> 2
 // layer, the loss, pooling, im2col / col2im, bias gradients and Adam are
 // elementwise kernels in FP32.  Every operand of a product is rounded to
 // bf16 (nearest even), at the same points as the CPU oracle.
@@ -32,7 +32,7 @@ using bf16 = __nv_bfloat16;
 
 constexpr int kS = 64;          // snippet side
 constexpr int kFc = 2048;       // 32 x 8 x 8 features
-constexpr int kHid = 64;
+constexpr int kHid = 96;        // hidden units of fc1 (202,786 parameters in all)
 constexpr int kLayers = 3;
 // per conv layer: input channels, output channels, input side
 __host__ __device__ constexpr int cin_of(int l) { return l == 0 ? 1 : (l == 1 ? 8 : 16); }
@@ -284,7 +284,7 @@ __global__ void transpose_kernel(const bf16 *__restrict__ in, int64_t ldi, int64
     }
 }
 
-// fc 64 -> 2 (CUDA cores): z5[b][o] = sum_k a4[b][k] * bf16(w5[o][k]) + b5[o].
+// fc 96 -> 2 (CUDA cores): z5[b][o] = sum_k a4[b][k] * bf16(w5[o][k]) + b5[o].
 __global__ void fc2_kernel(const bf16 *__restrict__ a4, const float *__restrict__ w5,
                            const float *__restrict__ b5, int B, float *__restrict__ z5) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -321,16 +321,16 @@ __global__ void loss_kernel(const float *__restrict__ z5, const int32_t *__restr
     if (threadIdx.x == 0 && loss_out) *loss_out = red[0] / (float)B;
 }
 
-// Back through fc 64 -> 2 and the ReLU of fc1 (CUDA cores):
+// Back through fc 96 -> 2 and the ReLU of fc1 (CUDA cores):
 //   dw5[o][k] = sum_b bf16(g5[b][o]) * a4[b][k],  db5[o] = sum_b g5[b][o]   (block 0)
 //   g4[b][k]  = (sum_o bf16(g5[b][o]) * bf16(w5[o][k])) * [z4[b][k] > 0]
-// g4 is written as bf16 [B][64] and transposed [64][ldT]; db4 += FP32 sums.
+// g4 is written as bf16 [B][96] and transposed [96][ldT]; db4 += FP32 sums.
 __global__ void fc2_back_kernel(const float *__restrict__ g5, const bf16 *__restrict__ a4,
                                 const float *__restrict__ w5, const float *__restrict__ z4,
                                 int B, float *__restrict__ dw5, float *__restrict__ db5,
                                 bf16 *__restrict__ g4, bf16 *__restrict__ g4T, int64_t ldT,
                                 float *__restrict__ db4) {
-    const int k = threadIdx.x;  // 64 threads: one hidden unit each
+    const int k = threadIdx.x;  // kHid threads: one hidden unit each
     if (blockIdx.x == 0) {
         float s0 = 0.0f, s1 = 0.0f, t0 = 0.0f, t1 = 0.0f;
         for (int b = 0; b < B; b++) {
@@ -378,7 +378,7 @@ __global__ void adam_kernel(float *__restrict__ p, const float *__restrict__ g,
 
 // bf16 GEMM copies of the conv weights: W[co][(ky*3+kx)*Cin + ci] (padded to
 // Kp) and its transpose WT[k][co] (ld Cout8), from w[co][ci][ky][kx]; and the
-// fc1 weight W4 [64][2048] with its transpose W4T [2048][64].
+// fc1 weight W4 [96][2048] with its transpose W4T [2048][96].
 __global__ void pack_kernel(const float *__restrict__ params, int64_t w1, int64_t w2, int64_t w3,
                             int64_t w4, bf16 *__restrict__ W0, bf16 *__restrict__ W0T,
                             bf16 *__restrict__ W1, bf16 *__restrict__ W1T, bf16 *__restrict__ W2,

@@ -35,6 +35,16 @@ def short_crafts(n_in=1 << 18, n_pulses=40):
     return dataclasses.replace(synth.WORKLOADS["crafts"], n_in=n_in, n_pulses=n_pulses)
 
 
+def learned_crafts(n_in=1 << 18, n_pulses=40):
+    """The learned + streaming workload's beams: CRAFTS-shaped chunks (4096
+    channels, 1000-1500 MHz, 49.152 us, 2^18 samples) with pulses injected at DM
+    10-1500, width 1-150 samples and S/N 5-40, searched over 2000 trials 0-1499.25
+    (step 0.75) so that every injected DM lies inside the grid."""
+    return dataclasses.replace(synth.WORKLOADS["crafts"], name="learned", n_in=n_in,
+                               dm_step=0.75, n_pulses=n_pulses, pulse_dm=(10.0, 1500.0),
+                               pulse_w=(1, 150), pulse_snr=(5.0, 40.0))
+
+
 def label_candidates(cands, pulses, dl, ndm):
     """Labels (1 / 0 / -1) and the matched pulse index (-1 if none)."""
     n = cands.size
@@ -105,6 +115,68 @@ class BeamSource:
             dc = torch.from_numpy(np.ascontiguousarray(cands).view(np.uint8).copy()).cuda()
             gsp.gsp_ranker_snippets(self.plan, self.D, dc, out)
         return out
+
+
+def subsample(x, y, pid, total, seed):
+    """Keep every positive and a seeded random subset of the negatives so that
+    `total` snippets remain (all of them if there are fewer)."""
+    torch = __import__("torch")
+    pos = np.nonzero(y == 1)[0]
+    neg = np.nonzero(y == 0)[0]
+    if pos.size + neg.size <= total:
+        return x, y, pid
+    rng = np.random.default_rng(seed)
+    keep = np.sort(np.concatenate([pos, rng.choice(neg, max(total - pos.size, 0),
+                                                   replace=False)]))
+    idx = torch.from_numpy(keep).cuda()
+    return x.index_select(0, idx), y[keep], pid[keep]
+
+
+class ScoredBeams:
+    """Searched beams whose candidates, labels, pulses and snippets are kept, so
+    that several rankers can be scored on the same beams (validation and
+    evaluation sets)."""
+
+    def __init__(self, src, beams, seed):
+        self.items = []
+        for b in range(beams):
+            cands, lab, pid, pulses = src.search(b, seed)
+            Ls = (src.n_out // 1024) * 1024
+            self.items.append((cands, lab, pid, pulses, src.snippets(cands), Ls))
+
+    def scores(self, ranker, chunk=4096):
+        """pulse_scores() of this set for one ranker."""
+        torch = __import__("torch")
+        nominal, width, det, best, neg, pos = [], [], [], [], [], []
+        n_scored, rank_s = 0, 0.0
+        for cands, lab, pid, pulses, x, Ls in self.items:
+            scores = np.empty(cands.size, np.float32)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            for i in range(0, cands.size, chunk):
+                m = min(chunk, cands.size - i)
+                logits = torch.empty((m, 2), dtype=torch.float32, device="cuda")
+                torch.cuda.synchronize()
+                e0.record()
+                gsp.gsp_ranker_forward(ranker, x[i:i + m], m, logits)
+                e1.record()
+                gsp.gsp_ranker_finish(ranker)
+                rank_s += e0.elapsed_time(e1) / 1e3
+                scores[i:i + m] = torch.softmax(logits, dim=1)[:, 1].cpu().numpy()
+            n_scored += cands.size
+            for i, p in enumerate(pulses):
+                if p.t0 + p.width > Ls:
+                    continue
+                mine = pid == i
+                nominal.append(p.snr)
+                width.append(p.width)
+                det.append(float(cands["snr"][mine].max()) if mine.any() else -1.0)
+                best.append(float(scores[mine].max()) if mine.any() else -1.0)
+            neg.append(scores[lab == 0])
+            pos.append(scores[lab == 1])
+        return {"nominal": np.array(nominal), "width": np.array(width),
+                "detected": np.array(det), "best": np.array(best),
+                "neg": np.concatenate(neg), "pos": np.concatenate(pos), "n_scored": n_scored,
+                "rank_s": rank_s}
 
 
 def build_training_set(src, beams, seed):
