@@ -36,7 +36,7 @@ DD_TRAFFIC_BYTES_PER_ADD = (1.5984e9 + 0.6663e9) / 6.899e11
 DD_TRAFFIC_VARIANT = "default"
 
 NOMINAL_SMS = 152
-RANKER_KEYS = ("recall", "recall_nominal", "precision", "negatives_rejected", "threshold",
+RANKER_KEYS = ("recall", "recall_nominal", "precision", "precision_snr8", "negatives_rejected", "threshold",
                "runs", "pulses_detected_snr_ge_min", "candidates_scored", "candidates_per_s",
                "train_snippets", "train_positives", "train_steps", "train_steps_per_s", "params",
                "recipe")
@@ -678,6 +678,7 @@ def run_ranker(args):
         detail.append(res)
         runs.append({"recall": _r(res["recall"]), "recall_nominal": _r(res["recall_nominal"]),
                      "precision": _r(res["precision"]),
+                     "precision_snr8": _r(res.get("precision_snr_ge_min")),
                      "negatives_rejected": _r(res["negatives_rejected"]),
                      "threshold": _r(thr), "missed": res["missed"][:3]})
         gsp.gsp_ranker_destroy(r)
@@ -689,6 +690,7 @@ def run_ranker(args):
     out = {"recall": min(d["recall"] for d in detail),
            "recall_nominal": min(d["recall_nominal"] for d in detail),
            "precision": min(d["precision"] for d in detail),
+           "precision_snr8": min(d.get("precision_snr_ge_min", 0.0) for d in detail),
            "negatives_rejected": min(d["negatives_rejected"] for d in detail),
            "threshold": runs[-1]["threshold"], "runs": runs,
            "pulses_detected_snr_ge_min": last["pulses_detected_snr_ge_min"],

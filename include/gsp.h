@@ -222,6 +222,20 @@ gsp_status gsp_plan_timing(gsp_plan_t plan, float *ms_dedisperse, float *ms_sear
 /* Kernel launches the last gsp_search / gsp_dedisperse call made. */
 int32_t gsp_plan_launches(gsp_plan_t plan);
 
+/* Limits of the bounded waits of the plan's tiled dedispersion pipeline (a
+ * test knob for the failure path; the paper has no counterpart).  Every wait of
+ * a consumer warp for a staged copy, and of the producer warp for a free ring
+ * slot, gives up after `cycles` SM clock cycles (1 .. 4e9, default 4e9, about
+ * 2 s): the kernel then sets the plan's error flag and its warps leave, and the
+ * next synchronising call (gsp_candidates, gsp_plan_timing) returns
+ * GSP_ERR_TIMEOUT and clears the flag, so the plan stays usable.  The producer
+ * always waits for every copy it issued to land (with the full limit) before
+ * its CTA can end, so no copy is ever in flight into released shared memory.
+ * With starve = 1 the producer issues no copies at all, so every consumer's
+ * first wait runs out (a failure made on purpose, with nothing in flight);
+ * starve = 0 restores normal operation.  Host only. */
+gsp_status gsp_plan_set_wait_limit(gsp_plan_t plan, int64_t cycles, int32_t starve);
+
 /* Tile variants of the dedispersion kernel (a tuning knob with no paper
  * counterpart; every variant computes the same bit-exact series).  Returns
  * the number of variants; if plan is not NULL and in_use is not NULL, writes
@@ -572,6 +586,26 @@ gsp_status gsp_ranker_finish(gsp_ranker_t r, void *stream);
 
 /* Kernel launches of the last forward or training step. */
 int32_t gsp_ranker_launches(gsp_ranker_t r);
+
+/* Host copy of an intermediate tensor of the last pass (a parity surface: the
+ * paper has no counterpart), for n = the last pass's snippets:
+ *   "a0" "a1" "a2"  bf16 pooled outputs of the conv layers, NHWC
+ *                   [n][32][32][8], [n][16][16][16], [n][8][8][32];
+ *   "z4" float [n][96] ReLU(fc1 + bias), "a4" bf16 [n][96] the same rounded
+ *                   to bf16, "z5" float [n][2] logits;
+ * and after a training step also
+ *   "z0" "z1" "z2"  float ReLU(conv + bias) before pooling, NHWC [n][H][H][C];
+ *   "idx0" .. "idx2" uint8 pooling argmax (0..3) per pooled output;
+ *   "g5" float [n][2] gradient of the mean loss w.r.t. the logits;
+ *   "g4" bf16 [n][96] gradient w.r.t. fc1's output before ReLU;
+ *   "ga0" .. "ga2"  float gradient w.r.t. the pooled output of conv layer l;
+ *   "gz0" .. "gz2"  bf16 gradient w.r.t. the pre-pool output of conv layer l.
+ * *bytes receives the size; GSP_ERR_CAPACITY (nothing copied) if host_out is
+ * NULL or cap_bytes is smaller, GSP_ERR_STATE before any pass or for a
+ * training tensor after an inference pass, GSP_ERR_INVALID_ARG for an unknown
+ * name.  Synchronises the device. */
+gsp_status gsp_ranker_tensor(gsp_ranker_t r, const char *name, void *host_out, int64_t cap_bytes,
+                             int64_t *bytes);
 
 /* Static text for a status code. */
 const char *gsp_status_string(gsp_status s);

@@ -89,7 +89,6 @@ cudaError_t launch_dedisperse_simple(const gsp_plan_s *p, const uint8_t *x, int6
 namespace {
 
 constexpr int kMaxBatchBeams = 32;  // beams per launch
-constexpr long long kWaitBudget = 4000000000ll;  // ~2 s of SM clock per wait
 
 // One beam of a launch: its input, delay tables, output and tiling.
 struct BeamTile {
@@ -129,6 +128,9 @@ struct TiledArgs {
     uint32_t one;  // 1, passed at run time so that x * one + acc stays on the multiply-add pipe
     int *err;      // set to 1 if a bounded wait gave up
     int64_t items;
+    long long budget;  // SM clock cycles a pipeline wait may take before it gives up
+    int starve;        // failure-path test: the producer issues nothing, so every stage wait
+                       // runs out (no copy is ever in flight)
 };
 
 // Work item -> beam, time tile and DM block.  Inside a beam: groups of `grp`
@@ -355,6 +357,7 @@ __global__ void __launch_bounds__((KDM / KW + 1) * 32, (KDM / KW + 1) * 32 <= 25
 
     if (warp == kCW) {
         // ------------------------------------------------------- producer warp
+        if (a.starve) return;  // failure-path test: nothing issued, nothing in flight
         int64_t gst = 0;  // stages issued by this CTA so far (across items)
         int slot = 0;           // ring slot of the next stage
         uint32_t rpar = 0;      // parity of the slot's current round
@@ -369,7 +372,7 @@ __global__ void __launch_bounds__((KDM / KW + 1) * 32, (KDM / KW + 1) * 32 <= 25
         const int32_t *bmin = bt.blkmin + (int64_t)blk * a.nchan;
         for (int st = 0; st < nst && ok; st++, gst++) {
             if (wrapped) {
-                const bool w = ptx::mbar_wait(empty(slot), rpar ^ 1u, kWaitBudget);
+                const bool w = ptx::mbar_wait(empty(slot), rpar ^ 1u, a.budget);
                 if (!__all_sync(0xffffffffu, w)) {
                     ok = false;
                     break;
@@ -424,10 +427,12 @@ __global__ void __launch_bounds__((KDM / KW + 1) * 32, (KDM / KW + 1) * 32 <= 25
         }
         }
         if (!ok && lane == 0) fail(a.err);
-        // never leave with copies in flight: wait for the last phase of each slot
+        // never leave with copies in flight: wait for the last phase of each slot (with
+        // the full limit, whatever a.budget is; the CTA's shared memory stays allocated
+        // until this warp returns, even if the consumer warps have given up and left)
         for (int64_t st = max((int64_t)0, gst - a.stages); st < gst; st++) {
             const bool w = ptx::mbar_wait(full((int)(st % a.stages)), (uint32_t)((st / a.stages) & 1),
-                                          kWaitBudget);
+                                          kWaitLimit);
             if (!__all_sync(0xffffffffu, w)) {
                 if (lane == 0) fail(a.err);
                 break;
@@ -543,7 +548,7 @@ __global__ void __launch_bounds__((KDM / KW + 1) * 32, (KDM / KW + 1) * 32 <= 25
             }
         }
         __syncwarp();
-        const bool landed = ptx::mbar_wait(full(slot), rpar, kWaitBudget);
+        const bool landed = ptx::mbar_wait(full(slot), rpar, a.budget);
         if (!__all_sync(0xffffffffu, landed)) {
             if (lane == 0) fail(a.err);
             return;
@@ -859,6 +864,9 @@ const TiledVariant kVariants[] = {
     {dd_tiled_kernel<1, false, 3, true, 6, 32, false, true, true, 15, 2, true>, 1, 6, 32, true, 15},
     {dd_tiled_kernel<1, false, 3, true, 4, 32, false, true, true, 15, 2, true>, 1, 4, 32, true, 15},
     {dd_tiled_kernel<1, false, 3, true, 6, 32, false, true, true, 7, 2, true>, 1, 6, 32, true, 7},
+    // four channels per step (one 16-byte list-entry load per four channels)
+    {dd_tiled_kernel<1, true, 3, true, 6, 64, false, true, true, 15, 2, true>, 1, 6, 64, true, 15},
+    {dd_tiled_kernel<1, true, 3, true, 6, 32, false, true, true, 15, 2, true>, 1, 6, 32, true, 15},
 };
 constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
 
@@ -1158,6 +1166,8 @@ cudaError_t launch_dedisperse_batch(const BeamLaunch *beams, int nbeams, int var
     a.one = 1u;
     a.err = err;
     a.items = items;
+    a.budget = beams[0].plan->wait_budget;
+    a.starve = beams[0].plan->wait_starve;
     int64_t grid = persistent ? std::min<int64_t>(items, (int64_t)num_sms * f.ctas_per_sm) : items;
     if (grid < 1 || grid > 0x7fffffffll) return cudaErrorInvalidConfiguration;
     v.fn<<<(unsigned)grid, (v.kdm / v.kw + 1) * 32, f.smem, s>>>(a);

@@ -644,6 +644,14 @@ gsp_status gsp_plan_timing(gsp_plan_t p, float *ms_dd, float *ms_search) {
 
 int32_t gsp_plan_launches(gsp_plan_t p) { return p ? p->launches : -1; }
 
+gsp_status gsp_plan_set_wait_limit(gsp_plan_t p, int64_t cycles, int32_t starve) {
+    if (!p || cycles < 1 || cycles > gsp::kWaitLimit || starve < 0 || starve > 1)
+        return GSP_ERR_INVALID_ARG;
+    p->wait_budget = cycles;
+    p->wait_starve = starve;
+    return GSP_OK;
+}
+
 gsp_status gsp_plan_series(gsp_plan_t p, const int32_t **d_D, int64_t *stride, int64_t *n_out) {
     if (!p || !d_D || !stride || !n_out) return GSP_ERR_INVALID_ARG;
     if (!p->have_search) return GSP_ERR_STATE;

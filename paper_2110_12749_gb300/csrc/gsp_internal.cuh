@@ -11,6 +11,7 @@
 namespace gsp {
 
 constexpr int kMaxWidths = 32;
+constexpr long long kWaitLimit = 4000000000ll;  // ~2 s of SM clock: the longest bounded wait
 
 // DM trials per CTA of the tiled dedispersion kernel (one per consumer warp):
 // 16; 15 so that the CTA (15 consumer warps + 1 producer) is 16 warps and each
@@ -115,6 +116,9 @@ struct gsp_plan_s {
     cudaStream_t h2d_stream = nullptr;
     cudaEvent_t h2d_ev[9] = {};  // one per chunk + one for the caller's stream
     bool timed = false;
+    // bounded waits of the tiled dedispersion pipeline (gsp_plan_set_wait_limit)
+    long long wait_budget = gsp::kWaitLimit;
+    int wait_starve = 0;
     cudaStream_t last_stream = nullptr;
     int64_t last_nout = -1;
     int64_t last_nb = 0;

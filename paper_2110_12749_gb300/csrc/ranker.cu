@@ -21,6 +21,7 @@
 #include <cmath>
 #include <cstring>
 #include <new>
+#include <string>
 #include <vector>
 
 #include "gsp_internal.cuh"
@@ -681,6 +682,8 @@ struct gsp_ranker_s {
     int *err = nullptr;
     std::vector<void *> allocs;
     int32_t launches = 0;
+    int32_t last_n = 0;      // snippets of the last pass
+    int last_pass = 0;       // 0 none, 1 inference (gsp_ranker_forward), 2 training step
 };
 
 namespace {
@@ -871,50 +874,72 @@ gsp_status status_of(cudaError_t e, const char *what) {
 // normalised series of row dm - 32 + i, ((D - m) - (c0 + beta j)) / sigma_ref
 // (0 in bad blocks, rows with sigma_ref = 0, outside the rows or past Ls),
 // divided by sqrt(f).
-__global__ void snippet_kernel(const int32_t *__restrict__ D, int64_t stride, int ndm, int64_t Ls,
-                               int B, const gsp::BlockParam *__restrict__ bp, int64_t nb_max,
-                               const double *__restrict__ sref, const gsp_cand *__restrict__ cands,
-                               float *__restrict__ out) {
+//
+// Warp w builds rows w, w + 8, ...; a row in two halves of 32 time bins.  The
+// warp first copies the half's 32 f consecutive samples of D into its shared
+// buffer (coalesced: consecutive lanes, consecutive samples), then lane l sums
+// bin 32 h + l from shared memory (f is odd except for f = 2, so the lanes'
+// strided reads hit distinct banks).  A bin is summed as exact integer runs
+// inside one search block, with the block's trend applied in closed form.
+constexpr int kSnipMaxF = 37;  // f of the widest default boxcar (150 / 4)
+
+__global__ void __launch_bounds__(256) snippet_kernel(
+    const int32_t *__restrict__ D, int64_t stride, int ndm, int64_t Ls, int B,
+    const gsp::BlockParam *__restrict__ bp, int64_t nb_max, const double *__restrict__ sref,
+    const gsp_cand *__restrict__ cands, float *__restrict__ out) {
     const gsp_cand c = cands[blockIdx.x];
     const int f = max(1, c.width / 4);
     const int64_t tc = c.t + c.width / 2;
     const float rs = 1.0f / sqrtf((float)f);
-    // 1 / sigma_ref of the snippet's rows, once per row (0: row left blank)
-    __shared__ float s_inv[kS];
-    for (int i = threadIdx.x; i < kS; i += blockDim.x) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __shared__ int32_t seg[8][32 * kSnipMaxF];
+    float *o = out + (int64_t)blockIdx.x * kS * kS;
+    for (int i = warp; i < kS; i += 8) {
         const int r = c.dm_idx - kS / 2 + i;
-        s_inv[i] = (r >= 0 && r < ndm && sref[r] > 0.0) ? (float)(1.0 / sref[r]) : 0.0f;
-    }
-    __syncthreads();
-    for (int o = threadIdx.x; o < kS * kS; o += blockDim.x) {
-        const int i = o / kS, j = o % kS;
-        const int r = c.dm_idx - kS / 2 + i;
-        float v = 0.0f;
-        const float inv = s_inv[i];
-        if (inv != 0.0f) {
-            const int64_t a = tc + (int64_t)(j - kS / 2) * f;
+        const float inv = (r >= 0 && r < ndm && sref[r] > 0.0) ? (float)(1.0 / sref[r]) : 0.0f;
+        if (inv == 0.0f) {  // warp-uniform: a blank row
+            o[i * kS + lane] = 0.0f;
+            o[i * kS + 32 + lane] = 0.0f;
+            continue;
+        }
+        const int32_t *drow = D + (int64_t)r * stride;
+        const gsp::BlockParam *brow = bp + (int64_t)r * nb_max;
+        for (int h = 0; h < 2; h++) {
+            const int64_t a0 = tc + (int64_t)(32 * h - kS / 2) * f;  // first sample of bin 32 h
+            if (f <= kSnipMaxF) {
+                __syncwarp();
+                for (int idx = lane; idx < 32 * f; idx += 32) {
+                    const int64_t t = a0 + idx;
+                    seg[warp][idx] = (t >= 0 && t < Ls) ? __ldg(drow + t) : 0;
+                }
+                __syncwarp();
+            }
+            const int64_t a = a0 + (int64_t)lane * f;
             int64_t s0 = max(a, (int64_t)0);
             const int64_t s1 = min(a + f, Ls);
-            const int32_t *drow = D + (int64_t)r * stride;
-            // the bin in runs of samples inside one block (at most two runs, f <= B):
-            // sum over the run of (D - m) - (c0 + beta jb) = (sum D - n m) - (n c0 + beta sum jb)
+            float v = 0.0f;
+            // at most two runs: f <= B
             while (s0 < s1) {
                 const int64_t b = s0 / B;
                 const int jb0 = (int)(s0 - b * B);
                 const int64_t e = min(s1, (b + 1) * (int64_t)B);
                 const int n = (int)(e - s0);
-                const gsp::BlockParam q = bp[(int64_t)r * nb_max + b];
+                const gsp::BlockParam q = brow[b];
                 if (q.good) {
                     int64_t sd = 0;  // exact
-                    for (int64_t t = s0; t < e; t++) sd += drow[t];
+                    if (f <= kSnipMaxF) {
+                        for (int64_t t = s0; t < e; t++) sd += seg[warp][t - a0];
+                    } else {
+                        for (int64_t t = s0; t < e; t++) sd += drow[t];
+                    }
                     const int64_t sj = (int64_t)n * jb0 + (int64_t)n * (n - 1) / 2;
                     v += ((float)(sd - (int64_t)n * q.m) - ((float)n * q.c0 + q.beta * (float)sj)) *
                          inv;
                 }
                 s0 = e;
             }
+            o[i * kS + 32 * h + lane] = v * rs;
         }
-        out[(int64_t)blockIdx.x * kS * kS + o] = v * rs;
     }
 }
 
@@ -1031,6 +1056,8 @@ gsp_status gsp_ranker_forward(gsp_ranker_t r, const float *d_x, int32_t n, float
     cudaStream_t s = (cudaStream_t)stream;
     r->launches = 0;
     cudaError_t e = forward(r, d_x, n, false, s);
+    r->last_n = n;
+    r->last_pass = 1;
     if (e == cudaSuccess && d_logits)
         e = cudaMemcpyAsync(d_logits, r->z5, (size_t)n * 2 * 4, cudaMemcpyDeviceToDevice, s);
     return status_of(e, "ranker forward");
@@ -1044,6 +1071,8 @@ gsp_status gsp_ranker_train_step(gsp_ranker_t r, const float *d_x, const int32_t
     r->launches = 0;
     cudaError_t e = forward(r, d_x, n, true, s);
     if (e == cudaSuccess) e = backward(r, d_labels, n, lr, s);
+    r->last_n = n;
+    r->last_pass = 2;
     if (e == cudaSuccess && d_loss)
         e = cudaMemcpyAsync(d_loss, r->loss, sizeof(float), cudaMemcpyDeviceToDevice, s);
     return status_of(e, "ranker train step");
@@ -1063,5 +1092,39 @@ gsp_status gsp_ranker_finish(gsp_ranker_t r, void *stream) {
 }
 
 int32_t gsp_ranker_launches(gsp_ranker_t r) { return r ? r->launches : -1; }
+
+gsp_status gsp_ranker_tensor(gsp_ranker_t r, const char *name, void *host_out, int64_t cap_bytes,
+                             int64_t *bytes) {
+    if (!r || !name || !bytes || cap_bytes < 0) return GSP_ERR_INVALID_ARG;
+    if (r->last_pass == 0) return GSP_ERR_STATE;
+    const int64_t n = r->last_n;
+    const void *src = nullptr;
+    int64_t size = 0;
+    bool train_only = false;
+    const std::string nm(name);
+    for (int l = 0; l < kLayers && !src; l++) {
+        const int64_t H = side_of(l), H2 = H / 2, C = cout_of(l);
+        const std::string d = std::to_string(l);
+        if (nm == "a" + d) { src = r->a[l]; size = n * H2 * H2 * C * 2; }
+        else if (nm == "z" + d) { src = r->z[l]; size = n * H * H * C * 4; train_only = true; }
+        else if (nm == "idx" + d) { src = r->idx[l]; size = n * H2 * H2 * C; train_only = true; }
+        else if (nm == "ga" + d) { src = r->ga[l]; size = n * H2 * H2 * C * 4; train_only = true; }
+        else if (nm == "gz" + d) { src = r->gz[l]; size = n * H * H * C * 2; train_only = true; }
+    }
+    if (!src) {
+        if (nm == "z4") { src = r->z4; size = n * kHid * 4; }
+        else if (nm == "a4") { src = r->a4; size = n * kHid * 2; }
+        else if (nm == "z5") { src = r->z5; size = n * 2 * 4; }
+        else if (nm == "g5") { src = r->g5; size = n * 2 * 4; train_only = true; }
+        else if (nm == "g4") { src = r->g4; size = n * kHid * 2; train_only = true; }
+        else return GSP_ERR_INVALID_ARG;
+    }
+    if (train_only && r->last_pass != 2) return GSP_ERR_STATE;
+    *bytes = size;
+    if (!host_out || cap_bytes < size) return GSP_ERR_CAPACITY;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(host_out, src, (size_t)size, cudaMemcpyDeviceToHost);
+    return status_of(e, "ranker tensor");
+}
 
 }  // extern "C"

@@ -33,79 +33,109 @@ __device__ __forceinline__ void stage_tile(uint8_t *dst, const __nv_bfloat16 *__
     }
 }
 
+constexpr int kStages = 4;  // shared-memory ring depth of the pipelined kernel
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src, uint32_t src_bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src),
+                 "r"(src_bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// Issue the 16-byte copies of one ROWS x 64 bf16 tile of a K-contiguous matrix
+// into the core-matrix layout (element (r, c) at byte (r/8)*1024 + (c/8)*128 +
+// (r%8)*16 + (c%8)*2); rows >= nrows and columns >= kend are zero-filled
+// (kend is a multiple of 8).  Consecutive threads take consecutive rows of
+// one 16-byte column chunk.
+template <int ROWS>
+__device__ __forceinline__ void issue_tile(uint32_t dst, const __nv_bfloat16 *__restrict__ src,
+                                           int64_t ld, int row0, int nrows, int k0, int kend) {
+#pragma unroll 4
+    for (int idx = threadIdx.x; idx < ROWS * 8; idx += 128) {
+        const int r = idx % ROWS, c8 = idx / ROWS;
+        const int gr = row0 + r, gk = k0 + c8 * 8;
+        const bool in = gr < nrows && gk < kend;
+        const __nv_bfloat16 *g = in ? src + (int64_t)gr * ld + gk : src;
+        cp_async16(dst + (uint32_t)((r >> 3) * 1024 + c8 * 128 + (r & 7) * 16), g, in ? 16u : 0u);
+    }
+}
+
+// C (+)= A B^T, one 128 x BN output column block per CTA row of the grid
+// (blockIdx.y), a K chunk per blockIdx.z (split-K), and CTAs striding over the
+// M tiles.  The CTA's (M tile, 64-wide K step) pairs form one sequence that
+// flows through a ring of kStages shared-memory stages: all 128 threads copy
+// stage j + kStages - 1 (cp.async) while thread 0's MMAs of stage j run, and
+// a stage is refilled only after the MMAs that read it have completed (one
+// mbarrier per stage, signalled by tcgen05.commit).  The accumulator
+// alternates between two TMEM column blocks per M tile, so the epilogue of
+// tile t (tcgen05.ld by all four warps, bias, ReLU, stores or split-K atomics)
+// runs while the MMAs of tile t + 1 accumulate into the other block.  Every
+// wait is bounded; a wait that gives up sets *err, and the CTA waits (bounded)
+// for its committed MMAs and its copies before it frees tensor memory.
 template <int BN>
 __global__ void __launch_bounds__(128) gemm_bf16_kernel(
     const __nv_bfloat16 *__restrict__ A, int64_t lda, const __nv_bfloat16 *__restrict__ B,
     int64_t ldb, float *C, int64_t ldc, __nv_bfloat16 *Cb, int64_t ldcb, int M, int N, int K,
     int kchunk, const float *__restrict__ bias, int relu, int *err) {
-    static_assert(BN % 16 == 0 && BN >= 16 && BN <= 256, "tcgen05 M=128 needs N in 16..256");
-    __shared__ __align__(1024) uint8_t sA[kBM * kBK * 2];
-    __shared__ __align__(1024) uint8_t sB[BN * kBK * 2];
-    __shared__ __align__(8) uint64_t mbar;
-    __shared__ uint32_t tmem_base;
-    constexpr uint32_t kCols = BN < 32 ? 32u : (uint32_t)BN;
+    static_assert(BN % 16 == 0 && BN >= 16 && BN <= 128, "tcgen05 M=128 with N in 16..128");
+    constexpr int kABytes = kBM * kBK * 2, kBBytes = BN * kBK * 2;
+    constexpr int kStageBytes = kABytes + kBBytes;
+    constexpr uint32_t kCols = 2 * BN < 32 ? 32u : (uint32_t)(2 * BN);  // two accumulators
     constexpr uint32_t kIdesc = tc::idesc_bf16(kBM, BN);
+    extern __shared__ __align__(1024) uint8_t smem[];
+    __shared__ __align__(8) uint64_t bar_stage[kStages];
+    __shared__ __align__(8) uint64_t bar_acc[2];
+    __shared__ uint32_t tmem_base;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int n0 = blockIdx.y * BN;
     const int kbeg = blockIdx.z * kchunk;
     const int kend = min(K, kbeg + kchunk);
     const int mtiles = (M + kBM - 1) / kBM;
-    const uint32_t bar = tc::smem_u32(&mbar);
+    const int nks = kend > kbeg ? (kend - kbeg + kBK - 1) / kBK : 0;  // K steps per tile
+    const int ntile_mine = blockIdx.x < mtiles ? (mtiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    const int total = ntile_mine * nks;                                   // sequence length
     if (warp == 0) tc::tmem_alloc(tc::smem_u32(&tmem_base), kCols);
-    if (tid == 0) tc::mbar_init1(bar);
+    if (tid == 0) {
+        for (int i = 0; i < kStages; i++) tc::mbar_init1(tc::smem_u32(&bar_stage[i]));
+        for (int i = 0; i < 2; i++) tc::mbar_init1(tc::smem_u32(&bar_acc[i]));
+    }
     tc::fence_before();
     __syncthreads();
     tc::fence_after();
     const uint32_t tmem = tmem_base;
-    const uint32_t aaddr = tc::smem_u32(sA), baddr = tc::smem_u32(sB);
-    uint32_t phase = 0;
-    bool ok = true;
-    bool pending = false;  // MMAs committed and not yet waited for
-    // CTAs stride over the M tiles; tensor memory and the barrier are reused
-    for (int mt = blockIdx.x; mt < mtiles && ok; mt += gridDim.x) {
-        const int m0 = mt * kBM;
-        for (int k0 = kbeg; k0 < kend; k0 += kBK) {
-            const int nk = min(kBK, kend - k0);       // a multiple of 8
-            const int nmma = (nk + 15) / 16;          // K = 16 per MMA
-            // stage the 16-byte chunks the MMAs read (2 per MMA; zeros past kend)
-            stage_tile<kBM>(sA, A, lda, m0, M, k0, kend, 2 * nmma);
-            stage_tile<BN>(sB, B, ldb, n0, N, k0, kend, 2 * nmma);
-            tc::fence_proxy_async();  // generic-proxy smem writes -> tensor-core reads
-            tc::fence_before();
-            __syncthreads();
-            if (tid == 0) {
-                tc::fence_after();
-                for (int kk = 0; kk < nmma; kk++) {
-                    // two core matrices along K (256 bytes) per MMA
-                    const uint64_t ad = tc::smem_desc(aaddr + kk * 256, 128, 1024);
-                    const uint64_t bd = tc::smem_desc(baddr + kk * 256, 128, 1024);
-                    tc::mma_bf16(tmem, ad, bd, kIdesc, (k0 > kbeg || kk > 0) ? 1u : 0u);
-                }
-                tc::mma_commit(bar);
-            }
-            pending = true;
-            const bool done = tc::mbar_wait_bounded(bar, phase, kGemmBudget);
-            phase ^= 1u;
-            if (!__syncthreads_and(done)) {
-                ok = false;
-                break;
-            }
-            pending = false;
-            tc::fence_after();
+    const uint32_t sbase = tc::smem_u32(smem);
+    auto load = [&](int j) {  // copies of sequence entry j into stage j % kStages
+        if (j < total) {
+            const int lt = j / nks, ks = j - lt * nks;
+            const int m0 = (blockIdx.x + lt * gridDim.x) * kBM;
+            const int k0 = kbeg + ks * kBK;
+            const uint32_t st = sbase + (uint32_t)((j % kStages) * kStageBytes);
+            issue_tile<kBM>(st, A, lda, m0, M, k0, kend);
+            issue_tile<BN>(st + kABytes, B, ldb, n0, N, k0, kend);
         }
-        if (!ok || kbeg >= kend) break;
+        cp_async_commit();  // one group per entry, empty past the end
+    };
+    auto epilogue = [&](int lt) {
+        const int m0 = (blockIdx.x + lt * gridDim.x) * kBM;
         const int row = m0 + warp * 32 + lane;
-        const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
+        const uint32_t lane_addr =
+            tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)((lt & 1) * BN);
 #pragma unroll 1
         for (int c0 = 0; c0 < BN; c0 += 16) {
             float v[16];
             tc::tmem_ld16(lane_addr + (uint32_t)c0, v);
             if (row < M) {
 #pragma unroll
-                for (int j = 0; j < 16; j++) {
-                    const int n = n0 + c0 + j;
+                for (int jj = 0; jj < 16; jj++) {
+                    const int n = n0 + c0 + jj;
                     if (n >= N) break;
-                    float val = v[j];
+                    float val = v[jj];
                     if (gridDim.z > 1) {
                         atomicAdd(C + (int64_t)row * ldc + n, val);
                     } else {
@@ -117,19 +147,100 @@ __global__ void __launch_bounds__(128) gemm_bf16_kernel(
                 }
             }
         }
-        // every lane's tensor-memory reads are complete before the next tile's MMAs
+    };
+    bool ok = true;
+    int committed = 0;  // stage mbarrier phases committed by thread 0 (MMAs issued)
+    for (int j = 0; j < kStages - 1; j++) load(j);
+    for (int j = 0; j < total && ok; j++) {
+        const int lt = j / nks, ks = j - lt * nks;
+        cp_async_wait<kStages - 2>();  // this thread's copies of entry j have landed
+        tc::fence_proxy_async();      // ... and are visible to the tensor cores
         tc::fence_before();
         __syncthreads();
-        tc::fence_after();
+        if (tid == 0) {
+            tc::fence_after();
+            const int k0 = kbeg + ks * kBK;
+            const int nmma = (min(kBK, kend - k0) + 15) / 16;  // K = 16 per MMA
+            const uint32_t st = sbase + (uint32_t)((j % kStages) * kStageBytes);
+            const uint32_t acc = tmem + (uint32_t)((lt & 1) * BN);
+            for (int kk = 0; kk < nmma; kk++) {
+                // two core matrices along K (256 bytes) per MMA
+                const uint64_t ad = tc::smem_desc(st + kk * 256, 128, 1024);
+                const uint64_t bd = tc::smem_desc(st + kABytes + kk * 256, 128, 1024);
+                tc::mma_bf16(acc, ad, bd, kIdesc, (ks > 0 || kk > 0) ? 1u : 0u);
+            }
+            tc::mma_commit(tc::smem_u32(&bar_stage[j % kStages]));
+            if (ks == nks - 1) tc::mma_commit(tc::smem_u32(&bar_acc[lt & 1]));
+        }
+        committed = j + 1;
+        // refill the stage of entry j - 1 once its MMAs are done
+        if (j >= 1) {
+            const int jp = j - 1;
+            const bool done = tc::mbar_wait_bounded(tc::smem_u32(&bar_stage[jp % kStages]),
+                                                    (uint32_t)((jp / kStages) & 1), kGemmBudget);
+            if (!__all_sync(0xffffffffu, done)) ok = false;
+        }
+        if (!__syncthreads_and(ok)) {
+            ok = false;
+            break;
+        }
+        load(j + kStages - 1);
+        // the previous tile's epilogue, while this tile's MMAs run
+        if (ks == 0 && lt > 0) {
+            const bool done = tc::mbar_wait_bounded(tc::smem_u32(&bar_acc[(lt - 1) & 1]),
+                                                    (uint32_t)(((lt - 1) >> 1) & 1), kGemmBudget);
+            if (!__syncthreads_and(done)) {
+                ok = false;
+                break;
+            }
+            tc::fence_after();
+            epilogue(lt - 1);
+        }
     }
+    if (ok && ntile_mine > 0 && nks > 0) {
+        const int lt = ntile_mine - 1;
+        const bool done = tc::mbar_wait_bounded(tc::smem_u32(&bar_acc[lt & 1]),
+                                                (uint32_t)((lt >> 1) & 1), kGemmBudget);
+        if (__syncthreads_and(done)) {
+            tc::fence_after();
+            epilogue(lt);
+        } else {
+            ok = false;
+        }
+    }
+    cp_async_wait<0>();  // no copy in flight into shared memory when the CTA ends
     if (!ok) {
         if (tid == 0) atomicExch(err, 1);
-        // never release tensor memory under MMAs still in flight (bounded)
-        if (pending) (void)tc::mbar_wait_bounded(bar, phase ^ 1u, kGemmBudget);
+        // never release tensor memory under MMAs still in flight (bounded): the
+        // last committed stage barrier completes after every earlier MMA
+        if (committed > 0) {
+            const int jl = committed - 1;
+            (void)tc::mbar_wait_bounded(tc::smem_u32(&bar_stage[jl % kStages]),
+                                        (uint32_t)((jl / kStages) & 1), kGemmBudget);
+        }
     }
     tc::fence_before();
     __syncthreads();
     if (warp == 0) tc::tmem_dealloc(tmem, kCols);
+}
+
+// Launch one instantiation; its dynamic shared-memory limit (above the 48 KB
+// default) is raised once per instantiation.
+template <int BN>
+cudaError_t launch_bn(dim3 grid, int smem, cudaStream_t s, const __nv_bfloat16 *A, int64_t lda,
+                      const __nv_bfloat16 *B, int64_t ldb, float *C, int64_t ldc,
+                      __nv_bfloat16 *Cb, int64_t ldcb, int M, int N, int K, int kchunk,
+                      const float *bias, int relu, int *err) {
+    static int configured = 0;
+    if (configured < smem) {
+        cudaError_t e = cudaFuncSetAttribute(gemm_bf16_kernel<BN>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        configured = smem;
+    }
+    gemm_bf16_kernel<BN><<<grid, 128, smem, s>>>(A, lda, B, ldb, C, ldc, Cb, ldcb, M, N, K, kchunk,
+                                                 bias, relu, err);
+    return cudaSuccess;
 }
 
 }  // namespace
@@ -150,31 +261,27 @@ cudaError_t launch_gemm_bf16(const __nv_bfloat16 *A, int64_t lda, const __nv_bfl
     const int kchunk = ((ksteps + splitk - 1) / splitk) * kBK;
     splitk = (K + kchunk - 1) / kchunk;
     const int BN = N <= 16 ? 16 : N <= 32 ? 32 : N <= 64 ? 64 : 128;
-    // one CTA per M tile: with one synchronous stage -> MMA -> epilogue chain
-    // per tile, many short CTAs overlap better than fewer CTAs striding over
-    // the tiles (measured); the kernel still strides if the grid is capped
+    // CTAs stride over the M tiles: enough CTAs for every SM (by shared memory,
+    // at most 227 KB per SM) across the N tiles and K chunks, at most one per M tile
     const int mtiles = (M + kBM - 1) / kBM, ntiles = (N + BN - 1) / BN;
-    const int mgrid = std::max(1, std::min(mtiles, 1 << 30));
+    const int smem = kStages * (kBM + BN) * kBK * 2;
+    int dev = 0, nsm = 152;
+    if (cudaGetDevice(&dev) == cudaSuccess)
+        (void)cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    (void)cudaGetLastError();
+    const int per_sm = std::max(1, (227 * 1024) / (smem + 1024));
+    const int64_t want = ((int64_t)nsm * per_sm + (int64_t)ntiles * splitk - 1) / ((int64_t)ntiles * splitk);
+    const int mgrid = (int)std::max<int64_t>(1, std::min<int64_t>(mtiles, want));
     dim3 grid((unsigned)mgrid, (unsigned)ntiles, (unsigned)splitk);
     const int r = relu ? 1 : 0;
+    cudaError_t e;
     switch (BN) {
-        case 16:
-            gemm_bf16_kernel<16><<<grid, 128, 0, s>>>(A, lda, B, ldb, C, ldc, Cb, ldcb, M, N, K,
-                                                      kchunk, bias, r, err);
-            break;
-        case 32:
-            gemm_bf16_kernel<32><<<grid, 128, 0, s>>>(A, lda, B, ldb, C, ldc, Cb, ldcb, M, N, K,
-                                                      kchunk, bias, r, err);
-            break;
-        case 64:
-            gemm_bf16_kernel<64><<<grid, 128, 0, s>>>(A, lda, B, ldb, C, ldc, Cb, ldcb, M, N, K,
-                                                      kchunk, bias, r, err);
-            break;
-        default:
-            gemm_bf16_kernel<128><<<grid, 128, 0, s>>>(A, lda, B, ldb, C, ldc, Cb, ldcb, M, N, K,
-                                                       kchunk, bias, r, err);
-            break;
+        case 16: e = launch_bn<16>(grid, smem, s, A, lda, B, ldb, C, ldc, Cb, ldcb, M, N, K, kchunk, bias, r, err); break;
+        case 32: e = launch_bn<32>(grid, smem, s, A, lda, B, ldb, C, ldc, Cb, ldcb, M, N, K, kchunk, bias, r, err); break;
+        case 64: e = launch_bn<64>(grid, smem, s, A, lda, B, ldb, C, ldc, Cb, ldcb, M, N, K, kchunk, bias, r, err); break;
+        default: e = launch_bn<128>(grid, smem, s, A, lda, B, ldb, C, ldc, Cb, ldcb, M, N, K, kchunk, bias, r, err); break;
     }
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 

@@ -110,6 +110,7 @@ def lib():
             "gsp_plan_launches": ([_vp], ctypes.c_int32),
             "gsp_dedisperse_variants": ([_vp, _vp], ctypes.c_int32),
             "gsp_plan_tune": ([_vp, _vp, _i64, _i64, _vp, _vp, _vp], ctypes.c_int),
+            "gsp_plan_set_wait_limit": ([_vp, _i64, ctypes.c_int32], ctypes.c_int),
             "gsp_plan_series": ([_vp, _vp, _vp, _vp], ctypes.c_int),
             "gsp_batch_tune_results": ([_vp, _vp, _vp, ctypes.c_int32], ctypes.c_int32),
             "gsp_stream_create": ([_vp, _vp, _i64, ctypes.c_int32], ctypes.c_int),
@@ -158,6 +159,7 @@ def lib():
                                       ctypes.c_int),
             "gsp_ranker_finish": ([_vp, _vp], ctypes.c_int),
             "gsp_ranker_launches": ([_vp], ctypes.c_int32),
+            "gsp_ranker_tensor": ([_vp, ctypes.c_char_p, _vp, _i64, _vp], ctypes.c_int),
             "gsp_status_string": ([ctypes.c_int], ctypes.c_char_p),
             "gsp_last_error_string": ([], ctypes.c_char_p),
             "gsp_version": ([], ctypes.c_int32),
@@ -388,6 +390,11 @@ def gsp_plan_timing(plan):
     _check(lib().gsp_plan_timing(plan.handle, ctypes.byref(a), ctypes.byref(b)),
            "gsp_plan_timing")
     return a.value, b.value
+
+
+def gsp_plan_set_wait_limit(plan, cycles, starve=0):
+    _check(lib().gsp_plan_set_wait_limit(plan.handle, int(cycles), int(starve)),
+           "gsp_plan_set_wait_limit")
 
 
 def gsp_plan_launches(plan):
@@ -867,6 +874,24 @@ def gsp_ranker_train_step(r, x, labels, n, lr, loss=None, stream=None):
 
 def gsp_ranker_finish(r, stream=None):
     _check(lib().gsp_ranker_finish(r.handle, _stream(stream)), "gsp_ranker_finish")
+
+
+def gsp_ranker_tensor(r, name):
+    """Host copy of an intermediate tensor of the last pass: numpy float64 for
+    bf16 and float tensors (bf16 widened exactly), uint8 for the argmaxes; flat."""
+    nb = ctypes.c_int64(0)
+    st = lib().gsp_ranker_tensor(r.handle, name.encode(), None, 0, ctypes.byref(nb))
+    if st != GSP_ERR_CAPACITY:
+        _check(st, "gsp_ranker_tensor")
+    raw = np.empty(nb.value, np.uint8)
+    _check(lib().gsp_ranker_tensor(r.handle, name.encode(), _np_ptr(raw), nb.value,
+                                   ctypes.byref(nb)), "gsp_ranker_tensor")
+    if name.startswith("idx"):
+        return raw
+    if name in ("a4", "g4") or name.startswith("gz") or (name[0] == "a" and name[1:].isdigit()):
+        u = raw.view(np.uint16).astype(np.uint32) << 16
+        return u.view(np.float32).astype(np.float64)
+    return raw.view(np.float32).astype(np.float64)
 
 
 def gsp_ranker_launches(r):

@@ -138,17 +138,27 @@ class ScoredBeams:
     evaluation sets)."""
 
     def __init__(self, src, beams, seed):
+        torch = __import__("torch")
         self.items = []
+        self.snip_s = 0.0   # device time of the snippet extraction (CUDA events)
         for b in range(beams):
             cands, lab, pid, pulses = src.search(b, seed)
             Ls = (src.n_out // 1024) * 1024
-            self.items.append((cands, lab, pid, pulses, src.snippets(cands), Ls))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record()
+            x = src.snippets(cands)
+            e1.record()
+            torch.cuda.synchronize()
+            self.snip_s += e0.elapsed_time(e1) / 1e3
+            self.items.append((cands, lab, pid, pulses, x, Ls))
 
     def scores(self, ranker, chunk=4096):
         """pulse_scores() of this set for one ranker."""
         torch = __import__("torch")
-        nominal, width, det, best, neg, pos = [], [], [], [], [], []
-        n_scored, rank_s = 0, 0.0
+        nominal, width, det, best, best8 = [], [], [], [], []
+        neg, pos, neg_snr, pos_snr = [], [], [], []
+        n_scored, rank_s = 0, self.snip_s
         for cands, lab, pid, pulses, x, Ls in self.items:
             scores = np.empty(cands.size, np.float32)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -171,12 +181,17 @@ class ScoredBeams:
                 width.append(p.width)
                 det.append(float(cands["snr"][mine].max()) if mine.any() else -1.0)
                 best.append(float(scores[mine].max()) if mine.any() else -1.0)
+                m8 = mine & (cands["snr"] >= 8.0)
+                best8.append(float(scores[m8].max()) if m8.any() else -1.0)
             neg.append(scores[lab == 0])
             pos.append(scores[lab == 1])
+            neg_snr.append(cands["snr"][lab == 0])
+            pos_snr.append(cands["snr"][lab == 1])
         return {"nominal": np.array(nominal), "width": np.array(width),
-                "detected": np.array(det), "best": np.array(best),
-                "neg": np.concatenate(neg), "pos": np.concatenate(pos), "n_scored": n_scored,
-                "rank_s": rank_s}
+                "detected": np.array(det), "best": np.array(best), "best8": np.array(best8),
+                "neg": np.concatenate(neg), "pos": np.concatenate(pos),
+                "neg_snr": np.concatenate(neg_snr), "pos_snr": np.concatenate(pos_snr),
+                "n_scored": n_scored, "rank_s": rank_s}
 
 
 def build_training_set(src, beams, seed):
@@ -244,8 +259,9 @@ def pulse_scores(ranker, src, beams, seed, chunk=4096):
 def threshold_for(ps, snr_min=8.0, keep=0.99):
     """The score that keeps `keep` of the pulses in pulse_scores output `ps`
     that the search detects at S/N >= snr_min (each by its best core
-    candidate), at most 0.5; 0.5 if there are none."""
-    v = np.sort(ps["best"][ps["detected"] >= snr_min])
+    candidate; with per-candidate S/N, its best core candidate detected at
+    S/N >= snr_min), at most 0.5; 0.5 if there are none."""
+    v = np.sort((ps["best8"] if "best8" in ps else ps["best"])[ps["detected"] >= snr_min])
     if v.size == 0:
         return 0.5
     return float(min(0.5, v[int(np.floor((1.0 - keep) * v.size))]))
@@ -315,7 +331,9 @@ def evaluate(ranker, src, beams, seed, snr_min=8.0, thresholds=(0.5,)):
 
 
 def summarise(ps, snr_min=8.0, thresholds=(0.5,)):
-    """Quality of the scores in pulse_scores output `ps`.  At each threshold:
+    """Quality of the scores in pulse_scores output `ps`.  At each threshold
+    (the first one as a two-tier operating point when `ps` has per-candidate
+    S/N: score >= threshold at detected S/N >= snr_min, score >= 0.5 below):
     recall on the injected pulses the search detects at S/N >= snr_min,
     recall on those of nominal S/N >= snr_min that it detects at all,
     precision and the share of negatives rejected; for the first threshold
@@ -332,8 +350,27 @@ def summarise(ps, snr_min=8.0, thresholds=(0.5,)):
                  "recall_nominal": float((best[n8] >= t).mean()) if n8.any() else 0.0,
                  "precision": tp / max(tp + fp, 1),
                  "negatives_rejected": 1.0 - fp / max(ps["neg"].size, 1)}
+        if "pos_snr" in ps:
+            # the same over the candidates the search reports at S/N >= snr_min
+            tp8 = int(((ps["pos"] >= t) & (ps["pos_snr"] >= snr_min)).sum())
+            fp8 = int(((ps["neg"] >= t) & (ps["neg_snr"] >= snr_min)).sum())
+            at[t]["precision_snr_ge_min"] = tp8 / max(tp8 + fp8, 1)
     t0 = thresholds[0]
     ok = best >= t0
+    if "best8" in ps:
+        # two-tier operating point: candidates detected at S/N >= snr_min are kept
+        # at score >= t0, weaker ones at score >= 0.5 (the recall target is set at
+        # S/N >= snr_min; the many faint noise candidates below it need a confident score)
+        lo = max(t0, 0.5)
+        ok = (ps["best8"] >= t0) | (best >= lo)
+        kp = ((ps["pos"] >= t0) & (ps["pos_snr"] >= snr_min)) | (ps["pos"] >= lo)
+        kn = ((ps["neg"] >= t0) & (ps["neg_snr"] >= snr_min)) | (ps["neg"] >= lo)
+        tp, fp = int(kp.sum()), int(kn.sum())
+        at[t0] = {"recall": float(ok[d8].mean()) if d8.any() else 0.0,
+                  "recall_nominal": float(ok[n8].mean()) if n8.any() else 0.0,
+                  "precision": tp / max(tp + fp, 1),
+                  "negatives_rejected": 1.0 - fp / max(ps["neg"].size, 1),
+                  "precision_snr_ge_min": at[t0].get("precision_snr_ge_min")}
 
     def rec(sel):
         sel = sel & d8

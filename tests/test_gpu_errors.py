@@ -1,7 +1,9 @@
 """Boundary behaviour of the C ABI on a GPU: every bad call returns a status
-(nothing traps), candidate overflow reports the true count, and the
+(nothing traps), candidate overflow reports the true count, the
 host-side fault hooks make allocation and launch failures observable
-without any GPU fault."""
+without any GPU fault, and a bounded wait of the dedispersion pipeline that
+runs out (on a barrier nothing completes, with no copy in flight) comes back
+as GSP_ERR_TIMEOUT with the plan still usable."""
 import os
 
 import numpy as np
@@ -119,3 +121,28 @@ def test_tie_margin_rejected(gsp):
         assert _status(lambda: gsp.gsp_plan_create(desc, keep)) == gsp.GSP_ERR_TIE
     else:
         pytest.skip("FP64 did not land within 1e-9 of the tie (margin %g)" % m)
+
+
+def test_wait_that_runs_out_reports_timeout_and_plan_recovers(gsp, orc, small):
+    plan, x, dl, n_in = small
+    _, used = gsp.gsp_dedisperse_variants(plan)
+    assert used >= 0
+    # the producer issues nothing, so each consumer's first stage wait runs out
+    # after about 1 ms (2e6 SM cycles); nothing is in flight when the warps leave
+    gsp.gsp_plan_set_wait_limit(plan, 2_000_000, 1)
+    gsp.gsp_search(plan, x, n_in)
+    with pytest.raises(gsp.GspError) as e:
+        gsp.gsp_candidates(plan)
+    assert e.value.status == gsp.GSP_ERR_TIMEOUT
+    # normal limits again: the same plan searches correctly
+    gsp.gsp_plan_set_wait_limit(plan, 4_000_000_000, 0)
+    n_out = n_in - orc.max_delay(dl)
+    D = torch.zeros((dl.shape[0], (n_out + 3) // 4 * 4), dtype=torch.int32, device="cuda")
+    gsp.gsp_search(plan, x, n_in, 0, D)
+    _, n, st = gsp.gsp_candidates(plan)
+    assert st in (gsp.GSP_OK, gsp.GSP_ERR_CAPACITY) and n > 0
+    ref = orc.dedisperse(x.cpu().numpy(), n_in, dl)
+    assert (D[:, :n_out].cpu().numpy().astype(np.int64) == ref).all()
+    for bad in [(0, 0), (5_000_000_000, 0), (100, 2)]:
+        with pytest.raises(gsp.GspError):
+            gsp.gsp_plan_set_wait_limit(plan, *bad)

@@ -183,3 +183,150 @@ def test_ranker_learns_pulse_shape(gsp):
     gsp.gsp_ranker_finish(r)
     pred = logits.argmax(dim=1).cpu().numpy()
     assert np.mean(pred == y) > 0.95
+
+
+# ---------------------------------------------------------------------------
+# Stage by stage, element by element.  Each stage of the GPU network is fed
+# the GPU's own inputs of that stage (read back with gsp_ranker_tensor) and
+# compared with the oracle's value of the same stage from those inputs.  The
+# bound of every element is derived from the arithmetic: an FP32 sum of K
+# products (+ bias) is within (K + 2) u sum|terms| of the exact sum (u = 2^-24,
+# any summation order, tensor-core or FMA chain), max-pool and ReLU do not
+# increase an error, and one rounding to bf16 moves a value by at most
+# 2^-8 of its magnitude.
+
+U32 = 2.0 ** -24
+BF = 2.0 ** -8
+
+
+def _nchw(t, n, side, c):
+    return t.reshape(n, side, side, c).transpose(0, 3, 1, 2)
+
+
+def _within(got, ref, bound, what):
+    d = np.abs(got - ref)
+    bad = d > bound
+    assert not bad.any(), "%s: %d of %d elements out of bound, worst %.3g vs bound %.3g" % (
+        what, int(bad.sum()), bad.size, float(d[bad].max()), float(bound[bad][np.argmax(d[bad])]))
+
+
+def _conv_stage(p, l, a_in, got_pooled, got_z=None):
+    """Layer l (1..3) from the GPU's input a_in (NCHW): returns the GPU's pooled
+    output checked against the oracle (and the pre-pool ReLU output if given)."""
+    w, b = p["w%d" % l], p["b%d" % l]
+    K = 9 * a_in.shape[1]
+    z = R.conv3x3(a_in, w, b)                                     # exact sum of bf16 products
+    za = R.conv3x3(np.abs(R.bf16(a_in)), np.abs(R.bf16(w)), np.abs(b), exact=True)
+    err = (K + 2) * U32 * za                                      # FP32 sum error bound
+    if got_z is not None:
+        _within(got_z, np.maximum(z, 0.0), err, "z%d" % (l - 1))
+    v, _ = R.maxpool2(np.maximum(z, 0.0))
+    e2, _ = R.maxpool2(err)                                       # the pool's error: max over window
+    _within(got_pooled, v, BF * np.abs(v) + e2 * (1 + BF), "a%d" % (l - 1))
+
+
+def _params_with_biases(seed):
+    p = R.init_params(seed)
+    rng = np.random.default_rng(seed)
+    for k in p:
+        if k.startswith("b"):
+            p[k] = rng.uniform(-0.05, 0.05, p[k].shape).astype(np.float32).astype(np.float64)
+    return p
+
+
+@pytest.mark.parametrize("train", [False, True])
+def test_forward_stages_element_by_element(gsp, train):
+    p = _params_with_biases(31)
+    n = 40
+    x, y = _batch(n, 17)
+    r = gsp.gsp_ranker_create(64, seed=2)
+    gsp.gsp_ranker_set_params(r, _flat(p))
+    xd = torch.from_numpy(x).cuda()
+    if train:
+        gsp.gsp_ranker_train_step(r, xd, torch.from_numpy(y).cuda(), n, 0.0)
+    else:
+        gsp.gsp_ranker_forward(r, xd, n, torch.zeros((n, 2), dtype=torch.float32, device="cuda"))
+    gsp.gsp_ranker_finish(r)
+    a_in = x[:, None, :, :].astype(np.float64)
+    for l, (side, c) in enumerate([(64, 8), (32, 16), (16, 32)]):
+        got = _nchw(gsp.gsp_ranker_tensor(r, "a%d" % l), n, side // 2, c)
+        gz = _nchw(gsp.gsp_ranker_tensor(r, "z%d" % l), n, side, c) if train else None
+        _conv_stage(p, l + 1, a_in, got, gz)
+        a_in = got
+    f3 = R.flatten_hwc(a_in)
+    z4 = gsp.gsp_ranker_tensor(r, "z4").reshape(n, -1)                 # after ReLU
+    ref4 = np.maximum(f3 @ R.bf16(p["w4"]).T + p["b4"], 0.0)
+    err4 = (f3.shape[1] + 2) * U32 * (np.abs(f3) @ np.abs(R.bf16(p["w4"])).T + np.abs(p["b4"]))
+    _within(z4, ref4, err4, "z4")
+    a4 = gsp.gsp_ranker_tensor(r, "a4").reshape(n, -1)
+    assert (a4 == R.bf16(np.maximum(z4, 0.0))).all()             # the epilogue's own rounding
+    z5 = gsp.gsp_ranker_tensor(r, "z5").reshape(n, 2)
+    ref5 = a4 @ R.bf16(p["w5"]).T + p["b5"]
+    err5 = (a4.shape[1] + 2) * U32 * (np.abs(a4) @ np.abs(R.bf16(p["w5"])).T + np.abs(p["b5"]))
+    _within(z5, ref5, err5, "z5")
+    gsp.gsp_ranker_destroy(r)
+
+
+def test_backward_stages_element_by_element(gsp):
+    p = _params_with_biases(32)
+    n = 40
+    x, y = _batch(n, 18)
+    r = gsp.gsp_ranker_create(64, seed=2)
+    gsp.gsp_ranker_set_params(r, _flat(p))
+    gsp.gsp_ranker_train_step(r, torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda(), n, 0.0)
+    gsp.gsp_ranker_finish(r)
+    T = {k: gsp.gsp_ranker_tensor(r, k) for k in
+         ("a0", "a1", "a2", "z0", "z1", "z2", "idx0", "idx1", "idx2", "z4", "a4", "z5", "g5",
+          "g4", "ga0", "ga1", "ga2", "gz0", "gz1", "gz2")}
+    _, grads = gsp.gsp_ranker_get_params(r)
+    G = _split(grads)
+    # the loss gradient w.r.t. the logits, from the GPU's logits
+    z5 = T["z5"].reshape(n, 2)
+    e = np.exp(z5 - z5.max(1, keepdims=True))
+    sm = e / e.sum(1, keepdims=True)
+    g5 = sm.copy()
+    g5[np.arange(n), y] -= 1.0
+    g5 /= n
+    got5 = T["g5"].reshape(n, 2)
+    _within(got5, g5, 16 * U32 * (sm + 1.0) / n, "g5")
+    # fc 96 -> 2 backward from the GPU's g5 and a4
+    a4 = T["a4"].reshape(n, -1)
+    gb5 = R.bf16(got5)
+    _within(G["w5"], gb5.T @ a4, (n + 2) * U32 * (np.abs(gb5).T @ np.abs(a4)), "dw5")
+    _within(G["b5"], got5.sum(0), (n + 2) * U32 * np.abs(got5).sum(0), "db5")
+    w5 = R.bf16(p["w5"])
+    z4 = T["z4"].reshape(n, -1)
+    u4 = (gb5 @ w5) * (z4 > 0)
+    t4 = (np.abs(gb5) @ np.abs(w5)) * (z4 > 0)
+    g4 = T["g4"].reshape(n, -1)
+    _within(g4, u4, BF * np.abs(u4) + 4 * U32 * t4 * (1 + BF), "g4")
+    # fc 2048 -> 96 backward from the GPU's g4 and pooled layer-3 output
+    f3 = R.flatten_hwc(_nchw(T["a2"], n, 8, 32))
+    _within(G["w4"], g4.T @ f3, (n + 2) * U32 * (np.abs(g4).T @ np.abs(f3)), "dw4")
+    _within(G["b4"], u4.sum(0), (n + 2) * U32 * np.abs(u4).sum(0) + 4 * U32 * t4.sum(0), "db4")
+    w4 = R.bf16(p["w4"])
+    ga = g4 @ w4
+    _within(T["ga2"].reshape(n, -1), ga, (w4.shape[0] + 2) * U32 * (np.abs(g4) @ np.abs(w4)),
+            "ga2")
+    # the conv layers, from the GPU's ga, argmax, pre-pool output and inputs
+    ins = [x[:, None, :, :].astype(np.float64), _nchw(T["a0"], n, 32, 8),
+           _nchw(T["a1"], n, 16, 16)]
+    for l, (side, c) in reversed(list(enumerate([(64, 8), (32, 16), (16, 32)]))):
+        gpool = _nchw(T["ga%d" % l], n, side // 2, c)
+        idx = _nchw(T["idx%d" % l].astype(np.int64), n, side // 2, c)
+        zl = _nchw(T["z%d" % l], n, side, c)
+        v = R.maxpool2_backward(gpool, idx) * (zl > 0)            # routed, exact in FP32
+        gz = _nchw(T["gz%d" % l], n, side, c)
+        assert (gz == R.bf16(v)).all(), "gz%d" % l
+        w = p["w%d" % (l + 1)]
+        da, dw = R.conv3x3_backward(gz, ins[l], w)
+        da_abs, dw_abs = R.conv3x3_backward(np.abs(gz), np.abs(R.bf16(ins[l])), np.abs(R.bf16(w)),
+                                            exact=True)
+        P = n * side * side
+        _within(G["w%d" % (l + 1)], dw, (P + 2) * U32 * dw_abs, "dw%d" % (l + 1))
+        _within(G["b%d" % (l + 1)], v.sum(axis=(0, 2, 3)),
+                (P + 2) * U32 * np.abs(v).sum(axis=(0, 2, 3)), "db%d" % (l + 1))
+        if l > 0:
+            _within(_nchw(T["ga%d" % (l - 1)], n, side, ins[l].shape[1]), da,
+                    (c + 9 + 2) * U32 * da_abs, "ga%d" % (l - 1))
+    gsp.gsp_ranker_destroy(r)

@@ -102,3 +102,22 @@ def test_bench_entry_points_wrap_the_host_summary(monkeypatch):
     assert set(ev["at"]) == {"0.05", "0.5"}
     import json
     json.dumps(ev)      # the bench line must serialise
+
+
+def test_two_tier_operating_point():
+    # three pulses detected at S/N >= 8; candidates at S/N >= 8 pass at the
+    # validation threshold, weaker ones only at a score >= 0.5
+    ps = {"nominal": np.array([9.0, 12.0, 8.5]), "width": np.array([3, 40, 90]),
+          "detected": np.array([9.1, 11.0, 8.2]),
+          "best": np.array([0.9, 0.02, 0.6]),      # best score over all core candidates
+          "best8": np.array([0.9, 0.02, 0.001]),   # best over core candidates at S/N >= 8
+          "pos": np.array([0.9, 0.02, 0.6, 0.001]), "pos_snr": np.array([9.1, 11.0, 7.0, 8.2]),
+          "neg": np.array([0.03, 0.4, 0.7, 0.0]), "neg_snr": np.array([9.0, 6.5, 6.1, 8.0]),
+          "n_scored": 8, "rank_s": 1.0}
+    out = ranker.summarise(ps, 8.0, (0.01,))
+    # pulse 0 (0.9 at S/N >= 8), pulse 1 (0.02 >= 0.01 at S/N 11), pulse 2 (0.6 >= 0.5 below 8)
+    assert out["recall"] == 1.0
+    # kept positives: 0.9, 0.02, 0.6 (< 8 but >= 0.5); kept negatives: 0.03 (S/N 9), 0.7
+    assert out["precision"] == 3 / 5
+    assert out["negatives_rejected"] == 0.5
+    assert ranker.threshold_for(ps, 8.0, keep=1.0) == 0.001
