@@ -28,10 +28,11 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 # DRAM bytes (read + write) per algorithmic add of the default dedispersion kernel
-# (variant 32): ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch on the
-# CRAFTS-like beam cut to 131072 samples (1.598 GB + 0.666 GB for 6.899e11 adds), the
-# capture size rule keeping full-size multi-pass captures off the GPU; traffic grows
-# with the number of time tiles, i.e. in proportion to the adds.
+# (variant 32, with per-stage copy windows): ncu dram__bytes_read.sum +
+# dram__bytes_write.sum of one launch on the CRAFTS-like beam cut to 131072 samples
+# (1.598 GB + 0.666 GB for 6.899e11 adds), the capture size rule keeping full-size
+# multi-pass captures off the GPU; traffic grows with the number of time tiles, i.e.
+# in proportion to the adds.
 DD_TRAFFIC_BYTES_PER_ADD = (1.5984e9 + 0.6663e9) / 6.899e11
 DD_TRAFFIC_VARIANT = "default"
 
@@ -80,10 +81,12 @@ def parse():
                     help="independent trainings of the ranker")
     ap.add_argument("--ranker-keep", type=float, default=0.995,
                     help="share of validation pulses detected at S/N >= 8 the threshold keeps")
-    ap.add_argument("--ranker-val-beams", type=int, default=8,
+    ap.add_argument("--ranker-val-beams", type=int, default=12,
                     help="validation beams that set the ranker's operating threshold")
-    ap.add_argument("--ranker-eval-beams", type=int, default=8,
+    ap.add_argument("--ranker-eval-beams", type=int, default=12,
                     help="fresh evaluation beams of the ranker")
+    ap.add_argument("--ranker-wide", type=int, default=30,
+                    help="positives at least this wide fill half of each batch's positive slots")
     ap.add_argument("--ranker-pulses", type=int, default=100,
                     help="injected pulses per training beam of the ranker")
     ap.add_argument("--ddplan-steps", type=int, default=3,
@@ -654,8 +657,11 @@ def run_ranker(args):
     from paper_2110_12749_gb300 import gsp, ranker, synth
     src = ranker.BeamSource(ranker.learned_crafts(1 << 18, n_pulses=args.ranker_pulses))
     t0 = time.perf_counter()
-    x, y, pid, _ = ranker.build_training_set(src, args.ranker_beams, synth.BASE_SEED + 500)
-    x, y, pid = ranker.subsample(x, y, pid, args.ranker_snippets, synth.BASE_SEED + 501)
+    x, y, pid, _, width = ranker.build_training_set(src, args.ranker_beams, synth.BASE_SEED + 500,
+                                                    with_width=True)
+    x, y, pid, width = ranker.subsample(x, y, pid, args.ranker_snippets, synth.BASE_SEED + 501,
+                                        width=width)
+    wide = np.nonzero((y == 1) & (width >= args.ranker_wide))[0]
     src.wl = ranker.learned_crafts(1 << 18, n_pulses=40)
     val = ranker.ScoredBeams(src, args.ranker_val_beams, synth.BASE_SEED + 700)
     ev = ranker.ScoredBeams(src, args.ranker_eval_beams, synth.BASE_SEED + 900)
@@ -667,7 +673,7 @@ def run_ranker(args):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
         e0.record()
-        losses = ranker.fit(r, x, y, steps=steps, seed=3 + 17 * k)
+        losses = ranker.fit(r, x, y, steps=steps, seed=3 + 17 * k, wide=wide)
         e1.record()
         torch.cuda.synchronize()
         train_ms = e0.elapsed_time(e1)
@@ -699,9 +705,12 @@ def run_ranker(args):
            "train_positives": npos, "train_steps": args.ranker_steps,
            "train_steps_per_s": last["train_steps_per_s"], "params": gsp.gsp_ranker_num_params(),
            "data_s": t_data, "detail": detail,
+           "train_wide_positives": int(wide.size),
            "recipe": "pulses DM 10-1500, width 1-150, S/N 5-40; grid 2000 trials to DM 1499.25; "
-                     "%d training beams, %d validation, %d evaluation"
-                     % (args.ranker_beams, args.ranker_val_beams, args.ranker_eval_beams)}
+                     "%d training beams, %d validation, %d evaluation; positives >= %d samples "
+                     "wide fill half of the positive slots" % (args.ranker_beams,
+                                                              args.ranker_val_beams,
+                                                              args.ranker_eval_beams, args.ranker_wide)}
     return out
 
 

@@ -864,9 +864,6 @@ const TiledVariant kVariants[] = {
     {dd_tiled_kernel<1, false, 3, true, 6, 32, false, true, true, 15, 2, true>, 1, 6, 32, true, 15},
     {dd_tiled_kernel<1, false, 3, true, 4, 32, false, true, true, 15, 2, true>, 1, 4, 32, true, 15},
     {dd_tiled_kernel<1, false, 3, true, 6, 32, false, true, true, 7, 2, true>, 1, 6, 32, true, 7},
-    // four channels per step (one 16-byte list-entry load per four channels)
-    {dd_tiled_kernel<1, true, 3, true, 6, 64, false, true, true, 15, 2, true>, 1, 6, 64, true, 15},
-    {dd_tiled_kernel<1, true, 3, true, 6, 32, false, true, true, 15, 2, true>, 1, 6, 32, true, 15},
 };
 constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
 

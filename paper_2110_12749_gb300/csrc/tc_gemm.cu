@@ -13,28 +13,6 @@ constexpr long long kGemmBudget = 2000000000ll;  // ~1 s of SM clock per wait
 
 __device__ int g_gemm_err;  // fallback error flag when the caller passes none
 
-// Copy the first nc8 8-column chunks of one 128 x 64 (or BN x 64) bf16 tile of a
-// K-contiguous matrix into the core-matrix layout: element (r, c) at byte
-// (r/8)*1024 + (c/8)*128 + (r%8)*16 + (c%8)*2.  Consecutive threads take
-// consecutive rows of one chunk, so each quarter warp writes 128 contiguous
-// bytes.  Rows >= nrows and columns >= kend read as zero (kend is a multiple
-// of 8).
-template <int ROWS>
-__device__ __forceinline__ void stage_tile(uint8_t *dst, const __nv_bfloat16 *__restrict__ src,
-                                           int64_t ld, int row0, int nrows, int k0, int kend,
-                                           int nc8) {
-    for (int idx = threadIdx.x; idx < ROWS * nc8; idx += 128) {
-        const int r = idx % ROWS, c8 = idx / ROWS;
-        const int gr = row0 + r, gk = k0 + c8 * 8;
-        uint4 v = make_uint4(0u, 0u, 0u, 0u);
-        if (gr < nrows && gk < kend)
-            v = __ldg(reinterpret_cast<const uint4 *>(src + (int64_t)gr * ld + gk));
-        *reinterpret_cast<uint4 *>(dst + (r >> 3) * 1024 + c8 * 128 + (r & 7) * 16) = v;
-    }
-}
-
-constexpr int kStages = 4;  // shared-memory ring depth of the pipelined kernel
-
 __device__ __forceinline__ void cp_async16(uint32_t dst, const void *src, uint32_t src_bytes) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src),
                  "r"(src_bytes)
@@ -48,48 +26,61 @@ __device__ __forceinline__ void cp_async_wait() {
     asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
-// Issue the 16-byte copies of one ROWS x 64 bf16 tile of a K-contiguous matrix
-// into the core-matrix layout (element (r, c) at byte (r/8)*1024 + (c/8)*128 +
-// (r%8)*16 + (c%8)*2); rows >= nrows and columns >= kend are zero-filled
-// (kend is a multiple of 8).  Consecutive threads take consecutive rows of
-// one 16-byte column chunk.
+// The 16-byte copies of one ROWS x 64 bf16 tile of a K-contiguous matrix into
+// the core-matrix layout (element (r, c) at byte (r/8)*1024 + (c/8)*128 +
+// (r%8)*16 + (c%8)*2).  Thread t copies column chunk t % 8 of rows t / 8 + 16 i,
+// so the 8 lanes of a row read its 128 contiguous bytes and a warp instruction
+// reads 4 whole rows (coalesced).  Rows >= nrows and columns >= kend are
+// zero-filled (kend is a multiple of 8).
 template <int ROWS>
-__device__ __forceinline__ void issue_tile(uint32_t dst, const __nv_bfloat16 *__restrict__ src,
-                                           int64_t ld, int row0, int nrows, int k0, int kend) {
-#pragma unroll 4
-    for (int idx = threadIdx.x; idx < ROWS * 8; idx += 128) {
-        const int r = idx % ROWS, c8 = idx / ROWS;
-        const int gr = row0 + r, gk = k0 + c8 * 8;
-        const bool in = gr < nrows && gk < kend;
-        const __nv_bfloat16 *g = in ? src + (int64_t)gr * ld + gk : src;
-        cp_async16(dst + (uint32_t)((r >> 3) * 1024 + c8 * 128 + (r & 7) * 16), g, in ? 16u : 0u);
+struct TileCopy {
+    static_assert(ROWS % 16 == 0, "16 rows per pass of 128 threads");
+    int c8, r0;
+    __device__ __forceinline__ TileCopy() : c8(threadIdx.x & 7), r0(threadIdx.x >> 3) {}
+    __device__ __forceinline__ void issue(uint32_t dst, const __nv_bfloat16 *__restrict__ src,
+                                          int64_t ld, int row0, int nrows, int k0,
+                                          int kend) const {
+        const int gk = k0 + c8 * 8;
+        const bool kin = gk < kend;
+#pragma unroll
+        for (int i = 0; i < ROWS / 16; i++) {
+            const int r = r0 + 16 * i;
+            const int gr = row0 + r;
+            const bool in = kin && gr < nrows;
+            const __nv_bfloat16 *g = in ? src + (int64_t)gr * ld + gk : src;
+            cp_async16(dst + (uint32_t)((r >> 3) * 1024 + c8 * 128 + (r & 7) * 16), g,
+                       in ? 16u : 0u);
+        }
     }
-}
+};
 
 // C (+)= A B^T, one 128 x BN output column block per CTA row of the grid
-// (blockIdx.y), a K chunk per blockIdx.z (split-K), and CTAs striding over the
-// M tiles.  The CTA's (M tile, 64-wide K step) pairs form one sequence that
-// flows through a ring of kStages shared-memory stages: all 128 threads copy
-// stage j + kStages - 1 (cp.async) while thread 0's MMAs of stage j run, and
-// a stage is refilled only after the MMAs that read it have completed (one
-// mbarrier per stage, signalled by tcgen05.commit).  The accumulator
-// alternates between two TMEM column blocks per M tile, so the epilogue of
-// tile t (tcgen05.ld by all four warps, bias, ReLU, stores or split-K atomics)
-// runs while the MMAs of tile t + 1 accumulate into the other block.  Every
-// wait is bounded; a wait that gives up sets *err, and the CTA waits (bounded)
-// for its committed MMAs and its copies before it frees tensor memory.
-template <int BN>
+// (blockIdx.y), a K chunk per blockIdx.z (split-K).  The CTA's (M tile,
+// 64-wide K step) pairs form one sequence that flows through a ring of S
+// shared-memory stages: all 128 threads copy stage j + S - 1 (cp.async) while
+// thread 0's MMAs of stage j run, and a stage is refilled only after the MMAs
+// that read it have completed (one mbarrier per stage, signalled by
+// tcgen05.commit).  NACC = 2: CTAs stride over the M tiles and the
+// accumulator alternates between two TMEM column blocks, so the epilogue of
+// tile t (tcgen05.ld by all four warps, bias, ReLU, stores or split-K
+// atomics) runs while the MMAs of tile t + 1 accumulate into the other block.
+// NACC = 1: one M tile per CTA (short K: many small CTAs per SM hide the
+// latency instead).  Every wait is bounded; a wait that gives up sets *err,
+// and the CTA waits (bounded) for its committed MMAs and its copies before it
+// frees tensor memory.
+template <int BN, int S, int NACC>
 __global__ void __launch_bounds__(128) gemm_bf16_kernel(
     const __nv_bfloat16 *__restrict__ A, int64_t lda, const __nv_bfloat16 *__restrict__ B,
     int64_t ldb, float *C, int64_t ldc, __nv_bfloat16 *Cb, int64_t ldcb, int M, int N, int K,
     int kchunk, const float *__restrict__ bias, int relu, int *err) {
     static_assert(BN % 16 == 0 && BN >= 16 && BN <= 128, "tcgen05 M=128 with N in 16..128");
+    static_assert(S >= 2 && (NACC == 1 || NACC == 2), "ring depth and accumulators");
     constexpr int kABytes = kBM * kBK * 2, kBBytes = BN * kBK * 2;
     constexpr int kStageBytes = kABytes + kBBytes;
-    constexpr uint32_t kCols = 2 * BN < 32 ? 32u : (uint32_t)(2 * BN);  // two accumulators
+    constexpr uint32_t kCols = NACC * BN < 32 ? 32u : (uint32_t)(NACC * BN);
     constexpr uint32_t kIdesc = tc::idesc_bf16(kBM, BN);
     extern __shared__ __align__(1024) uint8_t smem[];
-    __shared__ __align__(8) uint64_t bar_stage[kStages];
+    __shared__ __align__(8) uint64_t bar_stage[S];
     __shared__ __align__(8) uint64_t bar_acc[2];
     __shared__ uint32_t tmem_base;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -98,11 +89,12 @@ __global__ void __launch_bounds__(128) gemm_bf16_kernel(
     const int kend = min(K, kbeg + kchunk);
     const int mtiles = (M + kBM - 1) / kBM;
     const int nks = kend > kbeg ? (kend - kbeg + kBK - 1) / kBK : 0;  // K steps per tile
-    const int ntile_mine = blockIdx.x < mtiles ? (mtiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    const int ntile_mine = (int)blockIdx.x >= mtiles ? 0
+                           : (NACC == 1 ? 1 : (mtiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1);
     const int total = ntile_mine * nks;                                   // sequence length
     if (warp == 0) tc::tmem_alloc(tc::smem_u32(&tmem_base), kCols);
     if (tid == 0) {
-        for (int i = 0; i < kStages; i++) tc::mbar_init1(tc::smem_u32(&bar_stage[i]));
+        for (int i = 0; i < S; i++) tc::mbar_init1(tc::smem_u32(&bar_stage[i]));
         for (int i = 0; i < 2; i++) tc::mbar_init1(tc::smem_u32(&bar_acc[i]));
     }
     tc::fence_before();
@@ -110,22 +102,24 @@ __global__ void __launch_bounds__(128) gemm_bf16_kernel(
     tc::fence_after();
     const uint32_t tmem = tmem_base;
     const uint32_t sbase = tc::smem_u32(smem);
-    auto load = [&](int j) {  // copies of sequence entry j into stage j % kStages
+    const TileCopy<kBM> copyA;
+    const TileCopy<BN> copyB;
+    auto load = [&](int j) {  // copies of sequence entry j into stage j % S
         if (j < total) {
             const int lt = j / nks, ks = j - lt * nks;
-            const int m0 = (blockIdx.x + lt * gridDim.x) * kBM;
+            const int m0 = ((int)blockIdx.x + lt * (int)gridDim.x) * kBM;
             const int k0 = kbeg + ks * kBK;
-            const uint32_t st = sbase + (uint32_t)((j % kStages) * kStageBytes);
-            issue_tile<kBM>(st, A, lda, m0, M, k0, kend);
-            issue_tile<BN>(st + kABytes, B, ldb, n0, N, k0, kend);
+            const uint32_t st = sbase + (uint32_t)((j % S) * kStageBytes);
+            copyA.issue(st, A, lda, m0, M, k0, kend);
+            copyB.issue(st + kABytes, B, ldb, n0, N, k0, kend);
         }
         cp_async_commit();  // one group per entry, empty past the end
     };
     auto epilogue = [&](int lt) {
-        const int m0 = (blockIdx.x + lt * gridDim.x) * kBM;
+        const int m0 = ((int)blockIdx.x + lt * (int)gridDim.x) * kBM;
         const int row = m0 + warp * 32 + lane;
         const uint32_t lane_addr =
-            tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)((lt & 1) * BN);
+            tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)((NACC == 2 ? (lt & 1) : 0) * BN);
 #pragma unroll 1
         for (int c0 = 0; c0 < BN; c0 += 16) {
             float v[16];
@@ -134,15 +128,16 @@ __global__ void __launch_bounds__(128) gemm_bf16_kernel(
 #pragma unroll
                 for (int jj = 0; jj < 16; jj++) {
                     const int n = n0 + c0 + jj;
-                    if (n >= N) break;
-                    float val = v[jj];
-                    if (gridDim.z > 1) {
-                        atomicAdd(C + (int64_t)row * ldc + n, val);
-                    } else {
-                        if (bias) val += bias[n];
-                        if (relu) val = fmaxf(val, 0.0f);
-                        if (C) C[(int64_t)row * ldc + n] = val;
-                        if (Cb) Cb[(int64_t)row * ldcb + n] = __float2bfloat16_rn(val);
+                    if (n < N) {
+                        float val = v[jj];
+                        if (gridDim.z > 1) {
+                            atomicAdd(C + (int64_t)row * ldc + n, val);
+                        } else {
+                            if (bias) val += bias[n];
+                            if (relu) val = fmaxf(val, 0.0f);
+                            if (C) C[(int64_t)row * ldc + n] = val;
+                            if (Cb) Cb[(int64_t)row * ldcb + n] = __float2bfloat16_rn(val);
+                        }
                     }
                 }
             }
@@ -150,43 +145,44 @@ __global__ void __launch_bounds__(128) gemm_bf16_kernel(
     };
     bool ok = true;
     int committed = 0;  // stage mbarrier phases committed by thread 0 (MMAs issued)
-    for (int j = 0; j < kStages - 1; j++) load(j);
+    for (int j = 0; j < S - 1; j++) load(j);
     for (int j = 0; j < total && ok; j++) {
         const int lt = j / nks, ks = j - lt * nks;
-        cp_async_wait<kStages - 2>();  // this thread's copies of entry j have landed
-        tc::fence_proxy_async();      // ... and are visible to the tensor cores
+        cp_async_wait<S - 2>();   // this thread's copies of entry j have landed
+        tc::fence_proxy_async();  // ... and are visible to the tensor cores
         tc::fence_before();
         __syncthreads();
         if (tid == 0) {
             tc::fence_after();
             const int k0 = kbeg + ks * kBK;
             const int nmma = (min(kBK, kend - k0) + 15) / 16;  // K = 16 per MMA
-            const uint32_t st = sbase + (uint32_t)((j % kStages) * kStageBytes);
-            const uint32_t acc = tmem + (uint32_t)((lt & 1) * BN);
+            const uint32_t st = sbase + (uint32_t)((j % S) * kStageBytes);
+            const uint32_t acc = tmem + (uint32_t)((NACC == 2 ? (lt & 1) : 0) * BN);
             for (int kk = 0; kk < nmma; kk++) {
                 // two core matrices along K (256 bytes) per MMA
                 const uint64_t ad = tc::smem_desc(st + kk * 256, 128, 1024);
                 const uint64_t bd = tc::smem_desc(st + kABytes + kk * 256, 128, 1024);
                 tc::mma_bf16(acc, ad, bd, kIdesc, (ks > 0 || kk > 0) ? 1u : 0u);
             }
-            tc::mma_commit(tc::smem_u32(&bar_stage[j % kStages]));
+            tc::mma_commit(tc::smem_u32(&bar_stage[j % S]));
             if (ks == nks - 1) tc::mma_commit(tc::smem_u32(&bar_acc[lt & 1]));
         }
         committed = j + 1;
-        // refill the stage of entry j - 1 once its MMAs are done
-        if (j >= 1) {
+        // refill the stage of entry j - 1 once its MMAs are done (nothing to
+        // refill near the end of the sequence)
+        if (j >= 1 && j + S - 1 < total) {
             const int jp = j - 1;
-            const bool done = tc::mbar_wait_bounded(tc::smem_u32(&bar_stage[jp % kStages]),
-                                                    (uint32_t)((jp / kStages) & 1), kGemmBudget);
+            const bool done = tc::mbar_wait_bounded(tc::smem_u32(&bar_stage[jp % S]),
+                                                    (uint32_t)((jp / S) & 1), kGemmBudget);
             if (!__all_sync(0xffffffffu, done)) ok = false;
         }
         if (!__syncthreads_and(ok)) {
             ok = false;
             break;
         }
-        load(j + kStages - 1);
+        load(j + S - 1);
         // the previous tile's epilogue, while this tile's MMAs run
-        if (ks == 0 && lt > 0) {
+        if (NACC == 2 && ks == 0 && lt > 0) {
             const bool done = tc::mbar_wait_bounded(tc::smem_u32(&bar_acc[(lt - 1) & 1]),
                                                     (uint32_t)(((lt - 1) >> 1) & 1), kGemmBudget);
             if (!__syncthreads_and(done)) {
@@ -215,8 +211,8 @@ __global__ void __launch_bounds__(128) gemm_bf16_kernel(
         // last committed stage barrier completes after every earlier MMA
         if (committed > 0) {
             const int jl = committed - 1;
-            (void)tc::mbar_wait_bounded(tc::smem_u32(&bar_stage[jl % kStages]),
-                                        (uint32_t)((jl / kStages) & 1), kGemmBudget);
+            (void)tc::mbar_wait_bounded(tc::smem_u32(&bar_stage[jl % S]),
+                                        (uint32_t)((jl / S) & 1), kGemmBudget);
         }
     }
     tc::fence_before();
@@ -226,21 +222,45 @@ __global__ void __launch_bounds__(128) gemm_bf16_kernel(
 
 // Launch one instantiation; its dynamic shared-memory limit (above the 48 KB
 // default) is raised once per instantiation.
-template <int BN>
-cudaError_t launch_bn(dim3 grid, int smem, cudaStream_t s, const __nv_bfloat16 *A, int64_t lda,
+template <int BN, int S, int NACC>
+cudaError_t launch_bn(dim3 grid, cudaStream_t s, const __nv_bfloat16 *A, int64_t lda,
                       const __nv_bfloat16 *B, int64_t ldb, float *C, int64_t ldc,
                       __nv_bfloat16 *Cb, int64_t ldcb, int M, int N, int K, int kchunk,
                       const float *bias, int relu, int *err) {
-    static int configured = 0;
-    if (configured < smem) {
-        cudaError_t e = cudaFuncSetAttribute(gemm_bf16_kernel<BN>,
+    constexpr int smem = S * (kBM + BN) * kBK * 2;
+    static bool configured = false;
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(gemm_bf16_kernel<BN, S, NACC>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
-        configured = smem;
+        configured = true;
     }
-    gemm_bf16_kernel<BN><<<grid, 128, smem, s>>>(A, lda, B, ldb, C, ldc, Cb, ldcb, M, N, K, kchunk,
-                                                 bias, relu, err);
+    gemm_bf16_kernel<BN, S, NACC><<<grid, 128, smem, s>>>(A, lda, B, ldb, C, ldc, Cb, ldcb, M, N,
+                                                          K, kchunk, bias, relu, err);
     return cudaSuccess;
+}
+
+// Short K (at most two 64-wide steps per tile): one CTA per M tile, a 2-stage
+// ring and one accumulator.  Longer K: a 4-stage ring, two accumulators, and
+// persistent CTAs striding over the M tiles.
+template <int BN>
+cudaError_t launch_n(bool longk, int mtiles, int ntiles, int splitk, int nsm, cudaStream_t s,
+                     const __nv_bfloat16 *A, int64_t lda, const __nv_bfloat16 *B, int64_t ldb,
+                     float *C, int64_t ldc, __nv_bfloat16 *Cb, int64_t ldcb, int M, int N, int K,
+                     int kchunk, const float *bias, int relu, int *err) {
+    if (!longk) {
+        dim3 grid((unsigned)mtiles, (unsigned)ntiles, (unsigned)splitk);
+        return launch_bn<BN, 2, 1>(grid, s, A, lda, B, ldb, C, ldc, Cb, ldcb, M, N, K, kchunk,
+                                   bias, relu, err);
+    }
+    constexpr int smem = 4 * (kBM + BN) * kBK * 2;
+    const int per_sm = std::max(1, (227 * 1024) / (smem + 1024));
+    const int64_t want = ((int64_t)nsm * per_sm + (int64_t)ntiles * splitk - 1) /
+                         ((int64_t)ntiles * splitk);
+    const int mgrid = (int)std::max<int64_t>(1, std::min<int64_t>(mtiles, want));
+    dim3 grid((unsigned)mgrid, (unsigned)ntiles, (unsigned)splitk);
+    return launch_bn<BN, 4, 2>(grid, s, A, lda, B, ldb, C, ldc, Cb, ldcb, M, N, K, kchunk, bias,
+                               relu, err);
 }
 
 }  // namespace
@@ -260,26 +280,25 @@ cudaError_t launch_gemm_bf16(const __nv_bfloat16 *A, int64_t lda, const __nv_bfl
     splitk = std::max(1, std::min(splitk, ksteps));
     const int kchunk = ((ksteps + splitk - 1) / splitk) * kBK;
     splitk = (K + kchunk - 1) / kchunk;
-    const int BN = N <= 16 ? 16 : N <= 32 ? 32 : N <= 64 ? 64 : 128;
-    // CTAs stride over the M tiles: enough CTAs for every SM (by shared memory,
-    // at most 227 KB per SM) across the N tiles and K chunks, at most one per M tile
-    const int mtiles = (M + kBM - 1) / kBM, ntiles = (N + BN - 1) / BN;
-    const int smem = kStages * (kBM + BN) * kBK * 2;
     int dev = 0, nsm = 152;
     if (cudaGetDevice(&dev) == cudaSuccess)
         (void)cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     (void)cudaGetLastError();
-    const int per_sm = std::max(1, (227 * 1024) / (smem + 1024));
-    const int64_t want = ((int64_t)nsm * per_sm + (int64_t)ntiles * splitk - 1) / ((int64_t)ntiles * splitk);
-    const int mgrid = (int)std::max<int64_t>(1, std::min<int64_t>(mtiles, want));
-    dim3 grid((unsigned)mgrid, (unsigned)ntiles, (unsigned)splitk);
+    // the widest column block (at most 128) that covers N; narrower while the grid
+    // would leave more than half of the SMs without a CTA (few M tiles: the A
+    // tiles are then read by several CTAs, from L2)
+    const int mtiles = (M + kBM - 1) / kBM;
+    int BN = N <= 16 ? 16 : N <= 32 ? 32 : N <= 64 ? 64 : 128;
+    while (BN > 16 && (int64_t)mtiles * ((N + BN - 1) / BN) * splitk < nsm / 2) BN /= 2;
+    const int ntiles = (N + BN - 1) / BN;
+    const bool longk = kchunk > 2 * kBK;
     const int r = relu ? 1 : 0;
     cudaError_t e;
     switch (BN) {
-        case 16: e = launch_bn<16>(grid, smem, s, A, lda, B, ldb, C, ldc, Cb, ldcb, M, N, K, kchunk, bias, r, err); break;
-        case 32: e = launch_bn<32>(grid, smem, s, A, lda, B, ldb, C, ldc, Cb, ldcb, M, N, K, kchunk, bias, r, err); break;
-        case 64: e = launch_bn<64>(grid, smem, s, A, lda, B, ldb, C, ldc, Cb, ldcb, M, N, K, kchunk, bias, r, err); break;
-        default: e = launch_bn<128>(grid, smem, s, A, lda, B, ldb, C, ldc, Cb, ldcb, M, N, K, kchunk, bias, r, err); break;
+        case 16: e = launch_n<16>(longk, mtiles, ntiles, splitk, nsm, s, A, lda, B, ldb, C, ldc, Cb, ldcb, M, N, K, kchunk, bias, r, err); break;
+        case 32: e = launch_n<32>(longk, mtiles, ntiles, splitk, nsm, s, A, lda, B, ldb, C, ldc, Cb, ldcb, M, N, K, kchunk, bias, r, err); break;
+        case 64: e = launch_n<64>(longk, mtiles, ntiles, splitk, nsm, s, A, lda, B, ldb, C, ldc, Cb, ldcb, M, N, K, kchunk, bias, r, err); break;
+        default: e = launch_n<128>(longk, mtiles, ntiles, splitk, nsm, s, A, lda, B, ldb, C, ldc, Cb, ldcb, M, N, K, kchunk, bias, r, err); break;
     }
     if (e != cudaSuccess) return e;
     return cudaGetLastError();

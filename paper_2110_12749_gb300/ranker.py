@@ -117,19 +117,21 @@ class BeamSource:
         return out
 
 
-def subsample(x, y, pid, total, seed):
+def subsample(x, y, pid, total, seed, width=None):
     """Keep every positive and a seeded random subset of the negatives so that
-    `total` snippets remain (all of them if there are fewer)."""
+    `total` snippets remain (all of them if there are fewer).  `width` (per
+    snippet, optional) is subset alike and returned last."""
     torch = __import__("torch")
     pos = np.nonzero(y == 1)[0]
     neg = np.nonzero(y == 0)[0]
     if pos.size + neg.size <= total:
-        return x, y, pid
+        return (x, y, pid) if width is None else (x, y, pid, width)
     rng = np.random.default_rng(seed)
     keep = np.sort(np.concatenate([pos, rng.choice(neg, max(total - pos.size, 0),
                                                    replace=False)]))
     idx = torch.from_numpy(keep).cuda()
-    return x.index_select(0, idx), y[keep], pid[keep]
+    out = (x.index_select(0, idx), y[keep], pid[keep])
+    return out if width is None else out + (width[keep],)
 
 
 class ScoredBeams:
@@ -194,13 +196,13 @@ class ScoredBeams:
                 "n_scored": n_scored, "rank_s": rank_s}
 
 
-def build_training_set(src, beams, seed):
+def build_training_set(src, beams, seed, with_width=False):
     """Snippets (torch float CUDA) and labels of every candidate labelled 0 or
     1 in the given number of beams (candidates on a pulse's track excluded),
     a global pulse id per snippet (-1 for label 0) and the nominal S/N of
-    every pulse (indexed by that id)."""
+    every pulse (indexed by that id); with_width also the candidate widths."""
     torch = src.torch
-    xs, ys, ps, snr = [], [], [], []
+    xs, ys, ps, snr, ws = [], [], [], [], []
     base = 0
     for b in range(beams):
         cands, lab, pid, pulses = src.search(b, seed)
@@ -208,9 +210,11 @@ def build_training_set(src, beams, seed):
         xs.append(src.snippets(cands[keep]))
         ys.append(lab[keep].astype(np.int32))
         ps.append(np.where(pid[keep] >= 0, pid[keep] + base, -1))
+        ws.append(cands["width"][keep].astype(np.int32))
         snr.extend(p.snr for p in pulses)
         base += len(pulses)
-    return torch.cat(xs), np.concatenate(ys), np.concatenate(ps), np.array(snr)
+    out = (torch.cat(xs), np.concatenate(ys), np.concatenate(ps), np.array(snr))
+    return out + (np.concatenate(ws),) if with_width else out
 
 
 def pulse_scores(ranker, src, beams, seed, chunk=4096):
@@ -272,10 +276,13 @@ def choose_threshold(ranker, src, beams, seed, snr_min=8.0, keep=0.99):
     return threshold_for(pulse_scores(ranker, src, beams, seed), snr_min, keep)
 
 
-def train(ranker, x, y, steps, batch=256, lr=2e-3, seed=0, hard=None, pos_frac=0.25):
+def train(ranker, x, y, steps, batch=256, lr=2e-3, seed=0, hard=None, pos_frac=0.25,
+          wide=None):
     """Mini-batches with a fixed share of positives and Adam; negatives are
     drawn uniformly, or half of them from `hard` (indices of hard negatives)
-    when given.  Returns the losses seen every 50 steps."""
+    when given; positives uniformly, or half of them from `wide` (indices of
+    wide positives, the rare hard class) when given.  Returns the losses seen
+    every 50 steps."""
     torch = __import__("torch")
     rng = np.random.default_rng(seed)
     pos = np.nonzero(y == 1)[0]
@@ -290,7 +297,11 @@ def train(ranker, x, y, steps, batch=256, lr=2e-3, seed=0, hard=None, pos_frac=0
             negs = np.concatenate([rng.choice(hard, nneg // 2), rng.choice(neg, nneg - nneg // 2)])
         else:
             negs = rng.choice(neg, nneg)
-        idx = torch.from_numpy(np.concatenate([rng.choice(pos, npos), negs])).cuda()
+        if wide is not None and wide.size:
+            poss = np.concatenate([rng.choice(wide, npos // 2), rng.choice(pos, npos - npos // 2)])
+        else:
+            poss = rng.choice(pos, npos)
+        idx = torch.from_numpy(np.concatenate([poss, negs])).cuda()
         xb = x.index_select(0, idx).contiguous()
         yb = yd.index_select(0, idx).contiguous()
         gsp.gsp_ranker_train_step(ranker, xb, yb, batch, lr, loss=loss)
@@ -301,14 +312,15 @@ def train(ranker, x, y, steps, batch=256, lr=2e-3, seed=0, hard=None, pos_frac=0
     return losses
 
 
-def fit(ranker, x, y, steps=(400, 800), hard_count=20000, lr=2e-3, seed=0):
+def fit(ranker, x, y, steps=(400, 800), hard_count=20000, lr=2e-3, seed=0, wide=None):
     """Two phases: uniform negatives, then with the highest-scored negatives of
-    the training set (hard-negative mining) over-sampled."""
-    l1 = train(ranker, x, y, steps[0], lr=lr, seed=seed)
+    the training set (hard-negative mining) over-sampled; `wide` (indices of
+    wide positives) are over-sampled in both."""
+    l1 = train(ranker, x, y, steps[0], lr=lr, seed=seed, wide=wide)
     neg = np.nonzero(y == 0)[0]
     s = score(ranker, x)
     hard = neg[np.argsort(-s[neg])[:hard_count]]
-    l2 = train(ranker, x, y, steps[1], lr=lr * 0.5, seed=seed + 1, hard=hard)
+    l2 = train(ranker, x, y, steps[1], lr=lr * 0.5, seed=seed + 1, hard=hard, wide=wide)
     return l1 + l2
 
 
