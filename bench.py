@@ -239,6 +239,23 @@ def run_reference(args):
     return 0
 
 
+def busy_union(intervals):
+    """(length of the union of [a, b] intervals, span from the first start to the
+    last end); (0, 0) for none."""
+    busy, cur = 0.0, None
+    for a, b in sorted(intervals):
+        if cur is None or a > cur[1]:
+            if cur is not None:
+                busy += cur[1] - cur[0]
+            cur = [a, b]
+        else:
+            cur[1] = max(cur[1], b)
+    if cur is None:
+        return 0.0, 0.0
+    busy += cur[1] - cur[0]
+    return busy, max(b for _, b in intervals) - min(a for a, _ in intervals)
+
+
 def run_stream(args, wl, delays_fn, base_src):
     """Streaming loop of the learned + streaming workload: B beams of 2^18-sample
     chunks arriving round-robin at an aggregate rate (6 GB/s), each beam with its
@@ -371,17 +388,7 @@ def run_stream(args, wl, delays_fn, base_src):
         gsp.gsp_plan_destroy(p)
     del srcs
     # GPU busy: the union of the chunks' [first copy, last search kernel] intervals
-    busy, cur = 0.0, None
-    for a, b2 in sorted(intervals):
-        if cur is None or a > cur[1]:
-            if cur is not None:
-                busy += cur[1] - cur[0]
-            cur = [a, b2]
-        else:
-            cur[1] = max(cur[1], b2)
-    if cur is not None:
-        busy += cur[1] - cur[0]
-    span_ms = max(b2 for _, b2 in intervals) - min(a for a, _ in intervals)
+    busy, span_ms = busy_union(intervals)
     lat_sorted = sorted(lat)
     wall = max(done_at) - t_start
     return {"beams": B, "beams_requested": args.stream_beams, "pool_buffers": args.stream_pool,

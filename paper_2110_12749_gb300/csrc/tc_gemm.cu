@@ -30,7 +30,8 @@ __device__ __forceinline__ void cp_async_wait() {
 // the core-matrix layout (element (r, c) at byte (r/8)*1024 + (c/8)*128 +
 // (r%8)*16 + (c%8)*2).  Thread t copies column chunk t % 8 of rows t / 8 + 16 i,
 // so the 8 lanes of a row read its 128 contiguous bytes and a warp instruction
-// reads 4 whole rows (coalesced).  Rows >= nrows and columns >= kend are
+// reads 4 whole rows (coalesced).  Only the first nc8 chunks are copied (the
+// ones the MMAs of this K step read); rows >= nrows and columns >= kend are
 // zero-filled (kend is a multiple of 8).
 template <int ROWS>
 struct TileCopy {
@@ -38,8 +39,9 @@ struct TileCopy {
     int c8, r0;
     __device__ __forceinline__ TileCopy() : c8(threadIdx.x & 7), r0(threadIdx.x >> 3) {}
     __device__ __forceinline__ void issue(uint32_t dst, const __nv_bfloat16 *__restrict__ src,
-                                          int64_t ld, int row0, int nrows, int k0,
-                                          int kend) const {
+                                          int64_t ld, int row0, int nrows, int k0, int kend,
+                                          int nc8) const {
+        if (c8 >= nc8) return;
         const int gk = k0 + c8 * 8;
         const bool kin = gk < kend;
 #pragma unroll
@@ -74,7 +76,10 @@ __global__ void __launch_bounds__(128) gemm_bf16_kernel(
     int64_t ldb, float *C, int64_t ldc, __nv_bfloat16 *Cb, int64_t ldcb, int M, int N, int K,
     int kchunk, const float *__restrict__ bias, int relu, int *err) {
     static_assert(BN % 16 == 0 && BN >= 16 && BN <= 128, "tcgen05 M=128 with N in 16..128");
-    static_assert(S >= 2 && (NACC == 1 || NACC == 2), "ring depth and accumulators");
+    static_assert(S >= 1 && (NACC == 1 || NACC == 2), "ring depth and accumulators");
+    static_assert(S >= 2 || NACC == 1, "a single stage serves one tile per CTA");
+    constexpr int kAhead = S > 1 ? S - 1 : 1;  // entries copied ahead of the one in use
+    constexpr int kWait = S > 1 ? S - 2 : 0;   // copy groups that may still be pending
     constexpr int kABytes = kBM * kBK * 2, kBBytes = BN * kBK * 2;
     constexpr int kStageBytes = kABytes + kBBytes;
     constexpr uint32_t kCols = NACC * BN < 32 ? 32u : (uint32_t)(NACC * BN);
@@ -109,12 +114,16 @@ __global__ void __launch_bounds__(128) gemm_bf16_kernel(
             const int lt = j / nks, ks = j - lt * nks;
             const int m0 = ((int)blockIdx.x + lt * (int)gridDim.x) * kBM;
             const int k0 = kbeg + ks * kBK;
+            const int nc8 = 2 * ((min(kBK, kend - k0) + 15) / 16);  // chunks the MMAs read
             const uint32_t st = sbase + (uint32_t)((j % S) * kStageBytes);
-            copyA.issue(st, A, lda, m0, M, k0, kend);
-            copyB.issue(st + kABytes, B, ldb, n0, N, k0, kend);
+            copyA.issue(st, A, lda, m0, M, k0, kend, nc8);
+            copyB.issue(st + kABytes, B, ldb, n0, N, k0, kend, nc8);
         }
         cp_async_commit();  // one group per entry, empty past the end
     };
+    // 16-byte float stores (8-byte bf16 stores) when every row start is aligned
+    const bool vec_ok = ((ldc & 3) == 0) && (((uintptr_t)C & 15) == 0) && ((ldcb & 3) == 0) &&
+                        (((uintptr_t)Cb & 7) == 0);
     auto epilogue = [&](int lt) {
         const int m0 = ((int)blockIdx.x + lt * (int)gridDim.x) * kBM;
         const int row = m0 + warp * 32 + lane;
@@ -125,18 +134,42 @@ __global__ void __launch_bounds__(128) gemm_bf16_kernel(
             float v[16];
             tc::tmem_ld16(lane_addr + (uint32_t)c0, v);
             if (row < M) {
+                if (gridDim.z > 1) {
 #pragma unroll
-                for (int jj = 0; jj < 16; jj++) {
-                    const int n = n0 + c0 + jj;
-                    if (n < N) {
-                        float val = v[jj];
-                        if (gridDim.z > 1) {
-                            atomicAdd(C + (int64_t)row * ldc + n, val);
-                        } else {
-                            if (bias) val += bias[n];
+                    for (int jj = 0; jj < 16; jj++)
+                        if (n0 + c0 + jj < N) atomicAdd(C + (int64_t)row * ldc + n0 + c0 + jj, v[jj]);
+                } else {
+#pragma unroll
+                    for (int q = 0; q < 4; q++) {  // groups of four columns
+                        const int n = n0 + c0 + 4 * q;
+                        float w[4];
+#pragma unroll
+                        for (int e = 0; e < 4; e++) {
+                            float val = v[4 * q + e];
+                            if (bias && n + e < N) val += bias[n + e];
                             if (relu) val = fmaxf(val, 0.0f);
-                            if (C) C[(int64_t)row * ldc + n] = val;
-                            if (Cb) Cb[(int64_t)row * ldcb + n] = __float2bfloat16_rn(val);
+                            w[e] = val;
+                        }
+                        if (n + 4 <= N && vec_ok) {
+                            if (C)
+                                *reinterpret_cast<float4 *>(C + (int64_t)row * ldc + n) =
+                                    make_float4(w[0], w[1], w[2], w[3]);
+                            if (Cb) {
+                                __nv_bfloat162 lo = __floats2bfloat162_rn(w[0], w[1]);
+                                __nv_bfloat162 hi = __floats2bfloat162_rn(w[2], w[3]);
+                                uint2 pk;
+                                pk.x = *reinterpret_cast<uint32_t *>(&lo);
+                                pk.y = *reinterpret_cast<uint32_t *>(&hi);
+                                *reinterpret_cast<uint2 *>(Cb + (int64_t)row * ldcb + n) = pk;
+                            }
+                        } else {
+#pragma unroll
+                            for (int e = 0; e < 4; e++) {
+                                if (n + e < N) {
+                                    if (C) C[(int64_t)row * ldc + n + e] = w[e];
+                                    if (Cb) Cb[(int64_t)row * ldcb + n + e] = __float2bfloat16_rn(w[e]);
+                                }
+                            }
                         }
                     }
                 }
@@ -145,10 +178,10 @@ __global__ void __launch_bounds__(128) gemm_bf16_kernel(
     };
     bool ok = true;
     int committed = 0;  // stage mbarrier phases committed by thread 0 (MMAs issued)
-    for (int j = 0; j < S - 1; j++) load(j);
+    for (int j = 0; j < kAhead; j++) load(j);
     for (int j = 0; j < total && ok; j++) {
         const int lt = j / nks, ks = j - lt * nks;
-        cp_async_wait<S - 2>();   // this thread's copies of entry j have landed
+        cp_async_wait<kWait>();   // this thread's copies of entry j have landed
         tc::fence_proxy_async();  // ... and are visible to the tensor cores
         tc::fence_before();
         __syncthreads();
@@ -168,10 +201,10 @@ __global__ void __launch_bounds__(128) gemm_bf16_kernel(
             if (ks == nks - 1) tc::mma_commit(tc::smem_u32(&bar_acc[lt & 1]));
         }
         committed = j + 1;
-        // refill the stage of entry j - 1 once its MMAs are done (nothing to
-        // refill near the end of the sequence)
-        if (j >= 1 && j + S - 1 < total) {
-            const int jp = j - 1;
+        // entry j + kAhead goes into the stage of entry j + kAhead - S, once that
+        // entry's MMAs are done (nothing to refill near the end of the sequence)
+        const int nxt = j + kAhead, jp = nxt - S;
+        if (jp >= 0 && nxt < total) {
             const bool done = tc::mbar_wait_bounded(tc::smem_u32(&bar_stage[jp % S]),
                                                     (uint32_t)((jp / S) & 1), kGemmBudget);
             if (!__all_sync(0xffffffffu, done)) ok = false;
@@ -180,7 +213,7 @@ __global__ void __launch_bounds__(128) gemm_bf16_kernel(
             ok = false;
             break;
         }
-        load(j + S - 1);
+        load(nxt);
         // the previous tile's epilogue, while this tile's MMAs run
         if (NACC == 2 && ks == 0 && lt > 0) {
             const bool done = tc::mbar_wait_bounded(tc::smem_u32(&bar_acc[(lt - 1) & 1]),
@@ -240,16 +273,20 @@ cudaError_t launch_bn(dim3 grid, cudaStream_t s, const __nv_bfloat16 *A, int64_t
     return cudaSuccess;
 }
 
-// Short K (at most two 64-wide steps per tile): one CTA per M tile, a 2-stage
-// ring and one accumulator.  Longer K: a 4-stage ring, two accumulators, and
-// persistent CTAs striding over the M tiles.
+// Short K (one or two 64-wide steps per tile): one CTA per M tile, one
+// accumulator, and one or two stages (small CTAs, many per SM, hide the
+// latency).  Longer K: a 4-stage ring, two accumulators, and persistent CTAs
+// striding over the M tiles.
 template <int BN>
-cudaError_t launch_n(bool longk, int mtiles, int ntiles, int splitk, int nsm, cudaStream_t s,
+cudaError_t launch_n(int ksteps, int mtiles, int ntiles, int splitk, int nsm, cudaStream_t s,
                      const __nv_bfloat16 *A, int64_t lda, const __nv_bfloat16 *B, int64_t ldb,
                      float *C, int64_t ldc, __nv_bfloat16 *Cb, int64_t ldcb, int M, int N, int K,
                      int kchunk, const float *bias, int relu, int *err) {
-    if (!longk) {
+    if (ksteps <= 2) {
         dim3 grid((unsigned)mtiles, (unsigned)ntiles, (unsigned)splitk);
+        if (ksteps == 1)
+            return launch_bn<BN, 1, 1>(grid, s, A, lda, B, ldb, C, ldc, Cb, ldcb, M, N, K, kchunk,
+                                       bias, relu, err);
         return launch_bn<BN, 2, 1>(grid, s, A, lda, B, ldb, C, ldc, Cb, ldcb, M, N, K, kchunk,
                                    bias, relu, err);
     }
@@ -291,14 +328,14 @@ cudaError_t launch_gemm_bf16(const __nv_bfloat16 *A, int64_t lda, const __nv_bfl
     int BN = N <= 16 ? 16 : N <= 32 ? 32 : N <= 64 ? 64 : 128;
     while (BN > 16 && (int64_t)mtiles * ((N + BN - 1) / BN) * splitk < nsm / 2) BN /= 2;
     const int ntiles = (N + BN - 1) / BN;
-    const bool longk = kchunk > 2 * kBK;
+    const int csteps = kchunk / kBK;  // K steps of one CTA's chunk
     const int r = relu ? 1 : 0;
     cudaError_t e;
     switch (BN) {
-        case 16: e = launch_n<16>(longk, mtiles, ntiles, splitk, nsm, s, A, lda, B, ldb, C, ldc, Cb, ldcb, M, N, K, kchunk, bias, r, err); break;
-        case 32: e = launch_n<32>(longk, mtiles, ntiles, splitk, nsm, s, A, lda, B, ldb, C, ldc, Cb, ldcb, M, N, K, kchunk, bias, r, err); break;
-        case 64: e = launch_n<64>(longk, mtiles, ntiles, splitk, nsm, s, A, lda, B, ldb, C, ldc, Cb, ldcb, M, N, K, kchunk, bias, r, err); break;
-        default: e = launch_n<128>(longk, mtiles, ntiles, splitk, nsm, s, A, lda, B, ldb, C, ldc, Cb, ldcb, M, N, K, kchunk, bias, r, err); break;
+        case 16: e = launch_n<16>(csteps, mtiles, ntiles, splitk, nsm, s, A, lda, B, ldb, C, ldc, Cb, ldcb, M, N, K, kchunk, bias, r, err); break;
+        case 32: e = launch_n<32>(csteps, mtiles, ntiles, splitk, nsm, s, A, lda, B, ldb, C, ldc, Cb, ldcb, M, N, K, kchunk, bias, r, err); break;
+        case 64: e = launch_n<64>(csteps, mtiles, ntiles, splitk, nsm, s, A, lda, B, ldb, C, ldc, Cb, ldcb, M, N, K, kchunk, bias, r, err); break;
+        default: e = launch_n<128>(csteps, mtiles, ntiles, splitk, nsm, s, A, lda, B, ldb, C, ldc, Cb, ldcb, M, N, K, kchunk, bias, r, err); break;
     }
     if (e != cudaSuccess) return e;
     return cudaGetLastError();

@@ -43,3 +43,12 @@ def test_reference_arm_line_on_the_small_workload():
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == line["value"]
     assert "4 of 200 DM rows" in cb["sample"]
     assert line["config"]["workload"].startswith("tiny: 256 ch")
+
+
+def test_stream_busy_union():
+    import bench
+    assert bench.busy_union([]) == (0.0, 0.0)
+    # overlapping, nested and disjoint intervals, in any order
+    busy, span = bench.busy_union([(5.0, 7.0), (0.0, 2.0), (1.0, 3.0), (1.5, 2.5), (10.0, 11.0)])
+    assert busy == 3.0 + 2.0 + 1.0
+    assert span == 11.0
