@@ -114,6 +114,14 @@ def workload_desc(wl):
                wl.dm_lo, wl.dm_lo + wl.dm_step * (wl.ndm - 1)))
 
 
+def bench_config(wl, n_out, world):
+    """The `config` of the bench line, the same for the GPU arm and the reference arm."""
+    return {"workload": workload_desc(wl), "n_out": n_out, "beams": world,
+            "l2": "inputs larger than L2 (%.1f GB filterbank, %.1f GB series per step)"
+                  % (wl.nchan * wl.n_in / 1e9, 4.0 * wl.ndm * n_out / 1e9),
+            "parallelism": "independent beams" if world > 1 else "single gpu"}
+
+
 def cpu_model():
     try:
         out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
@@ -230,7 +238,7 @@ def run_reference(args):
             "impl": "reference", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "int64+fp64", "data": "synthetic",
-            "config": {"workload": workload_desc(wl), "l2": "inputs larger than L2"},
+            "config": bench_config(wl, n_out, world),
             "cpu_baseline": dict(res[-1], value=value),
             "e2e": {"value": value, "unit": "sky-s/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0},
@@ -859,10 +867,7 @@ def run_gsp(args):
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "int32+fp32", "data": "synthetic",
-            "config": {"workload": workload_desc(wl), "n_out": n_out,
-                       "beams": world, "l2": "inputs larger than L2 (4.3 GB filterbank, "
-                                             "8 GB series per step)",
-                       "parallelism": "independent beams" if world > 1 else "single gpu"},
+            "config": bench_config(wl, n_out, world),
             "dm_chan_samples_per_s": world * adds / (ms_step / 1e3),
             "kernel_ms": {"dedisperse": dd_avg, "search": sum(se_ms) / len(se_ms)},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tadd/s",
