@@ -39,6 +39,7 @@ DD_TRAFFIC_VARIANT = "default"
 NOMINAL_SMS = 152
 RANKER_KEYS = ("recall", "recall_nominal", "precision", "precision_snr8", "negatives_rejected", "threshold",
                "runs", "pulses_detected_snr_ge_min", "candidates_scored", "candidates_per_s",
+               "snippets_per_s", "forward_per_s",
                "train_snippets", "train_positives", "train_steps", "train_steps_per_s", "params",
                "recipe")
 INT_LANES_PER_SM = 128          # issue slots per SM per clock (4 schedulers x 32 lanes)
@@ -716,7 +717,9 @@ def run_ranker(args):
            "threshold": runs[-1]["threshold"], "runs": runs,
            "pulses_detected_snr_ge_min": last["pulses_detected_snr_ge_min"],
            "candidates_scored": last["candidates_scored"],
-           "candidates_per_s": last["candidates_per_s"], "train_snippets": npos + nneg,
+           "candidates_per_s": last["candidates_per_s"],
+           "snippets_per_s": last.get("snippets_per_s"), "forward_per_s": last.get("forward_per_s"),
+           "train_snippets": npos + nneg,
            "train_positives": npos, "train_steps": args.ranker_steps,
            "train_steps_per_s": last["train_steps_per_s"], "params": gsp.gsp_ranker_num_params(),
            "data_s": t_data, "detail": detail,

@@ -565,9 +565,24 @@ gsp_status gsp_ranker_get_params(gsp_ranker_t r, float *host_params, float *host
  * width / 4) samples s of time bin j, centred on t + width / 2, of the
  * normalised series of DM row dm_idx - 32 + i (detrended residual / sigma_ref;
  * 0 in bad blocks, outside the rows or past the searched length), divided by
- * sqrt(f).  GSP_ERR_STATE if the plan has not searched.  Asynchronous. */
+ * sqrt(f).  Every bin is summed as exact integer runs inside one search block.
+ * Two paths give the same floats: direct reads of the 64 f samples of each
+ * row (bulk copies through shared memory), or two to three reads per bin of
+ * block-local prefix sums of the series, which the plan builds once per
+ * search and series (one read and one write of the series into plan memory
+ * allocated on first use, ndm x searched length int32).  The prefix path is
+ * taken when n * 64 * 64 * 4 samples exceed twice the series (or as
+ * gsp_plan_set_snippet_path says).  GSP_ERR_STATE if the plan has not
+ * searched, GSP_ERR_OOM if the prefix memory cannot be allocated.  A bounded
+ * wait of the direct path that gives up sets the plan's error flag (reported
+ * by gsp_candidates or gsp_plan_timing as GSP_ERR_TIMEOUT).  Asynchronous. */
 gsp_status gsp_ranker_snippets(gsp_plan_t plan, const int32_t *d_D, int64_t stride,
                                const gsp_cand *d_cands, int32_t n, float *d_out, void *stream);
+
+/* Snippet path of gsp_ranker_snippets for this plan (a test and tuning knob;
+ * the paper has no counterpart): 0 automatic (default), 1 direct reads,
+ * 2 prefix sums.  Host only. */
+gsp_status gsp_plan_set_snippet_path(gsp_plan_t plan, int32_t path);
 
 /* Logits (device float [n][2]) of n snippets (device float [n][64][64]).
  * Asynchronous. */

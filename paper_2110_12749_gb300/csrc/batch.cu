@@ -261,6 +261,7 @@ gsp_status gsp_batch_search(gsp_batch_t b, const gsp_beam_input *in, void *strea
     }
     b->last_stream = s;
     b->have_search = true;
+    for (gsp_plan_s *p : b->plans) p->search_seq++;  // also on graph replays
     return GSP_OK;
 }
 

@@ -93,6 +93,7 @@ void free_plan(gsp_plan_s *p) {
     for (auto &row : p->d_stspread)
         for (auto *b : row) cudaFree(b);
     cudaFree(p->d_err);
+    cudaFree(p->d_prefix);
     cudaFree(p->d_bsum);
     cudaFree(p->d_sigma_b);
     cudaFree(p->d_bad);
@@ -209,6 +210,7 @@ gsp_status run_search(gsp_plan_s *p, const int32_t *D, int64_t n_out, int64_t st
     p->last_nout = n_out;
     p->last_nb = n_out / p->desc.block_len;
     p->have_search = true;
+    p->search_seq++;
     return GSP_OK;
 }
 
@@ -649,6 +651,12 @@ gsp_status gsp_plan_set_wait_limit(gsp_plan_t p, int64_t cycles, int32_t starve)
         return GSP_ERR_INVALID_ARG;
     p->wait_budget = cycles;
     p->wait_starve = starve;
+    return GSP_OK;
+}
+
+gsp_status gsp_plan_set_snippet_path(gsp_plan_t p, int32_t path) {
+    if (!p || path < 0 || path > 2) return GSP_ERR_INVALID_ARG;
+    p->snippet_path = path;
     return GSP_OK;
 }
 

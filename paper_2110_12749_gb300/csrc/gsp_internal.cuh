@@ -125,6 +125,16 @@ struct gsp_plan_s {
     const int32_t *last_D = nullptr;  // series of the last search and its row stride
     int64_t last_stride = 0;
     bool have_search = false;
+    uint64_t search_seq = 0;          // searches run (incremented by every search)
+    // block-local inclusive prefix sums of a series for the snippet kernel,
+    // lazily allocated [ndm][prefix_stride]; valid for (prefix_seq, prefix_src)
+    int32_t *d_prefix = nullptr;
+    size_t d_prefix_elems = 0;
+    int64_t prefix_stride = 0;
+    uint64_t prefix_seq = 0;
+    const int32_t *prefix_src = nullptr;
+    int64_t prefix_src_stride = 0;
+    int snippet_path = 0;             // 0 automatic, 1 direct reads, 2 prefix sums
     int32_t launches = 0;
 };
 

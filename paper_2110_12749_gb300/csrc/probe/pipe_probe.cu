@@ -60,6 +60,16 @@ __global__ void __launch_bounds__(512, 2) probe(uint32_t seed, uint32_t one, uin
                              : "r"(addr * 4 - 3 * (uint32_t)__cvta_generic_to_shared(sm) + 512 * (c & 3) + ((it & 3) << 11)));
                 asm volatile("mad.lo.u32 %0, %1, %2, %0;" : "+r"(a[c]) : "r"(x ^ y ^ z ^ w), "r"(one));
             }
+            if (OP == 11) {
+                // packed FP32 FMA: two independent FMAs per instruction (f[c], f[c ^ 1] as a pair)
+                if ((c & 1) == 0) {
+                    uint64_t pr = ((uint64_t)__float_as_uint(f[c + 1]) << 32) | __float_as_uint(f[c]);
+                    const uint64_t m2 = 0x3f8000003f800000ull, c2 = 0x3f0000003f000000ull;  // (1, 1), (0.5, 0.5)
+                    asm volatile("fma.rn.f32x2 %0, %0, %1, %2;" : "+l"(pr) : "l"(m2), "l"(c2));
+                    f[c] = __uint_as_float((uint32_t)pr);
+                    f[c + 1] = __uint_as_float((uint32_t)(pr >> 32));
+                }
+            }
             if (OP == 9) {
                 // the same mix without the shared loads (register operands only)
                 uint32_t w1 = a[c] ^ it, w2 = a[(c + 1) % CH];
@@ -125,6 +135,8 @@ int main() {
     run<8>("SWAR mix, byte-adds (LDS)", 8, nsm, out, cyc);
     run<9>("SWAR mix, byte-adds (regs)", 8, nsm, out, cyc);
     run<10>("ld.shared.v4 (bytes)", 16, nsm, out, cyc);
+    // OP 11: one fma.rn.f32x2 per two chains, i.e. one FP32 FMA per chain step
+    run<11>("fma.rn.f32x2 (FMAs)", 1, nsm, out, cyc);
     printf("done\n");
     return 0;
 }

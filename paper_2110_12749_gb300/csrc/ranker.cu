@@ -24,6 +24,7 @@
 #include <string>
 #include <vector>
 
+#include "dd_tiled.cuh"
 #include "gsp_internal.cuh"
 #include "tc_gemm.cuh"
 
@@ -113,59 +114,70 @@ __global__ void __launch_bounds__(256) im2col_kernel(const T *__restrict__ a, in
 // max-pool straight from the FP32 snippets, on the CUDA cores: with one input
 // channel the product has K = 9, too short for the tensor pipe to pay for its
 // staging.  The rounding points are those of the im2col + GEMM + pool path:
-// inputs and weights in bf16, the nine products and the bias summed in FP32,
-// the pooled maximum rounded to bf16.  One thread per pooled pixel reads its
-// 4 x 4 input patch, computes its 2 x 2 conv outputs for all 8 channels and
-// writes the 8 bf16 results as one 16-byte store (NHWC, as pool_kernel<8>).
+// inputs and weights in bf16, the nine products and the bias summed in FP32
+// (in the same order), the pooled maximum rounded to bf16.  One thread per pair
+// of horizontally adjacent pooled pixels reads its 4 x 6 input patch; per
+// channel it loads the nine weights once and computes the pair's 2 x 4 conv
+// outputs, then writes the two pixels' 8 bf16 results as two 16-byte stores
+// (NHWC, as pool_kernel<8>).
 __global__ void __launch_bounds__(256) conv0_pool_kernel(const float *__restrict__ x, int B,
                                                          const bf16 *__restrict__ W0,
                                                          const float *__restrict__ b0,
                                                          bf16 *__restrict__ a0) {
-    constexpr int C = 8, KP = kpad(0), H = kS, H2 = kS / 2;
+    constexpr int C = 8, KP = kpad(0), H = kS, H2 = kS / 2, HP = H2 / 2;
     __shared__ float sw[C][9];
     __shared__ float sb[C];
     for (int i = threadIdx.x; i < C * 9; i += blockDim.x)
         sw[i / 9][i % 9] = __bfloat162float(W0[(i / 9) * KP + i % 9]);
     for (int i = threadIdx.x; i < C; i += blockDim.x) sb[i] = b0[i];
     __syncthreads();
-    const int64_t total = (int64_t)B * H2 * H2;
+    const int64_t total = (int64_t)B * H2 * HP;  // pixel pairs
     for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total;
          q += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t b = q / (H2 * H2);
-        const int rem = (int)(q - b * H2 * H2);
-        const int y2 = rem / H2, x2 = rem - (rem / H2) * H2;
+        const int64_t b = q / (H2 * HP);
+        const int rem = (int)(q - b * H2 * HP);
+        const int y2 = rem / HP, x2 = 2 * (rem - (rem / HP) * HP);  // first pooled column
         const float *img = x + b * H * H;
-        float v[4][4];
+        float v[4][6];
 #pragma unroll
         for (int r = 0; r < 4; r++) {
             const int yy = 2 * y2 - 1 + r;
 #pragma unroll
-            for (int c = 0; c < 4; c++) {
+            for (int c = 0; c < 6; c++) {
                 const int xx = 2 * x2 - 1 + c;
                 const bool in = yy >= 0 && yy < H && xx >= 0 && xx < H;
                 v[r][c] = in ? __bfloat162float(__float2bfloat16_rn(__ldg(img + yy * H + xx)))
                              : 0.0f;
             }
         }
-        __align__(16) bf16 out[C];
+        __align__(16) bf16 out[2][C];
 #pragma unroll
         for (int co = 0; co < C; co++) {
-            float m = 0.0f;  // ReLU outputs are >= 0
+            float w[9];
 #pragma unroll
-            for (int dy = 0; dy < 2; dy++)
+            for (int k = 0; k < 9; k++) w[k] = sw[co][k];
+            const float bias = sb[co];
 #pragma unroll
-                for (int dx = 0; dx < 2; dx++) {
-                    float z = 0.0f;
+            for (int px = 0; px < 2; px++) {
+                float m = 0.0f;  // ReLU outputs are >= 0
 #pragma unroll
-                    for (int ky = 0; ky < 3; ky++)
+                for (int dy = 0; dy < 2; dy++)
 #pragma unroll
-                        for (int kx = 0; kx < 3; kx++)
-                            z = fmaf(v[dy + ky][dx + kx], sw[co][ky * 3 + kx], z);
-                    m = fmaxf(m, z + sb[co]);
-                }
-            out[co] = __float2bfloat16_rn(m);
+                    for (int dx = 0; dx < 2; dx++) {
+                        float z = 0.0f;
+#pragma unroll
+                        for (int ky = 0; ky < 3; ky++)
+#pragma unroll
+                            for (int kx = 0; kx < 3; kx++)
+                                z = fmaf(v[dy + ky][2 * px + dx + kx], w[ky * 3 + kx], z);
+                        m = fmaxf(m, z + bias);
+                    }
+                out[px][co] = __float2bfloat16_rn(m);
+            }
         }
-        *reinterpret_cast<uint4 *>(a0 + q * C) = *reinterpret_cast<const uint4 *>(out);
+        const int64_t pix = (b * H2 + y2) * H2 + x2;
+        *reinterpret_cast<uint4 *>(a0 + pix * C) = *reinterpret_cast<const uint4 *>(out[0]);
+        *reinterpret_cast<uint4 *>(a0 + (pix + 1) * C) = *reinterpret_cast<const uint4 *>(out[1]);
     }
 }
 
@@ -428,6 +440,7 @@ namespace {
 // ------------------------------------------- fused conv layers for inference
 
 namespace tc = gsp::tc;
+namespace ptx = gsp::ptx;
 
 constexpr long long kConvBudget = 2000000000ll;  // ~1 s of SM clock per wait
 
@@ -738,14 +751,32 @@ cudaError_t launch_conv_pool(gsp_ranker_s *r, const bf16 *act, int n, const bf16
     constexpr int smem = conv_pool_smem<CIN, COUT, SIDE>();
     static int blocks_per_sm = 0;
     if (blocks_per_sm == 0) {
+        // CTAs per SM from the kernel's resources: shared memory (stages + static +
+        // the per-CTA reservation), registers, threads, and at most 512 tensor-memory
+        // columns (two accumulators of COUT columns per CTA).  The runtime's occupancy
+        // query answers one CTA per SM for this kernel whatever its shared memory,
+        // while several do run side by side (four CTAs per SM run layer 1 2.3x faster
+        // than one), so the count is computed here.
         cudaError_t e = cudaFuncSetAttribute(conv_pool_tc_kernel<CIN, COUT, SIDE>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e == cudaSuccess)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                &blocks_per_sm, conv_pool_tc_kernel<CIN, COUT, SIDE>, 128, smem);
+            e = cudaFuncSetAttribute(conv_pool_tc_kernel<CIN, COUT, SIDE>,
+                                     cudaFuncAttributePreferredSharedMemoryCarveout,
+                                     (int)cudaSharedmemCarveoutMaxShared);
+        cudaFuncAttributes fa;
+        if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, conv_pool_tc_kernel<CIN, COUT, SIDE>);
+        int dev = 0, smem_sm = 0, resv = 0;
+        if (e == cudaSuccess) e = cudaGetDevice(&dev);
+        if (e == cudaSuccess)
+            e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+        if (e == cudaSuccess)
+            e = cudaDeviceGetAttribute(&resv, cudaDevAttrReservedSharedMemoryPerBlock, dev);
         if (e != cudaSuccess) return e;
-        // at most 512 tensor-memory columns per SM (2 accumulators of COUT columns)
-        blocks_per_sm = std::max(1, std::min(blocks_per_sm, 512 / std::max(32, 2 * COUT)));
+        const int per_cta = smem + (int)fa.sharedSizeBytes + resv;
+        const int by_smem = smem_sm / per_cta;
+        const int by_regs = 65536 / (128 * std::max(fa.numRegs, 1));
+        const int by_tmem = 512 / std::max(32, 2 * COUT);
+        blocks_per_sm = std::max(1, std::min(std::min(by_smem, by_regs), std::min(by_tmem, 16)));
     }
     int dev = 0, sms = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -770,7 +801,7 @@ cudaError_t forward(gsp_ranker_s *r, const float *x, int n, bool train, cudaStre
         if (!train) {
             cudaError_t e = cudaSuccess;
             if (l == 0)
-                RK_LAUNCH((conv0_pool_kernel<<<blocks_for(P / 4), 256, 0, s>>>(
+                RK_LAUNCH((conv0_pool_kernel<<<blocks_for(P / 8), 256, 0, s>>>(
                     x, n, r->W[0], r->params + r->off.b[0], r->a[0])));
             else if (l == 1)
                 e = launch_conv_pool<8, 16, 32>(r, r->a[0], n, r->W[1], r->params + r->off.b[1],
@@ -873,73 +904,294 @@ gsp_status status_of(cudaError_t e, const char *what) {
 // bin j (f = max(1, w / 4) samples, bins centred on t + w / 2) of the
 // normalised series of row dm - 32 + i, ((D - m) - (c0 + beta j)) / sigma_ref
 // (0 in bad blocks, rows with sigma_ref = 0, outside the rows or past Ls),
-// divided by sqrt(f).
+// divided by sqrt(f).  A bin is summed as exact integer runs inside one search
+// block, with the block's trend applied in closed form.
 //
-// Warp w builds rows w, w + 8, ...; a row in two halves of 32 time bins.  The
-// warp first copies the half's 32 f consecutive samples of D into its shared
-// buffer (coalesced: consecutive lanes, consecutive samples), then lane l sums
-// bin 32 h + l from shared memory (f is odd except for f = 2, so the lanes'
-// strided reads hit distinct banks).  A bin is summed as exact integer runs
-// inside one search block, with the block's trend applied in closed form.
-constexpr int kSnipMaxF = 37;  // f of the widest default boxcar (150 / 4)
+// A row of the snippet reads 64 f consecutive samples of D.  The CTA streams
+// them through a shared-memory ring of two halves with 1-D bulk copies (one
+// per row, 16-byte aligned span [t_al, t_end) around the row's 64 f samples,
+// completion counted on the half's mbarrier): thread 0 fills half (b & 1) with
+// the S rows of batch b while the warps sum batch b - 1 from the other half,
+// S = the rows of this candidate's span that fit a half.  The warps share the
+// batch's 2 S half-rows of 32 bins; lane l sums one bin (f is odd except for
+// f = 2, so the lanes' strided reads hit distinct banks).  A candidate whose span
+// leaves [0, stride) of its rows, or a series that is not 16-byte aligned,
+// reads D directly instead (same sums).  Every wait is bounded; a wait that
+// gives up sets *err, waits (bounded) for the copies it issued and leaves.
+// Bytes per half of the ring: a sweep of 8 to 48 KB halves (and of 128- and
+// 256-thread CTAs) over a searched beam's 130k candidates put 24 KB halves and
+// 256 threads first, at 4.6 TB/s of snippet reads (three CTAs per SM).
+constexpr int kSnipHalf = 24 * 1024;
+constexpr long long kSnipBudget = 2000000000ll;
 
+// One run's term of a bin, ((sd - n m) - (n c0 + beta sj)) / sigma_ref for the
+// run's exact sum sd and sj = the sum of its in-block sample indices, rounded
+// step by step (no contraction into FMAs), so that both snippet paths give the
+// same float.
+__device__ __forceinline__ float run_term(int64_t sd, int n, int64_t sj, const gsp::BlockParam &q,
+                                          float inv) {
+    const float a = (float)(sd - (int64_t)n * q.m);
+    const float t = __fadd_rn(__fmul_rn((float)n, q.c0), __fmul_rn(q.beta, (float)sj));
+    return __fmul_rn(__fsub_rn(a, t), inv);
+}
+
+// Bin [a, a + f) of one row; src[t - base] is sample t, b0 * B <= max(a, 0).
+// At most two runs (f <= B), each summed exactly in Acc (int32 when f times
+// the largest |D| stays below 2^31, else int64).
+template <typename Acc>
+__device__ __forceinline__ float snippet_bin(const int32_t *src, int64_t base, int64_t a, int f,
+                                             int64_t Ls, int B, int64_t b0,
+                                             const gsp::BlockParam *brow, float inv) {
+    int64_t s0 = max(a, (int64_t)0);
+    const int64_t s1 = min(a + f, Ls);
+    float v = 0.0f;
+    while (s0 < s1) {
+        const int64_t b = b0 + (int64_t)((uint32_t)(s0 - b0 * B) / (uint32_t)B);
+        const int jb0 = (int)(s0 - b * B);
+        const int64_t e = min(s1, (b + 1) * (int64_t)B);
+        const int n = (int)(e - s0);
+        const gsp::BlockParam q = brow[b];
+        if (q.good) {
+            const int32_t *p = src + (s0 - base);
+            Acc sd = 0;  // exact
+#pragma unroll 4
+            for (int k = 0; k < n; k++) sd += p[k];
+            const int64_t sj = (int64_t)n * jb0 + (int64_t)n * (n - 1) / 2;
+            v = __fadd_rn(v, run_term((int64_t)sd, n, sj, q, inv));
+        }
+        s0 = e;
+    }
+    return v;
+}
+
+template <int HALF>
 __global__ void __launch_bounds__(256) snippet_kernel(
     const int32_t *__restrict__ D, int64_t stride, int ndm, int64_t Ls, int B,
     const gsp::BlockParam *__restrict__ bp, int64_t nb_max, const double *__restrict__ sref,
-    const gsp_cand *__restrict__ cands, float *__restrict__ out) {
+    const gsp_cand *__restrict__ cands, int64_t dmax, float *__restrict__ out, int *err) {
+    extern __shared__ __align__(128) int32_t ring[];  // 2 * HALF bytes
+    __shared__ __align__(8) uint64_t bar[2];
+    __shared__ float s_inv[kS];
     const gsp_cand c = cands[blockIdx.x];
     const int f = max(1, c.width / 4);
-    const int64_t tc = c.t + c.width / 2;
+    const int64_t tlo = c.t + c.width / 2 - (int64_t)(kS / 2) * f;  // first sample of bin 0
     const float rs = 1.0f / sqrtf((float)f);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    __shared__ int32_t seg[8][32 * kSnipMaxF];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nwarps = (int)(blockDim.x >> 5);
     float *o = out + (int64_t)blockIdx.x * kS * kS;
-    for (int i = warp; i < kS; i += 8) {
+    // the 16-byte aligned span of every row: samples [t_al, t_end)
+    const int64_t t_al = tlo >= 0 ? (tlo & ~(int64_t)3) : -((-tlo + 3) & ~(int64_t)3);
+    const int64_t t_end = (tlo + (int64_t)kS * f + 3) & ~(int64_t)3;
+    const int64_t rowb64 = (t_end - t_al) * 4;
+    const bool bulk = ((reinterpret_cast<uintptr_t>(D) & 15u) == 0) && (stride % 4 == 0) &&
+                      t_al >= 0 && t_end <= stride && rowb64 <= HALF;
+    const uint32_t rowb = bulk ? (uint32_t)rowb64 : 0u;
+    const int S = bulk ? min(kS, (int)(HALF / rowb)) : kS;  // rows per batch
+    const int nbatch = (kS + S - 1) / S;
+    const int64_t b0 = max(tlo, (int64_t)0) / B;           // first search block of the span
+    const bool narrow = (int64_t)f * dmax < 2147483648ll;  // int32 run sums are exact
+    for (int i = tid; i < kS; i += blockDim.x) {
+        const int r = c.dm_idx - kS / 2 + i;
+        s_inv[i] = (r >= 0 && r < ndm && sref[r] > 0.0) ? (float)(1.0 / sref[r]) : 0.0f;
+    }
+    const uint32_t ring0 = ptx::smem_addr(ring);
+    const uint32_t bar0 = ptx::smem_addr(&bar[0]);
+    if (tid == 0) {
+        ptx::mbar_init(bar0, 1);
+        ptx::mbar_init(bar0 + 8, 1);
+        ptx::fence_barrier_init();
+    }
+    __syncthreads();
+    // thread 0: the copies of batch b into half b & 1 (rows with sigma_ref = 0
+    // are not copied); returns the bytes expected on the half's barrier
+    auto issue = [&](int b) {
+        const int r0 = b * S, n = min(S, kS - r0);
+        uint32_t bytes = 0;
+        for (int k = 0; k < n; k++) bytes += s_inv[r0 + k] != 0.0f ? rowb : 0u;
+        const uint32_t hb = bar0 + 8u * (uint32_t)(b & 1);
+        ptx::mbar_arrive_expect_tx(hb, bytes);
+        for (int k = 0; k < n; k++) {
+            if (s_inv[r0 + k] == 0.0f) continue;
+            const int r = c.dm_idx - kS / 2 + r0 + k;
+            ptx::bulk_g2s(ring0 + (uint32_t)(b & 1) * HALF + (uint32_t)k * rowb,
+                          D + (int64_t)r * stride + t_al, rowb, hb);
+        }
+    };
+    if (bulk && tid == 0) {
+        issue(0);
+        if (nbatch > 1) issue(1);
+    }
+    bool ok = true;
+    int waited = 0;  // batches whose copies are known to have landed
+    for (int b = 0; b < nbatch; b++) {
+        const int r0 = b * S, n = min(S, kS - r0);
+        if (bulk) {
+            const bool done = ptx::mbar_wait(bar0 + 8u * (uint32_t)(b & 1), (uint32_t)((b >> 1) & 1),
+                                             kSnipBudget);
+            if (!__syncthreads_and(done)) {
+                ok = false;
+                break;
+            }
+            waited = b + 1;
+        }
+        const int32_t *half = ring + (size_t)(b & 1) * (HALF / 4);
+        // 2 n half-rows of 32 bins over the warps: warp task wt is row wt / 2,
+        // bins 32 (wt % 2) + lane
+        for (int wt = warp; wt < 2 * n; wt += nwarps) {
+            const int k = wt >> 1, i = r0 + k, j = 32 * (wt & 1) + lane;
+            const float inv = s_inv[i];
+            float v = 0.0f;
+            if (inv != 0.0f) {  // warp-uniform
+                const int r = c.dm_idx - kS / 2 + i;
+                const gsp::BlockParam *brow = bp + (int64_t)r * nb_max;
+                const int32_t *src = bulk ? half + (size_t)k * (rowb / 4) : D + (int64_t)r * stride;
+                const int64_t base = bulk ? t_al : 0;
+                const int64_t a = tlo + (int64_t)j * f;
+                v = narrow ? snippet_bin<int32_t>(src, base, a, f, Ls, B, b0, brow, inv)
+                           : snippet_bin<int64_t>(src, base, a, f, Ls, B, b0, brow, inv);
+            }
+            o[i * kS + j] = v * rs;
+        }
+        if (bulk && b + 2 < nbatch) {
+            __syncthreads();  // every warp is done with half b & 1
+            if (tid == 0) issue(b + 2);
+        }
+    }
+    if (!ok) {
+        if (tid == 0) atomicExch(err, 1);
+        // the copies of the (at most two) batches issued but not waited for
+        for (int b = waited; b < min(nbatch, waited + 2); b++)
+            (void)ptx::mbar_wait(bar0 + 8u * (uint32_t)(b & 1), (uint32_t)((b >> 1) & 1), kSnipBudget);
+    }
+}
+
+// Block-local inclusive prefix sums of a series, for snippets of wide bins:
+// P[r][b B + k] = sum of D[r][b B .. b B + k] (mod 2^32) for every search block
+// b < nb of every row.  A run of samples inside one block then sums to the
+// difference of two entries, exact whenever the run's true sum lies within
+// int32 (at most f samples of at most nchan * 255 each).  One CTA per (row,
+// block) job, grid-stride; each warp scans 128 consecutive samples of a
+// 1024-sample chunk with shuffles, the warps' totals are combined through
+// shared memory, and a carry runs across the chunks of a block.
+__global__ void __launch_bounds__(256) block_prefix_kernel(const int32_t *__restrict__ D,
+                                                           int64_t stride, int ndm, int64_t nb,
+                                                           int B, int32_t *__restrict__ P,
+                                                           int64_t pstride) {
+    __shared__ uint32_t wsum[8];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int64_t job = blockIdx.x; job < (int64_t)ndm * nb; job += gridDim.x) {
+        const int64_t r = job / nb, b = job - r * nb;
+        const int32_t *src = D + r * stride + b * B;
+        int32_t *dst = P + r * pstride + b * B;
+        uint32_t carry = 0;  // sum of the block's samples before this chunk
+        for (int c0 = 0; c0 < B; c0 += 1024) {
+            uint32_t v[4], run = 0;
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                const int idx = c0 + warp * 128 + k * 32 + lane;
+                uint32_t x = idx < B ? (uint32_t)__ldg(src + idx) : 0u;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+                    if (lane >= o) x += y;
+                }
+                v[k] = x + run;
+                run += __shfl_sync(0xffffffffu, x, 31);
+            }
+            if (lane == 0) wsum[warp] = run;
+            __syncthreads();
+            uint32_t off = carry, tot = 0;
+#pragma unroll
+            for (int w = 0; w < 8; w++) {
+                off += w < warp ? wsum[w] : 0u;
+                tot += wsum[w];
+            }
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                const int idx = c0 + warp * 128 + k * 32 + lane;
+                if (idx < B) dst[idx] = (int32_t)(v[k] + off);
+            }
+            carry += tot;
+            __syncthreads();  // wsum is rewritten by the next chunk
+        }
+    }
+}
+
+// Bin [a, a + f) of one row from the block-local prefix sums prow (b0 * B <=
+// max(a, 0)): at most two runs (f <= B), the second one starting a block; the
+// three prefix entries are loaded before any is used.  The same run_term
+// arithmetic as snippet_bin on the same exact run sums, so the same float.
+__device__ __forceinline__ float snippet_bin_prefix(const int32_t *__restrict__ prow, int64_t a,
+                                                    int f, int64_t Ls, int B, int64_t b0,
+                                                    const gsp::BlockParam *brow, float inv) {
+    const int64_t s0 = max(a, (int64_t)0);
+    const int64_t s1 = min(a + f, Ls);
+    if (s0 >= s1) return 0.0f;
+    const int64_t b = b0 + (int64_t)((uint32_t)(s0 - b0 * B) / (uint32_t)B);
+    const int64_t bs = b * (int64_t)B, be = bs + B;
+    const bool split = s1 > be;
+    const int64_t e1 = split ? be : s1;
+    const uint32_t p_lo = s0 > bs ? (uint32_t)__ldg(prow + s0 - 1) : 0u;
+    const uint32_t p_hi = (uint32_t)__ldg(prow + e1 - 1);
+    const uint32_t p_2 = split ? (uint32_t)__ldg(prow + s1 - 1) : 0u;
+    float v = 0.0f;
+    {
+        const int n = (int)(e1 - s0), jb0 = (int)(s0 - bs);
+        const gsp::BlockParam q = brow[b];
+        if (q.good) {
+            const int64_t sd = (int32_t)(p_hi - p_lo);
+            const int64_t sj = (int64_t)n * jb0 + (int64_t)n * (n - 1) / 2;
+            v = __fadd_rn(v, run_term(sd, n, sj, q, inv));
+        }
+    }
+    if (split) {  // [be, s1) at the start of block b + 1
+        const int n = (int)(s1 - be);
+        const gsp::BlockParam q = brow[b + 1];
+        if (q.good) {
+            const int64_t sd = (int32_t)p_2;
+            const int64_t sj = (int64_t)n * (n - 1) / 2;
+            v = __fadd_rn(v, run_term(sd, n, sj, q, inv));
+        }
+    }
+    return v;
+}
+
+// Snippets from the block-local prefix sums P of the series D (see
+// snippet_kernel for the definition): two to three 4-byte loads per bin instead
+// of f.  CTA per candidate; warp w builds rows w, w + 8, ..., lane l bins l and
+// l + 32.  A candidate whose bins could span more than two blocks (f > B) or
+// whose run sums could leave int32 sums its bins from D directly.
+__global__ void __launch_bounds__(256) snippet_prefix_kernel(
+    const int32_t *__restrict__ P, int64_t pstride, const int32_t *__restrict__ D, int64_t stride,
+    int ndm, int64_t Ls, int B, const gsp::BlockParam *__restrict__ bp, int64_t nb_max,
+    const double *__restrict__ sref, const gsp_cand *__restrict__ cands, int64_t dmax,
+    float *__restrict__ out) {
+    const gsp_cand c = cands[blockIdx.x];
+    const int f = max(1, c.width / 4);
+    const bool via_prefix = f <= B && (int64_t)f * dmax < 2147483648ll;
+    const int64_t tlo = c.t + c.width / 2 - (int64_t)(kS / 2) * f;  // first sample of bin 0
+    const int64_t b0 = max(tlo, (int64_t)0) / B;
+    const float rs = 1.0f / sqrtf((float)f);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = (int)(blockDim.x >> 5);
+    float *o = out + (int64_t)blockIdx.x * kS * kS;
+    for (int i = warp; i < kS; i += nwarps) {
         const int r = c.dm_idx - kS / 2 + i;
         const float inv = (r >= 0 && r < ndm && sref[r] > 0.0) ? (float)(1.0 / sref[r]) : 0.0f;
-        if (inv == 0.0f) {  // warp-uniform: a blank row
-            o[i * kS + lane] = 0.0f;
-            o[i * kS + 32 + lane] = 0.0f;
-            continue;
-        }
-        const int32_t *drow = D + (int64_t)r * stride;
-        const gsp::BlockParam *brow = bp + (int64_t)r * nb_max;
-        for (int h = 0; h < 2; h++) {
-            const int64_t a0 = tc + (int64_t)(32 * h - kS / 2) * f;  // first sample of bin 32 h
-            if (f <= kSnipMaxF) {
-                __syncwarp();
-                for (int idx = lane; idx < 32 * f; idx += 32) {
-                    const int64_t t = a0 + idx;
-                    seg[warp][idx] = (t >= 0 && t < Ls) ? __ldg(drow + t) : 0;
-                }
-                __syncwarp();
+        float v0 = 0.0f, v1 = 0.0f;
+        if (inv != 0.0f) {  // warp-uniform
+            const gsp::BlockParam *brow = bp + (int64_t)r * nb_max;
+            const int64_t a0 = tlo + (int64_t)lane * f, a1 = tlo + (int64_t)(32 + lane) * f;
+            if (via_prefix) {
+                const int32_t *prow = P + (int64_t)r * pstride;
+                v0 = snippet_bin_prefix(prow, a0, f, Ls, B, b0, brow, inv);
+                v1 = snippet_bin_prefix(prow, a1, f, Ls, B, b0, brow, inv);
+            } else {
+                const int32_t *drow = D + (int64_t)r * stride;
+                v0 = snippet_bin<int64_t>(drow, 0, a0, f, Ls, B, b0, brow, inv);
+                v1 = snippet_bin<int64_t>(drow, 0, a1, f, Ls, B, b0, brow, inv);
             }
-            const int64_t a = a0 + (int64_t)lane * f;
-            int64_t s0 = max(a, (int64_t)0);
-            const int64_t s1 = min(a + f, Ls);
-            float v = 0.0f;
-            // at most two runs: f <= B
-            while (s0 < s1) {
-                const int64_t b = s0 / B;
-                const int jb0 = (int)(s0 - b * B);
-                const int64_t e = min(s1, (b + 1) * (int64_t)B);
-                const int n = (int)(e - s0);
-                const gsp::BlockParam q = brow[b];
-                if (q.good) {
-                    int64_t sd = 0;  // exact
-                    if (f <= kSnipMaxF) {
-                        for (int64_t t = s0; t < e; t++) sd += seg[warp][t - a0];
-                    } else {
-                        for (int64_t t = s0; t < e; t++) sd += drow[t];
-                    }
-                    const int64_t sj = (int64_t)n * jb0 + (int64_t)n * (n - 1) / 2;
-                    v += ((float)(sd - (int64_t)n * q.m) - ((float)n * q.c0 + q.beta * (float)sj)) *
-                         inv;
-                }
-                s0 = e;
-            }
-            o[i * kS + 32 * h + lane] = v * rs;
         }
+        o[i * kS + lane] = v0 * rs;
+        o[i * kS + 32 + lane] = v1 * rs;
     }
 }
 
@@ -952,10 +1204,61 @@ gsp_status gsp_ranker_snippets(gsp_plan_t p, const int32_t *d_D, int64_t stride,
     if (!p || !d_D || !d_cands || !d_out || n < 0) return GSP_ERR_INVALID_ARG;
     if (!p->have_search) return GSP_ERR_STATE;
     if (n == 0) return GSP_OK;
-    const int64_t Ls = p->last_nb * p->desc.block_len;
-    snippet_kernel<<<n, 256, 0, (cudaStream_t)stream>>>(d_D, stride, p->desc.ndm, Ls,
-                                                        p->desc.block_len, p->d_bparam, p->nb_max,
-                                                        p->d_sref, d_cands, d_out);
+    cudaStream_t s = (cudaStream_t)stream;
+    const int B = p->desc.block_len;
+    const int64_t Ls = p->last_nb * B;
+    const int64_t dmax = (int64_t)p->desc.nchan * 255;
+    // prefix sums pay off once the candidates' direct reads (64 x 64 f samples
+    // each; f is taken as 4 here, the narrowest bins that fill a 16-byte
+    // chunk) exceed building them (one read and one write of the series)
+    const bool big = (int64_t)n * kS * kS * 4 >= 2 * (int64_t)p->desc.ndm * Ls;
+    const bool use_prefix = Ls > 0 && (p->snippet_path == 2 || (p->snippet_path == 0 && big));
+    if (use_prefix) {
+        const int64_t pstride = (Ls + 3) & ~(int64_t)3;
+        const size_t need = (size_t)p->desc.ndm * (size_t)pstride;
+        if (need > p->d_prefix_elems) {
+            cudaFree(p->d_prefix);
+            p->d_prefix = nullptr;
+            p->d_prefix_elems = 0;
+            p->prefix_seq = 0;
+            if (cudaMalloc((void **)&p->d_prefix, need * sizeof(int32_t)) != cudaSuccess) {
+                (void)cudaGetLastError();
+                return GSP_ERR_OOM;
+            }
+            p->d_prefix_elems = need;
+        }
+        if (p->prefix_seq != p->search_seq || p->prefix_src != d_D || p->prefix_src_stride != stride ||
+            p->prefix_stride != pstride) {
+            const int64_t jobs = (int64_t)p->desc.ndm * p->last_nb;
+            const int grid = (int)std::min<int64_t>(jobs, (int64_t)p->num_sms * 8);
+            block_prefix_kernel<<<grid, 256, 0, s>>>(d_D, stride, p->desc.ndm, p->last_nb, B,
+                                                      p->d_prefix, pstride);
+            cudaError_t e = cudaGetLastError();
+            if (e != cudaSuccess) return status_of(e, "prefix launch");
+            p->prefix_seq = p->search_seq;
+            p->prefix_src = d_D;
+            p->prefix_src_stride = stride;
+            p->prefix_stride = pstride;
+        }
+        snippet_prefix_kernel<<<n, 256, 0, s>>>(p->d_prefix, pstride, d_D, stride, p->desc.ndm, Ls,
+                                                B, p->d_bparam, p->nb_max, p->d_sref, d_cands,
+                                                dmax, d_out);
+        return status_of(cudaGetLastError(), "snippet launch");
+    }
+    static bool configured = false;  // the ring's shared memory, once per process
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(snippet_kernel<kSnipHalf>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * kSnipHalf);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(snippet_kernel<kSnipHalf>,
+                                     cudaFuncAttributePreferredSharedMemoryCarveout,
+                                     (int)cudaSharedmemCarveoutMaxShared);
+        if (e != cudaSuccess) return status_of(e, "snippet attributes");
+        configured = true;
+    }
+    snippet_kernel<kSnipHalf><<<n, 256, 2 * kSnipHalf, s>>>(
+        d_D, stride, p->desc.ndm, Ls, B, p->d_bparam, p->nb_max, p->d_sref, d_cands, dmax, d_out,
+        p->d_err);
     return status_of(cudaGetLastError(), "snippet launch");
 }
 

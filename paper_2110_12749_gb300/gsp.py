@@ -111,6 +111,7 @@ def lib():
             "gsp_dedisperse_variants": ([_vp, _vp], ctypes.c_int32),
             "gsp_plan_tune": ([_vp, _vp, _i64, _i64, _vp, _vp, _vp], ctypes.c_int),
             "gsp_plan_set_wait_limit": ([_vp, _i64, ctypes.c_int32], ctypes.c_int),
+            "gsp_plan_set_snippet_path": ([_vp, ctypes.c_int32], ctypes.c_int),
             "gsp_plan_series": ([_vp, _vp, _vp, _vp], ctypes.c_int),
             "gsp_batch_tune_results": ([_vp, _vp, _vp, ctypes.c_int32], ctypes.c_int32),
             "gsp_stream_create": ([_vp, _vp, _i64, ctypes.c_int32], ctypes.c_int),
@@ -390,6 +391,15 @@ def gsp_plan_timing(plan):
     _check(lib().gsp_plan_timing(plan.handle, ctypes.byref(a), ctypes.byref(b)),
            "gsp_plan_timing")
     return a.value, b.value
+
+
+SNIPPET_AUTO, SNIPPET_DIRECT, SNIPPET_PREFIX = 0, 1, 2
+
+
+def gsp_plan_set_snippet_path(plan, path):
+    """Snippet path of gsp_ranker_snippets: SNIPPET_AUTO, SNIPPET_DIRECT or
+    SNIPPET_PREFIX."""
+    _check(lib().gsp_plan_set_snippet_path(plan.handle, int(path)), "gsp_plan_set_snippet_path")
 
 
 def gsp_plan_set_wait_limit(plan, cycles, starve=0):

@@ -193,7 +193,7 @@ class ScoredBeams:
                 "detected": np.array(det), "best": np.array(best), "best8": np.array(best8),
                 "neg": np.concatenate(neg), "pos": np.concatenate(pos),
                 "neg_snr": np.concatenate(neg_snr), "pos_snr": np.concatenate(pos_snr),
-                "n_scored": n_scored, "rank_s": rank_s}
+                "n_scored": n_scored, "rank_s": rank_s, "snip_s": self.snip_s}
 
 
 def build_training_set(src, beams, seed, with_width=False):
@@ -400,6 +400,9 @@ def summarise(ps, snr_min=8.0, thresholds=(0.5,)):
                             ">=20": rec(det >= 20)},
         "negatives": int(ps["neg"].size), "candidates_scored": ps["n_scored"],
         "rank_s": ps["rank_s"], "candidates_per_s": ps["n_scored"] / max(ps["rank_s"], 1e-9),
+        "snippets_per_s": (ps["n_scored"] / ps["snip_s"]) if ps.get("snip_s") else None,
+        "forward_per_s": (ps["n_scored"] / (ps["rank_s"] - ps["snip_s"]))
+                         if ps.get("snip_s") and ps["rank_s"] > ps["snip_s"] else None,
         "missed": [[round(float(nom[i]), 2), int(wid[i]), round(float(det[i]), 2),
                     round(float(best[i]), 4)] for i in np.nonzero(d8 & ~ok)[0][:10]],
         "at": {"%.4g" % t: at[t] for t in thresholds[1:]}})

@@ -98,6 +98,7 @@ def test_null_arguments_return_status(gsp):
     assert L.gsp_candidates(None, None, 0, None) == gsp.GSP_ERR_INVALID_ARG
     assert L.gsp_plan_tune(None, None, 0, 0, None, None, None) == gsp.GSP_ERR_INVALID_ARG
     assert L.gsp_plan_series(None, None, None, None) == gsp.GSP_ERR_INVALID_ARG
+    assert L.gsp_plan_set_snippet_path(None, 0) == gsp.GSP_ERR_INVALID_ARG
     assert L.gsp_batch_tune_results(None, None, None, 0) == -1
 
 

@@ -25,6 +25,7 @@ def gsp():
     (300, 130, 512, 1, True, True),       # several tiles in M and N
     (64, 9, 4096, 8, False, False),       # split-K (weight-gradient shape)
     (1024, 64, 2048, 1, True, True),      # fully connected layer shape
+    (4096, 96, 2048, 1, True, True),      # fc1 of an inference batch (narrow column blocks)
     (89600, 8, 16, 1, True, True),        # first conv layer shape: CTAs loop over M tiles
     (40000, 72, 32, 1, False, False),     # conv input-gradient shape
 ])

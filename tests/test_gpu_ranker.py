@@ -78,6 +78,98 @@ def test_snippets_match_oracle(gsp, orc):
         assert (np.abs(got[k] - ref) <= tol).all(), (k, float(np.abs(got[k] - ref).max()))
 
 
+@pytest.mark.parametrize("path,pad", [(1, 0), (1, 1), (2, 0), (2, 1)])
+def test_snippets_crafted_candidates(gsp, orc, path, pad):
+    """Snippets of placed candidates against the oracle: every default boxcar
+    width (f = 1 .. 37) and two wider ones (f = 150 and 300: a row no longer
+    fits half of the kernel's shared-memory ring), at the start and end of the
+    searched span (rows whose aligned span leaves the series) and at the first
+    and last DM rows (blank rows).  pad = 1 stores D with a row stride that is
+    not a multiple of four samples, so that every row is read directly instead
+    of by bulk copies; the sums must not change.  path 1 sums the samples of D
+    (the direct path), path 2 differences of block-local prefix sums; both
+    paths must give the same floats."""
+    from paper_2110_12749_gb300 import synth
+    wl = synth.WORKLOADS["tiny"]
+    dl, _ = orc.delays(wl.nchan, wl.f_lo, wl.f_hi, wl.t_samp, wl.dms)
+    n_out = wl.n_in - orc.max_delay(dl)
+    x, _, _, _ = synth.workload_filterbank(
+        wl, lambda dm: orc.delays(wl.nchan, wl.f_lo, wl.f_hi, wl.t_samp, [dm])[0][0], n_out)
+    desc, keep = gsp.make_desc(wl.nchan, wl.f_lo, wl.f_hi, wl.t_samp, wl.n_in, ndm=wl.ndm,
+                               dm_lo=wl.dm_lo, dm_step=wl.dm_step, threshold=4.0)
+    plan = gsp.gsp_plan_create(desc, keep)
+    D4 = torch.zeros((wl.ndm, (n_out + 3) // 4 * 4), dtype=torch.int32, device="cuda")
+    gsp.gsp_search(plan, torch.from_numpy(x).cuda(), wl.n_in, out=D4)
+    D = torch.zeros((wl.ndm, D4.shape[1] + pad), dtype=torch.int32, device="cuda")
+    D[:, :D4.shape[1]] = D4
+    Dref = orc.dedisperse(x, wl.n_in, dl)
+    xn = np.stack([orc.search_row(Dref[r], threshold=4.0, detail=True)["xnorm"]
+                   for r in range(wl.ndm)])
+    Ls = xn.shape[1]
+    widths = [1, 2, 3, 4, 6, 9, 14, 20, 30, 45, 70, 100, 150, 600, 1200]
+    times = [0, 3, 777, Ls // 2 + 1, Ls - 2300, Ls - 40, Ls - 1]
+    rows = [0, 17, wl.ndm // 2, wl.ndm - 1]
+    recs = [(d, w, t) for d in rows for w in widths for t in times]
+    cands = np.zeros(len(recs), dtype=gsp.CAND_DTYPE)
+    for k, (d, w, t) in enumerate(recs):
+        cands[k]["dm_idx"], cands[k]["width"], cands[k]["t"] = d, w, t
+        cands[k]["snr"] = 5.0
+    dc = torch.from_numpy(cands.view(np.uint8).copy()).cuda()
+    outs = {}
+    for pth in (path, 3 - path):
+        gsp.gsp_plan_set_snippet_path(plan, pth)
+        out = torch.full((len(cands), 64, 64), 7.0, dtype=torch.float32, device="cuda")
+        gsp.gsp_ranker_snippets(plan, D, dc, out)
+        torch.cuda.synchronize()
+        outs[pth] = out.cpu().numpy()
+    assert np.array_equal(outs[1], outs[2])
+    got = outs[path]
+    for k, c in enumerate(cands):
+        ref = R.snippet(xn, c["dm_idx"], c["t"], c["width"])
+        tol = 1e-4 * (1.0 + np.abs(ref)) * np.sqrt(R.time_bin(c["width"]))
+        assert (np.abs(got[k] - ref) <= tol).all(), (recs[k], float(np.abs(got[k] - ref).max()))
+    gsp.gsp_plan_destroy(plan)
+
+
+def test_snippet_prefix_follows_new_searches(gsp, orc):
+    """The prefix sums are rebuilt after every search: snippets of the same
+    candidates from two different beams searched by one plan match the oracle
+    of each beam (path 2 forced)."""
+    from paper_2110_12749_gb300 import synth
+    wl = synth.WORKLOADS["tiny"]
+    dl, _ = orc.delays(wl.nchan, wl.f_lo, wl.f_hi, wl.t_samp, wl.dms)
+    n_out = wl.n_in - orc.max_delay(dl)
+    desc, keep = gsp.make_desc(wl.nchan, wl.f_lo, wl.f_hi, wl.t_samp, wl.n_in, ndm=wl.ndm,
+                               dm_lo=wl.dm_lo, dm_step=wl.dm_step, threshold=4.0)
+    plan = gsp.gsp_plan_create(desc, keep)
+    gsp.gsp_plan_set_snippet_path(plan, 2)
+    D = torch.zeros((wl.ndm, (n_out + 3) // 4 * 4), dtype=torch.int32, device="cuda")
+    recs = [(wl.ndm // 2, 100, 5000), (40, 30, 12000), (150, 9, 20001)]
+    cands = np.zeros(len(recs), dtype=gsp.CAND_DTYPE)
+    for k, (d, w, t) in enumerate(recs):
+        cands[k]["dm_idx"], cands[k]["width"], cands[k]["t"] = d, w, t
+    dc = torch.from_numpy(cands.view(np.uint8).copy()).cuda()
+    for beam in (0, 1):
+        x, _, _, _ = synth.workload_filterbank(
+            wl, lambda dm: orc.delays(wl.nchan, wl.f_lo, wl.f_hi, wl.t_samp, [dm])[0][0], n_out,
+            beam=beam)
+        gsp.gsp_search(plan, torch.from_numpy(x).cuda(), wl.n_in, out=D)
+        out = torch.zeros((len(cands), 64, 64), dtype=torch.float32, device="cuda")
+        gsp.gsp_ranker_snippets(plan, D, dc, out)
+        got = out.cpu().numpy()
+        Dref = orc.dedisperse(x, wl.n_in, dl)
+        rows = sorted({r for d, _, _ in recs for r in range(max(d - 32, 0), min(d + 32, wl.ndm))})
+        xr = {r: orc.search_row(Dref[r], threshold=4.0, detail=True)["xnorm"] for r in rows}
+        xn = np.zeros((wl.ndm, len(xr[rows[0]])))
+        for r in rows:
+            xn[r] = xr[r]
+        for k, c in enumerate(cands):
+            ref = R.snippet(xn, c["dm_idx"], c["t"], c["width"])
+            tol = 1e-4 * (1.0 + np.abs(ref)) * np.sqrt(R.time_bin(c["width"]))
+            assert (np.abs(got[k] - ref) <= tol).all(), (beam, recs[k])
+    gsp.gsp_plan_destroy(plan)
+
+
 @pytest.mark.parametrize("n", [37, 130])
 def test_forward_matches_oracle(gsp, n):
     p = R.init_params(11)
