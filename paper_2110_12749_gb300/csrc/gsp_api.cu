@@ -94,6 +94,9 @@ void free_plan(gsp_plan_s *p) {
         for (auto *b : row) cudaFree(b);
     cudaFree(p->d_err);
     cudaFree(p->d_prefix);
+    cudaFree(p->d_order);
+    cudaFree(p->d_order_hist);
+    cudaFree(p->d_sinv);
     cudaFree(p->d_bsum);
     cudaFree(p->d_sigma_b);
     cudaFree(p->d_bad);

@@ -135,6 +135,10 @@ struct gsp_plan_s {
     const int32_t *prefix_src = nullptr;
     int64_t prefix_src_stride = 0;
     int snippet_path = 0;             // 0 automatic, 1 direct reads, 2 prefix sums
+    int32_t *d_order = nullptr;       // snippet CTAs' candidate order (by time bucket)
+    size_t d_order_elems = 0;
+    uint32_t *d_order_hist = nullptr;  // [1024] time-bucket counts / offsets
+    float *d_sinv = nullptr;          // [ndm] 1 / sigma_ref in FP32 for the snippet kernels
     int32_t launches = 0;
 };
 

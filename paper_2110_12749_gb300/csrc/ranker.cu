@@ -35,6 +35,7 @@ using bf16 = __nv_bfloat16;
 constexpr int kS = 64;          // snippet side
 constexpr int kFc = 2048;       // 32 x 8 x 8 features
 constexpr int kHid = 96;        // hidden units of fc1 (202,786 parameters in all)
+constexpr int kFc1Split = 8;    // most K chunks of fc1 (K = 2048: 32 steps of 64)
 constexpr int kLayers = 3;
 // per conv layer: input channels, output channels, input side
 __host__ __device__ constexpr int cin_of(int l) { return l == 0 ? 1 : (l == 1 ? 8 : 16); }
@@ -437,6 +438,22 @@ __global__ void unpack_conv_grad_kernel(const float *__restrict__ dW, int Cin, i
 
 namespace {
 
+// fc1's epilogue after a split-K product: z4 = ReLU(sum over the S partial
+// products, in chunk order, + bias) and a4 = bf16(z4).  One thread per output.
+__global__ void fc1_finish_kernel(const float *__restrict__ part, int S, int64_t zstride, int B,
+                                  const float *__restrict__ bias, float *__restrict__ z4,
+                                  bf16 *__restrict__ a4) {
+    const int64_t total = (int64_t)B * kHid;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        float acc = part[i];
+        for (int z = 1; z < S; z++) acc += part[(int64_t)z * zstride + i];
+        const float v = fmaxf(acc + bias[i % kHid], 0.0f);
+        z4[i] = v;
+        a4[i] = __float2bfloat16_rn(v);
+    }
+}
+
 // ------------------------------------------- fused conv layers for inference
 
 namespace tc = gsp::tc;
@@ -692,6 +709,7 @@ struct gsp_ranker_s {
     bf16 *gz[kLayers] = {}, *gzT[kLayers] = {};
     float *ga[kLayers] = {};    // gradient w.r.t. the pooled output of layer l
     float *dcol = nullptr, *dW = nullptr;
+    float *fc1_part = nullptr;  // [kFc1Split][max_batch][kHid] partial products of fc1
     int *err = nullptr;
     std::vector<void *> allocs;
     int32_t launches = 0;
@@ -828,9 +846,22 @@ cudaError_t forward(gsp_ranker_s *r, const float *x, int n, bool train, cudaStre
         else
             RK_LAUNCH((pool_kernel<32><<<blocks_for(P / 4), 256, 0, s>>>(r->z[2], n, H, r->a[2], r->idx[2])));
     }
-    cudaError_t e = gemm(r, r->a[2], kFc, r->W4, kFc, r->z4, kHid, r->a4, kHid, n, kHid, kFc,
-                         r->params + r->off.b[3], true, 1, s);
+    // fc1 (K = 2048) as a deterministic split-K product: enough K chunks for a
+    // CTA per SM even at one column block, at least four 64-wide steps each;
+    // the chunks' partial products are summed in order by fc1_finish_kernel
+    int dev = 0, nsm = 152;
+    if (cudaGetDevice(&dev) == cudaSuccess)
+        (void)cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const int mt = (n + 127) / 128;
+    const int want = std::max(1, std::min(kFc1Split, std::min(kFc / (4 * 64), nsm / mt)));
+    const int64_t zs = (int64_t)r->max_batch * kHid;
+    int used = 1;
+    cudaError_t e = gsp::launch_gemm_bf16(r->a[2], kFc, r->W4, kFc, r->fc1_part, kHid, nullptr, 0, n,
+                                          kHid, kFc, nullptr, false, want, r->err, s, zs, &used);
     if (e != cudaSuccess) return e;
+    r->launches++;
+    RK_LAUNCH((fc1_finish_kernel<<<blocks_for((int64_t)n * kHid), 256, 0, s>>>(
+        r->fc1_part, used, zs, n, r->params + r->off.b[3], r->z4, r->a4)));
     RK_LAUNCH((fc2_kernel<<<(2 * n + 127) / 128, 128, 0, s>>>(r->a4, r->params + r->off.w[4],
                                                               r->params + r->off.b[4], n, r->z5)));
     return cudaSuccess;
@@ -924,40 +955,50 @@ gsp_status status_of(cudaError_t e, const char *what) {
 constexpr int kSnipHalf = 24 * 1024;
 constexpr long long kSnipBudget = 2000000000ll;
 
-// One run's term of a bin, ((sd - n m) - (n c0 + beta sj)) / sigma_ref for the
-// run's exact sum sd and sj = the sum of its in-block sample indices, rounded
-// step by step (no contraction into FMAs), so that both snippet paths give the
-// same float.
-__device__ __forceinline__ float run_term(int64_t sd, int n, int64_t sj, const gsp::BlockParam &q,
+// One run's term of a bin, ((sd - n m) - (n c0 + beta sj)) / sigma_ref, from
+// dev = sd - n m (exact; sd the run's sum) and sj = the sum of its in-block
+// sample indices, rounded step by step (no contraction into FMAs), so that
+// both snippet paths give the same float.
+__device__ __forceinline__ float run_term(float dev, int n, int64_t sj, const gsp::BlockParam &q,
                                           float inv) {
-    const float a = (float)(sd - (int64_t)n * q.m);
     const float t = __fadd_rn(__fmul_rn((float)n, q.c0), __fmul_rn(q.beta, (float)sj));
-    return __fmul_rn(__fsub_rn(a, t), inv);
+    return __fmul_rn(__fsub_rn(dev, t), inv);
 }
 
-// Bin [a, a + f) of one row; src[t - base] is sample t, b0 * B <= max(a, 0).
-// At most two runs (f <= B), each summed exactly in Acc (int32 when f times
-// the largest |D| stays below 2^31, else int64).
+// Positions inside a candidate's rows are int32 offsets from T0 = b0 * B, the
+// start of the first search block its bins touch (b0 = max(tlo, 0) / B); a
+// block index bi is then relative to b0.  bsh = log2(B) when B is a power of
+// two, else -1.
+__device__ __forceinline__ int rel_block(int r, int B, int bsh) {
+    return bsh >= 0 ? (r >> bsh) : r / B;
+}
+
+// Bin [r0, r1) of one row (relative positions, clipped to the searched
+// span); src[off + r] is the sample at relative position r and brow[bi] the
+// parameters of relative block bi.  At most two runs (f <= B), each summed
+// exactly in Acc: int32 (wrapping, exact) when f times the largest D stays
+// below 2^31, else int64.
 template <typename Acc>
-__device__ __forceinline__ float snippet_bin(const int32_t *src, int64_t base, int64_t a, int f,
-                                             int64_t Ls, int B, int64_t b0,
-                                             const gsp::BlockParam *brow, float inv) {
-    int64_t s0 = max(a, (int64_t)0);
-    const int64_t s1 = min(a + f, Ls);
+__device__ __forceinline__ float snippet_bin(const int32_t *src, int off, int r0, int r1, int B,
+                                             int bsh, const gsp::BlockParam *brow, float inv) {
     float v = 0.0f;
-    while (s0 < s1) {
-        const int64_t b = b0 + (int64_t)((uint32_t)(s0 - b0 * B) / (uint32_t)B);
-        const int jb0 = (int)(s0 - b * B);
-        const int64_t e = min(s1, (b + 1) * (int64_t)B);
-        const int n = (int)(e - s0);
-        const gsp::BlockParam q = brow[b];
+    int s0 = r0;
+    while (s0 < r1) {
+        const int bi = rel_block(s0, B, bsh), bs = bi * B;
+        const int e = min(r1, bs + B);
+        const int n = e - s0;
+        const gsp::BlockParam q = brow[bi];
         if (q.good) {
-            const int32_t *p = src + (s0 - base);
+            const int32_t *p = src + off + s0;
             Acc sd = 0;  // exact
 #pragma unroll 4
             for (int k = 0; k < n; k++) sd += p[k];
-            const int64_t sj = (int64_t)n * jb0 + (int64_t)n * (n - 1) / 2;
-            v = __fadd_rn(v, run_term((int64_t)sd, n, sj, q, inv));
+            const int64_t sj = (int64_t)n * (s0 - bs) + (int64_t)n * (n - 1) / 2;
+            const float dev =
+                sizeof(Acc) == 4
+                    ? (float)(int32_t)((uint32_t)sd - (uint32_t)n * (uint32_t)q.m)
+                    : (float)((int64_t)sd - (int64_t)n * q.m);
+            v = __fadd_rn(v, run_term(dev, n, sj, q, inv));
         }
         s0 = e;
     }
@@ -967,17 +1008,19 @@ __device__ __forceinline__ float snippet_bin(const int32_t *src, int64_t base, i
 template <int HALF>
 __global__ void __launch_bounds__(256) snippet_kernel(
     const int32_t *__restrict__ D, int64_t stride, int ndm, int64_t Ls, int B,
-    const gsp::BlockParam *__restrict__ bp, int64_t nb_max, const double *__restrict__ sref,
-    const gsp_cand *__restrict__ cands, int64_t dmax, float *__restrict__ out, int *err) {
+    const gsp::BlockParam *__restrict__ bp, int64_t nb_max, const float *__restrict__ sinv,
+    const gsp_cand *__restrict__ cands, const int32_t *__restrict__ order, int64_t dmax,
+    float *__restrict__ out, int *err) {
     extern __shared__ __align__(128) int32_t ring[];  // 2 * HALF bytes
     __shared__ __align__(8) uint64_t bar[2];
     __shared__ float s_inv[kS];
-    const gsp_cand c = cands[blockIdx.x];
+    const int64_t ck = order ? order[blockIdx.x] : blockIdx.x;  // this CTA's candidate
+    const gsp_cand c = cands[ck];
     const int f = max(1, c.width / 4);
     const int64_t tlo = c.t + c.width / 2 - (int64_t)(kS / 2) * f;  // first sample of bin 0
     const float rs = 1.0f / sqrtf((float)f);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nwarps = (int)(blockDim.x >> 5);
-    float *o = out + (int64_t)blockIdx.x * kS * kS;
+    float *o = out + ck * kS * kS;
     // the 16-byte aligned span of every row: samples [t_al, t_end)
     const int64_t t_al = tlo >= 0 ? (tlo & ~(int64_t)3) : -((-tlo + 3) & ~(int64_t)3);
     const int64_t t_end = (tlo + (int64_t)kS * f + 3) & ~(int64_t)3;
@@ -988,10 +1031,14 @@ __global__ void __launch_bounds__(256) snippet_kernel(
     const int S = bulk ? min(kS, (int)(HALF / rowb)) : kS;  // rows per batch
     const int nbatch = (kS + S - 1) / S;
     const int64_t b0 = max(tlo, (int64_t)0) / B;           // first search block of the span
+    const int64_t T0 = b0 * B;
+    const int alo = (int)(tlo - T0);                       // bin 0 relative to T0
+    const int lrel = (int)min(Ls - T0, (int64_t)1 << 30);  // end of the searched span
+    const int bsh = (B & (B - 1)) == 0 ? __ffs(B) - 1 : -1;
     const bool narrow = (int64_t)f * dmax < 2147483648ll;  // int32 run sums are exact
     for (int i = tid; i < kS; i += blockDim.x) {
         const int r = c.dm_idx - kS / 2 + i;
-        s_inv[i] = (r >= 0 && r < ndm && sref[r] > 0.0) ? (float)(1.0 / sref[r]) : 0.0f;
+        s_inv[i] = (r >= 0 && r < ndm) ? sinv[r] : 0.0f;
     }
     const uint32_t ring0 = ptx::smem_addr(ring);
     const uint32_t bar0 = ptx::smem_addr(&bar[0]);
@@ -1042,12 +1089,13 @@ __global__ void __launch_bounds__(256) snippet_kernel(
             float v = 0.0f;
             if (inv != 0.0f) {  // warp-uniform
                 const int r = c.dm_idx - kS / 2 + i;
-                const gsp::BlockParam *brow = bp + (int64_t)r * nb_max;
-                const int32_t *src = bulk ? half + (size_t)k * (rowb / 4) : D + (int64_t)r * stride;
-                const int64_t base = bulk ? t_al : 0;
-                const int64_t a = tlo + (int64_t)j * f;
-                v = narrow ? snippet_bin<int32_t>(src, base, a, f, Ls, B, b0, brow, inv)
-                           : snippet_bin<int64_t>(src, base, a, f, Ls, B, b0, brow, inv);
+                const gsp::BlockParam *brow = bp + (int64_t)r * nb_max + b0;
+                // the ring row holds samples t_al.. (T0 - t_al <= 3); D's row from T0
+                const int32_t *src = bulk ? half + (size_t)k * (rowb / 4) : D + (int64_t)r * stride + T0;
+                const int off = bulk ? (int)(T0 - t_al) : 0;
+                const int r0 = max(alo + j * f, 0), r1 = min(alo + (j + 1) * f, lrel);
+                v = narrow ? snippet_bin<int32_t>(src, off, r0, r1, B, bsh, brow, inv)
+                           : snippet_bin<int64_t>(src, off, r0, r1, B, bsh, brow, inv);
             }
             o[i * kS + j] = v * rs;
         }
@@ -1061,6 +1109,56 @@ __global__ void __launch_bounds__(256) snippet_kernel(
         // the copies of the (at most two) batches issued but not waited for
         for (int b = waited; b < min(nbatch, waited + 2); b++)
             (void)ptx::mbar_wait(bar0 + 8u * (uint32_t)(b & 1), (uint32_t)((b >> 1) & 1), kSnipBudget);
+    }
+}
+
+// 1 / sigma_ref of every row in FP32 (0 where sigma_ref = 0), once per
+// snippet call: FP64 division is slow on this GPU, so the snippet CTAs read
+// these instead of dividing per row.
+__global__ void inv_sigma_kernel(const double *__restrict__ sref, int ndm, float *__restrict__ sinv) {
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < ndm; r += gridDim.x * blockDim.x)
+        sinv[r] = sref[r] > 0.0 ? (float)(1.0 / sref[r]) : 0.0f;
+}
+
+// The order in which the snippet CTAs take the candidates: by time bucket
+// (t >> shift), a counting sort.  Candidates close in time share the samples
+// of their rows' windows, so CTAs that run together then find them in L2
+// whatever the caller's order (gsp_candidates sorts by DM first).  Each CTA
+// still writes its own candidate's snippet, so the output does not depend on
+// the order within a bucket (which the atomics leave open).
+__global__ void time_bucket_count_kernel(const gsp_cand *__restrict__ cands, int n, int shift,
+                                         int nbk, uint32_t *__restrict__ hist) {
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        const int64_t bk = min(max(cands[k].t >> shift, (int64_t)0), (int64_t)nbk - 1);
+        atomicAdd(hist + bk, 1u);
+    }
+}
+
+// hist[0 .. nbk) -> exclusive prefix (one CTA of 1024 threads; nbk <= 1024)
+__global__ void __launch_bounds__(1024) time_bucket_scan_kernel(uint32_t *__restrict__ hist,
+                                                                int nbk) {
+    __shared__ uint32_t wsum[32];
+    const int i = threadIdx.x, lane = i & 31, warp = i >> 5;
+    const uint32_t v = i < nbk ? hist[i] : 0u;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[warp] = x;
+    __syncthreads();
+    uint32_t off = 0;
+    for (int w = 0; w < warp; w++) off += wsum[w];
+    if (i < nbk) hist[i] = off + x - v;
+}
+
+__global__ void time_bucket_scatter_kernel(const gsp_cand *__restrict__ cands, int n, int shift,
+                                           int nbk, uint32_t *__restrict__ next,
+                                           int32_t *__restrict__ order) {
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        const int64_t bk = min(max(cands[k].t >> shift, (int64_t)0), (int64_t)nbk - 1);
+        order[atomicAdd(next + bk, 1u)] = k;
     }
 }
 
@@ -1116,40 +1214,39 @@ __global__ void __launch_bounds__(256) block_prefix_kernel(const int32_t *__rest
     }
 }
 
-// Bin [a, a + f) of one row from the block-local prefix sums prow (b0 * B <=
-// max(a, 0)): at most two runs (f <= B), the second one starting a block; the
-// three prefix entries are loaded before any is used.  The same run_term
-// arithmetic as snippet_bin on the same exact run sums, so the same float.
-__device__ __forceinline__ float snippet_bin_prefix(const int32_t *__restrict__ prow, int64_t a,
-                                                    int f, int64_t Ls, int B, int64_t b0,
-                                                    const gsp::BlockParam *brow, float inv) {
-    const int64_t s0 = max(a, (int64_t)0);
-    const int64_t s1 = min(a + f, Ls);
-    if (s0 >= s1) return 0.0f;
-    const int64_t b = b0 + (int64_t)((uint32_t)(s0 - b0 * B) / (uint32_t)B);
-    const int64_t bs = b * (int64_t)B, be = bs + B;
-    const bool split = s1 > be;
-    const int64_t e1 = split ? be : s1;
-    const uint32_t p_lo = s0 > bs ? (uint32_t)__ldg(prow + s0 - 1) : 0u;
-    const uint32_t p_hi = (uint32_t)__ldg(prow + e1 - 1);
-    const uint32_t p_2 = split ? (uint32_t)__ldg(prow + s1 - 1) : 0u;
+// Bin [r0, r1) of one row (relative positions as in snippet_bin) from the
+// block-local prefix sums, pc[r] the entry at relative position r: at most two
+// runs (f <= B), the second one starting a block; the three prefix entries are
+// loaded before any is used.  Run sums are differences mod 2^32, exact since
+// they lie within int32; the same run_term arithmetic as snippet_bin, so the
+// same float.
+__device__ __forceinline__ float snippet_bin_prefix(const int32_t *__restrict__ pc, int r0, int r1,
+                                                    int B, int bsh, const gsp::BlockParam *brow,
+                                                    float inv) {
+    if (r0 >= r1) return 0.0f;
+    const int bi = rel_block(r0, B, bsh), bs = bi * B, be = bs + B;
+    const bool split = r1 > be;
+    const int e1 = split ? be : r1;
+    const uint32_t p_lo = r0 > bs ? (uint32_t)__ldg(pc + r0 - 1) : 0u;
+    const uint32_t p_hi = (uint32_t)__ldg(pc + e1 - 1);
+    const uint32_t p_2 = split ? (uint32_t)__ldg(pc + r1 - 1) : 0u;
     float v = 0.0f;
     {
-        const int n = (int)(e1 - s0), jb0 = (int)(s0 - bs);
-        const gsp::BlockParam q = brow[b];
+        const int n = e1 - r0;
+        const gsp::BlockParam q = brow[bi];
         if (q.good) {
-            const int64_t sd = (int32_t)(p_hi - p_lo);
-            const int64_t sj = (int64_t)n * jb0 + (int64_t)n * (n - 1) / 2;
-            v = __fadd_rn(v, run_term(sd, n, sj, q, inv));
+            const float dev = (float)(int32_t)(p_hi - p_lo - (uint32_t)n * (uint32_t)q.m);
+            const int64_t sj = (int64_t)n * (r0 - bs) + (int64_t)n * (n - 1) / 2;
+            v = __fadd_rn(v, run_term(dev, n, sj, q, inv));
         }
     }
-    if (split) {  // [be, s1) at the start of block b + 1
-        const int n = (int)(s1 - be);
-        const gsp::BlockParam q = brow[b + 1];
+    if (split) {  // [be, r1) at the start of block bi + 1
+        const int n = r1 - be;
+        const gsp::BlockParam q = brow[bi + 1];
         if (q.good) {
-            const int64_t sd = (int32_t)p_2;
+            const float dev = (float)(int32_t)(p_2 - (uint32_t)n * (uint32_t)q.m);
             const int64_t sj = (int64_t)n * (n - 1) / 2;
-            v = __fadd_rn(v, run_term(sd, n, sj, q, inv));
+            v = __fadd_rn(v, run_term(dev, n, sj, q, inv));
         }
     }
     return v;
@@ -1163,31 +1260,36 @@ __device__ __forceinline__ float snippet_bin_prefix(const int32_t *__restrict__ 
 __global__ void __launch_bounds__(256) snippet_prefix_kernel(
     const int32_t *__restrict__ P, int64_t pstride, const int32_t *__restrict__ D, int64_t stride,
     int ndm, int64_t Ls, int B, const gsp::BlockParam *__restrict__ bp, int64_t nb_max,
-    const double *__restrict__ sref, const gsp_cand *__restrict__ cands, int64_t dmax,
-    float *__restrict__ out) {
-    const gsp_cand c = cands[blockIdx.x];
+    const float *__restrict__ sinv, const gsp_cand *__restrict__ cands,
+    const int32_t *__restrict__ order, int64_t dmax, float *__restrict__ out) {
+    const int64_t ck = order ? order[blockIdx.x] : blockIdx.x;  // this CTA's candidate
+    const gsp_cand c = cands[ck];
     const int f = max(1, c.width / 4);
     const bool via_prefix = f <= B && (int64_t)f * dmax < 2147483648ll;
     const int64_t tlo = c.t + c.width / 2 - (int64_t)(kS / 2) * f;  // first sample of bin 0
-    const int64_t b0 = max(tlo, (int64_t)0) / B;
+    const int64_t b0 = max(tlo, (int64_t)0) / B, T0 = b0 * B;
+    const int alo = (int)(tlo - T0);
+    const int lrel = (int)min(Ls - T0, (int64_t)1 << 30);
+    const int bsh = (B & (B - 1)) == 0 ? __ffs(B) - 1 : -1;
     const float rs = 1.0f / sqrtf((float)f);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = (int)(blockDim.x >> 5);
-    float *o = out + (int64_t)blockIdx.x * kS * kS;
+    float *o = out + ck * kS * kS;
+    const int ra0 = max(alo + lane * f, 0), ra1 = min(alo + (lane + 1) * f, lrel);
+    const int rb0 = max(alo + (32 + lane) * f, 0), rb1 = min(alo + (33 + lane) * f, lrel);
     for (int i = warp; i < kS; i += nwarps) {
         const int r = c.dm_idx - kS / 2 + i;
-        const float inv = (r >= 0 && r < ndm && sref[r] > 0.0) ? (float)(1.0 / sref[r]) : 0.0f;
+        const float inv = (r >= 0 && r < ndm) ? sinv[r] : 0.0f;
         float v0 = 0.0f, v1 = 0.0f;
         if (inv != 0.0f) {  // warp-uniform
-            const gsp::BlockParam *brow = bp + (int64_t)r * nb_max;
-            const int64_t a0 = tlo + (int64_t)lane * f, a1 = tlo + (int64_t)(32 + lane) * f;
+            const gsp::BlockParam *brow = bp + (int64_t)r * nb_max + b0;
             if (via_prefix) {
-                const int32_t *prow = P + (int64_t)r * pstride;
-                v0 = snippet_bin_prefix(prow, a0, f, Ls, B, b0, brow, inv);
-                v1 = snippet_bin_prefix(prow, a1, f, Ls, B, b0, brow, inv);
+                const int32_t *pc = P + (int64_t)r * pstride + T0;
+                v0 = snippet_bin_prefix(pc, ra0, ra1, B, bsh, brow, inv);
+                v1 = snippet_bin_prefix(pc, rb0, rb1, B, bsh, brow, inv);
             } else {
-                const int32_t *drow = D + (int64_t)r * stride;
-                v0 = snippet_bin<int64_t>(drow, 0, a0, f, Ls, B, b0, brow, inv);
-                v1 = snippet_bin<int64_t>(drow, 0, a1, f, Ls, B, b0, brow, inv);
+                const int32_t *dc = D + (int64_t)r * stride + T0;
+                v0 = snippet_bin<int64_t>(dc, 0, ra0, ra1, B, bsh, brow, inv);
+                v1 = snippet_bin<int64_t>(dc, 0, rb0, rb1, B, bsh, brow, inv);
             }
         }
         o[i * kS + lane] = v0 * rs;
@@ -1213,6 +1315,47 @@ gsp_status gsp_ranker_snippets(gsp_plan_t p, const int32_t *d_D, int64_t stride,
     // chunk) exceed building them (one read and one write of the series)
     const bool big = (int64_t)n * kS * kS * 4 >= 2 * (int64_t)p->desc.ndm * Ls;
     const bool use_prefix = Ls > 0 && (p->snippet_path == 2 || (p->snippet_path == 0 && big));
+    // CTAs take the candidates in time order (buckets of 2^shift samples, at
+    // most 1024 buckets over the series)
+    int shift = 12;
+    while (shift < 40 && (std::max<int64_t>(Ls, 1) >> shift) >= 1024) shift++;
+    const int nbk = (int)std::min<int64_t>(1024, (std::max<int64_t>(Ls, 1) >> shift) + 1);
+    if ((size_t)n > p->d_order_elems) {
+        cudaFree(p->d_order);
+        p->d_order = nullptr;
+        p->d_order_elems = 0;
+        if (cudaMalloc((void **)&p->d_order, (size_t)n * sizeof(int32_t)) != cudaSuccess) {
+            (void)cudaGetLastError();
+            return GSP_ERR_OOM;
+        }
+        p->d_order_elems = (size_t)n;
+    }
+    if (!p->d_order_hist &&
+        cudaMalloc((void **)&p->d_order_hist, 1024 * sizeof(uint32_t)) != cudaSuccess) {
+        (void)cudaGetLastError();
+        p->d_order_hist = nullptr;
+        return GSP_ERR_OOM;
+    }
+    if (!p->d_sinv &&
+        cudaMalloc((void **)&p->d_sinv, (size_t)p->desc.ndm * sizeof(float)) != cudaSuccess) {
+        (void)cudaGetLastError();
+        p->d_sinv = nullptr;
+        return GSP_ERR_OOM;
+    }
+    {
+        const int g = (int)std::min<int64_t>(((int64_t)n + 255) / 256, (int64_t)p->num_sms * 4);
+        cudaError_t e = cudaMemsetAsync(p->d_order_hist, 0, (size_t)nbk * sizeof(uint32_t), s);
+        if (e == cudaSuccess) {
+            time_bucket_count_kernel<<<g, 256, 0, s>>>(d_cands, n, shift, nbk, p->d_order_hist);
+            time_bucket_scan_kernel<<<1, 1024, 0, s>>>(p->d_order_hist, nbk);
+            time_bucket_scatter_kernel<<<g, 256, 0, s>>>(d_cands, n, shift, nbk, p->d_order_hist,
+                                                         p->d_order);
+            inv_sigma_kernel<<<(p->desc.ndm + 255) / 256, 256, 0, s>>>(p->d_sref, p->desc.ndm,
+                                                                     p->d_sinv);
+            e = cudaGetLastError();
+        }
+        if (e != cudaSuccess) return status_of(e, "snippet order launch");
+    }
     if (use_prefix) {
         const int64_t pstride = (Ls + 3) & ~(int64_t)3;
         const size_t need = (size_t)p->desc.ndm * (size_t)pstride;
@@ -1241,8 +1384,8 @@ gsp_status gsp_ranker_snippets(gsp_plan_t p, const int32_t *d_D, int64_t stride,
             p->prefix_stride = pstride;
         }
         snippet_prefix_kernel<<<n, 256, 0, s>>>(p->d_prefix, pstride, d_D, stride, p->desc.ndm, Ls,
-                                                B, p->d_bparam, p->nb_max, p->d_sref, d_cands,
-                                                dmax, d_out);
+                                                B, p->d_bparam, p->nb_max, p->d_sinv, d_cands,
+                                                p->d_order, dmax, d_out);
         return status_of(cudaGetLastError(), "snippet launch");
     }
     static bool configured = false;  // the ring's shared memory, once per process
@@ -1257,8 +1400,8 @@ gsp_status gsp_ranker_snippets(gsp_plan_t p, const int32_t *d_D, int64_t stride,
         configured = true;
     }
     snippet_kernel<kSnipHalf><<<n, 256, 2 * kSnipHalf, s>>>(
-        d_D, stride, p->desc.ndm, Ls, B, p->d_bparam, p->nb_max, p->d_sref, d_cands, dmax, d_out,
-        p->d_err);
+        d_D, stride, p->desc.ndm, Ls, B, p->d_bparam, p->nb_max, p->d_sinv, d_cands, p->d_order,
+        dmax, d_out, p->d_err);
     return status_of(cudaGetLastError(), "snippet launch");
 }
 
@@ -1292,7 +1435,8 @@ gsp_status gsp_ranker_create(gsp_ranker_t *out, int32_t max_batch, uint64_t seed
         if (l > 0) dcol = std::max(dcol, (size_t)P * Kp);
         dw = std::max(dw, (size_t)Cout * Kp);
     }
-    ok = ok && ralloc(r, &r->dcol, dcol) && ralloc(r, &r->dW, dw);
+    ok = ok && ralloc(r, &r->dcol, dcol) && ralloc(r, &r->dW, dw) &&
+         ralloc(r, &r->fc1_part, (size_t)kFc1Split * Bm * kHid);
     if (!ok) {
         free_ranker(r);
         return GSP_ERR_OOM;

@@ -74,7 +74,7 @@ template <int BN, int S, int NACC>
 __global__ void __launch_bounds__(128) gemm_bf16_kernel(
     const __nv_bfloat16 *__restrict__ A, int64_t lda, const __nv_bfloat16 *__restrict__ B,
     int64_t ldb, float *C, int64_t ldc, __nv_bfloat16 *Cb, int64_t ldcb, int M, int N, int K,
-    int kchunk, const float *__restrict__ bias, int relu, int *err) {
+    int kchunk, int64_t zstride, const float *__restrict__ bias, int relu, int *err) {
     static_assert(BN % 16 == 0 && BN >= 16 && BN <= 128, "tcgen05 M=128 with N in 16..128");
     static_assert(S >= 1 && (NACC == 1 || NACC == 2), "ring depth and accumulators");
     static_assert(S >= 2 || NACC == 1, "a single stage serves one tile per CTA");
@@ -134,7 +134,13 @@ __global__ void __launch_bounds__(128) gemm_bf16_kernel(
             float v[16];
             tc::tmem_ld16(lane_addr + (uint32_t)c0, v);
             if (row < M) {
-                if (gridDim.z > 1) {
+                if (gridDim.z > 1 && zstride > 0) {
+                    // this K chunk's partial product into its own slice of C
+                    float *cz = C + (int64_t)blockIdx.z * zstride + (int64_t)row * ldc + n0 + c0;
+#pragma unroll
+                    for (int jj = 0; jj < 16; jj++)
+                        if (n0 + c0 + jj < N) cz[jj] = v[jj];
+                } else if (gridDim.z > 1) {
 #pragma unroll
                     for (int jj = 0; jj < 16; jj++)
                         if (n0 + c0 + jj < N) atomicAdd(C + (int64_t)row * ldc + n0 + c0 + jj, v[jj]);
@@ -259,7 +265,7 @@ template <int BN, int S, int NACC>
 cudaError_t launch_bn(dim3 grid, cudaStream_t s, const __nv_bfloat16 *A, int64_t lda,
                       const __nv_bfloat16 *B, int64_t ldb, float *C, int64_t ldc,
                       __nv_bfloat16 *Cb, int64_t ldcb, int M, int N, int K, int kchunk,
-                      const float *bias, int relu, int *err) {
+                      int64_t zstride, const float *bias, int relu, int *err) {
     constexpr int smem = S * (kBM + BN) * kBK * 2;
     static bool configured = false;
     if (!configured) {
@@ -269,7 +275,7 @@ cudaError_t launch_bn(dim3 grid, cudaStream_t s, const __nv_bfloat16 *A, int64_t
         configured = true;
     }
     gemm_bf16_kernel<BN, S, NACC><<<grid, 128, smem, s>>>(A, lda, B, ldb, C, ldc, Cb, ldcb, M, N,
-                                                          K, kchunk, bias, relu, err);
+                                                          K, kchunk, zstride, bias, relu, err);
     return cudaSuccess;
 }
 
@@ -281,14 +287,14 @@ template <int BN>
 cudaError_t launch_n(int ksteps, int mtiles, int ntiles, int splitk, int nsm, cudaStream_t s,
                      const __nv_bfloat16 *A, int64_t lda, const __nv_bfloat16 *B, int64_t ldb,
                      float *C, int64_t ldc, __nv_bfloat16 *Cb, int64_t ldcb, int M, int N, int K,
-                     int kchunk, const float *bias, int relu, int *err) {
+                     int kchunk, int64_t zstride, const float *bias, int relu, int *err) {
     if (ksteps <= 2) {
         dim3 grid((unsigned)mtiles, (unsigned)ntiles, (unsigned)splitk);
         if (ksteps == 1)
             return launch_bn<BN, 1, 1>(grid, s, A, lda, B, ldb, C, ldc, Cb, ldcb, M, N, K, kchunk,
-                                       bias, relu, err);
+                                       zstride, bias, relu, err);
         return launch_bn<BN, 2, 1>(grid, s, A, lda, B, ldb, C, ldc, Cb, ldcb, M, N, K, kchunk,
-                                   bias, relu, err);
+                                   zstride, bias, relu, err);
     }
     constexpr int smem = 4 * (kBM + BN) * kBK * 2;
     const int per_sm = std::max(1, (227 * 1024) / (smem + 1024));
@@ -296,8 +302,8 @@ cudaError_t launch_n(int ksteps, int mtiles, int ntiles, int splitk, int nsm, cu
                          ((int64_t)ntiles * splitk);
     const int mgrid = (int)std::max<int64_t>(1, std::min<int64_t>(mtiles, want));
     dim3 grid((unsigned)mgrid, (unsigned)ntiles, (unsigned)splitk);
-    return launch_bn<BN, 4, 2>(grid, s, A, lda, B, ldb, C, ldc, Cb, ldcb, M, N, K, kchunk, bias,
-                               relu, err);
+    return launch_bn<BN, 4, 2>(grid, s, A, lda, B, ldb, C, ldc, Cb, ldcb, M, N, K, kchunk, zstride,
+                               bias, relu, err);
 }
 
 }  // namespace
@@ -305,9 +311,10 @@ cudaError_t launch_n(int ksteps, int mtiles, int ntiles, int splitk, int nsm, cu
 cudaError_t launch_gemm_bf16(const __nv_bfloat16 *A, int64_t lda, const __nv_bfloat16 *B,
                              int64_t ldb, float *C, int64_t ldc, __nv_bfloat16 *Cb,
                              int64_t ldcb, int M, int N, int K, const float *bias, bool relu,
-                             int splitk, int *err, cudaStream_t s) {
+                             int splitk, int *err, cudaStream_t s, int64_t zstride, int *nsplit) {
     if (M <= 0 || N <= 0 || K <= 0 || (K & 7) || (lda & 7) || (ldb & 7) || lda < K || ldb < K ||
-        (((uintptr_t)A | (uintptr_t)B) & 15) || (!C && !Cb) || (splitk > 1 && !C))
+        (((uintptr_t)A | (uintptr_t)B) & 15) || (!C && !Cb) || (splitk > 1 && !C) ||
+        zstride < 0 || (zstride > 0 && (!C || Cb || bias || relu || zstride < (int64_t)M * ldc)))
         return cudaErrorInvalidValue;
     if (!err) {
         cudaError_t e = cudaGetSymbolAddress((void **)&err, g_gemm_err);
@@ -317,6 +324,7 @@ cudaError_t launch_gemm_bf16(const __nv_bfloat16 *A, int64_t lda, const __nv_bfl
     splitk = std::max(1, std::min(splitk, ksteps));
     const int kchunk = ((ksteps + splitk - 1) / splitk) * kBK;
     splitk = (K + kchunk - 1) / kchunk;
+    if (nsplit) *nsplit = splitk;
     int dev = 0, nsm = 152;
     if (cudaGetDevice(&dev) == cudaSuccess)
         (void)cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
@@ -332,10 +340,10 @@ cudaError_t launch_gemm_bf16(const __nv_bfloat16 *A, int64_t lda, const __nv_bfl
     const int r = relu ? 1 : 0;
     cudaError_t e;
     switch (BN) {
-        case 16: e = launch_n<16>(csteps, mtiles, ntiles, splitk, nsm, s, A, lda, B, ldb, C, ldc, Cb, ldcb, M, N, K, kchunk, bias, r, err); break;
-        case 32: e = launch_n<32>(csteps, mtiles, ntiles, splitk, nsm, s, A, lda, B, ldb, C, ldc, Cb, ldcb, M, N, K, kchunk, bias, r, err); break;
-        case 64: e = launch_n<64>(csteps, mtiles, ntiles, splitk, nsm, s, A, lda, B, ldb, C, ldc, Cb, ldcb, M, N, K, kchunk, bias, r, err); break;
-        default: e = launch_n<128>(csteps, mtiles, ntiles, splitk, nsm, s, A, lda, B, ldb, C, ldc, Cb, ldcb, M, N, K, kchunk, bias, r, err); break;
+        case 16: e = launch_n<16>(csteps, mtiles, ntiles, splitk, nsm, s, A, lda, B, ldb, C, ldc, Cb, ldcb, M, N, K, kchunk, zstride, bias, r, err); break;
+        case 32: e = launch_n<32>(csteps, mtiles, ntiles, splitk, nsm, s, A, lda, B, ldb, C, ldc, Cb, ldcb, M, N, K, kchunk, zstride, bias, r, err); break;
+        case 64: e = launch_n<64>(csteps, mtiles, ntiles, splitk, nsm, s, A, lda, B, ldb, C, ldc, Cb, ldcb, M, N, K, kchunk, zstride, bias, r, err); break;
+        default: e = launch_n<128>(csteps, mtiles, ntiles, splitk, nsm, s, A, lda, B, ldb, C, ldc, Cb, ldcb, M, N, K, kchunk, zstride, bias, r, err); break;
     }
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
@@ -352,7 +360,7 @@ extern "C" gsp_status gsp_gemm_bf16(const void *d_A, int64_t lda, const void *d_
         return GSP_ERR_ALIGN;
     cudaError_t e = gsp::launch_gemm_bf16(
         (const __nv_bfloat16 *)d_A, lda, (const __nv_bfloat16 *)d_B, ldb, d_C, ldc, nullptr, 0, M,
-        N, K, d_bias, relu != 0, splitk, d_err, (cudaStream_t)stream);
+        N, K, d_bias, relu != 0, splitk, d_err, (cudaStream_t)stream, 0, nullptr);
     if (e != cudaSuccess) {
         gsp::record_error(e, "gemm launch");
         return e == cudaErrorInvalidValue ? GSP_ERR_INVALID_ARG : GSP_ERR_CUDA;

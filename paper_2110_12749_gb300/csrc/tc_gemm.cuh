@@ -122,13 +122,18 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity,
 
 // Launch C (+)= A * B^T on stream s.  A: [M][lda], B: [N][ldb] bf16 with
 // lda, ldb multiples of 8 and columns K..round8(K) zero (16-byte rows);
-// C: [M][ldc] float (optional), Cb: [M][ldcb] bf16 (optional).  splitk > 1:
-// C must be zeroed and receives atomic partial sums (no bias, ReLU or Cb).
-// bias: [N] float or null; relu: apply max(0, .) after the bias.  err: set to 1
-// if a bounded wait gave up.  Returns the launch error.
+// C: [M][ldc] float (optional), Cb: [M][ldcb] bf16 (optional).  splitk > 1
+// with zstride = 0: C must be zeroed and receives atomic partial sums (no
+// bias, ReLU or Cb).  splitk > 1 with zstride >= M * ldc: the partial product
+// of K chunk z is stored (not added) into C + z * zstride, for a reduction in a
+// fixed order by the caller (no bias, ReLU or Cb); *nsplit (optional) receives
+// the number of chunks used.  bias: [N] float or null; relu: apply max(0, .)
+// after the bias.  err: set to 1 if a bounded wait gave up.  Returns the
+// launch error.
 cudaError_t launch_gemm_bf16(const __nv_bfloat16 *A, int64_t lda, const __nv_bfloat16 *B,
                              int64_t ldb, float *C, int64_t ldc, __nv_bfloat16 *Cb,
                              int64_t ldcb, int M, int N, int K, const float *bias, bool relu,
-                             int splitk, int *err, cudaStream_t s);
+                             int splitk, int *err, cudaStream_t s, int64_t zstride = 0,
+                             int *nsplit = nullptr);
 
 }  // namespace gsp

@@ -179,8 +179,8 @@ def test_forward_matches_oracle(gsp, n):
     logits = torch.zeros((n, 2), dtype=torch.float32, device="cuda")
     gsp.gsp_ranker_forward(r, torch.from_numpy(x).cuda(), n, logits)
     gsp.gsp_ranker_finish(r)
-    # three fused conv + pool layers, fc1 GEMM, fc2
-    assert gsp.gsp_ranker_launches(r) == 5
+    # three fused conv + pool layers, fc1 split-K GEMM and its ordered sum, fc2
+    assert gsp.gsp_ranker_launches(r) == 6
     got = logits.cpu().numpy().astype(np.float64)
     ref, _ = R.forward(p, x.astype(np.float64))
     err = np.abs(got - ref)
