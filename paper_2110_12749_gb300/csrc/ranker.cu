@@ -498,6 +498,7 @@ __global__ void __launch_bounds__(128) conv_pool_tc_kernel(const bf16 *__restric
                                                            bf16 *__restrict__ out, int *err) {
     static_assert(CIN % 8 == 0 && COUT % 16 == 0 && COUT <= 32, "shapes of layers 1 and 2");
     static_assert((SIDE * SIDE) % 128 == 0 && 128 % (2 * SIDE) == 0, "tiles of whole row pairs");
+    static_assert((SIDE & (SIDE - 1)) == 0, "power-of-two sides");
     constexpr int K = 9 * CIN;                  // im2col K (a multiple of 8)
     constexpr int NK16 = (K + 15) / 16;         // MMAs per tile
     constexpr int KC = K / 8;                   // 16-byte K chunks carrying data
@@ -554,18 +555,18 @@ __global__ void __launch_bounds__(128) conv_pool_tc_kernel(const bf16 *__restric
     // this thread's row of tile `tile`: pixel m0 + tid, all 9 taps
     auto gather = [&](int64_t tile, uint32_t dst_base) {
         const int64_t p = tile * 128 + tid;
-        const int64_t b = p / (SIDE * SIDE);
-        const int rem = (int)(p - b * SIDE * SIDE);
+        const int rem = (int)(p & (SIDE * SIDE - 1));  // SIDE is a power of two
         const int y = rem / SIDE, x = rem % SIDE;
+        const bf16 *base = act + p * CIN;  // tap (dy, dx) is base + (dy SIDE + dx) CIN
         const uint32_t dst = dst_base + (tid >> 3) * SBO + (tid & 7) * 16;
 #pragma unroll
         for (int tap = 0; tap < 9; tap++) {
-            const int yy = y + tap / 3 - 1, xx = x + tap % 3 - 1;
-            const bool in = yy >= 0 && yy < SIDE && xx >= 0 && xx < SIDE;
-            const bf16 *src = in ? act + ((b * SIDE + yy) * SIDE + xx) * CIN : act;
+            const int dy = tap / 3 - 1, dx = tap % 3 - 1;
+            const bool in = (unsigned)(y + dy) < (unsigned)SIDE && (unsigned)(x + dx) < (unsigned)SIDE;
+            const bf16 *src = in ? base + (dy * SIDE + dx) * CIN : act;
 #pragma unroll
             for (int j = 0; j < CIN / 8; j++)
-                cp_async16(dst + (tap * (CIN / 8) + j) * 128, in ? src + j * 8 : act, in ? 16u : 0u);
+                cp_async16(dst + (tap * (CIN / 8) + j) * 128, src + (in ? j * 8 : 0), in ? 16u : 0u);
         }
     };
     // bias + ReLU + 2x2 max-pool of the tile in accumulator `acc`
