@@ -80,7 +80,7 @@ def parse():
                     help="snippets in the ranker's training set")
     ap.add_argument("--ranker-runs", type=int, default=3,
                     help="independent trainings of the ranker")
-    ap.add_argument("--ranker-keep", type=float, default=0.995,
+    ap.add_argument("--ranker-keep", type=float, default=0.998,
                     help="share of validation pulses detected at S/N >= 8 the threshold keeps")
     ap.add_argument("--ranker-val-beams", type=int, default=12,
                     help="validation beams that set the ranker's operating threshold")
