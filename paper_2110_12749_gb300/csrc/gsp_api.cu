@@ -591,8 +591,22 @@ gsp_status gsp_search_host(gsp_plan_t p, const uint8_t *h_x, int64_t n_in, int64
     if (!p->h2d_stream) GSP_CK(cudaStreamCreateWithFlags(&p->h2d_stream, cudaStreamNonBlocking));
     for (auto &e : p->h2d_ev)
         if (!e) GSP_CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    // chunk sizes in the weights 1, 1, 2, 4, 8, 8, ...: the first dedispersion
+    // launch waits only for a small copy (its columns plus the max_delay
+    // overhang), and each later copy is at most the size of the launch it hides
+    // behind; equal chunks when the series is too short for the smallest ones
+    int64_t wts[kHostChunks], wsum = 0;
+    for (int k = 0; k < nch; k++) {
+        wts[k] = k == 0 ? 1 : std::min<int64_t>((int64_t)1 << (k - 1), 8);
+        wsum += wts[k];
+    }
+    const bool grow = n_out >= wsum * unit;
     int64_t a[kHostChunks + 1];
-    for (int k = 0; k <= nch; k++) a[k] = (n_out * k / nch) / unit * unit;
+    a[0] = 0;
+    for (int k = 0, cum = 0; k < nch; k++) {
+        cum += (int)wts[k];
+        a[k + 1] = (grow ? n_out * cum / wsum : n_out * (k + 1) / nch) / unit * unit;
+    }
     a[nch] = n_out;
     // the copies start after the caller's earlier work on s (which may still
     // read the staging buffer)

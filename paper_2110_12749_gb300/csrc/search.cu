@@ -6,6 +6,7 @@
 //      (row_sigma_kernel);
 //   3. boxcar S/N over the widths, best width per sample, threshold and the
 //      per-window maximum, appended to the candidate buffer (boxcar_kernel).
+#include <algorithm>
 #include <cfloat>
 #include <cmath>
 
@@ -210,7 +211,7 @@ constexpr int kNumDefaultWidths = 13;
 template <bool kWriteSnr, bool kDefaultW = false>
 __global__ void __launch_bounds__(kBoxThreads) boxcar_kernel(
     const int32_t *__restrict__ D, int64_t stride, int64_t Ls, int B, int64_t nb_max,
-    int64_t t_offset, int64_t win_len, int64_t k0, WidthTable wt,
+    int64_t t_offset, int64_t win_len, int64_t k0, int64_t nwin, int wpc, WidthTable wt,
     const BlockParam *__restrict__ bparam, const float *__restrict__ scale, float threshold,
     float *__restrict__ snr_out, gsp_cand *__restrict__ cands,
     unsigned long long *__restrict__ ncand, int64_t max_cands,
@@ -220,10 +221,6 @@ __global__ void __launch_bounds__(kBoxThreads) boxcar_kernel(
     __shared__ Best wbest[kBoxThreads / 32];
     __shared__ float s_scale[kMaxWidths];
     const int row = blockIdx.y;
-    const int64_t win = k0 + blockIdx.x;
-    int64_t ws = win * win_len - t_offset, we = ws + win_len;
-    if (ws < 0) ws = 0;
-    if (we > Ls) we = Ls;
     const int32_t *d = D + (int64_t)row * stride;
     const BlockParam *bp = bparam + (int64_t)row * nb_max;
     const int nb = (int)(Ls / B);
@@ -234,9 +231,18 @@ __global__ void __launch_bounds__(kBoxThreads) boxcar_kernel(
 #pragma unroll
     for (int iw = 0; iw < kNumDefaultWidths; iw++) sc[iw] = kDefaultW ? s_scale[iw] : 0.0f;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    constexpr int kPer = (kChunk + 1024 + kBoxThreads - 1) / kBoxThreads;  // <= 8 samples/thread
+    // this CTA's windows wi in [wfirst, wlast) of the row (CTAs of a few windows
+    // each: a CTA per window spent most of its time being launched)
+    const int64_t wfirst = (int64_t)blockIdx.x * wpc;
+    const int64_t wlast = min(wfirst + (int64_t)wpc, nwin);
+    for (int64_t wi = wfirst; wi < wlast; wi++) {
+    const int64_t win = k0 + wi;
+    int64_t ws = win * win_len - t_offset, we = ws + win_len;
+    if (ws < 0) ws = 0;
+    if (we > Ls) we = Ls;
     Best run{-FLT_MAX, 0, 0};
     bool have = false;
-    constexpr int kPer = (kChunk + 1024 + kBoxThreads - 1) / kBoxThreads;  // <= 8 samples/thread
 
     for (int64_t s = ws; s < we; s += kChunk) {
         const int64_t e = min(s + (int64_t)kChunk, we);
@@ -291,11 +297,16 @@ __global__ void __launch_bounds__(kBoxThreads) boxcar_kernel(
         __syncthreads();
 
         Best mine{-FLT_MAX, INT64_MAX, 0};
-        for (int i = threadIdx.x; i < (int)(e - s); i += kBoxThreads) {
+        // this thread's first sample, as block offset bo from b_s and index j1 in
+        // that block; both advance by kBoxThreads samples per iteration (no division)
+        int bo = (j_s + (int)threadIdx.x) / B;
+        int j1 = j_s + (int)threadIdx.x - bo * B;
+        for (int i = threadIdx.x; i < (int)(e - s); i += kBoxThreads, j1 += kBoxThreads) {
+            while (j1 >= B) {
+                j1 -= B;
+                bo++;
+            }
             const int64_t t = s + i;
-            const int rel = j_s + i;
-            const int bo = rel / B;                 // block offset from b_s
-            const int j1 = rel - bo * B;
             const int b = (int)b_s + bo;
             const BlockParam q = bp[b];
             const int rem = B - j1;                 // samples left in block b
@@ -411,7 +422,9 @@ __global__ void __launch_bounds__(kBoxThreads) boxcar_kernel(
                 if (better(c, mine)) mine = c;
             }
         }
-        // block argmax (S/N desc, t asc)
+        // block argmax (S/N desc, t asc), skipped when no sample of the sub-chunk
+        // reached the threshold (most of them)
+        if (!__syncthreads_or(mine.w > 0)) continue;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             Best other;
@@ -442,7 +455,7 @@ __global__ void __launch_bounds__(kBoxThreads) boxcar_kernel(
             c.t = run.t;
             c.snr = run.snr;
             c.beam = 0;
-            slots[(int64_t)row * gridDim.x + blockIdx.x] = c;
+            slots[(int64_t)row * nwin + wi] = c;
         }
     } else if (threadIdx.x == 0 && have) {
         const unsigned long long idx = atomicAdd(ncand, 1ull);
@@ -456,6 +469,7 @@ __global__ void __launch_bounds__(kBoxThreads) boxcar_kernel(
             cands[idx] = c;
         }
     }
+    }  // windows
 }
 
 // Stream compaction of the (row, window) slots into a dense candidate list in
@@ -564,28 +578,32 @@ cudaError_t launch_search(gsp_plan_s *p, const int32_t *D, int64_t n_out, int64_
     const int64_t k0 = fdiv(t_offset, L);
     const int64_t k1 = fdiv(t_offset + Ls - 1, L);
     const size_t sm_box = (size_t)(kChunk + wt.wmax + 1) * sizeof(uint32_t);
-    dim3 grid((unsigned)(k1 - k0 + 1), (unsigned)ndm);
+    // windows per CTA: up to 8 while there are still 16 CTAs per SM
+    const int64_t nwin = k1 - k0 + 1;
+    const int wpc = (int)std::max<int64_t>(
+        1, std::min<int64_t>(8, nwin * ndm / (16 * (int64_t)std::max(p->num_sms, 1))));
+    dim3 grid((unsigned)((nwin + wpc - 1) / wpc), (unsigned)ndm);
     bool dflt = wt.n == kNumDefaultWidths;
     for (int i = 0; dflt && i < wt.n; i++) dflt = wt.w[i] == default_width(i);
     if (snr_out && dflt)
         boxcar_kernel<true, true><<<grid, kBoxThreads, sm_box, s>>>(
-            D, stride, Ls, B, p->nb_max, t_offset, L, k0, wt, p->d_bparam, p->d_scale,
+            D, stride, Ls, B, p->nb_max, t_offset, L, k0, nwin, wpc, wt, p->d_bparam, p->d_scale,
             p->desc.threshold, snr_out, p->d_cands, p->d_ncand, p->desc.max_cands, p->d_slots);
     else if (snr_out)
         boxcar_kernel<true><<<grid, kBoxThreads, sm_box, s>>>(
-            D, stride, Ls, B, p->nb_max, t_offset, L, k0, wt, p->d_bparam, p->d_scale,
+            D, stride, Ls, B, p->nb_max, t_offset, L, k0, nwin, wpc, wt, p->d_bparam, p->d_scale,
             p->desc.threshold, snr_out, p->d_cands, p->d_ncand, p->desc.max_cands, p->d_slots);
     else if (dflt)
         boxcar_kernel<false, true><<<grid, kBoxThreads, sm_box, s>>>(
-            D, stride, Ls, B, p->nb_max, t_offset, L, k0, wt, p->d_bparam, p->d_scale,
+            D, stride, Ls, B, p->nb_max, t_offset, L, k0, nwin, wpc, wt, p->d_bparam, p->d_scale,
             p->desc.threshold, snr_out, p->d_cands, p->d_ncand, p->desc.max_cands, p->d_slots);
     else
         boxcar_kernel<false><<<grid, kBoxThreads, sm_box, s>>>(
-            D, stride, Ls, B, p->nb_max, t_offset, L, k0, wt, p->d_bparam, p->d_scale,
+            D, stride, Ls, B, p->nb_max, t_offset, L, k0, nwin, wpc, wt, p->d_bparam, p->d_scale,
             p->desc.threshold, snr_out, p->d_cands, p->d_ncand, p->desc.max_cands, p->d_slots);
     *nlaunch += 1;
     // dense candidate list in (row, t) order
-    const int64_t nslots = (int64_t)grid.x * ndm;
+    const int64_t nslots = nwin * ndm;
     const int64_t nchunks = (nslots + kCompact - 1) / kCompact;
     slot_count_kernel<<<(unsigned)nchunks, kCompact, 0, s>>>(p->d_slots, nslots, p->d_chunk);
     slot_scan_kernel<<<1, kCompact, 0, s>>>(p->d_chunk, nchunks, p->d_ncand);
@@ -625,7 +643,8 @@ cudaError_t launch_search_explicit(const SearchScratch &sc, const SearchConfig &
     const int64_t k1 = fdiv(t_offset + Ls - 1, L);
     const size_t sm_box = (size_t)(kChunk + wt.wmax + 1) * sizeof(uint32_t);
     boxcar_kernel<false><<<dim3((unsigned)(k1 - k0 + 1), (unsigned)cfg.ndm), kBoxThreads, sm_box, s>>>(
-        D, stride, Ls, B, sc.nb_stride, t_offset, L, k0, wt, sc.bparam, sc.scale, cfg.threshold,
+        D, stride, Ls, B, sc.nb_stride, t_offset, L, k0, k1 - k0 + 1, 1, wt, sc.bparam, sc.scale,
+        cfg.threshold,
         nullptr, cands, ncand, max_cands);
     return cudaGetLastError();
 }

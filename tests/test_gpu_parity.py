@@ -202,10 +202,15 @@ def test_custom_widths_blocks_windows_offset(gsp, orc, tiny):
     assert ncmp >= 10
 
 
-@pytest.mark.parametrize("chunks,flags", [("8", 0), ("3", 0), ("1", 0), ("8", 2)])
-def test_host_input_in_chunks_equals_device_search(gsp, orc, monkeypatch, chunks, flags):
+@pytest.mark.parametrize("chunks,flags,block_len",
+                         [("8", 0, 1000), ("3", 0, 1000), ("1", 0, 1000), ("8", 2, 1000),
+                          ("8", 0, 256), ("5", 0, 256)])
+def test_host_input_in_chunks_equals_device_search(gsp, orc, monkeypatch, chunks, flags,
+                                                   block_len):
     # gsp_search_host copies the input in time chunks that overlap the
-    # dedispersion; block_len 1000 makes the chunk unit lcm(1000, 16) = 2000, and
+    # dedispersion; block_len 1000 makes the chunk unit lcm(1000, 16) = 2000
+    # (equal chunks: the series is too short for the growing ones), block_len
+    # 256 a unit of 256 (chunks growing 1, 1, 2, 4, 8, ... units of weight), and
     # the host rows have a stride that is not a multiple of 16.  One chunk and
     # the simple kernel (flags 2) take the copy-first path.
     monkeypatch.setenv("GSP_HOST_CHUNKS", chunks)
@@ -214,7 +219,7 @@ def test_host_input_in_chunks_equals_device_search(gsp, orc, monkeypatch, chunks
     dms = np.arange(0.0, 40.0, 0.5)
     x = rng.integers(0, 256, (nchan, n_in + 7), dtype=np.uint8)
     x[:, 12000:12004] = 255
-    desc, keep = gsp.make_desc(nchan, 1200.0, 1500.0, 1e-4, n_in, dms=dms, block_len=1000,
+    desc, keep = gsp.make_desc(nchan, 1200.0, 1500.0, 1e-4, n_in, dms=dms, block_len=block_len,
                                threshold=4.0, flags=gsp.GSP_FLAG_TIMING | flags)
     plan = gsp.gsp_plan_create(desc, keep)
     c1, n1, _ = gsp.gsp_search_host(plan, x, n_in, t_offset=4000)
@@ -234,7 +239,7 @@ def test_host_input_in_chunks_equals_device_search(gsp, orc, monkeypatch, chunks
     D = orc.dedisperse(np.ascontiguousarray(x[:, :n_in]), n_in, dl)
     cont, ora = {}, []
     for r in range(len(dms)):
-        det = orc.search_row(D[r], dm_idx=r, block_len=1000, threshold=4.0, t_offset=4000,
+        det = orc.search_row(D[r], dm_idx=r, block_len=block_len, threshold=4.0, t_offset=4000,
                              detail=True)
         cont[r] = window_contenders(det, 1024, 4000, 4.0)
         ora.append(det["cands"])
