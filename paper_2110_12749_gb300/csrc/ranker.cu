@@ -691,6 +691,157 @@ constexpr int conv_pool_smem() {
            128 * (COUT + 4) * 4 + 2 * 8 + 16;
 }
 
+// Layer 2 of an inference pass (16 x 16 images): the same implicit GEMM, with
+// one A buffer and one accumulator per CTA so that four CTAs fit an SM.  A
+// 128-pixel tile is 8 image rows, warp w holding rows 2w and 2w + 1 (lane l:
+// row 2w + l / 16, column l % 16), so each 2x2 pooling window lies in one warp
+// and the epilogue pools with two shuffles (partners l ^ 1 and l ^ 16) instead
+// of a shared-memory tile.  Per tile: wait for the gather, MMAs, wait for them;
+// then the next tile's gather runs under this tile's epilogue.  Same products,
+// rounding points and output as conv_pool_tc_kernel.  Bounded waits.
+template <int CIN, int COUT>
+__global__ void __launch_bounds__(128) conv_pool16_tc_kernel(const bf16 *__restrict__ act, int B,
+                                                             const bf16 *__restrict__ W,
+                                                             const float *__restrict__ bias,
+                                                             bf16 *__restrict__ out, int *err) {
+    constexpr int SIDE = 16, PW = SIDE / 2;
+    static_assert(CIN % 8 == 0 && COUT % 16 == 0 && COUT <= 32, "shapes of layer 2");
+    constexpr int K = 9 * CIN;
+    constexpr int NK16 = (K + 15) / 16;
+    constexpr int KC = K / 8;
+    constexpr int KCS = NK16 * 2;
+    constexpr uint32_t SBO = KCS * 128;
+    constexpr int A_BYTES = 128 * KCS * 16;
+    constexpr uint32_t kCols = COUT < 32 ? 32u : (uint32_t)COUT;
+    constexpr uint32_t kIdesc = tc::idesc_bf16(128, COUT);
+    constexpr int KP = (K + 7) & ~7;
+    extern __shared__ __align__(1024) uint8_t smem[];
+    uint8_t *sA = smem, *sB = smem + A_BYTES;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(sB + COUT * KCS * 16);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bar + 1);
+    __shared__ float sbias[COUT];
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int64_t ntiles = (int64_t)B * SIDE * SIDE / 128;
+    const int64_t my = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    if (warp == 0) tc::tmem_alloc(tc::smem_u32(tmem_slot), kCols);
+    if (tid == 0) tc::mbar_init1(tc::smem_u32(bar));
+    for (int i = tid; i < COUT; i += 128) sbias[i] = bias[i];
+    for (int idx = tid; idx < COUT * KCS; idx += 128) {
+        const int n = idx % COUT, q = idx / COUT;
+        uint4 v = make_uint4(0u, 0u, 0u, 0u);
+        if (q < KC) v = __ldg(reinterpret_cast<const uint4 *>(W + (int64_t)n * KP) + q);
+        *reinterpret_cast<uint4 *>(sB + (n >> 3) * SBO + q * 128 + (n & 7) * 16) = v;
+    }
+    for (int idx = tid; idx < 128 * (KCS - KC); idx += 128) {
+        const int r = idx & 127, q = KC + (idx >> 7);
+        *reinterpret_cast<uint4 *>(sA + (r >> 3) * SBO + q * 128 + (r & 7) * 16) =
+            make_uint4(0u, 0u, 0u, 0u);
+    }
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    const uint32_t tmem = *tmem_slot;
+    const uint32_t a_addr = tc::smem_u32(sA), b_addr = tc::smem_u32(sB);
+    const uint32_t bar0 = tc::smem_u32(bar);
+
+    auto gather = [&](int64_t tile) {
+        const int64_t p = tile * 128 + tid;
+        const int rem = (int)(p & (SIDE * SIDE - 1));
+        const int y = rem / SIDE, x = rem % SIDE;
+        const bf16 *base = act + p * CIN;
+        const uint32_t dst = a_addr + (tid >> 3) * SBO + (tid & 7) * 16;
+#pragma unroll
+        for (int tap = 0; tap < 9; tap++) {
+            const int dy = tap / 3 - 1, dx = tap % 3 - 1;
+            const bool in = (unsigned)(y + dy) < (unsigned)SIDE && (unsigned)(x + dx) < (unsigned)SIDE;
+            const bf16 *src = in ? base + (dy * SIDE + dx) * CIN : act;
+#pragma unroll
+            for (int j = 0; j < CIN / 8; j++)
+                cp_async16(dst + (tap * (CIN / 8) + j) * 128, src + (in ? j * 8 : 0), in ? 16u : 0u);
+        }
+    };
+    // bias + ReLU, 2x2 max over lanes {l, l ^ 1, l ^ 16, l ^ 17}, bf16 stores by
+    // the lanes of even column in the first row of each window
+    auto epilogue = [&](int64_t tile) {
+        const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
+        const int64_t m0 = tile * 128;
+        const int64_t b = m0 / (SIDE * SIDE);
+        const int py = (int)(m0 - b * SIDE * SIDE) / (2 * SIDE) + warp;  // pooled row
+        const int px = (lane & 15) >> 1;
+        bf16 *dst = out + ((b * PW + py) * PW + px) * COUT;
+        const bool writer = (lane & 17) == 0;
+#pragma unroll
+        for (int c0 = 0; c0 < COUT; c0 += 16) {
+            float v[16];
+            tc::tmem_ld16(taddr + (uint32_t)c0, v);
+            __align__(16) bf16 o[16];
+#pragma unroll
+            for (int c = 0; c < 16; c++) {
+                float z = fmaxf(v[c] + sbias[c0 + c], 0.0f);
+                z = fmaxf(z, __shfl_xor_sync(0xffffffffu, z, 1));
+                z = fmaxf(z, __shfl_xor_sync(0xffffffffu, z, 16));
+                o[c] = __float2bfloat16_rn(z);
+            }
+            if (writer) {
+                *reinterpret_cast<uint4 *>(dst + c0) = *reinterpret_cast<const uint4 *>(o);
+                *reinterpret_cast<uint4 *>(dst + c0 + 8) = *reinterpret_cast<const uint4 *>(o + 8);
+            }
+        }
+    };
+
+    uint32_t ph = 0u;
+    bool pend = false, ok = true;
+    if (my > 0) {
+        gather(blockIdx.x);
+        cp_async_commit();
+    }
+    for (int64_t k = 0; k < my; k++) {
+        const int64_t tile = blockIdx.x + k * gridDim.x;
+        cp_async_wait<0>();
+        tc::fence_proxy_async();  // this thread's copies -> tensor-core reads
+        tc::fence_before();
+        __syncthreads();
+        tc::fence_after();
+        if (tid == 0) {
+#pragma unroll
+            for (int kk = 0; kk < NK16; kk++) {
+                const uint64_t ad = tc::smem_desc(a_addr + kk * 256, 128, SBO);
+                const uint64_t bd = tc::smem_desc(b_addr + kk * 256, 128, SBO);
+                tc::mma_bf16(tmem, ad, bd, kIdesc, kk > 0 ? 1u : 0u);
+            }
+            tc::mma_commit(bar0);
+        }
+        pend = true;
+        const bool done = tc::mbar_wait_bounded(bar0, ph, kConvBudget);
+        if (!__syncthreads_and(done)) {
+            ok = false;
+            break;
+        }
+        ph ^= 1u;
+        pend = false;
+        tc::fence_after();
+        if (k + 1 < my) {  // the MMAs are done with A: refill it under the epilogue
+            gather(tile + gridDim.x);
+            cp_async_commit();
+        }
+        epilogue(tile);
+    }
+    cp_async_wait<0>();
+    if (!ok) {
+        if (tid == 0) atomicExch(err, 1);
+        if (pend) (void)tc::mbar_wait_bounded(bar0, ph, kConvBudget);
+    }
+    tc::fence_before();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, kCols);
+}
+
+template <int CIN, int COUT>
+constexpr int conv_pool16_smem() {
+    return 128 * ((9 * CIN + 15) / 16) * 2 * 16 + COUT * ((9 * CIN + 15) / 16) * 2 * 16 + 8 + 16;
+}
+
 }  // namespace
 
 struct gsp_ranker_s {
@@ -764,38 +915,42 @@ cudaError_t gemm(gsp_ranker_s *r, const bf16 *A, int64_t lda, const bf16 *B, int
     return e;
 }
 
+// CTAs per SM of a fused conv kernel from its resources: shared memory (stages +
+// static + the per-CTA reservation), registers, threads, and at most 512
+// tensor-memory columns per SM (cols per CTA).  The runtime's occupancy query
+// answers one CTA per SM for these kernels whatever their shared memory, while
+// several do run side by side (four CTAs per SM run layer 1 2.3x faster than
+// one), so the count is computed here.  Also raises the kernel's dynamic
+// shared-memory limit and asks for the largest shared-memory carveout.
+template <typename Kern>
+cudaError_t conv_ctas_per_sm(Kern kern, int smem, int cols, int *out) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 (int)cudaSharedmemCarveoutMaxShared);
+    cudaFuncAttributes fa;
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, kern);
+    int dev = 0, smem_sm = 0, resv = 0;
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&resv, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+    if (e != cudaSuccess) return e;
+    const int by_smem = smem_sm / (smem + (int)fa.sharedSizeBytes + resv);
+    const int by_regs = 65536 / (128 * std::max(fa.numRegs, 1));
+    const int by_tmem = 512 / std::max(32, cols);
+    *out = std::max(1, std::min(std::min(by_smem, by_regs), std::min(by_tmem, 16)));
+    return cudaSuccess;
+}
+
 template <int CIN, int COUT, int SIDE>
 cudaError_t launch_conv_pool(gsp_ranker_s *r, const bf16 *act, int n, const bf16 *W,
                              const float *bias, bf16 *out, cudaStream_t s) {
     constexpr int smem = conv_pool_smem<CIN, COUT, SIDE>();
     static int blocks_per_sm = 0;
     if (blocks_per_sm == 0) {
-        // CTAs per SM from the kernel's resources: shared memory (stages + static +
-        // the per-CTA reservation), registers, threads, and at most 512 tensor-memory
-        // columns (two accumulators of COUT columns per CTA).  The runtime's occupancy
-        // query answers one CTA per SM for this kernel whatever its shared memory,
-        // while several do run side by side (four CTAs per SM run layer 1 2.3x faster
-        // than one), so the count is computed here.
-        cudaError_t e = cudaFuncSetAttribute(conv_pool_tc_kernel<CIN, COUT, SIDE>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(conv_pool_tc_kernel<CIN, COUT, SIDE>,
-                                     cudaFuncAttributePreferredSharedMemoryCarveout,
-                                     (int)cudaSharedmemCarveoutMaxShared);
-        cudaFuncAttributes fa;
-        if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, conv_pool_tc_kernel<CIN, COUT, SIDE>);
-        int dev = 0, smem_sm = 0, resv = 0;
-        if (e == cudaSuccess) e = cudaGetDevice(&dev);
-        if (e == cudaSuccess)
-            e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
-        if (e == cudaSuccess)
-            e = cudaDeviceGetAttribute(&resv, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+        cudaError_t e = conv_ctas_per_sm(conv_pool_tc_kernel<CIN, COUT, SIDE>, smem, 2 * COUT,
+                                         &blocks_per_sm);
         if (e != cudaSuccess) return e;
-        const int per_cta = smem + (int)fa.sharedSizeBytes + resv;
-        const int by_smem = smem_sm / per_cta;
-        const int by_regs = 65536 / (128 * std::max(fa.numRegs, 1));
-        const int by_tmem = 512 / std::max(32, 2 * COUT);
-        blocks_per_sm = std::max(1, std::min(std::min(by_smem, by_regs), std::min(by_tmem, 16)));
     }
     int dev = 0, sms = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -805,6 +960,26 @@ cudaError_t launch_conv_pool(gsp_ranker_s *r, const bf16 *act, int n, const bf16
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(ntiles, (int64_t)sms * blocks_per_sm));
     RK_LAUNCH((conv_pool_tc_kernel<CIN, COUT, SIDE><<<grid, 128, smem, s>>>(act, n, W, bias, out,
                                                                            r->err)));
+    return cudaSuccess;
+}
+
+template <int CIN, int COUT>
+cudaError_t launch_conv_pool16(gsp_ranker_s *r, const bf16 *act, int n, const bf16 *W,
+                               const float *bias, bf16 *out, cudaStream_t s) {
+    constexpr int smem = conv_pool16_smem<CIN, COUT>();
+    static int blocks_per_sm = 0;
+    if (blocks_per_sm == 0) {
+        cudaError_t e = conv_ctas_per_sm(conv_pool16_tc_kernel<CIN, COUT>, smem, COUT,
+                                         &blocks_per_sm);
+        if (e != cudaSuccess) return e;
+    }
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    const int64_t ntiles = (int64_t)n * 16 * 16 / 128;
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(ntiles, (int64_t)sms * blocks_per_sm));
+    RK_LAUNCH((conv_pool16_tc_kernel<CIN, COUT><<<grid, 128, smem, s>>>(act, n, W, bias, out, r->err)));
     return cudaSuccess;
 }
 
@@ -826,7 +1001,7 @@ cudaError_t forward(gsp_ranker_s *r, const float *x, int n, bool train, cudaStre
                 e = launch_conv_pool<8, 16, 32>(r, r->a[0], n, r->W[1], r->params + r->off.b[1],
                                                 r->a[1], s);
             else
-                e = launch_conv_pool<16, 32, 16>(r, r->a[1], n, r->W[2], r->params + r->off.b[2],
+                e = launch_conv_pool16<16, 32>(r, r->a[1], n, r->W[2], r->params + r->off.b[2],
                                                  r->a[2], s);
             if (e != cudaSuccess) return e;
             continue;
