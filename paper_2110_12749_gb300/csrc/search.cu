@@ -231,7 +231,9 @@ __global__ void __launch_bounds__(kBoxThreads) boxcar_kernel(
 #pragma unroll
     for (int iw = 0; iw < kNumDefaultWidths; iw++) sc[iw] = kDefaultW ? s_scale[iw] : 0.0f;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    constexpr int kPer = (kChunk + 1024 + kBoxThreads - 1) / kBoxThreads;  // <= 8 samples/thread
+    // samples per thread in the prefix phase: a sub-chunk plus the widest boxcar
+    // minus one (150 for the default widths, at most 1024)
+    constexpr int kPer = (kChunk + (kDefaultW ? 150 : 1024) + kBoxThreads - 1) / kBoxThreads;
     // this CTA's windows wi in [wfirst, wlast) of the row (CTAs of a few windows
     // each: a CTA per window spent most of its time being launched)
     const int64_t wfirst = (int64_t)blockIdx.x * wpc;
