@@ -303,6 +303,9 @@ __global__ void __launch_bounds__(kBoxThreads) boxcar_kernel(
         // that block; both advance by kBoxThreads samples per iteration (no division)
         int bo = (j_s + (int)threadIdx.x) / B;
         int j1 = j_s + (int)threadIdx.x - bo * B;
+        // samples i <= fit150 (fitw) have every default (every) boxcar inside the series
+        const int fit150 = (int)max((int64_t)-1, min((int64_t)kChunk, Ls - 150 - s));
+        const int fitw = (int)max((int64_t)-1, min((int64_t)kChunk, Ls - (int64_t)wt.wmax - s));
         for (int i = threadIdx.x; i < (int)(e - s); i += kBoxThreads, j1 += kBoxThreads) {
             while (j1 >= B) {
                 j1 -= B;
@@ -317,7 +320,7 @@ __global__ void __launch_bounds__(kBoxThreads) boxcar_kernel(
             const uint32_t p0 = sP[i];
             float bsnr = -FLT_MAX;
             int bw = 0;
-            if (kDefaultW && !kWriteSnr && t + 150 <= Ls && 150 <= rem) {
+            if (kDefaultW && !kWriteSnr && i <= fit150 && 150 <= rem) {
                 // default widths inside block b: the maximum S/N first (one max per
                 // width); the width that reaches it is recovered only when it
                 // passes the threshold (rare)
@@ -336,7 +339,7 @@ __global__ void __launch_bounds__(kBoxThreads) boxcar_kernel(
                     for (int iw = kNumDefaultWidths - 1; iw >= 0; iw--)
                         if (v[iw] == bsnr) bw = default_width(iw);
                 }
-            } else if (kDefaultW && !kWriteSnr && t + 150 <= Ls) {
+            } else if (kDefaultW && !kWriteSnr && i <= fit150) {
                 // default widths near the end of block b: boxcars longer than the
                 // samples left run into block b + 1 and take its line there
                 const BlockParam q2 = bp[b + 1];
@@ -360,7 +363,7 @@ __global__ void __launch_bounds__(kBoxThreads) boxcar_kernel(
                         bw = w;
                     }
                 }
-            } else if (kDefaultW && t + 150 <= Ls && 150 <= rem) {
+            } else if (kDefaultW && i <= fit150 && 150 <= rem) {
                 // default widths, every boxcar inside block b
 #pragma unroll
                 for (int iw = 0; iw < kNumDefaultWidths; iw++) {
@@ -374,7 +377,7 @@ __global__ void __launch_bounds__(kBoxThreads) boxcar_kernel(
                         bw = w;
                     }
                 }
-            } else if (!kDefaultW && t + wt.wmax <= Ls && wt.wmax <= rem) {
+            } else if (!kDefaultW && i <= fitw && wt.wmax <= rem) {
                 // every boxcar inside block b: no bounds or straddle checks
 #pragma unroll
                 for (int iw = 0; iw < kMaxWidths; iw++) {
