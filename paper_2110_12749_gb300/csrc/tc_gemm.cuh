@@ -1,13 +1,18 @@
 // BF16 GEMM on the 5th-generation tensor cores (tcgen05), FP32 accumulation
 // in tensor memory (TMEM):
 //   C[m][n] (+)= sum_k A[m][k] * B[n][k]      (A, B bf16 row-major, K contiguous)
-// One CTA (4 warps) per 128 x BN output tile; K in steps of 64: the CTA
-// stages the A and B tiles in shared memory in the K-major core-matrix layout
-// (8 rows x 16 bytes per core matrix, no swizzle), one thread issues four
-// tcgen05.mma (K = 16 each) and commits them to an mbarrier, and after the K
-// loop each warp reads its 32 TMEM lanes (rows) with tcgen05.ld.  Optional
-// split-K (gridDim.z > 1) adds partial tiles atomically; otherwise the
-// epilogue adds a bias, applies ReLU, and writes FP32 and/or BF16.
+// in 128 x BN output tiles and K steps of 64.  Two kernels (tc_gemm.cu):
+//  * TMA-fed and warp-specialised (most shapes): 2-D tensor-map tile loads with
+//    the 128-byte swizzle fill an S-stage shared-memory ring; one lane issues
+//    the loads and the tcgen05.mma (K = 16 each), four warps read the two TMEM
+//    accumulators with tcgen05.ld for the epilogue of one tile while the next
+//    one accumulates; persistent CTAs stride over the M tiles.
+//  * cp.async-fed (one or two K steps at 64- or 128-column blocks): all threads
+//    copy 16-byte chunks into the K-major core-matrix layout (8 rows x 16 bytes
+//    per core matrix, no swizzle), one CTA per M tile.
+// Optional split-K (gridDim.z > 1) adds partial tiles atomically or stores
+// each K chunk's partial tile in its own slice; otherwise the epilogue adds a
+// bias, applies ReLU, and writes FP32 and/or BF16.
 #pragma once
 
 #include <cuda_bf16.h>
