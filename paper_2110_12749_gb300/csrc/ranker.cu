@@ -111,6 +111,19 @@ __global__ void __launch_bounds__(256) im2col_kernel(const T *__restrict__ a, in
     }
 }
 
+// fma(a, b.x, c.x), fma(a, b.y, c.y) as one packed instruction (two IEEE
+// single-precision FMAs, the same results as two fmaf): half the issue slots
+__device__ __forceinline__ float2 fma_pair(float a, float2 b, float2 c) {
+    uint64_t av, bv, cv, d;
+    asm("mov.b64 %0, {%1, %1};" : "=l"(av) : "f"(a));
+    asm("mov.b64 %0, {%1, %2};" : "=l"(bv) : "f"(b.x), "f"(b.y));
+    asm("mov.b64 %0, {%1, %2};" : "=l"(cv) : "f"(c.x), "f"(c.y));
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(av), "l"(bv), "l"(cv));
+    float2 r;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(d));
+    return r;
+}
+
 // Layer 0 of an inference pass: conv 3x3 (1 -> 8, pad 1) + bias + ReLU + 2x2
 // max-pool straight from the FP32 snippets, on the CUDA cores: with one input
 // channel the product has K = 9, too short for the tensor pipe to pay for its
@@ -120,17 +133,23 @@ __global__ void __launch_bounds__(256) im2col_kernel(const T *__restrict__ a, in
 // of horizontally adjacent pooled pixels reads its 4 x 6 input patch; per
 // channel it loads the nine weights once and computes the pair's 2 x 4 conv
 // outputs, then writes the two pixels' 8 bf16 results as two 16-byte stores
-// (NHWC, as pool_kernel<8>).
+// (NHWC, as pool_kernel<8>).  Channels 2p and 2p + 1 share each packed FMA.
 __global__ void __launch_bounds__(256) conv0_pool_kernel(const float *__restrict__ x, int B,
                                                          const bf16 *__restrict__ W0,
                                                          const float *__restrict__ b0,
                                                          bf16 *__restrict__ a0) {
     constexpr int C = 8, KP = kpad(0), H = kS, H2 = kS / 2, HP = H2 / 2;
-    __shared__ float sw[C][9];
-    __shared__ float sb[C];
-    for (int i = threadIdx.x; i < C * 9; i += blockDim.x)
-        sw[i / 9][i % 9] = __bfloat162float(W0[(i / 9) * KP + i % 9]);
-    for (int i = threadIdx.x; i < C; i += blockDim.x) sb[i] = b0[i];
+    __shared__ float2 sw[C / 2][9];  // channels 2p and 2p + 1 side by side
+    __shared__ float2 sb[C / 2];
+    for (int i = threadIdx.x; i < C * 9; i += blockDim.x) {
+        const float w = __bfloat162float(W0[(i / 9) * KP + i % 9]);
+        if ((i / 9) & 1) sw[i / 18][i % 9].y = w;
+        else sw[i / 18][i % 9].x = w;
+    }
+    for (int i = threadIdx.x; i < C; i += blockDim.x) {
+        if (i & 1) sb[i / 2].y = b0[i];
+        else sb[i / 2].x = b0[i];
+    }
     __syncthreads();
     const int64_t total = (int64_t)B * H2 * HP;  // pixel pairs
     for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total;
@@ -153,27 +172,29 @@ __global__ void __launch_bounds__(256) conv0_pool_kernel(const float *__restrict
         }
         __align__(16) bf16 out[2][C];
 #pragma unroll
-        for (int co = 0; co < C; co++) {
-            float w[9];
+        for (int cp = 0; cp < C / 2; cp++) {  // channels 2 cp and 2 cp + 1 together
+            float2 w[9];
 #pragma unroll
-            for (int k = 0; k < 9; k++) w[k] = sw[co][k];
-            const float bias = sb[co];
+            for (int k = 0; k < 9; k++) w[k] = sw[cp][k];
+            const float2 bias = sb[cp];
 #pragma unroll
             for (int px = 0; px < 2; px++) {
-                float m = 0.0f;  // ReLU outputs are >= 0
+                float m0 = 0.0f, m1 = 0.0f;  // ReLU outputs are >= 0
 #pragma unroll
                 for (int dy = 0; dy < 2; dy++)
 #pragma unroll
                     for (int dx = 0; dx < 2; dx++) {
-                        float z = 0.0f;
+                        float2 z = make_float2(0.0f, 0.0f);
 #pragma unroll
                         for (int ky = 0; ky < 3; ky++)
 #pragma unroll
                             for (int kx = 0; kx < 3; kx++)
-                                z = fmaf(v[dy + ky][2 * px + dx + kx], w[ky * 3 + kx], z);
-                        m = fmaxf(m, z + bias);
+                                z = fma_pair(v[dy + ky][2 * px + dx + kx], w[ky * 3 + kx], z);
+                        m0 = fmaxf(m0, z.x + bias.x);
+                        m1 = fmaxf(m1, z.y + bias.y);
                     }
-                out[px][co] = __float2bfloat16_rn(m);
+                out[px][2 * cp] = __float2bfloat16_rn(m0);
+                out[px][2 * cp + 1] = __float2bfloat16_rn(m1);
             }
         }
         const int64_t pix = (b * H2 + y2) * H2 + x2;
