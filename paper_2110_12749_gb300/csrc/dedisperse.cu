@@ -1119,12 +1119,9 @@ cudaError_t launch_dedisperse_batch(const BeamLaunch *beams, int nbeams, int var
     }
     const TileFit f = fit_variant(v, spread);
     if (!f.ok) return cudaErrorInvalidValue;
-    static int configured_smem[kNumVariants] = {0};
-    if (f.smem > configured_smem[variant]) {
-        cudaError_t e = cudaFuncSetAttribute(v.fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             f.smem);
+    {
+        cudaError_t e = ensure_kernel_smem(reinterpret_cast<const void *>(v.fn), f.smem);
         if (e != cudaSuccess) return e;
-        configured_smem[variant] = f.smem;
     }
     TiledArgs a;
     std::memset(&a, 0, sizeof(a));

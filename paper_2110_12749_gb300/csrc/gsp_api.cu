@@ -5,6 +5,8 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -222,6 +224,23 @@ gsp_status run_search(gsp_plan_s *p, const int32_t *D, int64_t n_out, int64_t st
 namespace gsp {
 
 void record_error(cudaError_t e, const char *what) { set_err(e, what); }
+
+cudaError_t ensure_kernel_smem(const void *fn, int smem, bool max_carveout) {
+    static std::mutex mu;
+    static std::map<std::pair<int, const void *>, int> done;  // (device, kernel) -> bytes
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = done.find({dev, fn});
+    if (it != done.end() && it->second >= smem) return cudaSuccess;
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess && max_carveout)
+        e = cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 (int)cudaSharedmemCarveoutMaxShared);
+    if (e == cudaSuccess) done[{dev, fn}] = smem;
+    return e;
+}
 
 // Used by the batch module: make sure the plan's series scratch exists and
 // tell whether block sums can be fused into the tiled dedispersion kernel.

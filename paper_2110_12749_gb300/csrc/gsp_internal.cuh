@@ -179,6 +179,12 @@ int dedisperse_choose_variant(const gsp_plan_s *const *plans, int nplans);
 
 // gsp_api.cu helpers shared with the batch module.
 void record_error(cudaError_t e, const char *what);
+
+// Raise kernel fn's dynamic shared-memory limit to at least smem bytes on the
+// current device, and (max_carveout) ask for the largest shared-memory
+// carveout.  Kernel attributes belong to a device, so the setting is
+// remembered per (device, kernel); thread-safe.  Returns the CUDA error.
+cudaError_t ensure_kernel_smem(const void *fn, int smem, bool max_carveout = false);
 gsp_status plan_prepare_search(gsp_plan_s *p, int64_t n_out, int32_t **D, int64_t *stride,
                                unsigned long long **bsum);
 gsp_status plan_check_input(gsp_plan_s *p, const uint8_t *x, int64_t n_in, int64_t x_stride,

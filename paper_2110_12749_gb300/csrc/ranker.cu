@@ -942,13 +942,11 @@ cudaError_t gemm(gsp_ranker_s *r, const bf16 *A, int64_t lda, const bf16 *B, int
 // answers one CTA per SM for these kernels whatever their shared memory, while
 // several do run side by side (four CTAs per SM run layer 1 2.3x faster than
 // one), so the count is computed here.  Also raises the kernel's dynamic
-// shared-memory limit and asks for the largest shared-memory carveout.
+// shared-memory limit on the current device and asks for the largest
+// shared-memory carveout (every launch calls that too: attributes are per device).
 template <typename Kern>
 cudaError_t conv_ctas_per_sm(Kern kern, int smem, int cols, int *out) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                 (int)cudaSharedmemCarveoutMaxShared);
+    cudaError_t e = gsp::ensure_kernel_smem(reinterpret_cast<const void *>(kern), smem, true);
     cudaFuncAttributes fa;
     if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, kern);
     int dev = 0, smem_sm = 0, resv = 0;
@@ -972,6 +970,10 @@ cudaError_t launch_conv_pool(gsp_ranker_s *r, const bf16 *act, int n, const bf16
         cudaError_t e = conv_ctas_per_sm(conv_pool_tc_kernel<CIN, COUT, SIDE>, smem, 2 * COUT,
                                          &blocks_per_sm);
         if (e != cudaSuccess) return e;
+    } else {
+        cudaError_t e = gsp::ensure_kernel_smem(
+            reinterpret_cast<const void *>(conv_pool_tc_kernel<CIN, COUT, SIDE>), smem, true);
+        if (e != cudaSuccess) return e;
     }
     int dev = 0, sms = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -992,6 +994,10 @@ cudaError_t launch_conv_pool16(gsp_ranker_s *r, const bf16 *act, int n, const bf
     if (blocks_per_sm == 0) {
         cudaError_t e = conv_ctas_per_sm(conv_pool16_tc_kernel<CIN, COUT>, smem, COUT,
                                          &blocks_per_sm);
+        if (e != cudaSuccess) return e;
+    } else {
+        cudaError_t e = gsp::ensure_kernel_smem(
+            reinterpret_cast<const void *>(conv_pool16_tc_kernel<CIN, COUT>), smem, true);
         if (e != cudaSuccess) return e;
     }
     int dev = 0, sms = 0;
@@ -1585,16 +1591,10 @@ gsp_status gsp_ranker_snippets(gsp_plan_t p, const int32_t *d_D, int64_t stride,
                                                 p->d_order, dmax, d_out);
         return status_of(cudaGetLastError(), "snippet launch");
     }
-    static bool configured = false;  // the ring's shared memory, once per process
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(snippet_kernel<kSnipHalf>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * kSnipHalf);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(snippet_kernel<kSnipHalf>,
-                                     cudaFuncAttributePreferredSharedMemoryCarveout,
-                                     (int)cudaSharedmemCarveoutMaxShared);
+    {
+        cudaError_t e = gsp::ensure_kernel_smem(
+            reinterpret_cast<const void *>(snippet_kernel<kSnipHalf>), 2 * kSnipHalf, true);
         if (e != cudaSuccess) return status_of(e, "snippet attributes");
-        configured = true;
     }
     snippet_kernel<kSnipHalf><<<n, 256, 2 * kSnipHalf, s>>>(
         d_D, stride, p->desc.ndm, Ls, B, p->d_bparam, p->nb_max, p->d_sinv, d_cands, p->d_order,

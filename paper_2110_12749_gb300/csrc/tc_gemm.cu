@@ -541,33 +541,25 @@ cudaError_t launch_tma(dim3 grid, cudaStream_t s, const CUtensorMap &tmA, const 
                        float *C, int64_t ldc, __nv_bfloat16 *Cb, int64_t ldcb, int M, int N, int K,
                        int kchunk, int64_t zstride, const float *bias, int relu, int *err) {
     constexpr int smem = tma_smem<BN>();
-    static bool configured = false;
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(gemm_tma_kernel<BN, kTmaStages>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
+    cudaError_t e =
+        ensure_kernel_smem(reinterpret_cast<const void *>(gemm_tma_kernel<BN, kTmaStages>), smem);
+    if (e != cudaSuccess) return e;
     gemm_tma_kernel<BN, kTmaStages><<<grid, 160, smem, s>>>(tmA, tmB, C, ldc, Cb, ldcb, M, N, K,
                                                             kchunk, zstride, bias, relu, err);
     return cudaSuccess;
 }
 
 // Launch one instantiation; its dynamic shared-memory limit (above the 48 KB
-// default) is raised once per instantiation.
+// default) is raised once per device.
 template <int BN, int S, int NACC>
 cudaError_t launch_bn(dim3 grid, cudaStream_t s, const __nv_bfloat16 *A, int64_t lda,
                       const __nv_bfloat16 *B, int64_t ldb, float *C, int64_t ldc,
                       __nv_bfloat16 *Cb, int64_t ldcb, int M, int N, int K, int kchunk,
                       int64_t zstride, const float *bias, int relu, int *err) {
     constexpr int smem = S * (kBM + BN) * kBK * 2;
-    static bool configured = false;
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(gemm_bf16_kernel<BN, S, NACC>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
+    cudaError_t e =
+        ensure_kernel_smem(reinterpret_cast<const void *>(gemm_bf16_kernel<BN, S, NACC>), smem);
+    if (e != cudaSuccess) return e;
     gemm_bf16_kernel<BN, S, NACC><<<grid, 128, smem, s>>>(A, lda, B, ldb, C, ldc, Cb, ldcb, M, N,
                                                           K, kchunk, zstride, bias, relu, err);
     return cudaSuccess;
