@@ -507,226 +507,26 @@ __device__ __forceinline__ void cp_async_wait() {
 // SIDE whole image rows, so every 2x2 pooling window lies inside it).  Each
 // thread gathers the 9 taps of its pixel straight from act with 16-byte
 // cp.async copies (zero-filled outside the image) into the K-major
-// core-matrix layout; two A buffers and two tensor-memory accumulators let
-// the gather of tile k+1 and the MMAs of tile k run under the epilogue of
-// tile k-1.  The weights are staged once per CTA.  Every wait is bounded; on
-// a timeout the kernel sets *err, waits (bounded) for its MMAs in flight and
-// releases its tensor memory.
+// core-matrix layout; the weights are staged once per CTA.  One A buffer and
+// one accumulator per CTA, so that many CTAs fit an SM.  Per tile: wait for
+// the gather, MMAs, wait for them; then the next tile's gather runs under
+// this tile's epilogue, which pools mostly in registers:
+//  * SIDE 16: a tile is 8 image rows, warp w holding rows 2w and 2w + 1
+//    (lane l: row 2w + l / 16, column l % 16), so each pooling window lies in
+//    one warp: two shuffles (partners l ^ 1 and l ^ 16).
+//  * SIDE 32: a tile is 4 image rows, warp w holding row w: a shuffle pools
+//    column pairs (l ^ 1), and warps 1 and 3 hand their row maxima to warps 0
+//    and 2 through a 2 KB shared buffer.
+// Every wait is bounded; on a timeout the kernel sets *err, waits (bounded)
+// for its MMAs in flight and releases its tensor memory.
 template <int CIN, int COUT, int SIDE>
-__global__ void __launch_bounds__(128) conv_pool_tc_kernel(const bf16 *__restrict__ act, int B,
-                                                           const bf16 *__restrict__ W,
-                                                           const float *__restrict__ bias,
-                                                           bf16 *__restrict__ out, int *err) {
-    static_assert(CIN % 8 == 0 && COUT % 16 == 0 && COUT <= 32, "shapes of layers 1 and 2");
-    static_assert((SIDE * SIDE) % 128 == 0 && 128 % (2 * SIDE) == 0, "tiles of whole row pairs");
-    static_assert((SIDE & (SIDE - 1)) == 0, "power-of-two sides");
-    constexpr int K = 9 * CIN;                  // im2col K (a multiple of 8)
-    constexpr int NK16 = (K + 15) / 16;         // MMAs per tile
-    constexpr int KC = K / 8;                   // 16-byte K chunks carrying data
-    constexpr int KCS = NK16 * 2;               // staged K chunks (zero past KC)
-    constexpr uint32_t SBO = KCS * 128;         // bytes between 8-row groups
-    constexpr int A_BYTES = 128 * KCS * 16;
-    constexpr int B_BYTES = COUT * KCS * 16;
-    constexpr int LDZ = COUT + 4;               // padded FP32 row of the epilogue tile
-    constexpr uint32_t kCols = 2 * COUT < 32 ? 32u : (uint32_t)(2 * COUT);
-    constexpr uint32_t kIdesc = tc::idesc_bf16(128, COUT);
+__global__ void __launch_bounds__(128) conv_pool_solo_tc_kernel(const bf16 *__restrict__ act,
+                                                                int B, const bf16 *__restrict__ W,
+                                                                const float *__restrict__ bias,
+                                                                bf16 *__restrict__ out, int *err) {
     constexpr int PW = SIDE / 2;
-    constexpr int KP = (K + 7) & ~7;            // row length of W
-    extern __shared__ __align__(1024) uint8_t smem[];
-    uint8_t *sA0 = smem, *sA1 = smem + A_BYTES, *sB = smem + 2 * A_BYTES;
-    float *sz = reinterpret_cast<float *>(smem + 2 * A_BYTES + B_BYTES);
-    uint64_t *bars = reinterpret_cast<uint64_t *>(sz + 128 * LDZ);
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2);
-    __shared__ float sbias[COUT];
-
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int64_t ntiles = (int64_t)B * SIDE * SIDE / 128;
-    const int64_t my = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
-
-    if (warp == 0) tc::tmem_alloc(tc::smem_u32(tmem_slot), kCols);
-    if (tid == 0) {
-        tc::mbar_init1(tc::smem_u32(bars));
-        tc::mbar_init1(tc::smem_u32(bars + 1));
-    }
-    for (int i = tid; i < COUT; i += 128) sbias[i] = bias[i];
-    // weights once: W[n][k] into the core-matrix layout, zero past K
-    for (int idx = tid; idx < COUT * KCS; idx += 128) {
-        const int n = idx % COUT, q = idx / COUT;
-        uint4 v = make_uint4(0u, 0u, 0u, 0u);
-        if (q < KC) v = __ldg(reinterpret_cast<const uint4 *>(W + (int64_t)n * KP) + q);
-        *reinterpret_cast<uint4 *>(sB + (n >> 3) * SBO + q * 128 + (n & 7) * 16) = v;
-    }
-    // the zero K chunks of both A buffers (never written by the gathers)
-    for (int idx = tid; idx < 128 * (KCS - KC); idx += 128) {
-        const int r = idx & 127, q = KC + (idx >> 7);
-        const uint32_t o = (r >> 3) * SBO + q * 128 + (r & 7) * 16;
-        *reinterpret_cast<uint4 *>(sA0 + o) = make_uint4(0u, 0u, 0u, 0u);
-        *reinterpret_cast<uint4 *>(sA1 + o) = make_uint4(0u, 0u, 0u, 0u);
-    }
-    tc::fence_before();
-    __syncthreads();
-    tc::fence_after();
-    const uint32_t tmem = *tmem_slot;
-    const uint32_t a_addr0 = tc::smem_u32(sA0), a_addr1 = tc::smem_u32(sA1);
-    const uint32_t b_addr = tc::smem_u32(sB);
-    const uint32_t bar0 = tc::smem_u32(bars), bar1 = tc::smem_u32(bars + 1);
-    auto a_addr = [&](int j) { return j ? a_addr1 : a_addr0; };
-    auto bar = [&](int j) { return j ? bar1 : bar0; };
-
-    // this thread's row of tile `tile`: pixel m0 + tid, all 9 taps
-    auto gather = [&](int64_t tile, uint32_t dst_base) {
-        const int64_t p = tile * 128 + tid;
-        const int rem = (int)(p & (SIDE * SIDE - 1));  // SIDE is a power of two
-        const int y = rem / SIDE, x = rem % SIDE;
-        const bf16 *base = act + p * CIN;  // tap (dy, dx) is base + (dy SIDE + dx) CIN
-        const uint32_t dst = dst_base + (tid >> 3) * SBO + (tid & 7) * 16;
-#pragma unroll
-        for (int tap = 0; tap < 9; tap++) {
-            const int dy = tap / 3 - 1, dx = tap % 3 - 1;
-            const bool in = (unsigned)(y + dy) < (unsigned)SIDE && (unsigned)(x + dx) < (unsigned)SIDE;
-            const bf16 *src = in ? base + (dy * SIDE + dx) * CIN : act;
-#pragma unroll
-            for (int j = 0; j < CIN / 8; j++)
-                cp_async16(dst + (tap * (CIN / 8) + j) * 128, src + (in ? j * 8 : 0), in ? 16u : 0u);
-        }
-    };
-    // bias + ReLU + 2x2 max-pool of the tile in accumulator `acc`
-    auto epilogue = [&](int64_t tile, int acc) {
-        const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(acc * COUT);
-        float *zr = sz + (warp * 32 + lane) * LDZ;
-#pragma unroll
-        for (int c0 = 0; c0 < COUT; c0 += 16) {
-            float v[16];
-            tc::tmem_ld16(taddr + (uint32_t)c0, v);
-#pragma unroll
-            for (int c = 0; c < 16; c += 4) {
-                float4 o;
-                o.x = fmaxf(v[c] + sbias[c0 + c], 0.0f);
-                o.y = fmaxf(v[c + 1] + sbias[c0 + c + 1], 0.0f);
-                o.z = fmaxf(v[c + 2] + sbias[c0 + c + 2], 0.0f);
-                o.w = fmaxf(v[c + 3] + sbias[c0 + c + 3], 0.0f);
-                *reinterpret_cast<float4 *>(zr + c0 + c) = o;
-            }
-        }
-        __syncthreads();
-        const int64_t m0 = tile * 128;
-        const int64_t b = m0 / (SIDE * SIDE);
-        const int y0 = (int)(m0 - b * SIDE * SIDE) / SIDE;
-        const int64_t pbase = b * PW * PW + (int64_t)(y0 / 2) * PW;
-        for (int it = tid; it < 32 * (COUT / 4); it += 128) {
-            const int pp = it / (COUT / 4), c4 = it % (COUT / 4);
-            const int py = pp / PW, px = pp % PW;
-            const int r00 = 2 * py * SIDE + 2 * px;
-            const float4 q0 = *reinterpret_cast<const float4 *>(sz + r00 * LDZ + c4 * 4);
-            const float4 q1 = *reinterpret_cast<const float4 *>(sz + (r00 + 1) * LDZ + c4 * 4);
-            const float4 q2 = *reinterpret_cast<const float4 *>(sz + (r00 + SIDE) * LDZ + c4 * 4);
-            const float4 q3 = *reinterpret_cast<const float4 *>(sz + (r00 + SIDE + 1) * LDZ + c4 * 4);
-            __align__(8) bf16 o[4];
-            o[0] = __float2bfloat16_rn(fmaxf(fmaxf(q0.x, q1.x), fmaxf(q2.x, q3.x)));
-            o[1] = __float2bfloat16_rn(fmaxf(fmaxf(q0.y, q1.y), fmaxf(q2.y, q3.y)));
-            o[2] = __float2bfloat16_rn(fmaxf(fmaxf(q0.z, q1.z), fmaxf(q2.z, q3.z)));
-            o[3] = __float2bfloat16_rn(fmaxf(fmaxf(q0.w, q1.w), fmaxf(q2.w, q3.w)));
-            *reinterpret_cast<uint2 *>(out + (pbase + pp) * COUT + c4 * 4) =
-                *reinterpret_cast<const uint2 *>(o);
-        }
-    };
-
-    // per accumulator j: parity of its barrier's next phase, MMAs in flight
-    uint32_t ph0 = 0u, ph1 = 0u;
-    bool pend0 = false, pend1 = false;
-    auto flip = [&](int j) {
-        if (j) ph1 ^= 1u; else ph0 ^= 1u;
-    };
-    auto set_pend = [&](int j, bool v) {
-        if (j) pend1 = v; else pend0 = v;
-    };
-    bool ok = true;
-    if (my > 0) {
-        gather(blockIdx.x, a_addr(0));
-        cp_async_commit();
-    }
-    for (int64_t k = 0; k < my; k++) {
-        const int cur = (int)(k & 1), nxt = cur ^ 1;
-        const int64_t tile = blockIdx.x + k * gridDim.x;
-        if (k >= 1) {
-            // MMAs of tile k-1 done: its A buffer may be refilled, its accumulator read
-            const bool done = tc::mbar_wait_bounded(bar(nxt), nxt ? ph1 : ph0, kConvBudget);
-            if (!__syncthreads_and(done)) {
-                ok = false;
-                break;
-            }
-            flip(nxt);
-            set_pend(nxt, false);
-            tc::fence_after();
-        }
-        if (k + 1 < my) {
-            gather(tile + gridDim.x, a_addr(nxt));
-            cp_async_commit();
-            cp_async_wait<1>();
-        } else {
-            cp_async_wait<0>();
-        }
-        tc::fence_proxy_async();  // this thread's copies -> tensor-core reads
-        tc::fence_before();
-        __syncthreads();
-        tc::fence_after();
-        if (tid == 0) {
-#pragma unroll
-            for (int kk = 0; kk < NK16; kk++) {
-                const uint64_t ad = tc::smem_desc(a_addr(cur) + kk * 256, 128, SBO);
-                const uint64_t bd = tc::smem_desc(b_addr + kk * 256, 128, SBO);
-                tc::mma_bf16(tmem + (uint32_t)(cur * COUT), ad, bd, kIdesc, kk > 0 ? 1u : 0u);
-            }
-            tc::mma_commit(bar(cur));
-        }
-        set_pend(cur, true);
-        if (k >= 1) epilogue(tile - gridDim.x, nxt);
-    }
-    if (ok && my > 0) {
-        const int last = (int)((my - 1) & 1);
-        const bool done = tc::mbar_wait_bounded(bar(last), last ? ph1 : ph0, kConvBudget);
-        if (__syncthreads_and(done)) {
-            flip(last);
-            set_pend(last, false);
-            tc::fence_after();
-            epilogue(blockIdx.x + (my - 1) * gridDim.x, last);
-        } else {
-            ok = false;
-        }
-    }
-    cp_async_wait<0>();
-    if (!ok) {
-        if (tid == 0) atomicExch(err, 1);
-        // never release tensor memory under MMAs still in flight (bounded)
-        if (pend0) (void)tc::mbar_wait_bounded(bar0, ph0, kConvBudget);
-        if (pend1) (void)tc::mbar_wait_bounded(bar1, ph1, kConvBudget);
-    }
-    tc::fence_before();
-    __syncthreads();
-    if (warp == 0) tc::tmem_dealloc(tmem, kCols);
-}
-
-template <int CIN, int COUT, int SIDE>
-constexpr int conv_pool_smem() {
-    return 2 * (128 * ((9 * CIN + 15) / 16) * 2 * 16) + COUT * ((9 * CIN + 15) / 16) * 2 * 16 +
-           128 * (COUT + 4) * 4 + 2 * 8 + 16;
-}
-
-// Layer 2 of an inference pass (16 x 16 images): the same implicit GEMM, with
-// one A buffer and one accumulator per CTA so that four CTAs fit an SM.  A
-// 128-pixel tile is 8 image rows, warp w holding rows 2w and 2w + 1 (lane l:
-// row 2w + l / 16, column l % 16), so each 2x2 pooling window lies in one warp
-// and the epilogue pools with two shuffles (partners l ^ 1 and l ^ 16) instead
-// of a shared-memory tile.  Per tile: wait for the gather, MMAs, wait for them;
-// then the next tile's gather runs under this tile's epilogue.  Same products,
-// rounding points and output as conv_pool_tc_kernel.  Bounded waits.
-template <int CIN, int COUT>
-__global__ void __launch_bounds__(128) conv_pool16_tc_kernel(const bf16 *__restrict__ act, int B,
-                                                             const bf16 *__restrict__ W,
-                                                             const float *__restrict__ bias,
-                                                             bf16 *__restrict__ out, int *err) {
-    constexpr int SIDE = 16, PW = SIDE / 2;
-    static_assert(CIN % 8 == 0 && COUT % 16 == 0 && COUT <= 32, "shapes of layer 2");
+    static_assert(CIN % 8 == 0 && COUT % 16 == 0 && COUT <= 32, "shapes of layers 1 and 2");
+    static_assert(SIDE == 16 || SIDE == 32, "16 x 16 or 32 x 32 images");
     constexpr int K = 9 * CIN;
     constexpr int NK16 = (K + 15) / 16;
     constexpr int KC = K / 8;
@@ -741,6 +541,7 @@ __global__ void __launch_bounds__(128) conv_pool16_tc_kernel(const bf16 *__restr
     uint64_t *bar = reinterpret_cast<uint64_t *>(sB + COUT * KCS * 16);
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bar + 1);
     __shared__ float sbias[COUT];
+    __shared__ __align__(16) float sx[SIDE == 32 ? 2 : 1][16][16];  // SIDE 32: odd rows' maxima
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int64_t ntiles = (int64_t)B * SIDE * SIDE / 128;
@@ -782,29 +583,52 @@ __global__ void __launch_bounds__(128) conv_pool16_tc_kernel(const bf16 *__restr
                 cp_async16(dst + (tap * (CIN / 8) + j) * 128, src + (in ? j * 8 : 0), in ? 16u : 0u);
         }
     };
-    // bias + ReLU, 2x2 max over lanes {l, l ^ 1, l ^ 16, l ^ 17}, bf16 stores by
-    // the lanes of even column in the first row of each window
+    // bias + ReLU, 2x2 max, bf16 stores by the lane of each window's first pixel
     auto epilogue = [&](int64_t tile) {
         const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
         const int64_t m0 = tile * 128;
         const int64_t b = m0 / (SIDE * SIDE);
-        const int py = (int)(m0 - b * SIDE * SIDE) / (2 * SIDE) + warp;  // pooled row
-        const int px = (lane & 15) >> 1;
+        const int y0 = (int)(m0 - b * SIDE * SIDE) / SIDE;  // the tile's first image row
+        const int py = SIDE == 16 ? y0 / 2 + warp : y0 / 2 + (warp >> 1);  // pooled row
+        const int px = SIDE == 16 ? (lane & 15) >> 1 : lane >> 1;
         bf16 *dst = out + ((b * PW + py) * PW + px) * COUT;
-        const bool writer = (lane & 17) == 0;
+        const bool writer = SIDE == 16 ? (lane & 17) == 0 : ((lane & 1) == 0 && (warp & 1) == 0);
 #pragma unroll
         for (int c0 = 0; c0 < COUT; c0 += 16) {
             float v[16];
             tc::tmem_ld16(taddr + (uint32_t)c0, v);
-            __align__(16) bf16 o[16];
+            float z[16];
 #pragma unroll
             for (int c = 0; c < 16; c++) {
-                float z = fmaxf(v[c] + sbias[c0 + c], 0.0f);
-                z = fmaxf(z, __shfl_xor_sync(0xffffffffu, z, 1));
-                z = fmaxf(z, __shfl_xor_sync(0xffffffffu, z, 16));
-                o[c] = __float2bfloat16_rn(z);
+                z[c] = fmaxf(v[c] + sbias[c0 + c], 0.0f);
+                z[c] = fmaxf(z[c], __shfl_xor_sync(0xffffffffu, z[c], 1));
+                if (SIDE == 16) z[c] = fmaxf(z[c], __shfl_xor_sync(0xffffffffu, z[c], 16));
+            }
+            if (SIDE == 32) {
+                // the odd row of each row pair hands its column-pair maxima over
+                if ((warp & 1) && (lane & 1) == 0) {
+#pragma unroll
+                    for (int c = 0; c < 16; c += 4)
+                        *reinterpret_cast<float4 *>(&sx[warp >> 1][lane >> 1][c]) =
+                            make_float4(z[c], z[c + 1], z[c + 2], z[c + 3]);
+                }
+                __syncthreads();
+                if (writer) {
+#pragma unroll
+                    for (int c = 0; c < 16; c += 4) {
+                        const float4 q = *reinterpret_cast<const float4 *>(&sx[warp >> 1][lane >> 1][c]);
+                        z[c] = fmaxf(z[c], q.x);
+                        z[c + 1] = fmaxf(z[c + 1], q.y);
+                        z[c + 2] = fmaxf(z[c + 2], q.z);
+                        z[c + 3] = fmaxf(z[c + 3], q.w);
+                    }
+                }
+                __syncthreads();  // sx is rewritten by the next column block or tile
             }
             if (writer) {
+                __align__(16) bf16 o[16];
+#pragma unroll
+                for (int c = 0; c < 16; c++) o[c] = __float2bfloat16_rn(z[c]);
                 *reinterpret_cast<uint4 *>(dst + c0) = *reinterpret_cast<const uint4 *>(o);
                 *reinterpret_cast<uint4 *>(dst + c0 + 8) = *reinterpret_cast<const uint4 *>(o + 8);
             }
@@ -859,7 +683,7 @@ __global__ void __launch_bounds__(128) conv_pool16_tc_kernel(const bf16 *__restr
 }
 
 template <int CIN, int COUT>
-constexpr int conv_pool16_smem() {
+constexpr int conv_pool_solo_smem() {
     return 128 * ((9 * CIN + 15) / 16) * 2 * 16 + COUT * ((9 * CIN + 15) / 16) * 2 * 16 + 8 + 16;
 }
 
@@ -962,17 +786,17 @@ cudaError_t conv_ctas_per_sm(Kern kern, int smem, int cols, int *out) {
 }
 
 template <int CIN, int COUT, int SIDE>
-cudaError_t launch_conv_pool(gsp_ranker_s *r, const bf16 *act, int n, const bf16 *W,
-                             const float *bias, bf16 *out, cudaStream_t s) {
-    constexpr int smem = conv_pool_smem<CIN, COUT, SIDE>();
+cudaError_t launch_conv_pool_solo(gsp_ranker_s *r, const bf16 *act, int n, const bf16 *W,
+                               const float *bias, bf16 *out, cudaStream_t s) {
+    constexpr int smem = conv_pool_solo_smem<CIN, COUT>();
     static int blocks_per_sm = 0;
     if (blocks_per_sm == 0) {
-        cudaError_t e = conv_ctas_per_sm(conv_pool_tc_kernel<CIN, COUT, SIDE>, smem, 2 * COUT,
+        cudaError_t e = conv_ctas_per_sm(conv_pool_solo_tc_kernel<CIN, COUT, SIDE>, smem, COUT,
                                          &blocks_per_sm);
         if (e != cudaSuccess) return e;
     } else {
         cudaError_t e = gsp::ensure_kernel_smem(
-            reinterpret_cast<const void *>(conv_pool_tc_kernel<CIN, COUT, SIDE>), smem, true);
+            reinterpret_cast<const void *>(conv_pool_solo_tc_kernel<CIN, COUT, SIDE>), smem, true);
         if (e != cudaSuccess) return e;
     }
     int dev = 0, sms = 0;
@@ -981,32 +805,8 @@ cudaError_t launch_conv_pool(gsp_ranker_s *r, const bf16 *act, int n, const bf16
     if (e != cudaSuccess) return e;
     const int64_t ntiles = (int64_t)n * SIDE * SIDE / 128;
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(ntiles, (int64_t)sms * blocks_per_sm));
-    RK_LAUNCH((conv_pool_tc_kernel<CIN, COUT, SIDE><<<grid, 128, smem, s>>>(act, n, W, bias, out,
-                                                                           r->err)));
-    return cudaSuccess;
-}
-
-template <int CIN, int COUT>
-cudaError_t launch_conv_pool16(gsp_ranker_s *r, const bf16 *act, int n, const bf16 *W,
-                               const float *bias, bf16 *out, cudaStream_t s) {
-    constexpr int smem = conv_pool16_smem<CIN, COUT>();
-    static int blocks_per_sm = 0;
-    if (blocks_per_sm == 0) {
-        cudaError_t e = conv_ctas_per_sm(conv_pool16_tc_kernel<CIN, COUT>, smem, COUT,
-                                         &blocks_per_sm);
-        if (e != cudaSuccess) return e;
-    } else {
-        cudaError_t e = gsp::ensure_kernel_smem(
-            reinterpret_cast<const void *>(conv_pool16_tc_kernel<CIN, COUT>), smem, true);
-        if (e != cudaSuccess) return e;
-    }
-    int dev = 0, sms = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e != cudaSuccess) return e;
-    const int64_t ntiles = (int64_t)n * 16 * 16 / 128;
-    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(ntiles, (int64_t)sms * blocks_per_sm));
-    RK_LAUNCH((conv_pool16_tc_kernel<CIN, COUT><<<grid, 128, smem, s>>>(act, n, W, bias, out, r->err)));
+    RK_LAUNCH((conv_pool_solo_tc_kernel<CIN, COUT, SIDE><<<grid, 128, smem, s>>>(act, n, W, bias, out,
+                                                                               r->err)));
     return cudaSuccess;
 }
 
@@ -1025,10 +825,10 @@ cudaError_t forward(gsp_ranker_s *r, const float *x, int n, bool train, cudaStre
                 RK_LAUNCH((conv0_pool_kernel<<<blocks_for(P / 8), 256, 0, s>>>(
                     x, n, r->W[0], r->params + r->off.b[0], r->a[0])));
             else if (l == 1)
-                e = launch_conv_pool<8, 16, 32>(r, r->a[0], n, r->W[1], r->params + r->off.b[1],
+                e = launch_conv_pool_solo<8, 16, 32>(r, r->a[0], n, r->W[1], r->params + r->off.b[1],
                                                 r->a[1], s);
             else
-                e = launch_conv_pool16<16, 32>(r, r->a[1], n, r->W[2], r->params + r->off.b[2],
+                e = launch_conv_pool_solo<16, 32, 16>(r, r->a[1], n, r->W[2], r->params + r->off.b[2],
                                                  r->a[2], s);
             if (e != cudaSuccess) return e;
             continue;
