@@ -185,6 +185,32 @@ void record_error(cudaError_t e, const char *what);
 // carveout.  Kernel attributes belong to a device, so the setting is
 // remembered per (device, kernel); thread-safe.  Returns the CUDA error.
 cudaError_t ensure_kernel_smem(const void *fn, int smem, bool max_carveout = false);
+
+// A kernel launched as a programmatic dependent of the previous kernel in its
+// stream (launch_dependent) may start while that kernel drains; it waits here,
+// before it touches that kernel's output, until the kernel has completed and
+// its writes are visible.  A no-op when the kernel was launched normally.
+__device__ __forceinline__ void wait_prior_grid() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
+// Launch kern as a programmatic dependent of the previous kernel in stream s
+// (its blocks may be scheduled before that kernel ends; see wait_prior_grid).
+template <typename... KArgs, typename... Args>
+cudaError_t launch_dependent(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                             cudaStream_t s, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, args...);
+}
 gsp_status plan_prepare_search(gsp_plan_s *p, int64_t n_out, int32_t **D, int64_t *stride,
                                unsigned long long **bsum);
 gsp_status plan_check_input(gsp_plan_s *p, const uint8_t *x, int64_t n_in, int64_t x_stride,

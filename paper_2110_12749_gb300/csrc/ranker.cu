@@ -322,6 +322,7 @@ __global__ void transpose_kernel(const bf16 *__restrict__ in, int64_t ldi, int64
 // fc 96 -> 2 (CUDA cores): z5[b][o] = sum_k a4[b][k] * bf16(w5[o][k]) + b5[o].
 __global__ void fc2_kernel(const bf16 *__restrict__ a4, const float *__restrict__ w5,
                            const float *__restrict__ b5, int B, float *__restrict__ z5) {
+    gsp::wait_prior_grid();  // a4 comes from the kernel launched just before
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= B * 2) return;
     const int b = i / 2, o = i % 2;
@@ -464,6 +465,7 @@ namespace {
 __global__ void fc1_finish_kernel(const float *__restrict__ part, int S, int64_t zstride, int B,
                                   const float *__restrict__ bias, float *__restrict__ z4,
                                   bf16 *__restrict__ a4) {
+    gsp::wait_prior_grid();  // part comes from the kernel launched just before
     const int64_t total = (int64_t)B * kHid;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
          i += (int64_t)gridDim.x * blockDim.x) {
@@ -564,6 +566,7 @@ __global__ void __launch_bounds__(128) conv_pool_solo_tc_kernel(const bf16 *__re
     __syncthreads();
     tc::fence_after();
     const uint32_t tmem = *tmem_slot;
+    gsp::wait_prior_grid();  // act comes from the kernel launched just before
     const uint32_t a_addr = tc::smem_u32(sA), b_addr = tc::smem_u32(sB);
     const uint32_t bar0 = tc::smem_u32(bar);
 
@@ -787,7 +790,7 @@ cudaError_t conv_ctas_per_sm(Kern kern, int smem, int cols, int *out) {
 
 template <int CIN, int COUT, int SIDE>
 cudaError_t launch_conv_pool_solo(gsp_ranker_s *r, const bf16 *act, int n, const bf16 *W,
-                               const float *bias, bf16 *out, cudaStream_t s) {
+                                  const float *bias, bf16 *out, cudaStream_t s, bool dependent) {
     constexpr int smem = conv_pool_solo_smem<CIN, COUT>();
     static int blocks_per_sm = 0;
     if (blocks_per_sm == 0) {
@@ -805,6 +808,13 @@ cudaError_t launch_conv_pool_solo(gsp_ranker_s *r, const bf16 *act, int n, const
     if (e != cudaSuccess) return e;
     const int64_t ntiles = (int64_t)n * SIDE * SIDE / 128;
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(ntiles, (int64_t)sms * blocks_per_sm));
+    if (dependent) {
+        e = gsp::launch_dependent(conv_pool_solo_tc_kernel<CIN, COUT, SIDE>, dim3(grid), dim3(128),
+                                  (size_t)smem, s, act, n, W, bias, out, r->err);
+        if (e != cudaSuccess) return e;
+        r->launches++;
+        return cudaSuccess;
+    }
     RK_LAUNCH((conv_pool_solo_tc_kernel<CIN, COUT, SIDE><<<grid, 128, smem, s>>>(act, n, W, bias, out,
                                                                                r->err)));
     return cudaSuccess;
@@ -826,10 +836,10 @@ cudaError_t forward(gsp_ranker_s *r, const float *x, int n, bool train, cudaStre
                     x, n, r->W[0], r->params + r->off.b[0], r->a[0])));
             else if (l == 1)
                 e = launch_conv_pool_solo<8, 16, 32>(r, r->a[0], n, r->W[1], r->params + r->off.b[1],
-                                                r->a[1], s);
+                                                     r->a[1], s, true);
             else
                 e = launch_conv_pool_solo<16, 32, 16>(r, r->a[1], n, r->W[2], r->params + r->off.b[2],
-                                                 r->a[2], s);
+                                                      r->a[2], s, true);
             if (e != cudaSuccess) return e;
             continue;
         }
@@ -859,10 +869,26 @@ cudaError_t forward(gsp_ranker_s *r, const float *x, int n, bool train, cudaStre
     const int want = std::max(1, std::min(kFc1Split, std::min(kFc / (4 * 64), nsm / mt)));
     const int64_t zs = (int64_t)r->max_batch * kHid;
     int used = 1;
+    // in an inference pass each kernel after the first is launched as a
+    // programmatic dependent of the one before (its blocks are scheduled while
+    // that kernel drains and wait for its output in wait_prior_grid)
     cudaError_t e = gsp::launch_gemm_bf16(r->a[2], kFc, r->W4, kFc, r->fc1_part, kHid, nullptr, 0, n,
-                                          kHid, kFc, nullptr, false, want, r->err, s, zs, &used);
+                                          kHid, kFc, nullptr, false, want, r->err, s, zs, &used,
+                                          !train);
     if (e != cudaSuccess) return e;
     r->launches++;
+    if (!train) {
+        e = gsp::launch_dependent(fc1_finish_kernel, dim3(blocks_for((int64_t)n * kHid)), dim3(256),
+                                  0, s, (const float *)r->fc1_part, used, zs, n,
+                                  (const float *)(r->params + r->off.b[3]), r->z4, r->a4);
+        if (e == cudaSuccess)
+            e = gsp::launch_dependent(fc2_kernel, dim3((2 * n + 127) / 128), dim3(128), 0, s,
+                                      (const bf16 *)r->a4, (const float *)(r->params + r->off.w[4]),
+                                      (const float *)(r->params + r->off.b[4]), n, r->z5);
+        if (e != cudaSuccess) return e;
+        r->launches += 2;
+        return cudaSuccess;
+    }
     RK_LAUNCH((fc1_finish_kernel<<<blocks_for((int64_t)n * kHid), 256, 0, s>>>(
         r->fc1_part, used, zs, n, r->params + r->off.b[3], r->z4, r->a4)));
     RK_LAUNCH((fc2_kernel<<<(2 * n + 127) / 128, 128, 0, s>>>(r->a4, r->params + r->off.w[4],

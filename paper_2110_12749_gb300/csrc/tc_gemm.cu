@@ -406,6 +406,7 @@ __global__ void __launch_bounds__(160) gemm_tma_kernel(
     tc::fence_before();
     __syncthreads();
     tc::fence_after();
+    wait_prior_grid();  // the operands may come from the kernel launched just before
     const uint32_t tmem = tmem_base;
     bool ok = true;
     if (warp == 4) {
@@ -537,13 +538,17 @@ constexpr int tma_smem() {
 }
 
 template <int BN>
-cudaError_t launch_tma(dim3 grid, cudaStream_t s, const CUtensorMap &tmA, const CUtensorMap &tmB,
+cudaError_t launch_tma(dim3 grid, bool dependent, cudaStream_t s, const CUtensorMap &tmA,
+                       const CUtensorMap &tmB,
                        float *C, int64_t ldc, __nv_bfloat16 *Cb, int64_t ldcb, int M, int N, int K,
                        int kchunk, int64_t zstride, const float *bias, int relu, int *err) {
     constexpr int smem = tma_smem<BN>();
     cudaError_t e =
         ensure_kernel_smem(reinterpret_cast<const void *>(gemm_tma_kernel<BN, kTmaStages>), smem);
     if (e != cudaSuccess) return e;
+    if (dependent)
+        return launch_dependent(gemm_tma_kernel<BN, kTmaStages>, grid, dim3(160), (size_t)smem, s, tmA,
+                                tmB, C, ldc, Cb, ldcb, M, N, K, kchunk, zstride, bias, relu, err);
     gemm_tma_kernel<BN, kTmaStages><<<grid, 160, smem, s>>>(tmA, tmB, C, ldc, Cb, ldcb, M, N, K,
                                                             kchunk, zstride, bias, relu, err);
     return cudaSuccess;
@@ -571,7 +576,8 @@ cudaError_t launch_bn(dim3 grid, cudaStream_t s, const __nv_bfloat16 *A, int64_t
 // TMA-fed warp-specialised kernel, a 4-stage ring, two accumulators, and
 // persistent CTAs striding over the M tiles.
 template <int BN>
-cudaError_t launch_n(int ksteps, int mtiles, int ntiles, int splitk, int nsm, cudaStream_t s,
+cudaError_t launch_n(int ksteps, int mtiles, int ntiles, int splitk, int nsm, bool dependent,
+                     cudaStream_t s,
                      const __nv_bfloat16 *A, int64_t lda, const __nv_bfloat16 *B, int64_t ldb,
                      float *C, int64_t ldc, __nv_bfloat16 *Cb, int64_t ldcb, int M, int N, int K,
                      int kchunk, int64_t zstride, const float *bias, int relu, int *err) {
@@ -599,7 +605,7 @@ cudaError_t launch_n(int ksteps, int mtiles, int ntiles, int splitk, int nsm, cu
     cudaError_t e = make_tmap(&tmA, A, M, K, lda, kBM);
     if (e == cudaSuccess) e = make_tmap(&tmB, B, N, K, ldb, BN);
     if (e != cudaSuccess) return e;
-    return launch_tma<BN>(grid, s, tmA, tmB, C, ldc, Cb, ldcb, M, N, K, kchunk, zstride, bias, relu,
+    return launch_tma<BN>(grid, dependent, s, tmA, tmB, C, ldc, Cb, ldcb, M, N, K, kchunk, zstride, bias, relu,
                           err);
 }
 
@@ -608,7 +614,8 @@ cudaError_t launch_n(int ksteps, int mtiles, int ntiles, int splitk, int nsm, cu
 cudaError_t launch_gemm_bf16(const __nv_bfloat16 *A, int64_t lda, const __nv_bfloat16 *B,
                              int64_t ldb, float *C, int64_t ldc, __nv_bfloat16 *Cb,
                              int64_t ldcb, int M, int N, int K, const float *bias, bool relu,
-                             int splitk, int *err, cudaStream_t s, int64_t zstride, int *nsplit) {
+                             int splitk, int *err, cudaStream_t s, int64_t zstride, int *nsplit,
+                             bool dependent) {
     if (M <= 0 || N <= 0 || K <= 0 || (K & 7) || (lda & 7) || (ldb & 7) || lda < K || ldb < K ||
         (((uintptr_t)A | (uintptr_t)B) & 15) || (!C && !Cb) || (splitk > 1 && !C) ||
         zstride < 0 || (zstride > 0 && (!C || Cb || bias || relu || zstride < (int64_t)M * ldc)))
@@ -637,10 +644,10 @@ cudaError_t launch_gemm_bf16(const __nv_bfloat16 *A, int64_t lda, const __nv_bfl
     const int r = relu ? 1 : 0;
     cudaError_t e;
     switch (BN) {
-        case 16: e = launch_n<16>(csteps, mtiles, ntiles, splitk, nsm, s, A, lda, B, ldb, C, ldc, Cb, ldcb, M, N, K, kchunk, zstride, bias, r, err); break;
-        case 32: e = launch_n<32>(csteps, mtiles, ntiles, splitk, nsm, s, A, lda, B, ldb, C, ldc, Cb, ldcb, M, N, K, kchunk, zstride, bias, r, err); break;
-        case 64: e = launch_n<64>(csteps, mtiles, ntiles, splitk, nsm, s, A, lda, B, ldb, C, ldc, Cb, ldcb, M, N, K, kchunk, zstride, bias, r, err); break;
-        default: e = launch_n<128>(csteps, mtiles, ntiles, splitk, nsm, s, A, lda, B, ldb, C, ldc, Cb, ldcb, M, N, K, kchunk, zstride, bias, r, err); break;
+        case 16: e = launch_n<16>(csteps, mtiles, ntiles, splitk, nsm, dependent, s, A, lda, B, ldb, C, ldc, Cb, ldcb, M, N, K, kchunk, zstride, bias, r, err); break;
+        case 32: e = launch_n<32>(csteps, mtiles, ntiles, splitk, nsm, dependent, s, A, lda, B, ldb, C, ldc, Cb, ldcb, M, N, K, kchunk, zstride, bias, r, err); break;
+        case 64: e = launch_n<64>(csteps, mtiles, ntiles, splitk, nsm, dependent, s, A, lda, B, ldb, C, ldc, Cb, ldcb, M, N, K, kchunk, zstride, bias, r, err); break;
+        default: e = launch_n<128>(csteps, mtiles, ntiles, splitk, nsm, dependent, s, A, lda, B, ldb, C, ldc, Cb, ldcb, M, N, K, kchunk, zstride, bias, r, err); break;
     }
     if (e != cudaSuccess) return e;
     return cudaGetLastError();

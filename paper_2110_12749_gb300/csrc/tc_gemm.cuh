@@ -139,6 +139,6 @@ cudaError_t launch_gemm_bf16(const __nv_bfloat16 *A, int64_t lda, const __nv_bfl
                              int64_t ldb, float *C, int64_t ldc, __nv_bfloat16 *Cb,
                              int64_t ldcb, int M, int N, int K, const float *bias, bool relu,
                              int splitk, int *err, cudaStream_t s, int64_t zstride = 0,
-                             int *nsplit = nullptr);
+                             int *nsplit = nullptr, bool dependent = false);
 
 }  // namespace gsp
