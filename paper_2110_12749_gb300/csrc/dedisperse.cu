@@ -492,7 +492,9 @@ __global__ void __launch_bounds__((KDM / KW + 1) * 32, (KDM / KW + 1) * 32 <= 25
 
     for (int st = 0; st < nst; st++) {
         int cur_min[kH], cur_dl[kKW][kH];
-        const uint32_t cur_fc = nx_fc;
+        // the same word in every lane; a warp reduction makes that visible to the compiler,
+        // so the family loops below branch on a warp-uniform count
+        const uint32_t cur_fc = PRE ? __reduce_or_sync(0xffffffffu, nx_fc) : 0u;
         if (PRE && st + 1 < nst) nx_fc = fcrow[st + 1];
 #pragma unroll
         for (int h = 0; h < kH; h++) {
