@@ -538,19 +538,27 @@ gsp_status gsp_candidates(gsp_plan_t p, gsp_cand *host_out, int64_t cap, int64_t
     GSP_CK(cudaMemcpy(&n, p->d_ncand, sizeof(n), cudaMemcpyDeviceToHost));
     *n_total = (int64_t)n;
     const int64_t kept = std::min<int64_t>((int64_t)n, p->desc.max_cands);
-    std::vector<gsp_cand> v((size_t)kept);
-    if (kept > 0)
-        GSP_CK(cudaMemcpy(v.data(), p->d_cands, (size_t)kept * sizeof(gsp_cand),
-                          cudaMemcpyDeviceToHost));
     auto less = [](const gsp_cand &a, const gsp_cand &b) {
         if (a.dm_idx != b.dm_idx) return a.dm_idx < b.dm_idx;
         if (a.t != b.t) return a.t < b.t;
         return a.width < b.width;
     };
-    // the device list is already in (dm, t) order; sort only if it is not
-    if (!std::is_sorted(v.begin(), v.end(), less)) std::sort(v.begin(), v.end(), less);
     const int64_t m = std::min<int64_t>(kept, cap);
-    if (m > 0) std::memcpy(host_out, v.data(), (size_t)m * sizeof(gsp_cand));
+    if (kept <= cap) {
+        // everything fits: read straight into the caller's buffer (no staging copy)
+        if (kept > 0)
+            GSP_CK(cudaMemcpy(host_out, p->d_cands, (size_t)kept * sizeof(gsp_cand),
+                              cudaMemcpyDeviceToHost));
+        // the device list is already in (dm, t) order; sort only if it is not
+        if (!std::is_sorted(host_out, host_out + kept, less)) std::sort(host_out, host_out + kept, less);
+    } else {
+        // the first cap of the sorted list: sort the whole kept list first
+        std::vector<gsp_cand> v((size_t)kept);
+        GSP_CK(cudaMemcpy(v.data(), p->d_cands, (size_t)kept * sizeof(gsp_cand),
+                          cudaMemcpyDeviceToHost));
+        if (!std::is_sorted(v.begin(), v.end(), less)) std::sort(v.begin(), v.end(), less);
+        if (m > 0) std::memcpy(host_out, v.data(), (size_t)m * sizeof(gsp_cand));
+    }
     return ((int64_t)n > m) ? GSP_ERR_CAPACITY : GSP_OK;
 }
 

@@ -366,7 +366,8 @@ def gsp_candidates(plan, cap=None):
     st = lib().gsp_candidates(plan.handle, _np_ptr(out), cap, ctypes.byref(n))
     if st not in (GSP_OK, GSP_ERR_CAPACITY):
         _check(st, "gsp_candidates")
-    return out[:min(n.value, cap)].copy(), n.value, st
+    # a view: the pages of `out` past the first n records are never touched
+    return out[:min(n.value, cap)], n.value, st
 
 
 def gsp_search_host(plan, x_host, n_in, t_offset=0, cap=None, stream=None):
@@ -383,7 +384,7 @@ def gsp_search_host(plan, x_host, n_in, t_offset=0, cap=None, stream=None):
                                ctypes.byref(n), _stream(stream))
     if st not in (GSP_OK, GSP_ERR_CAPACITY):
         _check(st, "gsp_search_host")
-    return out[:min(n.value, cap)].copy(), n.value, st
+    return out[:min(n.value, cap)], n.value, st
 
 
 def gsp_plan_timing(plan):
