@@ -879,10 +879,10 @@ constexpr int kDefaultVariant = 32;  // 15 DMs x 768 samples, 64-channel stages,
 // slots 0.675 against 0.617 for 32-channel stages with five (2500 trials to DM
 // 1500); on the wide band 32-channel stages with two slots 0.610, 7-DM blocks
 // 0.40 (one CTA per SM) and 0.49 (two per SM, 4 words per lane).
-const int kAutoList[] = {32, 42, 34, 44, 40, 41};
+const int kAutoList[] = {kDefaultVariant, 42, 34, 44, 40, 41};
 
 // Variants the batch autotuner times (those that fit the batch are timed).
-const int kTuneList[] = {32, 42, 35, 31, 22, 43, 44, 36, 34, 40};
+const int kTuneList[] = {kDefaultVariant, 42, 35, 31, 22, 43, 44, 36, 34, 40};
 
 // Shared memory of one CTA: all of an SM's 227 KB, or half of it (less the
 // per-CTA reserve) for CTAs of at most 8 warps that run two per SM.
