@@ -28,7 +28,9 @@ inline int kdm_index(int kdm) { return kdm == 15 ? 1 : (kdm == 7 ? 2 : 0); }
 //   c0   = alpha - m  (intercept of the fitted line minus m),
 //   beta = slope of the fitted line,
 //   good = 1 if the block is searched, 0 if it is bad (zeroed).
-struct BlockParam {
+// 16-byte aligned, so that a kernel reads one record with a single 128-bit load
+// (every array of them is a cudaMalloc block or a 256-byte aligned region).
+struct alignas(16) BlockParam {
     int32_t m;
     float c0;
     float beta;
