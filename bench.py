@@ -28,12 +28,12 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 # DRAM bytes (read + write) per algorithmic add of the default dedispersion kernel
-# (variant 32, with per-stage copy windows): ncu dram__bytes_read.sum +
-# dram__bytes_write.sum of one launch on the CRAFTS-like beam cut to 131072 samples
-# (1.598 GB + 0.666 GB for 6.899e11 adds), the capture size rule keeping full-size
-# multi-pass captures off the GPU; traffic grows with the number of time tiles, i.e.
-# in proportion to the adds.
-DD_TRAFFIC_BYTES_PER_ADD = (1.5984e9 + 0.6663e9) / 6.899e11
+# (variant 32, with per-stage copy windows and warp-uniform family counts): ncu
+# dram__bytes_read.sum + dram__bytes_write.sum of one launch on the CRAFTS-like beam
+# cut to 131072 samples (1.574 GB + 0.665 GB for 6.899e11 adds), the capture size
+# rule keeping full-size multi-pass captures off the GPU; traffic grows with the
+# number of time tiles, i.e. in proportion to the adds.
+DD_TRAFFIC_BYTES_PER_ADD = (1.5738e9 + 0.6653e9) / 6.899e11
 DD_TRAFFIC_VARIANT = "default"
 
 NOMINAL_SMS = 152
